@@ -1,0 +1,213 @@
+"""FP64 CPU oracle of the DRT hot path (ctypes binding of drt_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` are the only callers.  Nothing here is shared with the CUDA library; the two meet only
+through the seeded inputs of ``paper_2205_00237_gb300.inputs``.
+
+Every function is pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "drt_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libdrt_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+METHOD_DRT, METHOD_RESOLVE = 0, 1
+F_FACE, F_EDGE, F_SIDE, F_NOCONV, F_DEGEN = 1, 2, 4, 8, 16
+MAX_INT = 4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with plain gcc -O2 (no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm",
+                               "-lpthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Term(C.Structure):
+    _fields_ = [("r", C.c_double * 3), ("v", C.c_double * 3), ("a", C.c_double * 3)]
+
+
+class _Scene(C.Structure):
+    _fields_ = [("tx", _Term), ("rx", _Term), ("n_bodies", C.c_int32), ("n_materials", C.c_int32),
+                ("n_faces", C.c_int32), ("n_edges", C.c_int32), ("n_tiles", C.c_int32),
+                ("pad_", C.c_int32), ("bodies", C.c_void_p), ("mats", C.c_void_p),
+                ("faces", C.c_void_p), ("edges", C.c_void_p), ("tiles", C.c_void_p)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            dp = C.POINTER(C.c_double)
+            L.or_extrapolate.restype = C.c_int
+            L.or_extrapolate.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_double, C.c_double, C.c_int32, C.c_double,
+                                         C.c_int32, C.c_int32] + [C.c_void_p] * 8
+            L.or_synthesize_H.restype = C.c_int
+            L.or_synthesize_H.argtypes = [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_void_p]
+            L.or_fresnel_coeffs.argtypes = [C.c_double] * 5 + [dp]
+            L.or_fresnel_G_ri.argtypes = [C.c_double, dp]
+            L.or_transition_F_ri.argtypes = [C.c_double, dp]
+            L.or_utd_ri.argtypes = [C.c_double] * 10 + [dp]
+            L.or_er_norm.restype = C.c_double
+            L.or_er_norm.argtypes = [C.c_double, C.c_double]
+            L.or_er_amp.restype = C.c_double
+            L.or_er_amp.argtypes = [C.c_double] * 5
+            L.or_body_point.argtypes = [C.c_void_p, dp, C.c_double, dp]
+            L.or_frame_roundtrip.argtypes = [C.c_void_p, C.c_int32, C.c_double, dp, dp, dp]
+            L.or_ref_point_local.argtypes = [dp, dp, dp]
+            L.or_diff_point_local.argtypes = [dp, dp, dp]
+            L.or_doppler_chain.restype = C.c_double
+            L.or_doppler_chain.argtypes = [C.c_int32, dp, dp, C.c_double]
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class _SceneHandle:
+    """Keeps the contiguous arrays alive while the C structure points at them."""
+
+    def __init__(self, scene):
+        self.arrays = [np.ascontiguousarray(x) for x in
+                       (scene.bodies, scene.materials, scene.faces, scene.edges, scene.tiles)]
+        s = _Scene()
+        for dst, src in ((s.tx, scene.tx), (s.rx, scene.rx)):
+            for f in ("r", "v", "a"):
+                getattr(dst, f)[:] = [float(x) for x in src[f]]
+        s.n_bodies, s.n_materials, s.n_faces, s.n_edges, s.n_tiles = (len(a) for a in self.arrays)
+        s.bodies, s.mats, s.faces, s.edges, s.tiles = (a.ctypes.data if len(a) else None
+                                                      for a in self.arrays)
+        self.s = s
+
+    @property
+    def ref(self):
+        return C.byref(self.s)
+
+
+def extrapolate(scene, paths, tgrid, fc, method=METHOD_DRT, n_threads=1, points=False,
+                velocities=False):
+    """Per-(step, path) records over the time grid; dict of [T][P] numpy arrays."""
+    L = lib()
+    T, P = int(tgrid.n_steps), paths.n_paths
+    out = dict(tau=np.empty((T, P)), amp=np.empty((T, P, 2)), fd=np.empty((T, P)),
+               ang=np.empty((T, P, 4)), flags=np.empty((T, P), np.uint8), margin=np.empty((T, P)))
+    out["pts"] = np.empty((T, P, MAX_INT, 3)) if points else None
+    out["vel"] = np.empty((T, P, MAX_INT + 2, 3)) if velocities else None
+    h = _SceneHandle(scene)
+    n_int = np.ascontiguousarray(paths.n_int, np.uint8)
+    types = np.ascontiguousarray(paths.types, np.uint8)
+    prims = np.ascontiguousarray(paths.prims, np.int32)
+    s0 = np.ascontiguousarray(paths.s0, np.float64)
+    rc = L.or_extrapolate(h.ref, P, _ptr(n_int), _ptr(types), _ptr(prims), _ptr(s0),
+                          float(tgrid.t_start), float(tgrid.dt), T, float(fc), int(method),
+                          int(n_threads), _ptr(out["tau"]), _ptr(out["amp"]), _ptr(out["fd"]),
+                          _ptr(out["ang"]), _ptr(out["flags"]), _ptr(out["margin"]),
+                          _ptr(out["pts"]), _ptr(out["vel"]))
+    if rc != 0:
+        raise RuntimeError(f"or_extrapolate failed: {rc}")
+    out["a"] = out["amp"][..., 0] + 1j * out["amp"][..., 1]
+    return out
+
+
+def synthesize_H(rec, fgrid, n_threads=1):
+    """Direct FP64 sum H[t][k] over the valid paths of an extrapolate() record."""
+    L = lib()
+    T, P = rec["tau"].shape
+    H = np.empty((T, int(fgrid.n_bins), 2))
+    tau = np.ascontiguousarray(rec["tau"])
+    amp = np.ascontiguousarray(rec["amp"])
+    flags = np.ascontiguousarray(rec["flags"])
+    L.or_synthesize_H(T, P, _ptr(tau), _ptr(amp), _ptr(flags), float(fgrid.fc),
+                      float(fgrid.bandwidth), int(fgrid.n_bins), int(n_threads), _ptr(H))
+    return H[..., 0] + 1j * H[..., 1]
+
+
+# ---------------------------------------------------------------------------- unit-level calls
+def fresnel(eps_r, sigma, pec, fc, cos_theta):
+    o = np.empty(4)
+    lib().or_fresnel_coeffs(eps_r, sigma, float(pec), fc, cos_theta, _dp(o))
+    return o[0] + 1j * o[1], o[2] + 1j * o[3]
+
+
+def fresnel_G(x):
+    o = np.empty(2)
+    lib().or_fresnel_G_ri(x, _dp(o))
+    return o[0] + 1j * o[1]
+
+
+def transition_F(X):
+    o = np.empty(2)
+    lib().or_transition_F_ri(X, _dp(o))
+    return o[0] + 1j * o[1]
+
+
+def utd(n, phi, phip, sinb0, L, k, eps_r=1.0, sigma=0.0, pec=True, fc=1e9):
+    o = np.empty(4)
+    lib().or_utd_ri(n, phi, phip, sinb0, L, k, eps_r, sigma, float(pec), fc, _dp(o))
+    return o[0] + 1j * o[1], o[2] + 1j * o[3]
+
+
+def er_norm(alpha, cos_theta_i):
+    return lib().or_er_norm(alpha, cos_theta_i)
+
+
+def er_amp(alpha, S, area, cos_theta_i, cos_psi):
+    return lib().or_er_amp(alpha, S, area, cos_theta_i, cos_psi)
+
+
+def body_point(body_rec, p0, t):
+    b = np.ascontiguousarray(np.array(body_rec))
+    o = np.empty(9)
+    p = np.ascontiguousarray(p0, np.float64)
+    lib().or_body_point(_ptr(b), _dp(p), t, _dp(o))
+    return o.reshape(3, 3)
+
+
+def frame_roundtrip(scene, face, t, state9):
+    h = _SceneHandle(scene)
+    i = np.ascontiguousarray(state9, np.float64)
+    loc, out = np.empty(9), np.empty(9)
+    lib().or_frame_roundtrip(h.ref, face, t, _dp(i), _dp(loc), _dp(out))
+    return loc.reshape(3, 3), out.reshape(3, 3)
+
+
+def ref_point_local(t9, r9):
+    q = np.empty(9)
+    lib().or_ref_point_local(_dp(np.ascontiguousarray(t9, float)), _dp(np.ascontiguousarray(r9, float)), _dp(q))
+    return q.reshape(3, 3)
+
+
+def diff_point_local(t9, r9):
+    q = np.empty(9)
+    lib().or_diff_point_local(_dp(np.ascontiguousarray(t9, float)), _dp(np.ascontiguousarray(r9, float)), _dp(q))
+    return q.reshape(3, 3)
+
+
+def doppler_chain(pos, vel, fc):
+    pos = np.ascontiguousarray(pos, float)
+    vel = np.ascontiguousarray(vel, float)
+    return lib().or_doppler_chain(pos.shape[0] - 2, _dp(pos), _dp(vel), fc)

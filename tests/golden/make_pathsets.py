@@ -1,0 +1,92 @@
+"""Write the committed path sets of the synthetic workloads (the "ray-tracing run at t0").
+
+DRT starts from the multipath geometry found by a conventional ray-tracing run at t0 (Sec. II); that
+run is outside the DRT hot path.  This script stands in for it: it draws candidate interaction
+chains from the seeded generators of ``paper_2205_00237_gb300.inputs`` and keeps those that the FP64
+oracle finds valid at t0 (every point on its face or edge, every neighbour on the correct side).  It
+calls only ``oracle/`` and the input generators, never the CUDA library.
+
+  python tests/golden/make_pathsets.py        # rewrites tests/golden/pathset_*.npz
+
+Chain draws for the canyon follow the stated recipe: LoS plus chains of length uniform on {1,2,3}
+with i.i.d. types R:D:S = 0.6:0.2:0.2 and uniform primitives; a drawn type sequence gets up to
+`tries` random primitive assignments and is redrawn when none of them is valid at t0.
+"""
+from __future__ import annotations
+
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import oracle as O  # noqa: E402
+from paper_2205_00237_gb300 import inputs as I  # noqa: E402
+
+
+def keep_valid_at_t0(scene, ps, fc, n_threads=8):
+    r = O.extrapolate(scene, ps, I.TimeGrid(0.0, 1.0, 1), fc, n_threads=n_threads, points=True)
+    ok = np.nonzero(r["flags"][0] == 0)[0]
+    out = ps.subset(ok)
+    # edge parameters of the D vertices at t0 (the ray-tracing result the Newton warm start uses)
+    pts = r["pts"][0, ok]
+    for p in range(out.n_paths):
+        for j in range(int(out.n_int[p])):
+            if out.types[p, j] == I.T_D:
+                e = scene.edges[out.prims[p, j]]
+                ed = (e["b"] - e["a"]) / np.linalg.norm(e["b"] - e["a"])
+                out.s0[p, j] = float(np.dot(pts[p, j] - e["a"], ed))
+    return out
+
+
+def canyon_pathset(seed, n_paths=512, tries=60000, batch=3000, fc=60e9):
+    scene = I.scene_canyon(seed)
+    rng = np.random.default_rng(77 + seed)
+    kept = [keep_valid_at_t0(scene, I.chains_to_pathset([[]]), fc)]       # line of sight
+    n = 1
+    while n < n_paths:
+        types = I.draw_chain_types(rng)
+        found = None
+        for _ in range(tries // batch):
+            chains, s0s = [], []
+            for _ in range(batch):
+                ch, s0 = I.draw_chain_prims(rng, scene, types)
+                if ch is not None:
+                    chains.append(ch)
+                    s0s.append(s0)
+            ps = I.chains_to_pathset(chains)
+            for i, s in enumerate(s0s):
+                ps.s0[i, :len(s)] = s
+            v = keep_valid_at_t0(scene, ps, fc)
+            if v.n_paths:
+                found = v.subset([0])
+                break
+        if found is not None:
+            kept.append(found)
+            n += 1
+    return scene, I.PathSet.concat(kept)
+
+
+def tiny_pathset(seed, fc=28e9):
+    scene = I.scene_tiny(seed)
+    return scene, keep_valid_at_t0(scene, I.chains_tiny(scene), fc)
+
+
+def main():
+    for seed in (0, 1):
+        scene, ps = tiny_pathset(seed)
+        ps.to_npz(os.path.join(HERE, f"pathset_tiny_seed{seed}.npz"))
+        print(f"tiny seed {seed}: {ps.n_paths} paths")
+    scene, ps = canyon_pathset(0)
+    ps.to_npz(os.path.join(HERE, "pathset_canyon_seed0.npz"))
+    sig = {}
+    for p in range(ps.n_paths):
+        k = "".join("xRDS"[t] for t in ps.types[p, :ps.n_int[p]]) or "LoS"
+        sig[k] = sig.get(k, 0) + 1
+    print(f"canyon seed 0: {ps.n_paths} paths", sorted(sig.items(), key=lambda x: -x[1]))
+
+
+if __name__ == "__main__":
+    main()
