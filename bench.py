@@ -1,0 +1,292 @@
+#!/usr/bin/env python3
+"""Benchmark of the DRT hot path on the full-3D canyon workload (one GB300 per rank).
+
+Workload (the full-3D FP64 DRT case): urban canyon 20 m wide, 40 facades, 8 moving and yawing
+vehicles, 512 ray chains of <= 3 interactions (R:D:S = 6:2:2, committed t0 path set), 60 GHz,
+2000 steps x 0.5 ms, 512 frequency bins over 1 GHz, FP64 form.
+
+One step = one drt_synthesize_H call on the resident link: pose table (a2), extrapolation of every
+(path, time-step) with field coefficients and Doppler (a3-a8), H(t, f) synthesis (a9).
+value = path-timesteps/s over all ranks (each rank runs its own link: weak scaling, no data-path
+collective).  L2 (129 MB) is flushed by a 256 MB write between timed steps, outside the events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reference implementation of this method here) on
+the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2205_00237_gb300 import inputs as I  # noqa: E402
+
+METRIC = "path-timesteps/s and H(t,f) samples/s at stated error vs FP64 oracle"
+UNIT = "path-timesteps/s"
+WORKLOAD = "canyon"
+PATHSET = os.path.join(ROOT, "tests", "golden", "pathset_canyon_seed0.npz")
+
+# Roofline of the dominant kernel (k_extrapolate_fp64, FP64-pipe bound).  FP64 FLOPs executed per
+# path-step (DADD + DMUL + 2 DFMA thread-instructions per ncu on this workload, see
+# profiles/k_extrapolate_fp64_canyon.md) and the FP64 peak of the GB300 (1.25 TFLOP/s nominal,
+# 152 SMs, no FP64 tensor path used).  DRAM bytes per launch from the same capture (None until taken).
+FP64_FLOP_PER_PATH_STEP = None
+FP64_PEAK_FLOPS = 1.25e12
+K1_DRAM_BYTES_PER_LAUNCH = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    scene = I.scene_canyon(0)
+    paths = I.PathSet.from_npz(PATHSET)
+    tg, fg = I.grids(WORKLOAD)
+    return scene, paths, tg, fg
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def cpu_baseline(scene, paths, tg, fg, n_steps):
+    """The FP64 oracle as it stands (O-DRT extrapolation + direct H sum) on all host cores."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    sub = I.TimeGrid(tg.t_start, tg.dt, n_steps)
+    t0 = time.perf_counter()
+    rec = O.extrapolate(scene, paths, sub, fg.fc, n_threads=cores)
+    O.synthesize_H(rec, fg, n_threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": paths.n_paths * n_steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{paths.n_paths} paths x first {n_steps} of {tg.n_steps} steps x {fg.n_bins} bins "
+                      f"(extrapolation + H), {dt:.2f} s wall",
+            "h_samples_per_s": n_steps * fg.n_bins / dt}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    scene, paths, tg, fg = workload()
+    import oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    n_sub = 64   # time steps per step: a bounded sample of the workload
+    times = []
+    for k in range(args.warmup + args.steps):
+        sub = I.TimeGrid(tg.t_start + (k * n_sub % tg.n_steps) * tg.dt, tg.dt, n_sub)
+        t0 = time.perf_counter()
+        rec = O.extrapolate(scene, paths, sub, fg.fc, n_threads=cores)
+        O.synthesize_H(rec, fg, n_threads=cores)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = paths.n_paths * n_sub * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "h_samples_per_s": n_sub * fg.n_bins * args.steps / total,
+            "config": {"workload": "canyon-512paths-2000x0.5ms-512bins-60GHz-fp64",
+                       "sample_per_step": f"{paths.n_paths} paths x {n_sub} steps x {fg.n_bins} bins"},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
+                             "sample": f"{paths.n_paths} paths x {n_sub} consecutive steps per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_00237_gb300 import drt
+
+    scene, paths, tg, fg = workload()
+    P, T, F = paths.n_paths, tg.n_steps, fg.n_bins
+    dev = torch.device("cuda", local_rank)
+    ctx = drt.Context(local_rank)
+    link = ctx.load(scene, paths)
+    H = torch.empty((T, F), dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        link.synthesize_H(tg, fg, drt.FP64, H)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_read()
+    sampler = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    evs = []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        link.synthesize_H(tg, fg, drt.FP64, H)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier()
+    clocks = sampler.stop()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_s = sum(step_ms) * 1e-3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * P * T * args.steps / total_s
+    n_launch, k1_ms = prof["extrapolate"]
+    k1_avg_s = k1_ms * 1e-3 / max(1, n_launch)
+    kernel_launches = sum(v[0] for v in prof.values())
+
+    # end to end through the public API with host buffers: load (H2D) + synthesize to host (D2H)
+    h2d = sum(np.ascontiguousarray(a).nbytes for a in (scene.bodies, scene.materials, scene.faces, scene.edges,
+                                                       scene.tiles, paths.n_int, paths.types, paths.prims, paths.s0))
+    Hh = torch.empty((T, F), dtype=torch.complex64, pin_memory=True)
+    torch.cuda.synchronize()
+    e2e_s = []
+    for _ in range(args.e2e_steps):
+        t0 = time.perf_counter()
+        lk = ctx.load(scene, paths)
+        lk.synthesize_H_host(tg, fg, drt.FP64, Hh)
+        lk.unload()
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_val = world * P * T * len(e2e_s) / sum(e2e_s)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "h_samples_per_s": world * T * F * args.steps / total_s,
+            "config": {"workload": "canyon-512paths-2000x0.5ms-512bins-60GHz-fp64", "paths": P, "steps": T,
+                       "bins": F, "fc_hz": fg.fc, "bandwidth_hz": fg.bandwidth, "precision": "DRT_FP64",
+                       "l2": "flushed by a 256 MB write between timed steps (outside the events)",
+                       "parallelism": f"{world} independent links, one per GPU"},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(T * F * 8),
+                    "note": "drt_load_paths + drt_synthesize_H_host + drt_unload per step, wall clock"},
+            "gpu_launches": int(kernel_launches),
+            "kernel_ms": {k: (v[1] / max(1, v[0])) for k, v in prof.items() if v[0]},
+            "wall_s": wall, "clocks": clocks}
+    if FP64_FLOP_PER_PATH_STEP:
+        achieved = FP64_FLOP_PER_PATH_STEP * P * T / k1_avg_s
+        line["roofline"] = {"bound": "alu", "kernel": "k_extrapolate_fp64", "achieved": achieved / 1e12,
+                            "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS,
+                            "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s)",
+                            "traffic": K1_DRAM_BYTES_PER_LAUNCH}
+    else:
+        line["roofline"] = {"bound": "alu", "kernel": "k_extrapolate_fp64", "achieved": None,
+                            "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s", "frac": None,
+                            "traffic": None, "note": "per-path-step FLOP count not yet measured"}
+    probe = ctx.probe_peak(0)
+    line["roofline"]["probe_fp64_tflops"] = probe / 1e12
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(scene, paths, tg, fg, n_steps=400)
+    link.unload()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * drt.h -- C ABI of the GB300 Dynamic Ray Tracing (DRT) hot path.
+ *
+ * Method: Bilibashi, Vitucci, Degli-Esposti, "On Dynamic Ray Tracing and Anticipative Channel
+ * Prediction for Dynamic Environments".  Given the multipath geometry of one ray-tracing run at t0
+ * (Sec. II: chains of specular reflections, edge diffractions and diffuse-scattering tiles) and the
+ * kinematics of terminals and rigid bodies (Eq. Taylor, Sec. III-A), the library extrapolates every
+ * path to t0 + dt (Sec. III) and synthesises the time-varying channel
+ *     H(t, f) = sum_p a_p(t) exp(-j 2 pi f tau_p(t))
+ * from the per-path complex amplitudes a_p and delays tau_p ("time-variant channel's transfer
+ * function", Sec. II).
+ *
+ * Conventions
+ *   - SI units; time-harmonic convention exp(+j w t); c = 299792458 m/s.
+ *   - Times are seconds after t0: t_n = t_start + n dt, n = 0 .. n_steps-1.
+ *   - Frequencies f_k = fc - bandwidth/2 + k bandwidth/n_bins; coefficients are evaluated at fc.
+ *   - Per-(time-step, path) outputs are row-major [n_steps][n_paths] (path index fastest) in the
+ *     caller's path order.
+ *   - Antennas are isotropic and vertically polarised (vertical projected transverse to the ray,
+ *     x if the ray is vertical); line of sight gives a = lambda / (4 pi d).
+ *   - Every call returns a drt_status; the message of the last failure on the calling thread is
+ *     available from drt_last_error().  Per-result conditions (a point left its face or edge, a
+ *     Newton solve did not converge, ...) are reported as flag bits in the outputs, never as call
+ *     errors.
+ *   - Device pointers are CUDA global-memory pointers on the context's device; `stream` is a
+ *     cudaStream_t (NULL = legacy default stream).  Calls on one context are serialised internally;
+ *     device work is ordered on the given stream and the call returns without synchronising unless
+ *     stated otherwise.
+ *   - No CPU fallback: without a usable device, drt_create fails with DRT_ECUDA.
+ */
+#ifndef DRT_H
+#define DRT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct drt_ctx drt_ctx;
+typedef int32_t drt_status;
+
+#define DRT_OK 0
+#define DRT_EINVAL (-1)     /* malformed argument (message says which)                        */
+#define DRT_ENOMEM (-2)     /* device allocation failed or the HBM budget would be exceeded   */
+#define DRT_ECUDA (-3)      /* a CUDA runtime call failed                                     */
+#define DRT_EBUSY (-4)      /* no serving slot / budget free right now                        */
+#define DRT_ETIMEOUT (-5)   /* a bounded wait expired                                         */
+#define DRT_ENOTFOUND (-6)  /* unknown link or ticket                                         */
+
+/* interaction types of a chain vertex (Sec. II, Fig. ray_path) */
+#define DRT_T_NONE 0
+#define DRT_T_R 1   /* specular reflection on a face (Sec. III-A)              */
+#define DRT_T_D 2   /* UTD edge diffraction (Sec. III-B)                        */
+#define DRT_T_S 3   /* diffuse scattering from a tile centroid (Sec. III-C)     */
+#define DRT_MAX_INT 4
+
+/* per-(time-step, path) flag bits; 0 means the path exists at that instant (the multipath
+ * structure of the t0 run still holds, Sec. II "multipath lifetime") */
+#define DRT_F_FACE 1     /* a reflection point lies outside its face rectangle                    */
+#define DRT_F_EDGE 2     /* a diffraction point lies outside its edge segment                     */
+#define DRT_F_SIDE 4     /* a neighbour of a vertex is behind its face / inside its wedge / behind its tile */
+#define DRT_F_NOCONV 8   /* the Newton solve of a segment with >= 2 diffractions did not converge */
+#define DRT_F_DEGEN 16   /* a zero-length segment or a degenerate diffraction geometry            */
+
+/* precision of a call */
+#define DRT_FP64 0        /* all per-path-step geometry, field and Doppler work in FP64           */
+#define DRT_FP32_BULK 1   /* FP32 work on deltas from per-chunk FP64 bases (delay, phase anchors) */
+
+/* ---- dynamic environment database (Sec. II); all positions in world coordinates at t0 ---- */
+typedef struct { double o[3], v[3], a[3], k[3], w0, wdot; } drt_body;      /* 112 B: rotation centre o,
+    its velocity v and constant acceleration a (Eq. Taylor), fixed unit rotation axis k, angular
+    speed w0 at t0 and constant angular acceleration wdot (theta(t) = w0 dt + wdot dt^2 / 2).
+    Body 0 is conventionally the static world. */
+typedef struct { double r[3], v[3], a[3]; } drt_terminal;                 /* 72 B, Eq. Taylor */
+typedef struct { double eps_r, sigma, rough_s, pec; } drt_material;       /* 32 B: relative
+    permittivity, conductivity (S/m), ER roughness of the face (specular term scaled by
+    sqrt(1 - S^2)), perfect conductor if pec != 0 */
+typedef struct { int32_t body, material; double c[3], n[3], u[3], hu, hw; } drt_face;  /* 96 B:
+    rectangle centred at c with unit outward normal n, in-plane unit axis u and half-extents hu
+    along u and hw along u x n; hu = hw = +inf for an unbounded plane */
+typedef struct { int32_t body, material; double a[3], b[3], n0[3], nn[3], wedge_n; } drt_edge; /*
+    112 B: wedge edge from a to b; n0 / nn are the outward normals of the 0-face and the n-face,
+    ordered so that (b - a) is parallel to n0 x nn; exterior wedge angle wedge_n * pi */
+typedef struct { int32_t body, material; double c[3], n[3], area, s, alpha_r, phase; } drt_tile; /*
+    88 B: ER scattering tile (centroid c, unit normal n, area, scattering parameter S, integer lobe
+    exponent alpha_R in 0..16, constant phase (rad)) */
+
+typedef struct {
+    drt_terminal tx, rx;
+    int32_t n_bodies, n_materials, n_faces, n_edges, n_tiles, reserved;
+    const drt_body *bodies;
+    const drt_material *materials;
+    const drt_face *faces;
+    const drt_edge *edges;
+    const drt_tile *tiles;
+} drt_scene;   /* host pointers; copied by drt_load_paths */
+
+/* ray chains of one link (the t0 ray-tracing result): vertex j of path p has type types[p*4+j]
+ * and primitive prims[p*4+j] (face / edge / tile index); s0[p*4+j] is the t0 edge parameter (m
+ * from edge point a) of a diffraction vertex, used as the starting point of the Newton solve of a
+ * segment with two or more diffractions (may be NULL: edge midpoints). */
+typedef struct {
+    int32_t n_paths, reserved;
+    const uint8_t *n_int;     /* [P] number of interactions, 0..4 */
+    const uint8_t *types;     /* [P][4]                            */
+    const int32_t *prims;     /* [P][4]                            */
+    const double *s0;         /* [P][4] or NULL                    */
+} drt_path_set;   /* host pointers; copied by drt_load_paths */
+
+typedef struct { double t_start, dt; int32_t n_steps, reserved; } drt_time_grid;
+typedef struct { double fc, bandwidth; int32_t n_bins, reserved; } drt_freq_grid;
+
+/* caller-owned DEVICE buffers, [n_steps][n_paths] unless stated; any member may be NULL */
+typedef struct {
+    double *tau;     /* delay (s), path length / c                                            */
+    void *amp;       /* complex amplitude a_p (re, im): double[2] for DRT_FP64, float[2] for   */
+                     /* DRT_FP32_BULK; excludes the propagation phase exp(-j 2 pi f tau)      */
+    void *doppler;   /* Doppler shift f' - fc (Hz), App. A Eq. doppler_freq: double / float    */
+    float *angles;   /* [T][P][4]: AoD azimuth, AoD elevation, AoA azimuth, AoA elevation (rad) */
+    uint8_t *flags;  /* DRT_F_* bits                                                           */
+    double *points;  /* [T][P][4][3] interaction points (m), NaN past the chain's length        */
+} drt_path_outputs;
+
+/* ---------------------------------------------------------------------------------------------
+ * Context.  drt_create binds `device`, creates the context's streams and sets the HBM budget
+ * (bytes of device memory the context may hold for links and scratch; 0 = no limit).
+ * Errors: DRT_EINVAL (out == NULL), DRT_ECUDA (no such device / CUDA failure).
+ * drt_destroy frees everything the context owns; NULL is ignored.  drt_last_error returns the
+ * message of the last failing call on this thread (valid until the next call on this thread). */
+drt_status drt_create(drt_ctx **out, int32_t device, uint64_t hbm_budget_bytes);
+void drt_destroy(drt_ctx *ctx);
+const char *drt_last_error(void);
+
+/* ---------------------------------------------------------------------------------------------
+ * a1 load / stage (Sec. II: dynamic environment database + t0 ray-tracing result).  Validates the
+ * scene and paths (indices in range, unit normals and axes, edge ordering, finite values, integer
+ * alpha_R), packs them into the device's structure-of-arrays layout (paths reordered by chain
+ * signature internally; outputs keep the caller's order) and copies them to the device.  Inputs
+ * are copied, so the caller may free them on return.  *out_link receives a handle valid until
+ * drt_unload.  Synchronous.  Errors: DRT_EINVAL, DRT_ENOMEM (budget or cudaMalloc), DRT_ECUDA. */
+drt_status drt_load_paths(drt_ctx *ctx, const drt_scene *scene, const drt_path_set *paths,
+                          uint64_t *out_link);
+drt_status drt_unload(drt_ctx *ctx, uint64_t link);
+
+/* ---------------------------------------------------------------------------------------------
+ * a2-a8: extrapolate every path of `link` over the time grid (Sec. III-A reflection points by the
+ * image method and back-tracking, Eq. ref_point; Sec. III-B diffraction points on the Keller cone,
+ * Eq. diff_point; Sec. III-C rigid scattering tiles), with delay, departure / arrival angles,
+ * Doppler (App. A Eq. doppler_freq, interaction-point velocities), validity flags and the complex
+ * amplitude (Fresnel, UTD, ER and ray spreading at fgrid->fc; only fgrid->fc is used).  Writes the
+ * non-NULL members of *out (device buffers sized for [tgrid->n_steps][n_paths]).
+ * Errors: DRT_EINVAL (bad grid / precision), DRT_ENOTFOUND (link), DRT_ECUDA. */
+drt_status drt_extrapolate(drt_ctx *ctx, uint64_t link, const drt_time_grid *tgrid,
+                           const drt_freq_grid *fgrid, const drt_path_outputs *out,
+                           int32_t precision, void *stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * a2-a9: the whole hot path: extrapolation as above into context-owned scratch, then
+ * H[t][k] = sum over valid paths of a_p(t) exp(-j 2 pi f_k tau_p(t)).  H is a caller-owned DEVICE
+ * buffer of [tgrid->n_steps][fgrid->n_bins] complex64 (float re, im), in both precisions (the
+ * synthesis accumulates in FP32 from phases reduced in FP64).  Scratch grows on demand within the
+ * HBM budget.  Errors: DRT_EINVAL, DRT_ENOTFOUND, DRT_ENOMEM, DRT_ECUDA. */
+drt_status drt_synthesize_H(drt_ctx *ctx, uint64_t link, const drt_time_grid *tgrid,
+                            const drt_freq_grid *fgrid, void *H, int32_t precision, void *stream);
+
+/* Same as drt_synthesize_H with H in HOST memory (pinned or pageable): the result is copied to
+ * the host on `stream` and the call synchronises the stream before returning. */
+drt_status drt_synthesize_H_host(drt_ctx *ctx, uint64_t link, const drt_time_grid *tgrid,
+                                 const drt_freq_grid *fgrid, void *H_host, int32_t precision,
+                                 void *stream);
+
+/* Number of paths of a link (for sizing outputs).  Errors: DRT_ENOTFOUND. */
+drt_status drt_link_info(drt_ctx *ctx, uint64_t link, int32_t *n_paths);
+
+/* ---------------------------------------------------------------------------------------------
+ * Tracing.  While enabled, every kernel the context launches is bracketed by CUDA events recorded
+ * on the launch stream.  drt_profile_read synchronises the device and returns, per kernel kind
+ * (0 = pose table, 1 = extrapolation, 2 = H synthesis, 3 = reserved), the number of launches and
+ * their summed device time in ms since the previous read, then clears the record.
+ * Errors: DRT_EINVAL (NULL arguments), DRT_ECUDA. */
+drt_status drt_profile_enable(drt_ctx *ctx, int32_t on);
+drt_status drt_profile_read(drt_ctx *ctx, int64_t counts[4], double ms[4]);
+
+/* ---------------------------------------------------------------------------------------------
+ * Utility: calibrated issue-rate probe of this device's arithmetic pipes, used to quote roofline
+ * fractions.  kind 0 = FP64 FMA, 1 = FP32 FMA.  Runs a fixed dependent-chain-free FMA loop over
+ * `blocks` x 256 threads and returns the achieved FLOP/s (2 per FMA) in *flops.  Synchronous. */
+drt_status drt_probe_peak(drt_ctx *ctx, int32_t kind, int32_t blocks, double *flops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DRT_H */

@@ -1,0 +1,530 @@
+// drt_api.cu -- C ABI of the DRT hot path (include/drt.h): contexts, link loading and validation,
+// structure-of-arrays packing, device memory under an HBM budget, launches on caller streams.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/drt.h"
+#include "drt_internal.h"
+
+using namespace drt;
+
+namespace {
+
+thread_local std::string g_err;
+
+drt_status fail(drt_status code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (expr);                                                                \
+        if (e_ != cudaSuccess) return fail(DRT_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+struct Link {
+    LinkDev dev;
+    std::vector<void *> allocs;
+    size_t bytes = 0;
+    int32_t n_paths = 0;
+};
+
+// a device buffer owned by the context that grows on demand
+struct Scratch {
+    void *ptr = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace
+
+struct drt_ctx {
+    int32_t device = 0;
+    uint64_t budget = 0, used = 0;
+    std::mutex mu;
+    std::map<uint64_t, Link> links;
+    uint64_t next_link = 1;
+    Scratch pose, rec_a, rec_b, h;
+    double *probe_sink = nullptr;
+    // tracing: (kind, start, stop) per bracketed launch
+    bool profiling = false;
+    struct Mark { int kind; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+};
+
+namespace {
+
+drt_status dev_alloc(drt_ctx *c, size_t bytes, void **out) {
+    if (c->budget && c->used + bytes > c->budget)
+        return fail(DRT_ENOMEM, "HBM budget exceeded: %llu + %llu > %llu bytes", (unsigned long long)c->used,
+                    (unsigned long long)bytes, (unsigned long long)c->budget);
+    cudaError_t e = cudaMalloc(out, bytes ? bytes : 16);
+    if (e != cudaSuccess) return fail(DRT_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    c->used += bytes;
+    return DRT_OK;
+}
+
+void dev_free(drt_ctx *c, void *p, size_t bytes) {
+    if (p) {
+        cudaFree(p);
+        c->used -= bytes;
+    }
+}
+
+drt_status ensure(drt_ctx *c, Scratch &s, size_t bytes) {
+    if (s.cap >= bytes) return DRT_OK;
+    // the previous contents may still be read by work queued on a stream
+    CUDA_TRY(cudaDeviceSynchronize());
+    dev_free(c, s.ptr, s.cap);
+    s.ptr = nullptr;
+    s.cap = 0;
+    size_t want = std::max(bytes, (size_t)1 << 20);
+    drt_status st = dev_alloc(c, want, &s.ptr);
+    if (st) return st;
+    s.cap = want;
+    return DRT_OK;
+}
+
+template <class X> drt_status upload(drt_ctx *c, Link &L, const std::vector<X> &v, const X **dst) {
+    void *p = nullptr;
+    size_t bytes = v.size() * sizeof(X);
+    drt_status st = dev_alloc(c, bytes, &p);
+    if (st) return st;
+    L.allocs.push_back(p);
+    L.bytes += bytes;
+    if (bytes) CUDA_TRY(cudaMemcpy(p, v.data(), bytes, cudaMemcpyHostToDevice));
+    *dst = reinterpret_cast<const X *>(p);
+    return DRT_OK;
+}
+
+bool finite3(const double *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+void cross3(const double *a, const double *b, double *o) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+bool unit3(const double *v) { return finite3(v) && std::fabs(std::sqrt(dot3(v, v)) - 1.0) < 1e-9; }
+
+drt_status validate(const drt_scene *s, const drt_path_set *ps) {
+    if (!s || !ps) return fail(DRT_EINVAL, "scene and paths must be non-NULL");
+    if (s->n_bodies < 1 || s->n_materials < 0 || s->n_faces < 0 || s->n_edges < 0 || s->n_tiles < 0)
+        return fail(DRT_EINVAL, "scene counts must be >= 0 (and >= 1 body)");
+    if (!s->bodies || (s->n_materials && !s->materials) || (s->n_faces && !s->faces) ||
+        (s->n_edges && !s->edges) || (s->n_tiles && !s->tiles))
+        return fail(DRT_EINVAL, "scene array pointer is NULL");
+    for (const drt_terminal *t : {&s->tx, &s->rx})
+        if (!finite3(t->r) || !finite3(t->v) || !finite3(t->a)) return fail(DRT_EINVAL, "terminal not finite");
+    for (int i = 0; i < s->n_bodies; ++i) {
+        const drt_body &b = s->bodies[i];
+        if (!finite3(b.o) || !finite3(b.v) || !finite3(b.a) || !unit3(b.k) || !std::isfinite(b.w0) ||
+            !std::isfinite(b.wdot))
+            return fail(DRT_EINVAL, "body %d: non-finite kinematics or non-unit axis", i);
+    }
+    for (int i = 0; i < s->n_materials; ++i) {
+        const drt_material &m = s->materials[i];
+        if (!(m.eps_r >= 1.0) || !(m.sigma >= 0.0) || !(m.rough_s >= 0.0 && m.rough_s <= 1.0) || !std::isfinite(m.pec))
+            return fail(DRT_EINVAL, "material %d: need eps_r >= 1, sigma >= 0, 0 <= rough_s <= 1", i);
+    }
+    auto chk = [&](int body, int mat, const char *what, int i) -> drt_status {
+        if (body < 0 || body >= s->n_bodies) return fail(DRT_EINVAL, "%s %d: body %d out of range", what, i, body);
+        if (mat < 0 || mat >= s->n_materials) return fail(DRT_EINVAL, "%s %d: material %d out of range", what, i, mat);
+        return DRT_OK;
+    };
+    for (int i = 0; i < s->n_faces; ++i) {
+        const drt_face &f = s->faces[i];
+        if (drt_status st = chk(f.body, f.material, "face", i)) return st;
+        if (!finite3(f.c) || !unit3(f.n) || !unit3(f.u) || std::fabs(dot3(f.n, f.u)) > 1e-9 || !(f.hu > 0) ||
+            !(f.hw > 0))
+            return fail(DRT_EINVAL, "face %d: need finite centre, unit n and u with u.n = 0, hu, hw > 0", i);
+    }
+    for (int i = 0; i < s->n_edges; ++i) {
+        const drt_edge &e = s->edges[i];
+        if (drt_status st = chk(e.body, e.material, "edge", i)) return st;
+        double d[3] = {e.b[0] - e.a[0], e.b[1] - e.a[1], e.b[2] - e.a[2]}, x[3];
+        double L = std::sqrt(dot3(d, d));
+        if (!finite3(e.a) || !finite3(e.b) || !(L > 0) || !unit3(e.n0) || !unit3(e.nn))
+            return fail(DRT_EINVAL, "edge %d: need distinct finite endpoints and unit face normals", i);
+        cross3(e.n0, e.nn, x);
+        if (std::fabs(dot3(e.n0, d)) > 1e-9 * L || std::fabs(dot3(e.nn, d)) > 1e-9 * L || !(dot3(x, d) > 0))
+            return fail(DRT_EINVAL, "edge %d: face normals must be perpendicular to the edge and (b-a).(n0 x nn) > 0", i);
+        if (!(e.wedge_n >= 1.0 && e.wedge_n <= 2.0)) return fail(DRT_EINVAL, "edge %d: wedge_n must be in [1, 2]", i);
+    }
+    for (int i = 0; i < s->n_tiles; ++i) {
+        const drt_tile &t = s->tiles[i];
+        if (drt_status st = chk(t.body, t.material, "tile", i)) return st;
+        if (!finite3(t.c) || !unit3(t.n) || !(t.area > 0) || !(t.s >= 0 && t.s <= 1) || !std::isfinite(t.phase) ||
+            !(t.alpha_r >= 0 && t.alpha_r <= 16 && t.alpha_r == std::floor(t.alpha_r)))
+            return fail(DRT_EINVAL, "tile %d: need unit normal, area > 0, 0 <= S <= 1, integer alpha_R in [0,16]", i);
+    }
+    if (ps->n_paths < 0 || (ps->n_paths && (!ps->n_int || !ps->types || !ps->prims)))
+        return fail(DRT_EINVAL, "path set: bad count or NULL arrays");
+    for (int p = 0; p < ps->n_paths; ++p) {
+        int n = ps->n_int[p];
+        if (n > DRT_MAX_INT) return fail(DRT_EINVAL, "path %d: %d interactions > %d", p, n, DRT_MAX_INT);
+        for (int j = 0; j < DRT_MAX_INT; ++j) {
+            int ty = ps->types[p * 4 + j], pr = ps->prims[p * 4 + j];
+            if (j >= n) {
+                if (ty != DRT_T_NONE) return fail(DRT_EINVAL, "path %d: type set past n_int", p);
+                continue;
+            }
+            int lim = ty == DRT_T_R ? s->n_faces : ty == DRT_T_D ? s->n_edges : ty == DRT_T_S ? s->n_tiles : -1;
+            if (lim < 0) return fail(DRT_EINVAL, "path %d vertex %d: bad type %d", p, j, ty);
+            if (pr < 0 || pr >= lim) return fail(DRT_EINVAL, "path %d vertex %d: primitive %d out of range", p, j, pr);
+            if (ps->s0 && !std::isfinite(ps->s0[p * 4 + j])) return fail(DRT_EINVAL, "path %d: s0 not finite", p);
+        }
+    }
+    return DRT_OK;
+}
+
+drt_status check_grids(const drt_time_grid *tg, const drt_freq_grid *fg, int32_t precision) {
+    if (!tg || !fg) return fail(DRT_EINVAL, "time and frequency grids must be non-NULL");
+    if (tg->n_steps < 0 || !std::isfinite(tg->t_start) || !std::isfinite(tg->dt))
+        return fail(DRT_EINVAL, "time grid: n_steps >= 0 and finite t_start, dt required");
+    if (!(fg->fc > 0) || !(fg->bandwidth >= 0) || fg->n_bins < 1 || fg->n_bins > 4096 || !std::isfinite(fg->fc))
+        return fail(DRT_EINVAL, "frequency grid: fc > 0, bandwidth >= 0, 1 <= n_bins <= 4096 required");
+    if (precision != DRT_FP64 && precision != DRT_FP32_BULK)
+        return fail(DRT_EINVAL, "precision must be DRT_FP64 or DRT_FP32_BULK");
+    return DRT_OK;
+}
+
+Link *find_link(drt_ctx *c, uint64_t id) {
+    auto it = c->links.find(id);
+    return it == c->links.end() ? nullptr : &it->second;
+}
+
+TimeGridD tgd(const drt_time_grid *g) { return TimeGridD{g->t_start, g->dt, g->n_steps}; }
+FreqGridD fgd(const drt_freq_grid *g) { return FreqGridD{g->fc, g->bandwidth, g->n_bins}; }
+
+// bracket one launch with events when tracing is on
+template <class F> drt_status traced(drt_ctx *c, int kind, cudaStream_t s, F &&launch) {
+    if (!c->profiling) {
+        CUDA_TRY(launch());
+        return DRT_OK;
+    }
+    drt_ctx::Mark m{kind, nullptr, nullptr};
+    CUDA_TRY(cudaEventCreate(&m.a));
+    CUDA_TRY(cudaEventCreate(&m.b));
+    CUDA_TRY(cudaEventRecord(m.a, s));
+    CUDA_TRY(launch());
+    CUDA_TRY(cudaEventRecord(m.b, s));
+    c->marks.push_back(m);
+    return DRT_OK;
+}
+
+// pose table + extrapolation (+ records) for one link
+drt_status run_extrapolation(drt_ctx *c, Link &L, const drt_time_grid *tg, const drt_freq_grid *fg,
+                             const OutD &out, const RecD &rec, int32_t precision, cudaStream_t s) {
+    size_t pose_bytes = (size_t)tg->n_steps * L.dev.n_bodies * POSE_W * sizeof(double);
+    if (drt_status st = ensure(c, c->pose, pose_bytes)) return st;
+    TimeGridD t = tgd(tg);
+    double *pose = reinterpret_cast<double *>(c->pose.ptr);
+    if (drt_status st = traced(c, 0, s, [&] { return launch_pose(L.dev, t, pose, s); })) return st;
+    (void)precision;   // the FP32-bulk form shares the FP64 kernel until its own lands
+    FreqGridD f = fgd(fg);
+    return traced(c, 1, s, [&] { return launch_extrapolate_fp64(L.dev, t, f, pose, out, rec, s); });
+}
+
+drt_status synth_into(drt_ctx *c, Link &L, const drt_time_grid *tg, const drt_freq_grid *fg, float2 *H,
+                      int32_t precision, cudaStream_t s) {
+    size_t n = (size_t)tg->n_steps * L.n_paths;
+    if (drt_status st = ensure(c, c->rec_a, n * sizeof(float4))) return st;
+    if (drt_status st = ensure(c, c->rec_b, n * sizeof(float))) return st;
+    RecD rec{reinterpret_cast<float4 *>(c->rec_a.ptr), reinterpret_cast<float *>(c->rec_b.ptr)};
+    OutD none{};
+    if (drt_status st = run_extrapolation(c, L, tg, fg, none, rec, precision, s)) return st;
+    TimeGridD t = tgd(tg);
+    FreqGridD f = fgd(fg);
+    return traced(c, 2, s, [&] { return launch_synth(rec, L.n_paths, t, f, H, s); });
+}
+
+}  // namespace
+
+// validated host-side structure-of-arrays image of one link (device pointers unset)
+drt_status drt::pack_link(const drt_scene *s, const drt_path_set *ps, PackedLink &H) {
+    if (drt_status st = validate(s, ps)) return st;
+    LinkDev &d = H.dev;
+    d.n_paths = ps->n_paths;
+    d.n_bodies = s->n_bodies;
+    d.n_faces = s->n_faces;
+    d.n_edges = s->n_edges;
+    d.n_tiles = s->n_tiles;
+    d.n_mats = s->n_materials;
+    std::memcpy(&d.tx, &s->tx, sizeof(TermD));
+    std::memcpy(&d.rx, &s->rx, sizeof(TermD));
+
+    std::vector<BodyD> &bodies = H.bodies;
+    bodies.resize(s->n_bodies);
+    std::memcpy(bodies.data(), s->bodies, sizeof(BodyD) * s->n_bodies);
+    auto rel = [&](int body, const double *x, double *o) {
+        for (int j = 0; j < 3; ++j) o[j] = x[j] - s->bodies[body].o[j];
+    };
+    std::vector<FaceD> &faces = H.faces;
+    faces.resize(s->n_faces);
+    for (int i = 0; i < s->n_faces; ++i) {
+        const drt_face &f = s->faces[i];
+        FaceD &g = faces[i];
+        rel(f.body, f.c, g.c);
+        std::memcpy(g.n, f.n, 24);
+        std::memcpy(g.u, f.u, 24);
+        g.hu = f.hu;
+        g.hw = f.hw;
+        g.body = f.body;
+        g.mat = f.material;
+    }
+    std::vector<EdgeD> &edges = H.edges;
+    edges.resize(s->n_edges);
+    for (int i = 0; i < s->n_edges; ++i) {
+        const drt_edge &e = s->edges[i];
+        EdgeD &g = edges[i];
+        double dv[3] = {e.b[0] - e.a[0], e.b[1] - e.a[1], e.b[2] - e.a[2]};
+        double L0 = std::sqrt(dot3(dv, dv));
+        rel(e.body, e.a, g.a);
+        for (int j = 0; j < 3; ++j) g.e[j] = dv[j] / L0;
+        cross3(e.n0, g.e, g.t0);
+        std::memcpy(g.n0, e.n0, 24);
+        g.len = L0;
+        g.wn = e.wedge_n;
+        g.body = e.body;
+        g.mat = e.material;
+        g.pad0 = g.pad1 = 0;
+    }
+    std::vector<TileD> &tiles = H.tiles;
+    tiles.resize(s->n_tiles);
+    for (int i = 0; i < s->n_tiles; ++i) {
+        const drt_tile &t = s->tiles[i];
+        TileD &g = tiles[i];
+        rel(t.body, t.c, g.c);
+        std::memcpy(g.n, t.n, 24);
+        g.area = t.area;
+        g.s = t.s;
+        g.alpha = t.alpha_r;
+        g.phase = t.phase;
+        g.body = t.body;
+        g.mat = t.material;
+    }
+    std::vector<MatD> &mats = H.mats;
+    mats.resize(s->n_materials);
+    std::memcpy(mats.data(), s->materials, sizeof(MatD) * s->n_materials);
+
+    // paths sorted by chain signature so that warps run uniform code
+    int P = ps->n_paths;
+    std::vector<uint32_t> code(P);
+    for (int p = 0; p < P; ++p) {
+        uint32_t c0 = 0;
+        for (int j = 0; j < DRT_MAX_INT; ++j) c0 |= (uint32_t)ps->types[p * 4 + j] << (8 * j);
+        code[p] = c0;
+    }
+    std::vector<int32_t> &perm = H.perm;
+    perm.resize(P);
+    std::iota(perm.begin(), perm.end(), 0);
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return code[a] < code[b]; });
+    std::vector<uint32_t> &ptypes = H.ptypes;
+    ptypes.resize(P);
+    std::vector<int4> &pprims = H.pprims;
+    pprims.resize(P);
+    std::vector<double> &ps0 = H.ps0;
+    ps0.resize((size_t)P * 4);
+    for (int q = 0; q < P; ++q) {
+        int p = perm[q];
+        ptypes[q] = code[p];
+        const int32_t *pr = ps->prims + p * 4;
+        int n = ps->n_int[p];
+        pprims[q] = make_int4(n > 0 ? pr[0] : 0, n > 1 ? pr[1] : 0, n > 2 ? pr[2] : 0, n > 3 ? pr[3] : 0);
+        for (int j = 0; j < 4; ++j) {
+            double v = 0.0;
+            if (j < n && ps->types[p * 4 + j] == DRT_T_D)
+                v = ps->s0 ? ps->s0[p * 4 + j] : 0.5 * edges[pr[j]].len;
+            ps0[(size_t)q * 4 + j] = v;
+        }
+    }
+    return DRT_OK;
+}
+
+
+extern "C" {
+
+const char *drt_last_error(void) { return g_err.c_str(); }
+
+drt_status drt_create(drt_ctx **out, int32_t device, uint64_t hbm_budget_bytes) {
+    if (!out) return fail(DRT_EINVAL, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0)
+        return fail(DRT_ECUDA, "no CUDA device: %s", e != cudaSuccess ? cudaGetErrorString(e) : "count is 0");
+    if (device < 0 || device >= n) return fail(DRT_ECUDA, "device %d out of range (%d devices)", device, n);
+    CUDA_TRY(cudaSetDevice(device));
+    drt_ctx *c = new drt_ctx();
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    if (cudaMalloc(&c->probe_sink, 64) != cudaSuccess) {
+        delete c;
+        return fail(DRT_ENOMEM, "cudaMalloc failed");
+    }
+    *out = c;
+    return DRT_OK;
+}
+
+void drt_destroy(drt_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto &kv : c->links)
+        for (void *p : kv.second.allocs) cudaFree(p);
+    for (Scratch *s : {&c->pose, &c->rec_a, &c->rec_b, &c->h})
+        if (s->ptr) cudaFree(s->ptr);
+    cudaFree(c->probe_sink);
+    delete c;
+}
+
+drt_status drt_load_paths(drt_ctx *c, const drt_scene *s, const drt_path_set *ps, uint64_t *out_link) {
+    if (!c || !out_link) return fail(DRT_EINVAL, "ctx and out_link must be non-NULL");
+    PackedLink H;
+    if (drt_status st = pack_link(s, ps, H)) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    CUDA_TRY(cudaSetDevice(c->device));
+    Link L;
+    L.dev = H.dev;
+    L.n_paths = ps->n_paths;
+    LinkDev &d = L.dev;
+    drt_status st = DRT_OK;
+    if (!st) st = upload(c, L, H.bodies, &d.bodies);
+    if (!st) st = upload(c, L, H.faces, &d.faces);
+    if (!st) st = upload(c, L, H.edges, &d.edges);
+    if (!st) st = upload(c, L, H.tiles, &d.tiles);
+    if (!st) st = upload(c, L, H.mats, &d.mats);
+    if (!st) st = upload(c, L, H.ptypes, &d.ptypes);
+    if (!st) st = upload(c, L, H.pprims, &d.pprims);
+    if (!st) st = upload(c, L, H.ps0, &d.ps0);
+    if (!st) st = upload(c, L, H.perm, &d.perm);
+    if (st) {
+        for (void *p : L.allocs) cudaFree(p);
+        c->used -= L.bytes;
+        return st;
+    }
+    uint64_t id = c->next_link++;
+    c->links.emplace(id, std::move(L));
+    *out_link = id;
+    return DRT_OK;
+}
+
+drt_status drt_unload(drt_ctx *c, uint64_t link) {
+    if (!c) return fail(DRT_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    Link *L = find_link(c, link);
+    if (!L) return fail(DRT_ENOTFOUND, "unknown link %llu", (unsigned long long)link);
+    CUDA_TRY(cudaSetDevice(c->device));
+    CUDA_TRY(cudaDeviceSynchronize());
+    for (void *p : L->allocs) cudaFree(p);
+    c->used -= L->bytes;
+    c->links.erase(link);
+    return DRT_OK;
+}
+
+drt_status drt_link_info(drt_ctx *c, uint64_t link, int32_t *n_paths) {
+    if (!c || !n_paths) return fail(DRT_EINVAL, "ctx and n_paths must be non-NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    Link *L = find_link(c, link);
+    if (!L) return fail(DRT_ENOTFOUND, "unknown link %llu", (unsigned long long)link);
+    *n_paths = L->n_paths;
+    return DRT_OK;
+}
+
+drt_status drt_extrapolate(drt_ctx *c, uint64_t link, const drt_time_grid *tg, const drt_freq_grid *fg,
+                           const drt_path_outputs *out, int32_t precision, void *stream) {
+    if (!c || !out) return fail(DRT_EINVAL, "ctx and out must be non-NULL");
+    if (drt_status st = check_grids(tg, fg, precision)) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    Link *L = find_link(c, link);
+    if (!L) return fail(DRT_ENOTFOUND, "unknown link %llu", (unsigned long long)link);
+    CUDA_TRY(cudaSetDevice(c->device));
+    OutD o{out->tau, out->amp, out->doppler, out->angles, out->flags, out->points};
+    RecD none{nullptr, nullptr};
+    return run_extrapolation(c, *L, tg, fg, o, none, precision, (cudaStream_t)stream);
+}
+
+drt_status drt_synthesize_H(drt_ctx *c, uint64_t link, const drt_time_grid *tg, const drt_freq_grid *fg, void *H,
+                            int32_t precision, void *stream) {
+    if (!c || !H) return fail(DRT_EINVAL, "ctx and H must be non-NULL");
+    if (drt_status st = check_grids(tg, fg, precision)) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    Link *L = find_link(c, link);
+    if (!L) return fail(DRT_ENOTFOUND, "unknown link %llu", (unsigned long long)link);
+    CUDA_TRY(cudaSetDevice(c->device));
+    return synth_into(c, *L, tg, fg, reinterpret_cast<float2 *>(H), precision, (cudaStream_t)stream);
+}
+
+drt_status drt_synthesize_H_host(drt_ctx *c, uint64_t link, const drt_time_grid *tg, const drt_freq_grid *fg,
+                                 void *H_host, int32_t precision, void *stream) {
+    if (!c || !H_host) return fail(DRT_EINVAL, "ctx and H_host must be non-NULL");
+    if (drt_status st = check_grids(tg, fg, precision)) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    Link *L = find_link(c, link);
+    if (!L) return fail(DRT_ENOTFOUND, "unknown link %llu", (unsigned long long)link);
+    CUDA_TRY(cudaSetDevice(c->device));
+    size_t bytes = (size_t)tg->n_steps * fg->n_bins * sizeof(float2);
+    if (drt_status st = ensure(c, c->h, bytes)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (drt_status st = synth_into(c, *L, tg, fg, reinterpret_cast<float2 *>(c->h.ptr), precision, s)) return st;
+    CUDA_TRY(cudaMemcpyAsync(H_host, c->h.ptr, bytes, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return DRT_OK;
+}
+
+drt_status drt_profile_enable(drt_ctx *c, int32_t on) {
+    if (!c) return fail(DRT_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->profiling = on != 0;
+    return DRT_OK;
+}
+
+drt_status drt_profile_read(drt_ctx *c, int64_t counts[4], double ms[4]) {
+    if (!c || !counts || !ms) return fail(DRT_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    CUDA_TRY(cudaSetDevice(c->device));
+    CUDA_TRY(cudaDeviceSynchronize());
+    for (int k = 0; k < 4; ++k) {
+        counts[k] = 0;
+        ms[k] = 0.0;
+    }
+    drt_status st = DRT_OK;
+    for (auto &m : c->marks) {
+        float x = 0.f;
+        if (cudaEventElapsedTime(&x, m.a, m.b) != cudaSuccess) st = fail(DRT_ECUDA, "cudaEventElapsedTime failed");
+        counts[m.kind] += 1;
+        ms[m.kind] += x;
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    c->marks.clear();
+    return st;
+}
+
+drt_status drt_probe_peak(drt_ctx *c, int32_t kind, int32_t blocks, double *flops) {
+    if (!c || !flops || (kind != 0 && kind != 1) || blocks < 1) return fail(DRT_EINVAL, "bad probe arguments");
+    std::lock_guard<std::mutex> lk(c->mu);
+    CUDA_TRY(cudaSetDevice(c->device));
+    float ms = 0.f;
+    CUDA_TRY(launch_probe(kind, blocks, c->probe_sink, 0, &ms));
+    const double iters = kind == 0 ? 2048 : 65536;
+    *flops = (double)blocks * 256 * iters * 8 * 2 / (ms * 1e-3);
+    return DRT_OK;
+}
+
+}  // extern "C"

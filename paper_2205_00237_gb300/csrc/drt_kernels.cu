@@ -1,0 +1,151 @@
+// drt_kernels.cu -- kernels of the DRT hot path on sm_103a:
+//   k_pose           a2: per (time-step, body) pose table R(t), O(t), v_O(t), omega(t) (FP64)
+//   k_extrapolate    a3-a8: one thread per (path, time-step); a warp covers 32 consecutive paths
+//                    (sorted by chain signature, so warps rarely diverge) at one time step
+//   k_synth          a9: H(t, f) = sum_p a_p exp(-j 2 pi f tau_p); one thread per (time-step,
+//                    16-bin frequency tile), sincos seed per tile and a complex rotation
+//                    recurrence inside it, FP32 FMA accumulation
+//   k_probe          FMA issue-rate probe for the roofline denominators
+#include "drt_internal.h"
+#include "drt_physics.cuh"
+
+namespace drt {
+
+// ------------------------------------------------------------------------------------------------
+// a2: poses.  theta(t) = w0 t + wdot t^2 / 2 about the fixed axis k (Rodrigues), O(t) by Eq. Taylor,
+// v_O(t) = v + a t, omega(t) = (w0 + wdot t) k.
+__global__ void k_pose(const BodyD *__restrict__ bodies, int n_bodies, double t_start, double dt, int n_steps,
+                       double *__restrict__ pose) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_steps * n_bodies) return;
+    int ti = i / n_bodies, b = i - ti * n_bodies;
+    body_pose_row(bodies[b], t_start + ti * dt, pose + (size_t)i * POSE_W);
+}
+
+cudaError_t launch_pose(const LinkDev &L, const TimeGridD &tg, double *pose, cudaStream_t s) {
+    int n = tg.n_steps * L.n_bodies;
+    if (n == 0) return cudaSuccess;
+    k_pose<<<(n + 255) / 256, 256, 0, s>>>(L.bodies, L.n_bodies, tg.t_start, tg.dt, tg.n_steps, pose);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// a3-a8 in FP64
+constexpr int EXT_TY = 4;   // time steps per block (one warp each)
+
+__global__ void __launch_bounds__(32 * EXT_TY)
+k_extrapolate_fp64(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const double *__restrict__ pose,
+                   const OutD out, const RecD rec) {
+    int p = blockIdx.x * 32 + threadIdx.x;
+    int ti = blockIdx.y * EXT_TY + threadIdx.y;
+    if (p >= L.n_paths || ti >= tg.n_steps) return;
+    path_step_fp64(L, tg, fg, pose, p, ti, out, rec);
+}
+
+cudaError_t launch_extrapolate_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg,
+                                    const double *pose, const OutD &out, const RecD &rec, cudaStream_t s) {
+    if (L.n_paths == 0 || tg.n_steps == 0) return cudaSuccess;
+    dim3 block(32, EXT_TY), grid((L.n_paths + 31) / 32, (tg.n_steps + EXT_TY - 1) / EXT_TY);
+    k_extrapolate_fp64<<<grid, block, 0, s>>>(L, tg, fg, pose, out, rec);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// a9: H synthesis.  Thread (t, tile) owns bins k0 .. k0+15 of one time step and loops over the
+// paths of that step; all threads of the step read the same record (broadcast).  Seed
+// exp(-j 2 pi frac(phi0 + k0 step)) by sincospi with the step split so k0 * hi is exact, then a
+// complex rotation by exp(-j 2 pi step) per bin.
+constexpr int KT = 16;
+
+__global__ void __launch_bounds__(128)
+k_synth(const float4 *__restrict__ rec_a, const float *__restrict__ rec_b, int n_paths, int n_steps, int n_bins,
+        float2 *__restrict__ H) {
+    int ntile = (n_bins + KT - 1) / KT;
+    int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    int ti = gid / ntile, tile = gid - ti * ntile;
+    if (ti >= n_steps) return;
+    int k0 = tile * KT;
+    float kf = (float)k0;
+    float2 acc[KT];
+#pragma unroll
+    for (int j = 0; j < KT; ++j) acc[j] = make_float2(0.f, 0.f);
+    const float4 *ra = rec_a + (size_t)ti * n_paths;
+    const float *rb = rec_b + (size_t)ti * n_paths;
+    for (int p = 0; p < n_paths; ++p) {
+        float4 r = __ldg(ra + p);
+        if (r.x == 0.f && r.y == 0.f) continue;
+        float lo = __ldg(rb + p);
+        float ph = kf * r.w;               // exact
+        ph -= floorf(ph);
+        ph += r.z + kf * lo;
+        ph -= floorf(ph);
+        float sn, cs, ws, wc;
+        sincospif(2.f * ph, &sn, &cs);
+        sincospif(2.f * (r.w + lo), &ws, &wc);
+        // z = a exp(-j 2 pi ph), w = exp(-j 2 pi step)
+        float zr = fmaf(r.x, cs, r.y * sn), zi = fmaf(r.y, cs, -r.x * sn);
+        float wr = wc, wi = -ws;
+#pragma unroll
+        for (int j = 0; j < KT; ++j) {
+            acc[j].x += zr;
+            acc[j].y += zi;
+            float nr = fmaf(zr, wr, -zi * wi);
+            zi = fmaf(zr, wi, zi * wr);
+            zr = nr;
+        }
+    }
+    float2 *out = H + (size_t)ti * n_bins + k0;
+#pragma unroll
+    for (int j = 0; j < KT; ++j)
+        if (k0 + j < n_bins) out[j] = acc[j];
+}
+
+cudaError_t launch_synth(const RecD &rec, int32_t n_paths, const TimeGridD &tg, const FreqGridD &fg, float2 *H,
+                         cudaStream_t s) {
+    int ntile = (fg.n_bins + KT - 1) / KT;
+    long long threads = (long long)tg.n_steps * ntile;
+    if (threads == 0) return cudaSuccess;
+    k_synth<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(rec.rec_a, rec.rec_b, n_paths, tg.n_steps, fg.n_bins,
+                                                               H);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// FMA issue-rate probe: 8 independent chains per thread, 4096 iterations
+template <class T>
+__global__ void k_probe(T *sink, int iters) {
+    T a[8];
+    T x = T(threadIdx.x) * T(1e-3), y = T(0.999999);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = x + T(j);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = fma(a[j], y, x);
+    }
+    T s = T(0);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += a[j];
+    if (s == T(-1)) sink[0] = s;   // never true; keeps the loop alive
+}
+
+cudaError_t launch_probe(int kind, int blocks, double *sink, cudaStream_t s, float *ms) {
+    const int iters = kind == 0 ? 2048 : 65536;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int rep = 0; rep < 2; ++rep) {   // first launch warms up
+        cudaEventRecord(e0, s);
+        if (kind == 0) k_probe<double><<<blocks, 256, 0, s>>>(sink, iters);
+        else k_probe<float><<<blocks, 256, 0, s>>>(reinterpret_cast<float *>(sink), iters);
+        cudaEventRecord(e1, s);
+    }
+    cudaError_t err = cudaEventSynchronize(e1);
+    cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // FLOPs: blocks * 256 threads * iters * 8 chains * 2
+    *ms = *ms;
+    return err != cudaSuccess ? err : cudaGetLastError();
+}
+
+}  // namespace drt

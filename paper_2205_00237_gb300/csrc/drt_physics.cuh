@@ -1,0 +1,693 @@
+// drt_physics.cuh -- per-(path, time-step) device work of the DRT hot path: posing primitives on
+// moving bodies, the interaction points (image method and back-tracking, Keller cone, rigid
+// tiles, Newton for several diffractions in one segment), validity, Doppler and the field
+// coefficients.  Templated on the working precision T; positions carry their time derivative as
+// dual numbers so interaction-point velocities come out of the same arithmetic.
+#pragma once
+#include "drt_internal.h"
+#include "drt_math.cuh"
+
+namespace drt {
+
+constexpr double C0 = 299792458.0;
+constexpr double EPS0 = 8.8541878128e-12;
+constexpr double PI = 3.14159265358979323846;
+
+enum : uint32_t { F_FACE = 1, F_EDGE = 2, F_SIDE = 4, F_NOCONV = 8, F_DEGEN = 16 };
+enum : int { T_NONE = 0, T_R = 1, T_D = 2, T_S = 3 };
+
+// ------------------------------------------------------------------------------------------------
+// posing (Sec. III-A: rotation about a fixed axis, Eq. RigidBodyMotion for body-point velocity)
+template <class T> struct Pose { v3<T> R0, R1, R2, O, vO, w; };   // rows of R
+
+template <class T> DRT_HD Pose<T> load_pose(const double *P) {
+    Pose<T> q;
+    q.R0 = V3<T>(P[0], P[1], P[2]);
+    q.R1 = V3<T>(P[3], P[4], P[5]);
+    q.R2 = V3<T>(P[6], P[7], P[8]);
+    q.O = V3<T>(P[9], P[10], P[11]);
+    q.vO = V3<T>(P[12], P[13], P[14]);
+    q.w = V3<T>(P[15], P[16], P[17]);
+    return q;
+}
+template <class T> DRT_HD v3<T> rot(const Pose<T> &q, const double *a) {
+    v3<T> x = V3<T>(a[0], a[1], a[2]);
+    return V3<T>(dot(q.R0, x), dot(q.R1, x), dot(q.R2, x));
+}
+// body point that sat at o + rel at t0: position O + R rel, velocity v_O + w x (R rel)
+template <class T> DRT_HD v3<dl<T>> pose_point(const Pose<T> &q, const double *rel) {
+    v3<T> r = rot(q, rel);
+    return dual(q.O + r, q.vO + cross(q.w, r));
+}
+// body-fixed direction: R d0, derivative w x (R d0)
+template <class T> DRT_HD v3<dl<T>> pose_dir(const Pose<T> &q, const double *d0) {
+    v3<T> n = rot(q, d0);
+    return dual(n, cross(q.w, n));
+}
+
+// pose record of one body at time t (seconds after t0): theta(t) = w0 t + wdot t^2 / 2 about the fixed
+// axis k (Rodrigues), O(t) by Eq. Taylor, v_O(t) = v + a t, omega(t) = (w0 + wdot t) k
+DRT_HD void body_pose_row(const BodyD &B, double t, double *P) {
+    double th = B.w0 * t + 0.5 * B.wdot * t * t, ws = B.w0 + B.wdot * t;
+    double s = sin(th), c = cos(th);
+    double C1 = 1.0 - c, kx = B.k[0], ky = B.k[1], kz = B.k[2];
+    P[0] = c + kx * kx * C1;      P[1] = kx * ky * C1 - kz * s; P[2] = kx * kz * C1 + ky * s;
+    P[3] = ky * kx * C1 + kz * s; P[4] = c + ky * ky * C1;      P[5] = ky * kz * C1 - kx * s;
+    P[6] = kz * kx * C1 - ky * s; P[7] = kz * ky * C1 + kx * s; P[8] = c + kz * kz * C1;
+    for (int j = 0; j < 3; ++j) {
+        P[9 + j] = B.o[j] + B.v[j] * t + 0.5 * B.a[j] * t * t;
+        P[12 + j] = B.v[j] + B.a[j] * t;
+        P[15 + j] = B.k[j] * ws;
+    }
+}
+
+// terminal state (Eq. Taylor)
+template <class T> DRT_HD v3<dl<T>> terminal(const TermD &m, T t) {
+    v3<T> r = V3<T>(m.r[0], m.r[1], m.r[2]), v = V3<T>(m.v[0], m.v[1], m.v[2]), a = V3<T>(m.a[0], m.a[1], m.a[2]);
+    return dual(r + v * t + a * (T(0.5) * t * t), v + a * t);
+}
+
+// ------------------------------------------------------------------------------------------------
+// interaction points
+// Eq. ref_point in vector form: tangential coordinates interpolated between source S and
+// receiver R with weight h_S / (h_S + h_R) (h = height above the wall), normal coordinate 0.
+template <class T> DRT_HD v3<dl<T>> refl_point(v3<dl<T>> S, v3<dl<T>> R, v3<dl<T>> c, v3<dl<T>> n) {
+    dl<T> hs = dot(S - c, n), hr = dot(R - c, n);
+    dl<T> g = hs / (hs + hr);
+    v3<dl<T>> Q = S + (R - S) * g;
+    return Q - n * dot(Q - c, n);
+}
+// image of X across the wall (c, n)
+template <class T> DRT_HD v3<dl<T>> mirror(v3<dl<T>> X, v3<dl<T>> c, v3<dl<T>> n) {
+    dl<T> h = dot(X - c, n);
+    return X - n * (h + h);
+}
+template <class T> DRT_HD v3<dl<T>> mirror_dir(v3<dl<T>> d, v3<dl<T>> n) {
+    dl<T> h = dot(d, n);
+    return d - n * (h + h);
+}
+
+// posed primitives of one chain vertex
+template <class T> struct Prim {
+    int type, mat;
+    v3<dl<T>> p;    // R: face centre, D: edge point a, S: tile centroid
+    v3<dl<T>> a;    // R: face normal, D: edge direction, S: tile normal
+    v3<T> b;        // R: face axis u, D: 0-face tangent t0 = n0 x e
+    v3<T> c;        // D: 0-face normal n0
+    T h1, h2;       // R: hu, hw; D: length, wedge n
+    int idx;
+};
+
+template <class T>
+DRT_HD Prim<T> load_prim(const LinkDev &L, const double *poseT, int type, int idx) {
+    Prim<T> q;
+    q.type = type;
+    q.idx = idx;
+    if (type == T_R) {
+        const FaceD &f = L.faces[idx];
+        Pose<T> P = load_pose<T>(poseT + (size_t)f.body * POSE_W);
+        q.p = pose_point(P, f.c);
+        q.a = pose_dir(P, f.n);
+        q.b = rot(P, f.u);
+        q.h1 = T(f.hu);
+        q.h2 = T(f.hw);
+        q.mat = f.mat;
+    } else if (type == T_D) {
+        const EdgeD &e = L.edges[idx];
+        Pose<T> P = load_pose<T>(poseT + (size_t)e.body * POSE_W);
+        q.p = pose_point(P, e.a);
+        q.a = pose_dir(P, e.e);
+        q.b = rot(P, e.t0);
+        q.c = rot(P, e.n0);
+        q.h1 = T(e.len);
+        q.h2 = T(e.wn);
+        q.mat = e.mat;
+    } else {
+        const TileD &tl = L.tiles[idx];
+        Pose<T> P = load_pose<T>(poseT + (size_t)tl.body * POSE_W);
+        q.p = pose_point(P, tl.c);
+        q.a = pose_dir(P, tl.n);
+        q.mat = tl.mat;
+    }
+    return q;
+}
+
+// back-tracking over the reflections strictly between vertices a and b (Sec. III-A.2): images of
+// V[a] through the walls in order, then from V[b] back towards V[a] each point by Eq. ref_point
+// between the image through the preceding walls and the point found at the previous step.
+template <class T>
+DRT_HD void backtrack(const Prim<T> *pr, v3<dl<T>> *V, int a, int b) {
+    int m = b - a - 1;
+    if (m <= 0) return;
+    v3<dl<T>> img[MAXI];
+    img[0] = V[a];
+#pragma unroll
+    for (int j = 1; j < MAXI; ++j)
+        if (j < m) img[j] = mirror(img[j - 1], pr[a + j - 1].p, pr[a + j - 1].a);
+    v3<dl<T>> next = V[b];
+#pragma unroll
+    for (int j = MAXI; j >= 1; --j) {
+        if (j > m) continue;
+        const Prim<T> &w = pr[a + j - 1];
+        next = refl_point(img[j - 1], next, w.p, w.a);
+        V[a + j] = next;
+    }
+}
+
+// Keller-cone point on the edge line (A, e) between a virtual source and a virtual receiver:
+// s = s_A + (s_B - s_A) rho_A / (rho_A + rho_B), the 3D form of Eq. diff_point.
+template <class T>
+DRT_HD dl<T> keller_s(v3<dl<T>> Sv, v3<dl<T>> Rv, const Prim<T> &e, uint32_t &fl) {
+    v3<dl<T>> wa = Sv - e.p, wb = Rv - e.p;
+    dl<T> sa = dot(wa, e.a), sb = dot(wb, e.a);
+    v3<dl<T>> pa = wa - e.a * sa, pb = wb - e.a * sb;
+    T ra2 = dot(val(pa), val(pa)), rb2 = dot(val(pb), val(pb));
+    if (!(ra2 > T(1e-24)) || !(rb2 > T(1e-24))) {
+        fl |= F_DEGEN;
+        return sa;
+    }
+    dl<T> ra = norm(pa), rb = norm(pb);
+    return sa + (sb - sa) * ra / (ra + rb);
+}
+
+// Edge parameters of a segment with m >= 2 diffractions: Newton on the unfolded length (the
+// stationary, here minimal, path; reflections between diffraction points unfolded by imaging)
+// with the analytic tridiagonal Hessian, started from the t0 parameters.  The length is convex in
+// the edge parameters, so a step that lengthens the path is halved until it does not (backtracking
+// line search).  Carried on dual numbers, the converged iterate's derivative is the implicit-function
+// derivative, so the diffraction points' sliding velocities come out of the same solve.
+template <class T>
+DRT_HD dl<T> unfolded_length(const Prim<T> *pr, const v3<dl<T>> *V, int a, int b, const int *didx, int m,
+                             const dl<T> *s, dl<T> *g, dl<T> *hd, dl<T> *ho) {
+    dl<T> Ltot = D<T>(T(0), T(0));
+    for (int j = 0; j < m; ++j) g[j] = hd[j] = ho[j] = D<T>(T(0), T(0));
+    for (int j = 0; j <= m; ++j) {
+        int i0 = (j == 0) ? a : didx[j - 1];
+        int i1 = (j == m) ? b : didx[j];
+        v3<dl<T>> X = (j == 0) ? V[a] : pr[i0 - 1].p + pr[i0 - 1].a * s[j - 1];
+        v3<dl<T>> ex = (j == 0) ? V[a] : pr[i0 - 1].a;
+        for (int i = i0 + 1; i < i1; ++i) {
+            X = mirror(X, pr[i - 1].p, pr[i - 1].a);
+            if (j > 0) ex = mirror_dir(ex, pr[i - 1].a);
+        }
+        v3<dl<T>> Y = (j == m) ? V[b] : pr[i1 - 1].p + pr[i1 - 1].a * s[j];
+        v3<dl<T>> r = X - Y;
+        dl<T> l = norm(r);
+        Ltot = Ltot + l;
+        dl<T> il = D<T>(T(1), T(0)) / l;
+        v3<dl<T>> rh = r * il;
+        if (j > 0) {
+            dl<T> q = dot(rh, ex);
+            g[j - 1] = g[j - 1] + q;
+            hd[j - 1] = hd[j - 1] + (D<T>(T(1), T(0)) - q * q) * il;
+        }
+        if (j < m) {
+            dl<T> q = dot(rh, pr[i1 - 1].a);
+            g[j] = g[j] - q;
+            hd[j] = hd[j] + (D<T>(T(1), T(0)) - q * q) * il;
+            if (j > 0) {
+                dl<T> qx = dot(rh, ex);
+                ho[j - 1] = ho[j - 1] + (qx * q - dot(ex, pr[i1 - 1].a)) * il;
+            }
+        }
+    }
+    return Ltot;
+}
+
+template <class T>
+DRT_HD void multi_diffraction(const Prim<T> *pr, v3<dl<T>> *V, int a, int b, const double *s0, uint32_t &fl) {
+    int didx[MAXI], m = 0;
+    dl<T> s[MAXI], step[MAXI];
+    for (int i = a + 1; i < b; ++i)
+        if (pr[i - 1].type == T_D) {
+            didx[m] = i;
+            s[m] = D<T>(T(s0[i - 1]), T(0));
+            step[m] = D<T>(T(0), T(0));
+            ++m;
+        }
+    bool conv = false;
+    int extra = 1, halvings = 0;
+    T Lprev = T(0), smax_prev = T(0);
+    bool have_prev = false;
+    for (int it = 0; it < 64; ++it) {
+        dl<T> g[MAXI], hd[MAXI], ho[MAXI];
+        dl<T> Lc = unfolded_length(pr, V, a, b, didx, m, s, g, hd, ho);
+        if (have_prev && smax_prev > T(1e-7) && !(Lc.v <= Lprev) && halvings < 40) {
+            for (int j = 0; j < m; ++j) {     // backtrack: s_prev + step / 2
+                step[j] = step[j] * T(0.5);
+                s[j] = s[j] - step[j];
+            }
+            smax_prev *= T(0.5);
+            ++halvings;
+            continue;
+        }
+        halvings = 0;
+        Lprev = Lc.v;
+        have_prev = true;
+        for (int j = 0; j < m; ++j)
+            if (!(hd[j].v > T(1e-12))) hd[j].v = T(1e-12);
+        // Thomas algorithm for H step = -g (H symmetric tridiagonal: diag hd, off-diagonal ho)
+        dl<T> cp[MAXI], dp[MAXI];
+        cp[0] = ho[0] / hd[0];
+        dp[0] = -g[0] / hd[0];
+        for (int j = 1; j < m; ++j) {
+            dl<T> den = hd[j] - ho[j - 1] * cp[j - 1];
+            cp[j] = ho[j] / den;
+            dp[j] = (-g[j] - ho[j - 1] * dp[j - 1]) / den;
+        }
+        T smax = T(0);
+        for (int j = m - 1; j >= 0; --j) {
+            if (j < m - 1) dp[j] = dp[j] - cp[j] * dp[j + 1];
+            smax = fmax(smax, fabs(dp[j].v));
+        }
+        if (!(smax == smax)) break;   // NaN
+        for (int j = 0; j < m; ++j) {
+            s[j] = s[j] + dp[j];
+            step[j] = dp[j];
+        }
+        smax_prev = smax;
+        if (conv) {
+            if (--extra < 0) break;
+        } else if (smax < T(1e-10)) {
+            conv = true;   // one more full step refines the derivative part
+        }
+    }
+    if (!conv) fl |= F_NOCONV;
+    for (int j = 0; j < m; ++j) V[didx[j]] = pr[didx[j] - 1].p + pr[didx[j] - 1].a * s[j];
+    int prev = a;
+    for (int i = a + 1; i <= b; ++i)
+        if (i == b || pr[i - 1].type == T_D) {
+            backtrack(pr, V, prev, i);
+            prev = i;
+        }
+}
+
+// geometry of one path-step: vertices V[0..n+1] (TX, interaction points, RX) with velocities
+template <class T>
+DRT_HD void solve_geometry(const Prim<T> *pr, int n, v3<dl<T>> *V, const double *s0,
+                                               uint32_t &fl) {
+    for (int i = 1; i <= n; ++i)
+        if (pr[i - 1].type == T_S) V[i] = pr[i - 1].p;   // Sec. III-C: tile centroid moves rigidly
+    int a = 0;
+    for (int b = 1; b <= n + 1; ++b) {
+        if (b <= n && pr[b - 1].type != T_S) continue;
+        int nd = 0, dpos = -1;
+        for (int i = a + 1; i < b; ++i)
+            if (pr[i - 1].type == T_D) {
+                ++nd;
+                dpos = i;
+            }
+        if (nd == 0) {
+            backtrack(pr, V, a, b);
+        } else if (nd == 1) {
+            v3<dl<T>> src = V[a], rcv = V[b];
+            for (int i = a + 1; i < dpos; ++i) src = mirror(src, pr[i - 1].p, pr[i - 1].a);
+            for (int i = b - 1; i > dpos; --i) rcv = mirror(rcv, pr[i - 1].p, pr[i - 1].a);
+            const Prim<T> &e = pr[dpos - 1];
+            V[dpos] = e.p + e.a * keller_s(src, rcv, e, fl);
+            backtrack(pr, V, a, dpos);
+            backtrack(pr, V, dpos, b);
+        } else {
+            multi_diffraction(pr, V, a, b, s0, fl);
+        }
+        a = b;
+    }
+}
+
+template <class T> DRT_HD T wrap2pi(T x) {
+    x = fmod(x, T(2 * PI));
+    return x < T(0) ? x + T(2 * PI) : x;
+}
+
+// validity (Sec. II: the t0 multipath structure still holds): reflection points inside their
+// faces with both neighbours in front, diffraction points on their edge segments with both
+// neighbours in the wedge exterior, tiles lit from and seen from the front
+template <class T>
+DRT_HD uint32_t validity(const Prim<T> *pr, int n, const v3<T> *P) {
+    uint32_t fl = 0;
+    for (int i = 1; i <= n + 1; ++i) {
+        v3<T> d = P[i] - P[i - 1];
+        if (!(dot(d, d) >= T(1e-18))) fl |= F_DEGEN;
+    }
+    for (int i = 1; i <= n; ++i) {
+        const Prim<T> &q = pr[i - 1];
+        if (q.type == T_R) {
+            v3<T> c = val(q.p), nn = val(q.a);
+            v3<T> r = P[i] - c;
+            T al = dot(r, q.b), be = dot(r, cross(q.b, nn));
+            if (fabs(al) > q.h1 || fabs(be) > q.h2) fl |= F_FACE;
+            if (!(dot(P[i - 1] - c, nn) > T(0)) || !(dot(P[i + 1] - c, nn) > T(0))) fl |= F_SIDE;
+        } else if (q.type == T_D) {
+            v3<T> A = val(q.p), e = val(q.a);
+            T s = dot(P[i] - A, e);
+            if (s < T(0) || s > q.h1) fl |= F_EDGE;
+            for (int side = -1; side <= 1; side += 2) {
+                v3<T> r = P[i + side] - P[i];
+                v3<T> rp = r - e * dot(r, e);
+                T ph = wrap2pi(atan2(dot(rp, q.c), dot(rp, q.b)));
+                if (!(ph > T(0) && ph < q.h2 * T(PI))) fl |= F_SIDE;
+            }
+        } else {
+            v3<T> nn = val(q.a);
+            if (!(dot(P[i - 1] - P[i], nn) > T(0)) || !(dot(P[i + 1] - P[i], nn) > T(0))) fl |= F_SIDE;
+        }
+    }
+    return fl;
+}
+
+// ------------------------------------------------------------------------------------------------
+// field coefficients
+// Fresnel reflection coefficients for the perpendicular (TE) and parallel (TM) components;
+// eps_c = eps_r - j sigma / (2 pi f eps0); a perfect conductor gives -1 and +1.
+template <class T>
+DRT_HD void fresnel(const MatD &m, T fc, T ct, cx<T> &rte, cx<T> &rtm) {
+    if (m.pec != 0.0) {
+        rte = C<T>(T(-1), T(0));
+        rtm = C<T>(T(1), T(0));
+        return;
+    }
+    cx<T> ec = C<T>(T(m.eps_r), -T(m.sigma) / (T(2 * PI) * fc * T(EPS0)));
+    cx<T> sq = csqrt_(C<T>(ec.re - T(1) + ct * ct, ec.im));
+    rte = cdiv(C<T>(ct - sq.re, -sq.im), C<T>(ct + sq.re, sq.im));
+    cx<T> ecct = ec * ct;
+    rtm = cdiv(ecct - sq, ecct + sq);
+}
+
+// UTD transition function F(X) = 2j sqrt(X) exp(jX) int_sqrt(X)^inf exp(-j u^2) du for X >= 0,
+// written as sqrt(pi X) exp(j pi/4) erfcx(exp(j pi/4) sqrt(X)) (erfcx(z) = exp(z^2) erfc(z)) and
+// evaluated by the Maclaurin series of erf (small X), Laplace's continued fraction for erfc
+// (middle range, evaluated bottom-up with a fixed depth) and the asymptotic series
+// F ~ sum_m (2m-1)!! / (-2jX)^m (large X) -- Abramowitz & Stegun 7.1.5, 7.1.14, 7.1.23.
+template <class T> struct TransitionCfg;
+template <> struct TransitionCfg<double> { static constexpr double x_ser = 6.0, x_asy = 100.0; static constexpr int n_cf = 40, n_asy = 12; };
+template <> struct TransitionCfg<float> { static constexpr float x_ser = 3.0f, x_asy = 40.0f; static constexpr int n_cf = 24, n_asy = 8; };
+
+template <class T> DRT_HD cx<T> transition_F(T X) {
+    using Cfg = TransitionCfg<T>;
+    if (!(X > T(0))) return C<T>(T(0), T(0));
+    const T sqpi = T(1.7724538509055160273);
+    const T r2 = T(0.70710678118654752440);
+    if (X >= T(Cfg::x_asy)) {
+        // 1 + sum_{m>=1} prod_{i<=m} (-(2i-1)) / (2jX) ; 1/(2jX) = -j/(2X)
+        cx<T> acc = C<T>(T(1), T(0)), term = C<T>(T(1), T(0));
+        cx<T> inv = C<T>(T(0), T(-0.5) / X);
+        for (int mm = 1; mm <= Cfg::n_asy; ++mm) {
+            term = term * inv * T(-(2 * mm - 1));
+            acc = acc + term;
+        }
+        return acc;
+    }
+    T sx = sqrt(X);
+    cx<T> z = C<T>(r2 * sx, r2 * sx);   // exp(j pi/4) sqrt(X)
+    cx<T> pre = C<T>(sqpi * sx * r2, sqpi * sx * r2);   // sqrt(pi X) exp(j pi/4)
+    if (X < T(Cfg::x_ser)) {
+        // erf(z) = 2/sqrt(pi) z sum_n (-z^2)^n / (n! (2n+1)), z^2 = jX
+        cx<T> term = C<T>(T(1), T(0)), acc = term;
+        cx<T> mz2 = C<T>(T(0), -X);
+        for (int k = 1; k < 64; ++k) {
+            term = term * mz2 * (T(1) / T(k));
+            cx<T> tk = term * (T(1) / T(2 * k + 1));
+            acc = acc + tk;
+            if (cabs2(tk) < T(1e-36) * cabs2(acc)) break;
+        }
+        cx<T> erf = z * acc * (T(2) / sqpi);
+        cx<T> one_m = C<T>(T(1) - erf.re, -erf.im);
+        return pre * cexpj(X) * one_m;
+    }
+    // erfcx(z) = 1 / (sqrt(pi) (z + (1/2)/(z + 1/(z + (3/2)/(z + ...)))))
+    cx<T> f = z;
+    for (int k = Cfg::n_cf; k >= 1; --k) f = z + cdiv(C<T>(T(0.5) * T(k), T(0)), f);
+    return cdiv(pre, f * sqpi);
+}
+
+// one Kouyoumjian-Pathak term cot((pi +- beta)/2n) F(kL a+-(beta)) with eps = (pi +- beta) - 2 pi n N:
+// cot(eps/2n) F(2 kL sin^2(eps/2)), -> n sqrt(2 pi kL) sgn(eps) exp(j pi/4) as eps -> 0
+template <class T> DRT_HD cx<T> utd_term(T eps, T n, T kL) {
+    if (fabs(eps) < T(1e-9)) {
+        T m = n * sqrt(T(2 * PI) * kL) * (eps >= T(0) ? T(1) : T(-1)) * T(0.70710678118654752440);
+        return C<T>(m, m);
+    }
+    T sh = sin(T(0.5) * eps);
+    T ct = T(1) / tan(eps / (T(2) * n));
+    return transition_F(T(2) * kL * sh * sh) * ct;
+}
+
+// soft / hard wedge diffraction coefficients: Kouyoumjian-Pathak with the spherical-wave distance
+// parameter L, Luebbers' face-coefficient weights for lossy wedges
+template <class T>
+DRT_HD void utd(T n, T phi, T phip, T sinb0, T L, T k, const MatD &m, T fc, cx<T> &Ds, cx<T> &Dh) {
+    T kL = k * L;
+    T pref = T(1) / (T(2) * n * sqrt(T(2 * PI) * k) * sinb0);
+    cx<T> Cc = C<T>(-pref * T(0.70710678118654752440), pref * T(0.70710678118654752440));  // -exp(-j pi/4) pref
+    T bm = phi - phip, bp = phi + phip, tpn = T(2 * PI) * n;
+    cx<T> t1 = utd_term(T(PI) + bm - tpn * round((bm + T(PI)) / tpn), n, kL);
+    cx<T> t2 = utd_term(T(PI) - bm + tpn * round((bm - T(PI)) / tpn), n, kL);
+    cx<T> t3 = utd_term(T(PI) - bp + tpn * round((bp - T(PI)) / tpn), n, kL);   // 0-face
+    cx<T> t4 = utd_term(T(PI) + bp - tpn * round((bp + T(PI)) / tpn), n, kL);   // n-face
+    cx<T> r0s, r0h, rns, rnh;
+    fresnel(m, fc, fabs(sin(phip)), r0s, r0h);
+    fresnel(m, fc, fabs(sin(n * T(PI) - phi)), rns, rnh);
+    cx<T> base = t1 + t2;
+    Ds = Cc * (base + r0s * t3 + rns * t4);
+    Dh = Cc * (base + r0h * t3 + rnh * t4);
+}
+
+// Effective-Roughness directive lobe normalisation for integer alpha:
+// F = 2^-alpha sum_j C(alpha, j) I_j with I_j = 2 pi / (j+1) for even j and
+// I_j = 2 pi / (j+1) cos(ti) sum_{w=0}^{(j-1)/2} C(2w, w) sin^{2w}(ti) / 4^w for odd j.
+template <class T> DRT_HD T er_norm(int alpha, T cti) {
+    T s2 = fmax(T(0), T(1) - cti * cti);
+    T acc = T(0), binom = T(1);   // C(alpha, j)
+    T oddsum = T(0), cw = T(1), s2w = T(1);   // running sum_{w} C(2w,w) s2^w / 4^w
+    int wmax = -1;
+    for (int j = 0; j <= alpha; ++j) {
+        T Ij;
+        if ((j & 1) == 0) {
+            Ij = T(2 * PI) / T(j + 1);
+        } else {
+            while (wmax < (j - 1) / 2) {
+                ++wmax;
+                if (wmax > 0) {
+                    cw = cw * T(2 * (2 * wmax - 1)) / T(wmax);   // C(2w,w) from C(2w-2,w-1)
+                    s2w = s2w * s2 * T(0.25);
+                }
+                oddsum += cw * s2w;
+            }
+            Ij = T(2 * PI) / T(j + 1) * cti * oddsum;
+        }
+        acc += binom * Ij;
+        binom = binom * T(alpha - j) / T(j + 1);
+    }
+    return ldexp(acc, -alpha);
+}
+
+template <class T> DRT_HD v3<T> vertical_pol(v3<T> k) {
+    v3<T> p = V3<T>(-k.z * k.x, -k.z * k.y, T(1) - k.z * k.z);
+    if (dot(p, p) < T(1e-18)) p = V3<T>(T(1) - k.x * k.x, -k.x * k.y, -k.x * k.z);
+    return unit(p);
+}
+
+// complex amplitude a_p excluding exp(-j k d): (lambda / 4 pi) x ray spreading (1/length per
+// segment between point sources; UTD sqrt(s'/(s(s'+s))) per diffraction) x polarimetric chain of
+// Fresnel / UTD / ER factors; TX and RX vertically polarised.
+template <class T>
+DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<T> *pr, int n, const v3<T> *P, T fc) {
+    v3<T> kd[MAXI + 2];
+    T len[MAXI + 2];
+    for (int i = 1; i <= n + 1; ++i) {
+        v3<T> d = P[i] - P[i - 1];
+        len[i] = norm(d);
+        kd[i] = d * (T(1) / len[i]);
+    }
+    T spread = T(1), sprime[MAXI + 1], sdist[MAXI + 1];
+    int a = 0;
+    for (int b = 1; b <= n + 1; ++b) {
+        if (b <= n && pr[b - 1].type != T_S) continue;
+        int prev = a;
+        T acc = T(0), sp = T(0);
+        for (int i = a + 1; i <= b; ++i) {
+            acc += len[i];
+            if (i == b || pr[i - 1].type == T_D) {
+                if (prev == a) {
+                    spread /= acc;
+                    sp = acc;
+                } else {
+                    sdist[prev] = acc;
+                    sprime[prev] = sp;
+                    spread *= sqrt(sp / (acc * (sp + acc)));
+                    sp = acc;
+                }
+                prev = i;
+                acc = T(0);
+            }
+        }
+        a = b;
+    }
+    const T k = T(2 * PI) * fc / T(C0);
+    c3<T> E = {C<T>(T(0), T(0)), C<T>(T(0), T(0)), C<T>(T(0), T(0))};
+    {
+        v3<T> e0 = vertical_pol(kd[1]);
+        E = cscale(e0, C<T>(T(1), T(0)));
+    }
+    for (int i = 1; i <= n; ++i) {
+        const Prim<T> &q = pr[i - 1];
+        const MatD m = L.mats[q.mat];
+        v3<T> kin = kd[i], kout = kd[i + 1];
+        if (q.type == T_R) {
+            v3<T> nf = val(q.a);
+            if (dot(nf, kin) > T(0)) nf = -nf;
+            T ct = -dot(nf, kin);
+            v3<T> ep = cross(kin, nf);
+            if (dot(ep, ep) < T(1e-24)) {
+                ep = cross(nf, V3<T>(T(1), T(0), T(0)));
+                if (dot(ep, ep) < T(1e-12)) ep = cross(nf, V3<T>(T(0), T(1), T(0)));
+            }
+            ep = unit(ep);
+            v3<T> epin = cross(ep, kin), epout = cross(ep, kout);
+            cx<T> rte, rtm;
+            fresnel(m, fc, ct, rte, rtm);
+            T rough = sqrt(fmax(T(0), T(1) - T(m.rough) * T(m.rough)));
+            E = cscale(ep, rte * cdot(E, ep) * rough) + cscale(epout, rtm * cdot(E, epin) * rough);
+        } else if (q.type == T_D) {
+            v3<T> e = val(q.a);
+            v3<T> wi = -kin + e * dot(kin, e);
+            v3<T> wo = kout - e * dot(kout, e);
+            T phip = wrap2pi(atan2(dot(wi, q.c), dot(wi, q.b)));
+            T phi = wrap2pi(atan2(dot(wo, q.c), dot(wo, q.b)));
+            T sinb0 = norm(cross(kin, e));
+            T Lp = sdist[i] * sprime[i] * sinb0 * sinb0 / (sdist[i] + sprime[i]);
+            cx<T> Ds, Dh;
+            utd(q.h2, phi, phip, sinb0, Lp, k, m, fc, Ds, Dh);
+            v3<T> php = -unit(cross(e, kin)), bpv = cross(php, kin);
+            v3<T> ph = unit(cross(e, kout)), bv = cross(ph, kout);
+            E = cscale(bv, -(Ds * cdot(E, bpv))) + cscale(ph, -(Dh * cdot(E, php)));
+        } else {
+            const TileD &tl = L.tiles[q.idx];
+            v3<T> nt = val(q.a);
+            if (dot(nt, kin) > T(0)) nt = -nt;
+            T cti = -dot(nt, kin);
+            v3<T> kspec = kin + nt * (T(2) * cti);
+            T cpsi = dot(kspec, kout);
+            int alpha = (int)tl.alpha;
+            T Fa = er_norm<T>(alpha, cti);
+            T lobe = T(1);
+            T hb = T(0.5) * (T(1) + cpsi);
+            for (int j = 0; j < alpha; ++j) lobe *= hb;   // ((1 + cos psi)/2)^alpha
+            T amp = T(tl.s) * sqrt(T(tl.area) * cti / Fa) * sqrt(lobe);
+            cx<T> ph = cexpj(T(tl.phase));
+            T nE = cnorm(E);
+            cx<T> ek = cdot(E, kout);
+            c3<T> Ep = E + cscale(kout, -ek);
+            T nEp = cnorm(Ep);
+            if (nEp < T(1e-12) * nE || nE == T(0)) Ep = cscale(vertical_pol(kout), C<T>(nE, T(0)));
+            else Ep = cscale(Ep, C<T>(nE / nEp, T(0)));
+            E = cscale(Ep, ph * amp);
+        }
+    }
+    T lam = T(C0) / fc;
+    return cdot(E, vertical_pol(kd[n + 1])) * (lam / T(4 * PI) * spread);
+}
+
+// App. A Eq. doppler_freq: f' = f0 prod_i (c - v_i.k_i) / (c - v_{i-1}.k_i), evaluated without
+// cancellation as f_D = f0 expm1( sum_i log1p(-v_i.k_i / c) - log1p(-v_{i-1}.k_i / c) )
+template <class T> DRT_HD T doppler(int n, const v3<dl<T>> *V, T fc) {
+    T acc = T(0);
+    const T ic = T(1) / T(C0);
+    for (int i = 1; i <= n + 1; ++i) {
+        v3<T> k = unit(val(V[i]) - val(V[i - 1]));
+        acc += log1p(-dot(der(V[i]), k) * ic) - log1p(-dot(der(V[i - 1]), k) * ic);
+    }
+    return fc * expm1(acc);
+}
+
+// ------------------------------------------------------------------------------------------------
+// one (path, time-step) of the FP64 form: geometry, validity, delay, Doppler, angles, amplitude;
+// user outputs at [ti][perm[p]], synthesis record at [ti][p]
+DRT_HD void write_outputs_fp64(const OutD &o, size_t oi, int n, const v3<double> *P, double tau, cx<double> a,
+                               double fd, uint32_t fl) {
+    if (o.tau) o.tau[oi] = tau;
+    if (o.amp) {
+        double *q = reinterpret_cast<double *>(o.amp) + 2 * oi;
+        q[0] = a.re;
+        q[1] = a.im;
+    }
+    if (o.doppler) reinterpret_cast<double *>(o.doppler)[oi] = fd;
+    if (o.angles) {
+        v3<double> kd = unit(P[1] - P[0]), ka = unit(P[n] - P[n + 1]);
+        float *q = o.angles + 4 * oi;
+        q[0] = (float)atan2(kd.y, kd.x);
+        q[1] = (float)atan2(kd.z, hypot(kd.x, kd.y));
+        q[2] = (float)atan2(ka.y, ka.x);
+        q[3] = (float)atan2(ka.z, hypot(ka.x, ka.y));
+    }
+    if (o.flags) o.flags[oi] = (uint8_t)fl;
+    if (o.points) {
+        double *q = o.points + oi * (MAXI * 3);
+        const double qn = nan("");
+        for (int j = 0; j < MAXI; ++j) {
+            bool in = j < n;
+            q[3 * j + 0] = in ? P[j + 1].x : qn;
+            q[3 * j + 1] = in ? P[j + 1].y : qn;
+            q[3 * j + 2] = in ? P[j + 1].z : qn;
+        }
+    }
+}
+
+// record for the synthesis: amplitude (0 if the path does not exist), phase seed frac(f_0 tau) and
+// per-bin step frac(df tau) split as hi (12 leading bits, so k * hi is exact in FP32) + lo
+DRT_HD void write_record(const RecD &r, size_t ri, double tau, cx<double> a, uint32_t fl, double f0, double df) {
+    double x = f0 * tau;
+    double phi0 = x - floor(x);
+    double y = df * tau;
+    double st = y - floor(y);
+    double hi = ldexp(rint(ldexp(st, 12)), -12);
+    float4 v;
+    v.x = fl ? 0.f : (float)a.re;
+    v.y = fl ? 0.f : (float)a.im;
+    v.z = (float)phi0;
+    v.w = (float)hi;
+    r.rec_a[ri] = v;
+    r.rec_b[ri] = (float)(st - hi);
+}
+
+DRT_HD void path_step_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const double *pose, int p,
+                           int ti, const OutD &out, const RecD &rec) {
+    typedef double T;
+    const T t = tg.t_start + ti * tg.dt;
+    const double *poseT = pose + (size_t)ti * L.n_bodies * POSE_W;
+    uint32_t code = L.ptypes[p];
+    int4 pi = L.pprims[p];
+    int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
+    int n = 0;
+    Prim<T> pr[MAXI];
+    for (int j = 0; j < MAXI; ++j) {
+        int ty = (code >> (8 * j)) & 0xff;
+        if (ty != T_NONE) {
+            pr[j] = load_prim<T>(L, poseT, ty, prim[j]);
+            n = j + 1;
+        }
+    }
+    v3<dl<T>> V[MAXI + 2];
+    V[0] = terminal<T>(L.tx, t);
+    V[n + 1] = terminal<T>(L.rx, t);
+    uint32_t fl = 0;
+    solve_geometry(pr, n, V, L.ps0 + (size_t)p * MAXI, fl);
+    v3<T> P[MAXI + 2];
+    for (int i = 0; i <= n + 1; ++i) P[i] = val(V[i]);
+    fl |= validity(pr, n, P);
+    T d = T(0);
+    for (int i = 1; i <= n + 1; ++i) d += norm(P[i] - P[i - 1]);
+    T tau = d / T(C0);
+    cx<T> a = (fl & F_DEGEN) ? C<T>(T(0), T(0)) : amplitude(L, pr, n, P, T(fg.fc));
+    if (out.tau || out.amp || out.doppler || out.angles || out.flags || out.points) {
+        T fd = doppler(n, V, T(fg.fc));
+        size_t oi = (size_t)ti * L.n_paths + L.perm[p];
+        write_outputs_fp64(out, oi, n, P, tau, a, fd, fl);
+    }
+    if (rec.rec_a) {
+        double f0 = fg.fc - 0.5 * fg.bandwidth, df = fg.bandwidth / fg.n_bins;
+        write_record(rec, (size_t)ti * L.n_paths + p, tau, a, fl, f0, df);
+    }
+}
+
+}  // namespace drt

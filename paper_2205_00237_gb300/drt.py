@@ -1,0 +1,246 @@
+"""Thin Python binding of the DRT C ABI (include/drt.h) over ctypes.
+
+Argument marshalling only: every step of the hot path runs in libdrt.so's CUDA kernels.  PyTorch
+provides device memory (tensors) and streams.  There is no CPU fallback: if the library has not been
+built (``__graft_entry__.build()`` / ``paper_2205_00237_gb300.build.build()``) or no CUDA device is
+present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import inputs as I
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdrt.so")
+
+DRT_OK, DRT_EINVAL, DRT_ENOMEM, DRT_ECUDA, DRT_EBUSY, DRT_ETIMEOUT, DRT_ENOTFOUND = 0, -1, -2, -3, -4, -5, -6
+FP64, FP32_BULK = 0, 1
+F_FACE, F_EDGE, F_SIDE, F_NOCONV, F_DEGEN = 1, 2, 4, 8, 16
+
+# every symbol include/drt.h declares
+EXPORTS = ["drt_create", "drt_destroy", "drt_last_error", "drt_load_paths", "drt_unload", "drt_extrapolate",
+           "drt_synthesize_H", "drt_synthesize_H_host", "drt_link_info", "drt_probe_peak", "drt_profile_enable",
+           "drt_profile_read"]
+
+
+class DrtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"drt error {code}: {msg}")
+        self.code = code
+
+
+class _Term(C.Structure):
+    _fields_ = [("r", C.c_double * 3), ("v", C.c_double * 3), ("a", C.c_double * 3)]
+
+
+class _Scene(C.Structure):
+    _fields_ = [("tx", _Term), ("rx", _Term), ("n_bodies", C.c_int32), ("n_materials", C.c_int32),
+                ("n_faces", C.c_int32), ("n_edges", C.c_int32), ("n_tiles", C.c_int32),
+                ("reserved", C.c_int32), ("bodies", C.c_void_p), ("materials", C.c_void_p),
+                ("faces", C.c_void_p), ("edges", C.c_void_p), ("tiles", C.c_void_p)]
+
+
+class _PathSet(C.Structure):
+    _fields_ = [("n_paths", C.c_int32), ("reserved", C.c_int32), ("n_int", C.c_void_p),
+                ("types", C.c_void_p), ("prims", C.c_void_p), ("s0", C.c_void_p)]
+
+
+class _TimeGrid(C.Structure):
+    _fields_ = [("t_start", C.c_double), ("dt", C.c_double), ("n_steps", C.c_int32), ("reserved", C.c_int32)]
+
+
+class _FreqGrid(C.Structure):
+    _fields_ = [("fc", C.c_double), ("bandwidth", C.c_double), ("n_bins", C.c_int32), ("reserved", C.c_int32)]
+
+
+class _Outputs(C.Structure):
+    _fields_ = [("tau", C.c_void_p), ("amp", C.c_void_p), ("doppler", C.c_void_p), ("angles", C.c_void_p),
+                ("flags", C.c_void_p), ("points", C.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libdrt.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build()")
+        L = C.CDLL(path)
+        vp, st = C.c_void_p, C.c_int32
+        L.drt_create.argtypes = [C.POINTER(vp), C.c_int32, C.c_uint64]
+        L.drt_create.restype = st
+        L.drt_destroy.argtypes = [vp]
+        L.drt_destroy.restype = None
+        L.drt_last_error.argtypes = []
+        L.drt_last_error.restype = C.c_char_p
+        L.drt_load_paths.argtypes = [vp, vp, vp, C.POINTER(C.c_uint64)]
+        L.drt_load_paths.restype = st
+        L.drt_unload.argtypes = [vp, C.c_uint64]
+        L.drt_unload.restype = st
+        L.drt_extrapolate.argtypes = [vp, C.c_uint64, vp, vp, vp, C.c_int32, vp]
+        L.drt_extrapolate.restype = st
+        L.drt_synthesize_H.argtypes = [vp, C.c_uint64, vp, vp, vp, C.c_int32, vp]
+        L.drt_synthesize_H.restype = st
+        L.drt_synthesize_H_host.argtypes = [vp, C.c_uint64, vp, vp, vp, C.c_int32, vp]
+        L.drt_synthesize_H_host.restype = st
+        L.drt_link_info.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int32)]
+        L.drt_link_info.restype = st
+        L.drt_probe_peak.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_double)]
+        L.drt_probe_peak.restype = st
+        L.drt_profile_enable.argtypes = [vp, C.c_int32]
+        L.drt_profile_enable.restype = st
+        L.drt_profile_read.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
+        L.drt_profile_read.restype = st
+        _lib = L
+        return L
+
+
+def _check(rc):
+    if rc != DRT_OK:
+        raise DrtError(rc, load_library().drt_last_error().decode())
+
+
+def _tg(tg: I.TimeGrid):
+    return _TimeGrid(float(tg.t_start), float(tg.dt), int(tg.n_steps), 0)
+
+
+def _fg(fg: I.FreqGrid):
+    return _FreqGrid(float(fg.fc), float(fg.bandwidth), int(fg.n_bins), 0)
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Context:
+    """A device context: owns loaded links, scratch and the HBM budget (drt_create)."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0):
+        L = load_library()
+        h = C.c_void_p()
+        _check(L.drt_create(C.byref(h), int(device), int(hbm_budget)))
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if self._h:
+            load_library().drt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def load(self, scene: I.Scene, paths: I.PathSet) -> "Link":
+        """drt_load_paths: validate, pack and copy one link's scene and chains to the device."""
+        arrays = [np.ascontiguousarray(x) for x in
+                  (scene.bodies, scene.materials, scene.faces, scene.edges, scene.tiles)]
+        s = _Scene()
+        for dst, src in ((s.tx, scene.tx), (s.rx, scene.rx)):
+            for f in ("r", "v", "a"):
+                getattr(dst, f)[:] = [float(x) for x in src[f]]
+        s.n_bodies, s.n_materials, s.n_faces, s.n_edges, s.n_tiles = (len(a) for a in arrays)
+        s.bodies, s.materials, s.faces, s.edges, s.tiles = (a.ctypes.data if len(a) else None for a in arrays)
+        n_int = np.ascontiguousarray(paths.n_int, np.uint8)
+        types = np.ascontiguousarray(paths.types, np.uint8)
+        prims = np.ascontiguousarray(paths.prims, np.int32)
+        s0 = np.ascontiguousarray(paths.s0, np.float64)
+        ps = _PathSet(int(paths.n_paths), 0, n_int.ctypes.data, types.ctypes.data, prims.ctypes.data,
+                      s0.ctypes.data)
+        out = C.c_uint64()
+        _check(load_library().drt_load_paths(self._h, C.byref(s), C.byref(ps), C.byref(out)))
+        return Link(self, out.value, int(paths.n_paths))
+
+    def profile(self, on: bool = True):
+        """drt_profile_enable: bracket every kernel launch with CUDA events."""
+        _check(load_library().drt_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        """drt_profile_read: {kind: (launches, total ms)} for pose / extrapolate / synth since last read."""
+        counts = (C.c_int64 * 4)()
+        ms = (C.c_double * 4)()
+        _check(load_library().drt_profile_read(self._h, counts, ms))
+        names = ("pose", "extrapolate", "synth", "other")
+        return {names[k]: (int(counts[k]), float(ms[k])) for k in range(4)}
+
+    def probe_peak(self, kind: int, blocks: int = 152 * 16) -> float:
+        f = C.c_double()
+        _check(load_library().drt_probe_peak(self._h, int(kind), int(blocks), C.byref(f)))
+        return f.value
+
+
+class Link:
+    """One loaded link (scene + chains resident on the device)."""
+
+    def __init__(self, ctx: Context, handle: int, n_paths: int):
+        self.ctx, self.handle, self.n_paths = ctx, handle, n_paths
+
+    def unload(self):
+        if self.handle:
+            _check(load_library().drt_unload(self.ctx._h, self.handle))
+            self.handle = 0
+
+    def extrapolate(self, tg: I.TimeGrid, fg: I.FreqGrid, precision: int = FP64, points: bool = False,
+                    out: dict | None = None, stream=None) -> dict:
+        """drt_extrapolate into torch CUDA tensors ([T][P] in the caller's path order)."""
+        import torch
+        T, P = int(tg.n_steps), self.n_paths
+        dev = torch.device("cuda", self.ctx.device)
+        if out is None:
+            ft = torch.float64 if precision == FP64 else torch.float32
+            out = dict(tau=torch.empty((T, P), dtype=torch.float64, device=dev),
+                       amp=torch.empty((T, P, 2), dtype=ft, device=dev),
+                       doppler=torch.empty((T, P), dtype=ft, device=dev),
+                       angles=torch.empty((T, P, 4), dtype=torch.float32, device=dev),
+                       flags=torch.empty((T, P), dtype=torch.uint8, device=dev),
+                       points=torch.empty((T, P, 4, 3), dtype=torch.float64, device=dev) if points else None)
+        o = _Outputs(*(_dptr(out.get(k)) for k in ("tau", "amp", "doppler", "angles", "flags", "points")))
+        tgs, fgs = _tg(tg), _fg(fg)
+        _check(load_library().drt_extrapolate(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs), C.byref(o),
+                                               int(precision), _stream_ptr(stream)))
+        return out
+
+    def synthesize_H(self, tg: I.TimeGrid, fg: I.FreqGrid, precision: int = FP64, H=None, stream=None):
+        """drt_synthesize_H into a complex64 CUDA tensor [T][F]."""
+        import torch
+        if H is None:
+            H = torch.empty((int(tg.n_steps), int(fg.n_bins)), dtype=torch.complex64,
+                            device=torch.device("cuda", self.ctx.device))
+        tgs, fgs = _tg(tg), _fg(fg)
+        _check(load_library().drt_synthesize_H(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs), _dptr(H),
+                                               int(precision), _stream_ptr(stream)))
+        return H
+
+    def synthesize_H_host(self, tg: I.TimeGrid, fg: I.FreqGrid, precision: int = FP64, H=None, stream=None):
+        """drt_synthesize_H_host into a (pinned) host complex64 tensor [T][F]; synchronous."""
+        import torch
+        if H is None:
+            H = torch.empty((int(tg.n_steps), int(fg.n_bins)), dtype=torch.complex64, pin_memory=True)
+        tgs, fgs = _tg(tg), _fg(fg)
+        _check(load_library().drt_synthesize_H_host(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs),
+                                                    _dptr(H), int(precision), _stream_ptr(stream)))
+        return H
