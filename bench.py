@@ -43,9 +43,9 @@ PATHSET = os.path.join(ROOT, "tests", "golden", "pathset_canyon_seed0.npz")
 # path-step (DADD + DMUL + 2 DFMA thread-instructions per ncu on this workload, see
 # profiles/k_extrapolate_fp64_canyon.md) and the FP64 peak of the GB300 (1.25 TFLOP/s nominal,
 # 152 SMs, no FP64 tensor path used).  DRAM bytes per launch from the same capture (None until taken).
-FP64_FLOP_PER_PATH_STEP = None
+FP64_FLOP_PER_PATH_STEP = 2450.0
 FP64_PEAK_FLOPS = 1.25e12
-K1_DRAM_BYTES_PER_LAUNCH = None
+K1_DRAM_BYTES_PER_LAUNCH = 55.81e6
 
 
 def parse():

@@ -1,7 +1,7 @@
 // drt_kernels.cu -- kernels of the DRT hot path on sm_103a:
 //   k_pose           a2: per (time-step, body) pose table R(t), O(t), v_O(t), omega(t) (FP64)
-//   k_extrapolate    a3-a8: one thread per (path, time-step); a warp covers 32 consecutive paths
-//                    (sorted by chain signature, so warps rarely diverge) at one time step
+//   k_extrapolate    a3-a8: one thread per (path, time-step); a warp covers 32 consecutive time
+//                    steps of one path, so all its lanes run the same chain signature
 //   k_synth          a9: H(t, f) = sum_p a_p exp(-j 2 pi f tau_p); one thread per (time-step,
 //                    16-bin frequency tile), sincos seed per tile and a complex rotation
 //                    recurrence inside it, FP32 FMA accumulation
@@ -18,7 +18,7 @@ __global__ void k_pose(const BodyD *__restrict__ bodies, int n_bodies, double t_
                        double *__restrict__ pose) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_steps * n_bodies) return;
-    int ti = i / n_bodies, b = i - ti * n_bodies;
+    int b = i / n_steps, ti = i - b * n_steps;   // layout [body][time-step]
     body_pose_row(bodies[b], t_start + ti * dt, pose + (size_t)i * POSE_W);
 }
 
@@ -30,14 +30,16 @@ cudaError_t launch_pose(const LinkDev &L, const TimeGridD &tg, double *pose, cud
 }
 
 // ------------------------------------------------------------------------------------------------
-// a3-a8 in FP64
-constexpr int EXT_TY = 4;   // time steps per block (one warp each)
+// a3-a8 in FP64.  A block covers 128 consecutive time steps of ONE path, so every lane of a warp
+// runs the same chain signature (no type divergence); branches that remain (validity, Newton
+// iteration counts, transition-function ranges) are correlated between neighbouring instants.
+constexpr int EXT_T = 128;
 
-__global__ void __launch_bounds__(32 * EXT_TY)
+__global__ void __launch_bounds__(EXT_T)
 k_extrapolate_fp64(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const double *__restrict__ pose,
                    const OutD out, const RecD rec) {
-    int p = blockIdx.x * 32 + threadIdx.x;
-    int ti = blockIdx.y * EXT_TY + threadIdx.y;
+    int p = blockIdx.x;
+    int ti = blockIdx.y * EXT_T + threadIdx.x;
     if (p >= L.n_paths || ti >= tg.n_steps) return;
     path_step_fp64(L, tg, fg, pose, p, ti, out, rec);
 }
@@ -45,8 +47,8 @@ k_extrapolate_fp64(const LinkDev L, const TimeGridD tg, const FreqGridD fg, cons
 cudaError_t launch_extrapolate_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg,
                                     const double *pose, const OutD &out, const RecD &rec, cudaStream_t s) {
     if (L.n_paths == 0 || tg.n_steps == 0) return cudaSuccess;
-    dim3 block(32, EXT_TY), grid((L.n_paths + 31) / 32, (tg.n_steps + EXT_TY - 1) / EXT_TY);
-    k_extrapolate_fp64<<<grid, block, 0, s>>>(L, tg, fg, pose, out, rec);
+    dim3 grid(L.n_paths, (tg.n_steps + EXT_T - 1) / EXT_T);
+    k_extrapolate_fp64<<<grid, EXT_T, 0, s>>>(L, tg, fg, pose, out, rec);
     return cudaGetLastError();
 }
 

@@ -98,14 +98,20 @@ template <class T> struct Prim {
     int idx;
 };
 
+// pose table layout [body][time-step][POSE_W]: the 32 lanes of a warp (consecutive time steps of
+// one path) read one contiguous 4.6 KB stretch per body
+DRT_HD const double *pose_at(const double *pose, int n_steps, int body, int ti) {
+    return pose + ((size_t)body * n_steps + ti) * POSE_W;
+}
+
 template <class T>
-DRT_HD Prim<T> load_prim(const LinkDev &L, const double *poseT, int type, int idx) {
+DRT_HD Prim<T> load_prim(const LinkDev &L, const double *pose, int n_steps, int ti, int type, int idx) {
     Prim<T> q;
     q.type = type;
     q.idx = idx;
     if (type == T_R) {
         const FaceD &f = L.faces[idx];
-        Pose<T> P = load_pose<T>(poseT + (size_t)f.body * POSE_W);
+        Pose<T> P = load_pose<T>(pose_at(pose, n_steps, f.body, ti));
         q.p = pose_point(P, f.c);
         q.a = pose_dir(P, f.n);
         q.b = rot(P, f.u);
@@ -114,7 +120,7 @@ DRT_HD Prim<T> load_prim(const LinkDev &L, const double *poseT, int type, int id
         q.mat = f.mat;
     } else if (type == T_D) {
         const EdgeD &e = L.edges[idx];
-        Pose<T> P = load_pose<T>(poseT + (size_t)e.body * POSE_W);
+        Pose<T> P = load_pose<T>(pose_at(pose, n_steps, e.body, ti));
         q.p = pose_point(P, e.a);
         q.a = pose_dir(P, e.e);
         q.b = rot(P, e.t0);
@@ -124,7 +130,7 @@ DRT_HD Prim<T> load_prim(const LinkDev &L, const double *poseT, int type, int id
         q.mat = e.mat;
     } else {
         const TileD &tl = L.tiles[idx];
-        Pose<T> P = load_pose<T>(poseT + (size_t)tl.body * POSE_W);
+        Pose<T> P = load_pose<T>(pose_at(pose, n_steps, tl.body, ti));
         q.p = pose_point(P, tl.c);
         q.a = pose_dir(P, tl.n);
         q.mat = tl.mat;
@@ -654,7 +660,6 @@ DRT_HD void path_step_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGrid
                            int ti, const OutD &out, const RecD &rec) {
     typedef double T;
     const T t = tg.t_start + ti * tg.dt;
-    const double *poseT = pose + (size_t)ti * L.n_bodies * POSE_W;
     uint32_t code = L.ptypes[p];
     int4 pi = L.pprims[p];
     int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
@@ -663,7 +668,7 @@ DRT_HD void path_step_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGrid
     for (int j = 0; j < MAXI; ++j) {
         int ty = (code >> (8 * j)) & 0xff;
         if (ty != T_NONE) {
-            pr[j] = load_prim<T>(L, poseT, ty, prim[j]);
+            pr[j] = load_prim<T>(L, pose, tg.n_steps, ti, ty, prim[j]);
             n = j + 1;
         }
     }
