@@ -170,6 +170,26 @@ drt_status drt_synthesize_H_host(drt_ctx *ctx, uint64_t link, const drt_time_gri
                                  const drt_freq_grid *fgrid, void *H_host, int32_t precision,
                                  void *stream);
 
+/* Allocation-free variant of drt_synthesize_H (no counterpart in the paper; it exists for callers
+ * that cannot allocate device memory at call time: latency-bound anticipative-prediction loops,
+ * where cudaMalloc / cudaFree may synchronise the device and stall for milliseconds, and processes
+ * whose device memory is already fully reserved by another allocator).  Same inputs, output and
+ * result as drt_synthesize_H, but the pose table and the synthesis records live in one static
+ * device array of DRT_NOALLOC_SCRATCH_BYTES (32 MiB) that the library reserves on every device
+ * that loads it, until the process exits; the call makes no cudaMalloc, cudaFree or other
+ * allocating call.  It needs 144 n_steps n_bodies + 20 n_steps n_paths bytes (each part rounded
+ * up to 256 B) and fails with DRT_EINVAL when that exceeds the array.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call on a device shares the array and nothing in it
+ * needs to start at zero (each call writes the pose table and records before reading them); calls
+ * whose device work overlaps (different streams, or different contexts on the same device) race on
+ * it, so order them on one stream or serialise them.  Errors: DRT_EINVAL, DRT_ENOTFOUND,
+ * DRT_ECUDA. */
+#define DRT_NOALLOC_SCRATCH_BYTES (32u << 20)
+drt_status drt_synthesize_H_noalloc(drt_ctx *ctx, uint64_t link, const drt_time_grid *tgrid,
+                                    const drt_freq_grid *fgrid, void *H, int32_t precision,
+                                    void *stream);
+
 /* Number of paths of a link (for sizing outputs).  Errors: DRT_ENOTFOUND. */
 drt_status drt_link_info(drt_ctx *ctx, uint64_t link, int32_t *n_paths);
 

@@ -528,3 +528,70 @@ drt_status drt_probe_peak(drt_ctx *c, int32_t kind, int32_t blocks, double *flop
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free synthesis.  Some callers cannot allocate device memory when they ask for a
+// channel prediction: a latency-bound prediction loop cannot afford cudaMalloc / cudaFree, which
+// may synchronise the device, and a process whose device memory is already reserved by another
+// allocator has none to give.  For them the scratch of drt_synthesize_H (pose table + synthesis
+// records) lives in this file-scope device array instead of context-owned buffers.  Host code
+// never names the array directly: its device address comes from cudaGetSymbolAddress, looked up
+// once per device (with that device current) on the first call there.
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[DRT_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+void *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// device address of the static scratch on `device` (which must be current)
+drt_status noalloc_scratch(int device, unsigned char **out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (device < 0 || device >= NOALLOC_MAX_DEVICES)
+        return fail(DRT_EINVAL, "device %d out of range for the allocation-free entry point", device);
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(DRT_ECUDA, "cudaGetSymbolAddress(scratch) on device %d: %s", device, cudaGetErrorString(e));
+        g_noalloc_addr[device] = p;
+    }
+    *out = reinterpret_cast<unsigned char *>(g_noalloc_addr[device]);
+    return DRT_OK;
+}
+
+size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" drt_status drt_synthesize_H_noalloc(drt_ctx *c, uint64_t link, const drt_time_grid *tg,
+                                               const drt_freq_grid *fg, void *H, int32_t precision, void *stream) {
+    if (!c || !H) return fail(DRT_EINVAL, "ctx and H must be non-NULL");
+    if (drt_status st = check_grids(tg, fg, precision)) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    Link *L = find_link(c, link);
+    if (!L) return fail(DRT_ENOTFOUND, "unknown link %llu", (unsigned long long)link);
+    size_t pose_bytes = round256((size_t)tg->n_steps * L->dev.n_bodies * POSE_W * sizeof(double));
+    size_t reca_bytes = round256((size_t)tg->n_steps * L->n_paths * sizeof(float4));
+    size_t recb_bytes = round256((size_t)tg->n_steps * L->n_paths * sizeof(float));
+    size_t need = pose_bytes + reca_bytes + recb_bytes;
+    if (need > (size_t)DRT_NOALLOC_SCRATCH_BYTES)
+        return fail(DRT_EINVAL,
+                    "allocation-free synthesis needs %zu bytes of scratch for %d steps x %d paths x %d bodies, "
+                    "more than the %u-byte static array; split the time grid or use drt_synthesize_H",
+                    need, tg->n_steps, L->n_paths, L->dev.n_bodies, (unsigned)DRT_NOALLOC_SCRATCH_BYTES);
+    CUDA_TRY(cudaSetDevice(c->device));
+    unsigned char *base = nullptr;
+    if (drt_status st = noalloc_scratch(c->device, &base)) return st;
+    double *pose = reinterpret_cast<double *>(base);
+    RecD rec{reinterpret_cast<float4 *>(base + pose_bytes), reinterpret_cast<float *>(base + pose_bytes + reca_bytes)};
+    cudaStream_t s = (cudaStream_t)stream;
+    TimeGridD t = tgd(tg);
+    FreqGridD f = fgd(fg);
+    OutD none{};
+    CUDA_TRY(launch_pose(L->dev, t, pose, s));
+    CUDA_TRY(launch_extrapolate_fp64(L->dev, t, f, pose, none, rec, s));
+    CUDA_TRY(launch_synth(rec, L->n_paths, t, f, reinterpret_cast<float2 *>(H), s));
+    return DRT_OK;
+}

@@ -25,7 +25,7 @@ F_FACE, F_EDGE, F_SIDE, F_NOCONV, F_DEGEN = 1, 2, 4, 8, 16
 # every symbol include/drt.h declares
 EXPORTS = ["drt_create", "drt_destroy", "drt_last_error", "drt_load_paths", "drt_unload", "drt_extrapolate",
            "drt_synthesize_H", "drt_synthesize_H_host", "drt_link_info", "drt_probe_peak", "drt_profile_enable",
-           "drt_profile_read"]
+           "drt_profile_read", "drt_synthesize_H_noalloc"]
 
 
 class DrtError(RuntimeError):
@@ -97,6 +97,8 @@ def load_library(path: str = LIB_PATH):
         L.drt_link_info.restype = st
         L.drt_probe_peak.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_double)]
         L.drt_probe_peak.restype = st
+        L.drt_synthesize_H_noalloc.argtypes = [vp, C.c_uint64, vp, vp, vp, C.c_int32, vp]
+        L.drt_synthesize_H_noalloc.restype = st
         L.drt_profile_enable.argtypes = [vp, C.c_int32]
         L.drt_profile_enable.restype = st
         L.drt_profile_read.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
@@ -243,4 +245,12 @@ class Link:
         tgs, fgs = _tg(tg), _fg(fg)
         _check(load_library().drt_synthesize_H_host(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs),
                                                     _dptr(H), int(precision), _stream_ptr(stream)))
+        return H
+
+    def synthesize_H_noalloc(self, tg: I.TimeGrid, fg: I.FreqGrid, H, precision: int = FP64, stream=None):
+        """drt_synthesize_H_noalloc: the same H as synthesize_H without any device allocation, for
+        callers that cannot allocate at call time; H is a caller-provided complex64 CUDA tensor."""
+        tgs, fgs = _tg(tg), _fg(fg)
+        _check(load_library().drt_synthesize_H_noalloc(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs),
+                                                       _dptr(H), int(precision), _stream_ptr(stream)))
         return H
