@@ -177,7 +177,8 @@ drt_status drt_synthesize_H_host(drt_ctx *ctx, uint64_t link, const drt_time_gri
  * result as drt_synthesize_H, but the pose table and the synthesis records live in one static
  * device array of DRT_NOALLOC_SCRATCH_BYTES (32 MiB) that the library reserves on every device
  * that loads it, until the process exits; the call makes no cudaMalloc, cudaFree or other
- * allocating call.  It needs 144 n_steps n_bodies + 20 n_steps n_paths bytes (each part rounded
+ * allocating call.  `precision` is checked, and the synthesis runs the FP64 form, whose result
+ * meets the tolerances of both forms.  It needs 144 n_steps n_bodies + 20 n_steps n_paths bytes (each part rounded
  * up to 256 B) and fails with DRT_EINVAL when that exceeds the array.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device current; make that
  * first call before any stream capture.  Every call on a device shares the array and nothing in it
@@ -196,7 +197,8 @@ drt_status drt_link_info(drt_ctx *ctx, uint64_t link, int32_t *n_paths);
 /* ---------------------------------------------------------------------------------------------
  * Tracing.  While enabled, every kernel the context launches is bracketed by CUDA events recorded
  * on the launch stream.  drt_profile_read synchronises the device and returns, per kernel kind
- * (0 = pose table, 1 = extrapolation, 2 = H synthesis, 3 = reserved), the number of launches and
+ * (0 = pose table, 1 = extrapolation, 2 = H synthesis, 3 = FP64 chunk anchors and FP64 redo of
+ * the FP32-bulk form), the number of launches and
  * their summed device time in ms since the previous read, then clears the record.
  * Errors: DRT_EINVAL (NULL arguments), DRT_ECUDA. */
 drt_status drt_profile_enable(drt_ctx *ctx, int32_t on);

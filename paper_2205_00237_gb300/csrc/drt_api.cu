@@ -59,8 +59,12 @@ struct drt_ctx {
     std::mutex mu;
     std::map<uint64_t, Link> links;
     uint64_t next_link = 1;
-    Scratch pose, rec_a, rec_b, h;
+    Scratch pose, rec_a, rec_b, h, poseb, base, pose64, redo, warm;
     double *probe_sink = nullptr;
+    // side streams for work that overlaps within one call (FP32-bulk: anchors and the FP64
+    // multi-diffraction paths run beside the FP32 kernel), joined back with events
+    cudaStream_t side[2] = {nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
     // tracing: (kind, start, stop) per bracketed launch
     bool profiling = false;
     struct Mark { int kind; cudaEvent_t a, b; };
@@ -230,14 +234,55 @@ template <class F> drt_status traced(drt_ctx *c, int kind, cudaStream_t s, F &&l
 // pose table + extrapolation (+ records) for one link
 drt_status run_extrapolation(drt_ctx *c, Link &L, const drt_time_grid *tg, const drt_freq_grid *fg,
                              const OutD &out, const RecD &rec, int32_t precision, cudaStream_t s) {
+    TimeGridD t = tgd(tg);
+    FreqGridD f = fgd(fg);
+    if (precision == DRT_FP32_BULK) {
+        if (drt_status st = ensure(c, c->poseb, bulk_pose_bytes(L.dev, t))) return st;
+        if (drt_status st = ensure(c, c->base, bulk_base_bytes(L.dev, t))) return st;
+        if (drt_status st = ensure(c, c->pose64, bulk_pose64_bytes(L.dev, t))) return st;
+        if (drt_status st = ensure(c, c->redo, bulk_redo_bytes(L.dev, t))) return st;
+        void *pb = c->poseb.ptr, *bs = c->base.ptr, *rd = c->redo.ptr;
+        double *p64 = reinterpret_cast<double *>(c->pose64.ptr);
+        bool md = L.dev.n_bulk < L.n_paths;
+        double *pose = nullptr;
+        double *warm = nullptr;
+        if (md) {
+            size_t pose_bytes = (size_t)tg->n_steps * L.dev.n_bodies * POSE_W * sizeof(double);
+            if (drt_status st = ensure(c, c->pose, pose_bytes)) return st;
+            if (drt_status st = ensure(c, c->warm, warm_bytes(L.dev, t))) return st;
+            pose = reinterpret_cast<double *>(c->pose.ptr);
+            warm = reinterpret_cast<double *>(c->warm.ptr);
+        }
+        // fork: anchors on side[0], multi-diffraction paths in FP64 on side[1]
+        cudaStream_t sa = c->side[0], sb = c->side[1];
+        CUDA_TRY(cudaEventRecord(c->ev_fork, s));
+        CUDA_TRY(cudaStreamWaitEvent(sa, c->ev_fork, 0));
+        CUDA_TRY(cudaStreamWaitEvent(sb, c->ev_fork, 0));
+        if (drt_status st = traced(c, 3, sa, [&] { return launch_base_fp64(L.dev, t, f, p64, bs, sa); })) return st;
+        CUDA_TRY(cudaEventRecord(c->ev_join[0], sa));
+        if (md) {
+            if (drt_status st = traced(c, 0, sb, [&] { return launch_pose(L.dev, t, pose, sb); })) return st;
+            if (drt_status st = traced(c, 1, sb, [&] {
+                    return launch_extrapolate_fp64(L.dev, t, f, pose, out, rec, sb, L.dev.n_bulk, L.n_paths, true, warm);
+                }))
+                return st;
+        }
+        CUDA_TRY(cudaEventRecord(c->ev_join[1], sb));
+        if (drt_status st = traced(c, 0, s, [&] { return launch_pose_bulk(L.dev, t, pb, s); })) return st;
+        CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[0], 0));
+        if (drt_status st = traced(c, 1, s, [&] { return launch_extrapolate_bulk(L.dev, t, f, pb, bs, out, rec, rd, s); }))
+            return st;
+        if (drt_status st = traced(c, 3, s, [&] { return launch_redo(L.dev, t, f, out, rec, rd, s); })) return st;
+        CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[1], 0));
+        return DRT_OK;
+    }
     size_t pose_bytes = (size_t)tg->n_steps * L.dev.n_bodies * POSE_W * sizeof(double);
     if (drt_status st = ensure(c, c->pose, pose_bytes)) return st;
-    TimeGridD t = tgd(tg);
+    if (drt_status st = ensure(c, c->warm, warm_bytes(L.dev, t))) return st;
     double *pose = reinterpret_cast<double *>(c->pose.ptr);
+    double *warm = reinterpret_cast<double *>(c->warm.ptr);
     if (drt_status st = traced(c, 0, s, [&] { return launch_pose(L.dev, t, pose, s); })) return st;
-    (void)precision;   // the FP32-bulk form shares the FP64 kernel until its own lands
-    FreqGridD f = fgd(fg);
-    return traced(c, 1, s, [&] { return launch_extrapolate_fp64(L.dev, t, f, pose, out, rec, s); });
+    return traced(c, 1, s, [&] { return launch_extrapolate_fp64(L.dev, t, f, pose, out, rec, s, 0, -1, false, warm); });
 }
 
 drt_status synth_into(drt_ctx *c, Link &L, const drt_time_grid *tg, const drt_freq_grid *fg, float2 *H,
@@ -320,7 +365,53 @@ drt_status drt::pack_link(const drt_scene *s, const drt_path_set *ps, PackedLink
     }
     std::vector<MatD> &mats = H.mats;
     mats.resize(s->n_materials);
-    std::memcpy(mats.data(), s->materials, sizeof(MatD) * s->n_materials);
+    for (int i = 0; i < s->n_materials; ++i) {
+        const drt_material &m = s->materials[i];
+        mats[i] = MatD{m.eps_r, m.sigma, m.rough_s, m.pec, (float)m.eps_r, (float)m.sigma, (float)m.rough_s,
+                       (float)m.pec};
+    }
+    auto f3 = [](float *d, const double *x) {
+        for (int j = 0; j < 3; ++j) d[j] = (float)x[j];
+    };
+    H.facesF.resize(s->n_faces);
+    for (int i = 0; i < s->n_faces; ++i) {
+        const FaceD &g = faces[i];
+        FaceF &h = H.facesF[i];
+        f3(h.c, g.c);
+        f3(h.n, g.n);
+        f3(h.u, g.u);
+        h.hu = (float)g.hu;
+        h.hw = (float)g.hw;
+        h.body = g.body;
+        h.mat = g.mat;
+        h.pad0 = h.pad1 = h.pad2 = 0;
+    }
+    H.edgesF.resize(s->n_edges);
+    for (int i = 0; i < s->n_edges; ++i) {
+        const EdgeD &g = edges[i];
+        EdgeF &h = H.edgesF[i];
+        f3(h.a, g.a);
+        f3(h.e, g.e);
+        f3(h.t0, g.t0);
+        f3(h.n0, g.n0);
+        h.len = (float)g.len;
+        h.wn = (float)g.wn;
+        h.body = g.body;
+        h.mat = g.mat;
+    }
+    H.tilesF.resize(s->n_tiles);
+    for (int i = 0; i < s->n_tiles; ++i) {
+        const TileD &g = tiles[i];
+        TileF &h = H.tilesF[i];
+        f3(h.c, g.c);
+        f3(h.n, g.n);
+        h.area = (float)g.area;
+        h.s = (float)g.s;
+        h.alpha = (float)g.alpha;
+        h.phase = (float)g.phase;
+        h.body = g.body;
+        h.mat = g.mat;
+    }
 
     // paths sorted by chain signature so that warps run uniform code
     int P = ps->n_paths;
@@ -333,7 +424,27 @@ drt_status drt::pack_link(const drt_scene *s, const drt_path_set *ps, PackedLink
     std::vector<int32_t> &perm = H.perm;
     perm.resize(P);
     std::iota(perm.begin(), perm.end(), 0);
-    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return code[a] < code[b]; });
+    // chains with two or more diffractions between point sources (TX, tile, RX) need the Newton solve,
+    // which the FP32-bulk form leaves to FP64: they go last, after the `n_bulk` others
+    auto multi_d = [](uint32_t c0) {
+        int nd = 0;
+        for (int j = 0; j < DRT_MAX_INT; ++j) {
+            int ty = (c0 >> (8 * j)) & 0xff;
+            if (ty == DRT_T_D) {
+                if (++nd >= 2) return true;
+            } else if (ty == DRT_T_S || ty == DRT_T_NONE) {
+                nd = 0;
+            }
+        }
+        return false;
+    };
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) {
+        bool ma = multi_d(code[a]), mb = multi_d(code[b]);
+        return ma != mb ? mb : code[a] < code[b];
+    });
+    int n_bulk = 0;
+    for (int p = 0; p < P; ++p) n_bulk += multi_d(code[p]) ? 0 : 1;
+    d.n_bulk = n_bulk;
     std::vector<uint32_t> &ptypes = H.ptypes;
     ptypes.resize(P);
     std::vector<int4> &pprims = H.pprims;
@@ -377,6 +488,17 @@ drt_status drt_create(drt_ctx **out, int32_t device, uint64_t hbm_budget_bytes) 
         delete c;
         return fail(DRT_ENOMEM, "cudaMalloc failed");
     }
+    for (int i = 0; i < 2; ++i) {
+        if (cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming) != cudaSuccess) {
+            drt_destroy(c);
+            return fail(DRT_ECUDA, "stream/event creation failed");
+        }
+    }
+    if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+        drt_destroy(c);
+        return fail(DRT_ECUDA, "event creation failed");
+    }
     *out = c;
     return DRT_OK;
 }
@@ -387,9 +509,18 @@ void drt_destroy(drt_ctx *c) {
     cudaDeviceSynchronize();
     for (auto &kv : c->links)
         for (void *p : kv.second.allocs) cudaFree(p);
-    for (Scratch *s : {&c->pose, &c->rec_a, &c->rec_b, &c->h})
+    for (Scratch *s : {&c->pose, &c->rec_a, &c->rec_b, &c->h, &c->poseb, &c->base, &c->pose64, &c->redo, &c->warm})
         if (s->ptr) cudaFree(s->ptr);
     cudaFree(c->probe_sink);
+    for (int i = 0; i < 2; ++i) {
+        if (c->side[i]) cudaStreamDestroy(c->side[i]);
+        if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    for (auto &m : c->marks) {
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
     delete c;
 }
 
@@ -409,6 +540,9 @@ drt_status drt_load_paths(drt_ctx *c, const drt_scene *s, const drt_path_set *ps
     if (!st) st = upload(c, L, H.edges, &d.edges);
     if (!st) st = upload(c, L, H.tiles, &d.tiles);
     if (!st) st = upload(c, L, H.mats, &d.mats);
+    if (!st) st = upload(c, L, H.facesF, &d.facesF);
+    if (!st) st = upload(c, L, H.edgesF, &d.edgesF);
+    if (!st) st = upload(c, L, H.tilesF, &d.tilesF);
     if (!st) st = upload(c, L, H.ptypes, &d.ptypes);
     if (!st) st = upload(c, L, H.pprims, &d.pprims);
     if (!st) st = upload(c, L, H.ps0, &d.ps0);

@@ -2,6 +2,9 @@
 //   k_pose           a2: per (time-step, body) pose table R(t), O(t), v_O(t), omega(t) (FP64)
 //   k_extrapolate    a3-a8: one thread per (path, time-step); a warp covers 32 consecutive time
 //                    steps of one path, so all its lanes run the same chain signature
+//   k_pose_bulk, k_base_fp64, k_extrapolate_bulk
+//                    FP32-bulk form: FP32 base poses and FP64 path-length / phase anchors per
+//                    32-step chunk, then FP32 delta-number geometry and field per (path, step)
 //   k_synth          a9: H(t, f) = sum_p a_p exp(-j 2 pi f tau_p); one thread per (time-step,
 //                    16-bin frequency tile), sincos seed per tile and a complex rotation
 //                    recurrence inside it, FP32 FMA accumulation
@@ -10,6 +13,8 @@
 #include "drt_physics.cuh"
 
 namespace drt {
+
+DRT_HD int n_chunks_of(const TimeGridD &tg) { return (tg.n_steps + CHUNK - 1) / CHUNK; }
 
 // ------------------------------------------------------------------------------------------------
 // a2: poses.  theta(t) = w0 t + wdot t^2 / 2 about the fixed axis k (Rodrigues), O(t) by Eq. Taylor,
@@ -37,18 +42,146 @@ constexpr int EXT_T = 128;
 
 __global__ void __launch_bounds__(EXT_T)
 k_extrapolate_fp64(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const double *__restrict__ pose,
-                   const OutD out, const RecD rec) {
-    int p = blockIdx.x;
+                   const OutD out, const RecD rec, int p0, int f32out, const double *__restrict__ warm) {
+    int p = p0 + blockIdx.x;
     int ti = blockIdx.y * EXT_T + threadIdx.x;
     if (p >= L.n_paths || ti >= tg.n_steps) return;
-    path_step_fp64(L, tg, fg, pose, p, ti, out, rec);
+    const double *w = nullptr;
+    if (warm && p >= L.n_bulk)
+        w = warm + ((size_t)(ti / CHUNK) * (L.n_paths - L.n_bulk) + (p - L.n_bulk)) * (2 * MAXI);
+    path_step_fp64(L, tg, fg, pose, p, ti, out, rec, f32out != 0, w);
+}
+
+// warm-start pre-pass over (multi-diffraction path, chunk)
+constexpr int WARM_T = 32;
+__global__ void __launch_bounds__(WARM_T)
+k_warm_fp64(const LinkDev L, const TimeGridD tg, const double *__restrict__ pose, double *__restrict__ warm) {
+    int p = L.n_bulk + blockIdx.x;
+    int c = blockIdx.y * WARM_T + threadIdx.x;
+    if (p >= L.n_paths || c >= n_chunks_of(tg)) return;
+    path_warm_fp64(L, tg, pose, p, c, warm);
+}
+
+size_t warm_bytes(const LinkDev &L, const TimeGridD &tg) {
+    return (size_t)(L.n_paths - L.n_bulk) * n_chunks_of(tg) * 2 * MAXI * sizeof(double);
 }
 
 cudaError_t launch_extrapolate_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg,
-                                    const double *pose, const OutD &out, const RecD &rec, cudaStream_t s) {
+                                    const double *pose, const OutD &out, const RecD &rec, cudaStream_t s, int p0,
+                                    int p1, bool f32out, double *warm) {
+    if (p1 < 0) p1 = L.n_paths;
+    if (p1 <= p0 || tg.n_steps == 0) return cudaSuccess;
+    if (warm && L.n_bulk < L.n_paths) {
+        dim3 gw(L.n_paths - L.n_bulk, (n_chunks_of(tg) + WARM_T - 1) / WARM_T);
+        k_warm_fp64<<<gw, WARM_T, 0, s>>>(L, tg, pose, warm);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid(p1 - p0, (tg.n_steps + EXT_T - 1) / EXT_T);
+    k_extrapolate_fp64<<<grid, EXT_T, 0, s>>>(L, tg, fg, pose, out, rec, p0, f32out ? 1 : 0, warm);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// FP32-bulk form: base poses per (body or terminal, chunk), FP64 anchors per (path, chunk), then
+// the per-(path, step) delta-number kernel with the same block mapping as the FP64 form
+size_t bulk_pose_bytes(const LinkDev &L, const TimeGridD &tg) {
+    return (size_t)(L.n_bodies + 2) * n_chunks_of(tg) * sizeof(PoseB);
+}
+size_t bulk_base_bytes(const LinkDev &L, const TimeGridD &tg) {
+    return (size_t)L.n_paths * n_chunks_of(tg) * sizeof(BaseRec);
+}
+
+__global__ void k_pose_bulk(const BodyD *__restrict__ bodies, int n_bodies, TermD tx, TermD rx, double t_start,
+                            double dt, int n_chunks, PoseB *__restrict__ poseb) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (n_bodies + 2) * n_chunks) return;
+    int b = i / n_chunks, c = i - b * n_chunks;
+    double tb = t_start + (double)c * CHUNK * dt;
+    if (b < n_bodies) body_pose_base(bodies[b], tb, poseb[i]);
+    else terminal_base(b == n_bodies ? tx : rx, tb, poseb[i]);
+}
+
+cudaError_t launch_pose_bulk(const LinkDev &L, const TimeGridD &tg, void *poseb, cudaStream_t s) {
+    int n = (L.n_bodies + 2) * n_chunks_of(tg);
+    if (tg.n_steps == 0) return cudaSuccess;
+    k_pose_bulk<<<(n + 127) / 128, 128, 0, s>>>(L.bodies, L.n_bodies, L.tx, L.rx, tg.t_start, tg.dt, n_chunks_of(tg),
+                                                reinterpret_cast<PoseB *>(poseb));
+    return cudaGetLastError();
+}
+
+size_t bulk_pose64_bytes(const LinkDev &L, const TimeGridD &tg) {
+    return (size_t)L.n_bodies * n_chunks_of(tg) * POSE_W * sizeof(double);
+}
+size_t bulk_redo_bytes(const LinkDev &L, const TimeGridD &tg) {
+    return 256 + (size_t)L.n_paths * tg.n_steps * sizeof(int2);
+}
+
+// one block per path, one thread per chunk: lanes share the chain signature; body poses at the
+// chunk bases come from an FP64 pose table [body][chunk] built first
+constexpr int BASE_T = 64;
+__global__ void __launch_bounds__(BASE_T)
+k_base_fp64(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const double *__restrict__ pose64,
+            BaseRec *__restrict__ base) {
+    int p = blockIdx.x;
+    int c = blockIdx.y * BASE_T + threadIdx.x;
+    if (p >= L.n_bulk || c >= n_chunks_of(tg)) return;
+    path_base_fp64(L, tg, fg, pose64, p, c, base);
+}
+
+cudaError_t launch_base_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, double *pose64, void *base,
+                             cudaStream_t s) {
+    if (L.n_bulk == 0 || tg.n_steps == 0) return cudaSuccess;
+    TimeGridD tc{tg.t_start, tg.dt * CHUNK, n_chunks_of(tg)};   // chunk bases
+    cudaError_t e = launch_pose(L, tc, pose64, s);
+    if (e != cudaSuccess) return e;
+    dim3 grid(L.n_bulk, (n_chunks_of(tg) + BASE_T - 1) / BASE_T);
+    k_base_fp64<<<grid, BASE_T, 0, s>>>(L, tg, fg, pose64, reinterpret_cast<BaseRec *>(base));
+    return cudaGetLastError();
+}
+
+static RedoList redo_list(void *redo, const LinkDev &L, const TimeGridD &tg) {
+    RedoList r;
+    r.count = reinterpret_cast<int *>(redo);
+    r.items = reinterpret_cast<int2 *>(reinterpret_cast<char *>(redo) + 256);
+    r.cap = L.n_paths * tg.n_steps;
+    return r;
+}
+
+__global__ void __launch_bounds__(EXT_T)
+k_extrapolate_bulk(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const PoseB *__restrict__ poseb,
+                   const BaseRec *__restrict__ base, const OutD out, const RecD rec, const RedoList redo) {
+    int p = blockIdx.x;
+    int ti = blockIdx.y * EXT_T + threadIdx.x;
+    if (p >= L.n_bulk || ti >= tg.n_steps) return;
+    path_step_bulk(L, tg, fg, poseb, base, p, ti, out, rec, redo);
+}
+
+cudaError_t launch_extrapolate_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const void *poseb,
+                                    const void *base, const OutD &out, const RecD &rec, void *redo, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(redo, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    if (L.n_bulk == 0 || tg.n_steps == 0) return cudaSuccess;
+    dim3 grid(L.n_bulk, (tg.n_steps + EXT_T - 1) / EXT_T);
+    k_extrapolate_bulk<<<grid, EXT_T, 0, s>>>(L, tg, fg, reinterpret_cast<const PoseB *>(poseb),
+                                              reinterpret_cast<const BaseRec *>(base), out, rec, redo_list(redo, L, tg));
+    return cudaGetLastError();
+}
+
+// FP64 redo of the queued path-steps: a fixed grid strides over the device-side count
+__global__ void __launch_bounds__(128)
+k_redo(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const OutD out, const RecD rec, const RedoList redo) {
+    int n = min(*redo.count, redo.cap);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int2 it = redo.items[k];
+        path_step_redo(L, tg, fg, it.x, it.y, out, rec);
+    }
+}
+
+cudaError_t launch_redo(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const OutD &out, const RecD &rec,
+                        void *redo, cudaStream_t s) {
     if (L.n_paths == 0 || tg.n_steps == 0) return cudaSuccess;
-    dim3 grid(L.n_paths, (tg.n_steps + EXT_T - 1) / EXT_T);
-    k_extrapolate_fp64<<<grid, EXT_T, 0, s>>>(L, tg, fg, pose, out, rec);
+    k_redo<<<152 * 2, 128, 0, s>>>(L, tg, fg, out, rec, redo_list(redo, L, tg));
     return cudaGetLastError();
 }
 

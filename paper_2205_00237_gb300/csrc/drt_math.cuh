@@ -30,7 +30,59 @@ template <class T> DRT_HD dl<T> dsqrt(dl<T> a) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// 3-vectors over any scalar (T or dl<T>)
+// delta numbers of the FP32-bulk form: x = b + d, where b is the value at the chunk's base instant
+// (FP32, only ever multiplied by small deltas), d the change since then, carried with rules that
+// never subtract two large numbers (d(xy) = b_x d_y + d_x b_y + d_x d_y, d(x/y) = (d_x - q d_y)/y,
+// d(sqrt x) = d_x / (sqrt(x) + sqrt(b_x))), and v the time derivative of x (dual part).
+struct dd { float b, d, v; };
+DRT_HD dd DD(float b, float d, float v) { return dd{b, d, v}; }
+DRT_HD dd operator+(dd a, dd c) { return {a.b + c.b, a.d + c.d, a.v + c.v}; }
+DRT_HD dd operator-(dd a, dd c) { return {a.b - c.b, a.d - c.d, a.v - c.v}; }
+DRT_HD dd operator-(dd a) { return {-a.b, -a.d, -a.v}; }
+DRT_HD dd operator*(dd a, dd c) {
+    float af = a.b + a.d, cf = c.b + c.d;
+    return {a.b * c.b, fmaf(a.b, c.d, a.d * cf), fmaf(a.v, cf, af * c.v)};
+}
+DRT_HD dd operator*(dd a, float s) { return {a.b * s, a.d * s, a.v * s}; }
+DRT_HD dd operator*(float s, dd a) { return {a.b * s, a.d * s, a.v * s}; }
+DRT_HD dd operator/(dd a, dd c) {
+    float q = a.b / c.b, cf = c.b + c.d;
+    float d = (a.d - q * c.d) / cf;
+    return {q, d, (a.v - (q + d) * c.v) / cf};
+}
+DRT_HD dd dsqrt(dd a) {
+    float r = sqrtf(fmaxf(a.b, 0.f)), rf = sqrtf(fmaxf(a.b + a.d, 0.f));
+    float den = rf + r;
+    return {r, den > 0.f ? a.d / den : 0.f, rf > 0.f ? a.v / (2.f * rf) : 0.f};
+}
+
+// scalar traits: real type, full value, time derivative, constants
+template <class S> struct ST;
+template <class T> struct ST<dl<T>> {
+    typedef T R;
+    static DRT_HD T val(dl<T> x) { return x.v; }
+    static DRT_HD T rate(dl<T> x) { return x.d; }
+    static DRT_HD dl<T> cst(T x) { return {x, T(0)}; }
+};
+template <> struct ST<dd> {
+    typedef float R;
+    static DRT_HD float val(dd x) { return x.b + x.d; }
+    static DRT_HD float rate(dd x) { return x.v; }
+    static DRT_HD dd cst(float x) { return {x, 0.f, 0.f}; }
+};
+template <> struct ST<double> {   // plain values (FP64 chunk-base solve: no derivative needed)
+    typedef double R;
+    static DRT_HD double val(double x) { return x; }
+    static DRT_HD double rate(double) { return 0.0; }
+    static DRT_HD double cst(double x) { return x; }
+};
+DRT_HD double dsqrt(double x) { return sqrt(x); }
+template <class S> DRT_HD typename ST<S>::R sval(S x) { return ST<S>::val(x); }
+template <class S> DRT_HD typename ST<S>::R srate(S x) { return ST<S>::rate(x); }
+template <class S> DRT_HD S scst(typename ST<S>::R x) { return ST<S>::cst(x); }
+
+// ------------------------------------------------------------------------------------------------
+// 3-vectors over any scalar (T, dl<T> or dd)
 template <class E> struct v3 { E x, y, z; };
 template <class E> DRT_HD v3<E> V3(E x, E y, E z) { return v3<E>{x, y, z}; }
 template <class E> DRT_HD v3<E> operator+(v3<E> a, v3<E> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
@@ -42,12 +94,15 @@ template <class E> DRT_HD v3<E> cross(v3<E> a, v3<E> b) {
     return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
 
-// value / derivative parts of a dual vector, and promotion of a plain vector
-template <class T> DRT_HD v3<T> val(v3<dl<T>> a) { return {a.x.v, a.y.v, a.z.v}; }
-template <class T> DRT_HD v3<T> der(v3<dl<T>> a) { return {a.x.d, a.y.d, a.z.d}; }
+// value / derivative parts of a vector of scalars, and promotion of a plain vector
+template <class S> DRT_HD v3<typename ST<S>::R> val(v3<S> a) { return {sval(a.x), sval(a.y), sval(a.z)}; }
+template <class S> DRT_HD v3<typename ST<S>::R> der(v3<S> a) { return {srate(a.x), srate(a.y), srate(a.z)}; }
 template <class T> DRT_HD v3<dl<T>> dual(v3<T> v, v3<T> d) { return {{v.x, d.x}, {v.y, d.y}, {v.z, d.z}}; }
-template <class T> DRT_HD T norm(v3<T> a) { return sqrt(dot(a, a)); }
+DRT_HD v3<dd> ddv(v3<float> b, v3<float> d, v3<float> v) { return {{b.x, d.x, v.x}, {b.y, d.y, v.y}, {b.z, d.z, v.z}}; }
+DRT_HD double norm(v3<double> a) { return sqrt(dot(a, a)); }
+DRT_HD float norm(v3<float> a) { return sqrtf(dot(a, a)); }
 template <class T> DRT_HD dl<T> norm(v3<dl<T>> a) { return dsqrt(dot(a, a)); }
+DRT_HD dd norm(v3<dd> a) { return dsqrt(dot(a, a)); }
 template <class T> DRT_HD v3<T> unit(v3<T> a) { return a * (T(1) / norm(a)); }
 
 // ------------------------------------------------------------------------------------------------

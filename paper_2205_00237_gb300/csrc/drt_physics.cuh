@@ -14,6 +14,13 @@ constexpr double EPS0 = 8.8541878128e-12;
 constexpr double PI = 3.14159265358979323846;
 
 enum : uint32_t { F_FACE = 1, F_EDGE = 2, F_SIDE = 4, F_NOCONV = 8, F_DEGEN = 16 };
+// internal: the FP32-bulk solve met a geometry it cannot resolve in FP32 (near-grazing Keller cone,
+// unconverged Newton, non-finite value); the path-step is redone in FP64.  Never written out.
+constexpr uint32_t F_REDO64 = 128;
+
+// time steps per chunk: the FP32-bulk form's FP64 anchors and the multi-diffraction warm starts
+// are taken at the first step of every chunk
+constexpr int CHUNK = 16;
 enum : int { T_NONE = 0, T_R = 1, T_D = 2, T_S = 3 };
 
 // ------------------------------------------------------------------------------------------------
@@ -68,30 +75,31 @@ template <class T> DRT_HD v3<dl<T>> terminal(const TermD &m, T t) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// interaction points
+// interaction points, generic over the scalar S (dl<double> for the FP64 form, dd for FP32-bulk)
 // Eq. ref_point in vector form: tangential coordinates interpolated between source S and
 // receiver R with weight h_S / (h_S + h_R) (h = height above the wall), normal coordinate 0.
-template <class T> DRT_HD v3<dl<T>> refl_point(v3<dl<T>> S, v3<dl<T>> R, v3<dl<T>> c, v3<dl<T>> n) {
-    dl<T> hs = dot(S - c, n), hr = dot(R - c, n);
-    dl<T> g = hs / (hs + hr);
-    v3<dl<T>> Q = S + (R - S) * g;
+template <class S> DRT_HD v3<S> refl_point(v3<S> Sv, v3<S> Rv, v3<S> c, v3<S> n) {
+    S hs = dot(Sv - c, n), hr = dot(Rv - c, n);
+    S g = hs / (hs + hr);
+    v3<S> Q = Sv + (Rv - Sv) * g;
     return Q - n * dot(Q - c, n);
 }
 // image of X across the wall (c, n)
-template <class T> DRT_HD v3<dl<T>> mirror(v3<dl<T>> X, v3<dl<T>> c, v3<dl<T>> n) {
-    dl<T> h = dot(X - c, n);
+template <class S> DRT_HD v3<S> mirror(v3<S> X, v3<S> c, v3<S> n) {
+    S h = dot(X - c, n);
     return X - n * (h + h);
 }
-template <class T> DRT_HD v3<dl<T>> mirror_dir(v3<dl<T>> d, v3<dl<T>> n) {
-    dl<T> h = dot(d, n);
+template <class S> DRT_HD v3<S> mirror_dir(v3<S> d, v3<S> n) {
+    S h = dot(d, n);
     return d - n * (h + h);
 }
 
 // posed primitives of one chain vertex
-template <class T> struct Prim {
+template <class S> struct Prim {
+    typedef typename ST<S>::R T;
     int type, mat;
-    v3<dl<T>> p;    // R: face centre, D: edge point a, S: tile centroid
-    v3<dl<T>> a;    // R: face normal, D: edge direction, S: tile normal
+    v3<S> p;        // R: face centre, D: edge point a, S: tile centroid
+    v3<S> a;        // R: face normal, D: edge direction, S: tile normal
     v3<T> b;        // R: face axis u, D: 0-face tangent t0 = n0 x e
     v3<T> c;        // D: 0-face normal n0
     T h1, h2;       // R: hu, hw; D: length, wedge n
@@ -104,14 +112,15 @@ DRT_HD const double *pose_at(const double *pose, int n_steps, int body, int ti) 
     return pose + ((size_t)body * n_steps + ti) * POSE_W;
 }
 
+// FP64 form: primitive posed from the pose record `P` of its body
 template <class T>
-DRT_HD Prim<T> load_prim(const LinkDev &L, const double *pose, int n_steps, int ti, int type, int idx) {
-    Prim<T> q;
+DRT_HD Prim<dl<T>> load_prim_row(const LinkDev &L, const double *Prow, int type, int idx) {
+    Prim<dl<T>> q;
     q.type = type;
     q.idx = idx;
+    Pose<T> P = load_pose<T>(Prow);
     if (type == T_R) {
         const FaceD &f = L.faces[idx];
-        Pose<T> P = load_pose<T>(pose_at(pose, n_steps, f.body, ti));
         q.p = pose_point(P, f.c);
         q.a = pose_dir(P, f.n);
         q.b = rot(P, f.u);
@@ -120,7 +129,6 @@ DRT_HD Prim<T> load_prim(const LinkDev &L, const double *pose, int n_steps, int 
         q.mat = f.mat;
     } else if (type == T_D) {
         const EdgeD &e = L.edges[idx];
-        Pose<T> P = load_pose<T>(pose_at(pose, n_steps, e.body, ti));
         q.p = pose_point(P, e.a);
         q.a = pose_dir(P, e.e);
         q.b = rot(P, e.t0);
@@ -130,7 +138,6 @@ DRT_HD Prim<T> load_prim(const LinkDev &L, const double *pose, int n_steps, int 
         q.mat = e.mat;
     } else {
         const TileD &tl = L.tiles[idx];
-        Pose<T> P = load_pose<T>(pose_at(pose, n_steps, tl.body, ti));
         q.p = pose_point(P, tl.c);
         q.a = pose_dir(P, tl.n);
         q.mat = tl.mat;
@@ -138,23 +145,41 @@ DRT_HD Prim<T> load_prim(const LinkDev &L, const double *pose, int n_steps, int 
     return q;
 }
 
+DRT_HD int prim_body(const LinkDev &L, int type, int idx) {
+    return type == T_R ? L.faces[idx].body : type == T_D ? L.edges[idx].body : L.tiles[idx].body;
+}
+
+// FP64 form: primitives posed from the pose table
+template <class T>
+DRT_HD Prim<dl<T>> load_prim(const LinkDev &L, const double *pose, int n_steps, int ti, int type, int idx) {
+    return load_prim_row<T>(L, pose_at(pose, n_steps, prim_body(L, type, idx), ti), type, idx);
+}
+
+// FP64 primitive posed directly from the body kinematics at time t (FP32-bulk redo path)
+template <class T>
+DRT_HD Prim<dl<T>> load_prim_direct(const LinkDev &L, double t, int type, int idx) {
+    double P[POSE_W];
+    body_pose_row(L.bodies[prim_body(L, type, idx)], t, P);
+    return load_prim_row<T>(L, P, type, idx);
+}
+
 // back-tracking over the reflections strictly between vertices a and b (Sec. III-A.2): images of
 // V[a] through the walls in order, then from V[b] back towards V[a] each point by Eq. ref_point
 // between the image through the preceding walls and the point found at the previous step.
-template <class T>
-DRT_HD void backtrack(const Prim<T> *pr, v3<dl<T>> *V, int a, int b) {
+template <class S>
+DRT_HD void backtrack(const Prim<S> *pr, v3<S> *V, int a, int b) {
     int m = b - a - 1;
     if (m <= 0) return;
-    v3<dl<T>> img[MAXI];
+    v3<S> img[MAXI];
     img[0] = V[a];
 #pragma unroll
     for (int j = 1; j < MAXI; ++j)
         if (j < m) img[j] = mirror(img[j - 1], pr[a + j - 1].p, pr[a + j - 1].a);
-    v3<dl<T>> next = V[b];
+    v3<S> next = V[b];
 #pragma unroll
     for (int j = MAXI; j >= 1; --j) {
         if (j > m) continue;
-        const Prim<T> &w = pr[a + j - 1];
+        const Prim<S> &w = pr[a + j - 1];
         next = refl_point(img[j - 1], next, w.p, w.a);
         V[a + j] = next;
     }
@@ -162,17 +187,20 @@ DRT_HD void backtrack(const Prim<T> *pr, v3<dl<T>> *V, int a, int b) {
 
 // Keller-cone point on the edge line (A, e) between a virtual source and a virtual receiver:
 // s = s_A + (s_B - s_A) rho_A / (rho_A + rho_B), the 3D form of Eq. diff_point.
-template <class T>
-DRT_HD dl<T> keller_s(v3<dl<T>> Sv, v3<dl<T>> Rv, const Prim<T> &e, uint32_t &fl) {
-    v3<dl<T>> wa = Sv - e.p, wb = Rv - e.p;
-    dl<T> sa = dot(wa, e.a), sb = dot(wb, e.a);
-    v3<dl<T>> pa = wa - e.a * sa, pb = wb - e.a * sb;
+template <class S>
+DRT_HD S keller_s(v3<S> Sv, v3<S> Rv, const Prim<S> &e, uint32_t &fl) {
+    typedef typename ST<S>::R T;
+    v3<S> wa = Sv - e.p, wb = Rv - e.p;
+    S sa = dot(wa, e.a), sb = dot(wb, e.a);
+    v3<S> pa = wa - e.a * sa, pb = wb - e.a * sb;
     T ra2 = dot(val(pa), val(pa)), rb2 = dot(val(pb), val(pb));
     if (!(ra2 > T(1e-24)) || !(rb2 > T(1e-24))) {
         fl |= F_DEGEN;
         return sa;
     }
-    dl<T> ra = norm(pa), rb = norm(pb);
+    // near grazing (a virtual terminal within 1 mm of the edge line) FP32 cannot resolve the cone
+    if (sizeof(T) == 4 && (ra2 < T(1e-6) || rb2 < T(1e-6))) fl |= F_REDO64;
+    S ra = norm(pa), rb = norm(pb);
     return sa + (sb - sa) * ra / (ra + rb);
 }
 
@@ -182,37 +210,39 @@ DRT_HD dl<T> keller_s(v3<dl<T>> Sv, v3<dl<T>> Rv, const Prim<T> &e, uint32_t &fl
 // the edge parameters, so a step that lengthens the path is halved until it does not (backtracking
 // line search).  Carried on dual numbers, the converged iterate's derivative is the implicit-function
 // derivative, so the diffraction points' sliding velocities come out of the same solve.
-template <class T>
-DRT_HD dl<T> unfolded_length(const Prim<T> *pr, const v3<dl<T>> *V, int a, int b, const int *didx, int m,
-                             const dl<T> *s, dl<T> *g, dl<T> *hd, dl<T> *ho) {
-    dl<T> Ltot = D<T>(T(0), T(0));
-    for (int j = 0; j < m; ++j) g[j] = hd[j] = ho[j] = D<T>(T(0), T(0));
+template <class S>
+DRT_HD S unfolded_length(const Prim<S> *pr, const v3<S> *V, int a, int b, const int *didx, int m, const S *s, S *g,
+                         S *hd, S *ho) {
+    typedef typename ST<S>::R T;
+    const S one = scst<S>(T(1));
+    S Ltot = scst<S>(T(0));
+    for (int j = 0; j < m; ++j) g[j] = hd[j] = ho[j] = scst<S>(T(0));
     for (int j = 0; j <= m; ++j) {
         int i0 = (j == 0) ? a : didx[j - 1];
         int i1 = (j == m) ? b : didx[j];
-        v3<dl<T>> X = (j == 0) ? V[a] : pr[i0 - 1].p + pr[i0 - 1].a * s[j - 1];
-        v3<dl<T>> ex = (j == 0) ? V[a] : pr[i0 - 1].a;
+        v3<S> X = (j == 0) ? V[a] : pr[i0 - 1].p + pr[i0 - 1].a * s[j - 1];
+        v3<S> ex = (j == 0) ? V[a] : pr[i0 - 1].a;
         for (int i = i0 + 1; i < i1; ++i) {
             X = mirror(X, pr[i - 1].p, pr[i - 1].a);
             if (j > 0) ex = mirror_dir(ex, pr[i - 1].a);
         }
-        v3<dl<T>> Y = (j == m) ? V[b] : pr[i1 - 1].p + pr[i1 - 1].a * s[j];
-        v3<dl<T>> r = X - Y;
-        dl<T> l = norm(r);
+        v3<S> Y = (j == m) ? V[b] : pr[i1 - 1].p + pr[i1 - 1].a * s[j];
+        v3<S> r = X - Y;
+        S l = norm(r);
         Ltot = Ltot + l;
-        dl<T> il = D<T>(T(1), T(0)) / l;
-        v3<dl<T>> rh = r * il;
+        S il = one / l;
+        v3<S> rh = r * il;
         if (j > 0) {
-            dl<T> q = dot(rh, ex);
+            S q = dot(rh, ex);
             g[j - 1] = g[j - 1] + q;
-            hd[j - 1] = hd[j - 1] + (D<T>(T(1), T(0)) - q * q) * il;
+            hd[j - 1] = hd[j - 1] + (one - q * q) * il;
         }
         if (j < m) {
-            dl<T> q = dot(rh, pr[i1 - 1].a);
+            S q = dot(rh, pr[i1 - 1].a);
             g[j] = g[j] - q;
-            hd[j] = hd[j] + (D<T>(T(1), T(0)) - q * q) * il;
+            hd[j] = hd[j] + (one - q * q) * il;
             if (j > 0) {
-                dl<T> qx = dot(rh, ex);
+                S qx = dot(rh, ex);
                 ho[j - 1] = ho[j - 1] + (qx * q - dot(ex, pr[i1 - 1].a)) * il;
             }
         }
@@ -220,15 +250,35 @@ DRT_HD dl<T> unfolded_length(const Prim<T> *pr, const v3<dl<T>> *V, int a, int b
     return Ltot;
 }
 
-template <class T>
-DRT_HD void multi_diffraction(const Prim<T> *pr, v3<dl<T>> *V, int a, int b, const double *s0, uint32_t &fl) {
+template <class S> DRT_HD void clamp_positive(S &x, typename ST<S>::R eps);
+template <> DRT_HD void clamp_positive<dl<double>>(dl<double> &x, double eps) {
+    if (!(x.v > eps)) x.v = eps;
+}
+template <> DRT_HD void clamp_positive<double>(double &x, double eps) {
+    if (!(x > eps)) x = eps;
+}
+template <> DRT_HD void clamp_positive<dd>(dd &x, float eps) {
+    if (!(x.b + x.d > eps)) {
+        x.b = eps;
+        x.d = 0.f;
+    }
+}
+
+template <class S>
+DRT_HD void multi_diffraction(const Prim<S> *pr, v3<S> *V, int a, int b, const double *s0, uint32_t &fl) {
+    typedef typename ST<S>::R T;
+    // convergence threshold on the Newton step (m): near round-off of the working precision
+    const T tol = sizeof(T) == 8 ? T(1e-10) : T(1e-4);
+    // below this step (m) the length change of a Newton step is at round-off of the ~100 m path
+    // length, so the backtracking test is only applied to larger steps
+    const T ls_min = sizeof(T) == 8 ? T(1e-4) : T(1e-2);
     int didx[MAXI], m = 0;
-    dl<T> s[MAXI], step[MAXI];
+    S s[MAXI], step[MAXI];
     for (int i = a + 1; i < b; ++i)
         if (pr[i - 1].type == T_D) {
             didx[m] = i;
-            s[m] = D<T>(T(s0[i - 1]), T(0));
-            step[m] = D<T>(T(0), T(0));
+            s[m] = scst<S>(T(s0[i - 1]));
+            step[m] = scst<S>(T(0));
             ++m;
         }
     bool conv = false;
@@ -236,9 +286,9 @@ DRT_HD void multi_diffraction(const Prim<T> *pr, v3<dl<T>> *V, int a, int b, con
     T Lprev = T(0), smax_prev = T(0);
     bool have_prev = false;
     for (int it = 0; it < 64; ++it) {
-        dl<T> g[MAXI], hd[MAXI], ho[MAXI];
-        dl<T> Lc = unfolded_length(pr, V, a, b, didx, m, s, g, hd, ho);
-        if (have_prev && smax_prev > T(1e-7) && !(Lc.v <= Lprev) && halvings < 40) {
+        S g[MAXI], hd[MAXI], ho[MAXI];
+        S Lc = unfolded_length(pr, V, a, b, didx, m, s, g, hd, ho);
+        if (have_prev && smax_prev > ls_min && !(sval(Lc) <= Lprev) && halvings < 40) {
             for (int j = 0; j < m; ++j) {     // backtrack: s_prev + step / 2
                 step[j] = step[j] * T(0.5);
                 s[j] = s[j] - step[j];
@@ -248,23 +298,22 @@ DRT_HD void multi_diffraction(const Prim<T> *pr, v3<dl<T>> *V, int a, int b, con
             continue;
         }
         halvings = 0;
-        Lprev = Lc.v;
+        Lprev = sval(Lc);
         have_prev = true;
-        for (int j = 0; j < m; ++j)
-            if (!(hd[j].v > T(1e-12))) hd[j].v = T(1e-12);
+        for (int j = 0; j < m; ++j) clamp_positive(hd[j], T(1e-12));
         // Thomas algorithm for H step = -g (H symmetric tridiagonal: diag hd, off-diagonal ho)
-        dl<T> cp[MAXI], dp[MAXI];
+        S cp[MAXI], dp[MAXI];
         cp[0] = ho[0] / hd[0];
         dp[0] = -g[0] / hd[0];
         for (int j = 1; j < m; ++j) {
-            dl<T> den = hd[j] - ho[j - 1] * cp[j - 1];
+            S den = hd[j] - ho[j - 1] * cp[j - 1];
             cp[j] = ho[j] / den;
             dp[j] = (-g[j] - ho[j - 1] * dp[j - 1]) / den;
         }
         T smax = T(0);
         for (int j = m - 1; j >= 0; --j) {
             if (j < m - 1) dp[j] = dp[j] - cp[j] * dp[j + 1];
-            smax = fmax(smax, fabs(dp[j].v));
+            smax = fmax(smax, fabs(sval(dp[j])));
         }
         if (!(smax == smax)) break;   // NaN
         for (int j = 0; j < m; ++j) {
@@ -274,7 +323,7 @@ DRT_HD void multi_diffraction(const Prim<T> *pr, v3<dl<T>> *V, int a, int b, con
         smax_prev = smax;
         if (conv) {
             if (--extra < 0) break;
-        } else if (smax < T(1e-10)) {
+        } else if (smax < tol) {
             conv = true;   // one more full step refines the derivative part
         }
     }
@@ -289,9 +338,8 @@ DRT_HD void multi_diffraction(const Prim<T> *pr, v3<dl<T>> *V, int a, int b, con
 }
 
 // geometry of one path-step: vertices V[0..n+1] (TX, interaction points, RX) with velocities
-template <class T>
-DRT_HD void solve_geometry(const Prim<T> *pr, int n, v3<dl<T>> *V, const double *s0,
-                                               uint32_t &fl) {
+template <class S>
+DRT_HD void solve_geometry(const Prim<S> *pr, int n, v3<S> *V, const double *s0, uint32_t &fl) {
     for (int i = 1; i <= n; ++i)
         if (pr[i - 1].type == T_S) V[i] = pr[i - 1].p;   // Sec. III-C: tile centroid moves rigidly
     int a = 0;
@@ -306,10 +354,10 @@ DRT_HD void solve_geometry(const Prim<T> *pr, int n, v3<dl<T>> *V, const double 
         if (nd == 0) {
             backtrack(pr, V, a, b);
         } else if (nd == 1) {
-            v3<dl<T>> src = V[a], rcv = V[b];
+            v3<S> src = V[a], rcv = V[b];
             for (int i = a + 1; i < dpos; ++i) src = mirror(src, pr[i - 1].p, pr[i - 1].a);
             for (int i = b - 1; i > dpos; --i) rcv = mirror(rcv, pr[i - 1].p, pr[i - 1].a);
-            const Prim<T> &e = pr[dpos - 1];
+            const Prim<S> &e = pr[dpos - 1];
             V[dpos] = e.p + e.a * keller_s(src, rcv, e, fl);
             backtrack(pr, V, a, dpos);
             backtrack(pr, V, dpos, b);
@@ -328,15 +376,16 @@ template <class T> DRT_HD T wrap2pi(T x) {
 // validity (Sec. II: the t0 multipath structure still holds): reflection points inside their
 // faces with both neighbours in front, diffraction points on their edge segments with both
 // neighbours in the wedge exterior, tiles lit from and seen from the front
-template <class T>
-DRT_HD uint32_t validity(const Prim<T> *pr, int n, const v3<T> *P) {
+template <class S>
+DRT_HD uint32_t validity(const Prim<S> *pr, int n, const v3<typename ST<S>::R> *P) {
+    typedef typename ST<S>::R T;
     uint32_t fl = 0;
     for (int i = 1; i <= n + 1; ++i) {
         v3<T> d = P[i] - P[i - 1];
         if (!(dot(d, d) >= T(1e-18))) fl |= F_DEGEN;
     }
     for (int i = 1; i <= n; ++i) {
-        const Prim<T> &q = pr[i - 1];
+        const Prim<S> &q = pr[i - 1];
         if (q.type == T_R) {
             v3<T> c = val(q.p), nn = val(q.a);
             v3<T> r = P[i] - c;
@@ -362,17 +411,34 @@ DRT_HD uint32_t validity(const Prim<T> *pr, int n, const v3<T> *P) {
 }
 
 // ------------------------------------------------------------------------------------------------
+// material and tile parameters in the working precision
+template <class T> struct MatV { T eps_r, sigma, rough; bool pec; };
+template <class T> DRT_HD MatV<T> matv(const MatD &m);
+template <> DRT_HD MatV<double> matv<double>(const MatD &m) { return {m.eps_r, m.sigma, m.rough, m.pec != 0.0}; }
+template <> DRT_HD MatV<float> matv<float>(const MatD &m) { return {m.eps_rf, m.sigmaf, m.roughf, m.pecf != 0.f}; }
+template <class T> struct TileV { T area, s, phase; int alpha; };
+template <class T> DRT_HD TileV<T> tilev(const LinkDev &L, int idx);
+template <> DRT_HD TileV<double> tilev<double>(const LinkDev &L, int idx) {
+    const TileD &t = L.tiles[idx];
+    return {t.area, t.s, t.phase, (int)t.alpha};
+}
+template <> DRT_HD TileV<float> tilev<float>(const LinkDev &L, int idx) {
+    const TileF &t = L.tilesF[idx];
+    return {t.area, t.s, t.phase, (int)t.alpha};
+}
+
+// ------------------------------------------------------------------------------------------------
 // field coefficients
 // Fresnel reflection coefficients for the perpendicular (TE) and parallel (TM) components;
 // eps_c = eps_r - j sigma / (2 pi f eps0); a perfect conductor gives -1 and +1.
 template <class T>
-DRT_HD void fresnel(const MatD &m, T fc, T ct, cx<T> &rte, cx<T> &rtm) {
-    if (m.pec != 0.0) {
+DRT_HD void fresnel(const MatV<T> &m, T fc, T ct, cx<T> &rte, cx<T> &rtm) {
+    if (m.pec) {
         rte = C<T>(T(-1), T(0));
         rtm = C<T>(T(1), T(0));
         return;
     }
-    cx<T> ec = C<T>(T(m.eps_r), -T(m.sigma) / (T(2 * PI) * fc * T(EPS0)));
+    cx<T> ec = C<T>(m.eps_r, -m.sigma / (T(2 * PI) * fc * T(EPS0)));
     cx<T> sq = csqrt_(C<T>(ec.re - T(1) + ct * ct, ec.im));
     rte = cdiv(C<T>(ct - sq.re, -sq.im), C<T>(ct + sq.re, sq.im));
     cx<T> ecct = ec * ct;
@@ -441,7 +507,7 @@ template <class T> DRT_HD cx<T> utd_term(T eps, T n, T kL) {
 // soft / hard wedge diffraction coefficients: Kouyoumjian-Pathak with the spherical-wave distance
 // parameter L, Luebbers' face-coefficient weights for lossy wedges
 template <class T>
-DRT_HD void utd(T n, T phi, T phip, T sinb0, T L, T k, const MatD &m, T fc, cx<T> &Ds, cx<T> &Dh) {
+DRT_HD void utd(T n, T phi, T phip, T sinb0, T L, T k, const MatV<T> &m, T fc, cx<T> &Ds, cx<T> &Dh) {
     T kL = k * L;
     T pref = T(1) / (T(2) * n * sqrt(T(2 * PI) * k) * sinb0);
     cx<T> Cc = C<T>(-pref * T(0.70710678118654752440), pref * T(0.70710678118654752440));  // -exp(-j pi/4) pref
@@ -496,14 +562,13 @@ template <class T> DRT_HD v3<T> vertical_pol(v3<T> k) {
 // complex amplitude a_p excluding exp(-j k d): (lambda / 4 pi) x ray spreading (1/length per
 // segment between point sources; UTD sqrt(s'/(s(s'+s))) per diffraction) x polarimetric chain of
 // Fresnel / UTD / ER factors; TX and RX vertically polarised.
-template <class T>
-DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<T> *pr, int n, const v3<T> *P, T fc) {
+template <class S, class T = typename ST<S>::R>
+DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *seg, T fc) {
     v3<T> kd[MAXI + 2];
     T len[MAXI + 2];
     for (int i = 1; i <= n + 1; ++i) {
-        v3<T> d = P[i] - P[i - 1];
-        len[i] = norm(d);
-        kd[i] = d * (T(1) / len[i]);
+        len[i] = norm(seg[i]);
+        kd[i] = seg[i] * (T(1) / len[i]);
     }
     T spread = T(1), sprime[MAXI + 1], sdist[MAXI + 1];
     int a = 0;
@@ -536,8 +601,8 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<T> *pr, int n, const v3<T> *
         E = cscale(e0, C<T>(T(1), T(0)));
     }
     for (int i = 1; i <= n; ++i) {
-        const Prim<T> &q = pr[i - 1];
-        const MatD m = L.mats[q.mat];
+        const Prim<S> &q = pr[i - 1];
+        const MatV<T> m = matv<T>(L.mats[q.mat]);
         v3<T> kin = kd[i], kout = kd[i + 1];
         if (q.type == T_R) {
             v3<T> nf = val(q.a);
@@ -552,7 +617,7 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<T> *pr, int n, const v3<T> *
             v3<T> epin = cross(ep, kin), epout = cross(ep, kout);
             cx<T> rte, rtm;
             fresnel(m, fc, ct, rte, rtm);
-            T rough = sqrt(fmax(T(0), T(1) - T(m.rough) * T(m.rough)));
+            T rough = sqrt(fmax(T(0), T(1) - m.rough * m.rough));
             E = cscale(ep, rte * cdot(E, ep) * rough) + cscale(epout, rtm * cdot(E, epin) * rough);
         } else if (q.type == T_D) {
             v3<T> e = val(q.a);
@@ -568,19 +633,19 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<T> *pr, int n, const v3<T> *
             v3<T> ph = unit(cross(e, kout)), bv = cross(ph, kout);
             E = cscale(bv, -(Ds * cdot(E, bpv))) + cscale(ph, -(Dh * cdot(E, php)));
         } else {
-            const TileD &tl = L.tiles[q.idx];
+            const TileV<T> tl = tilev<T>(L, q.idx);
             v3<T> nt = val(q.a);
             if (dot(nt, kin) > T(0)) nt = -nt;
             T cti = -dot(nt, kin);
             v3<T> kspec = kin + nt * (T(2) * cti);
             T cpsi = dot(kspec, kout);
-            int alpha = (int)tl.alpha;
+            int alpha = tl.alpha;
             T Fa = er_norm<T>(alpha, cti);
             T lobe = T(1);
             T hb = T(0.5) * (T(1) + cpsi);
             for (int j = 0; j < alpha; ++j) lobe *= hb;   // ((1 + cos psi)/2)^alpha
-            T amp = T(tl.s) * sqrt(T(tl.area) * cti / Fa) * sqrt(lobe);
-            cx<T> ph = cexpj(T(tl.phase));
+            T amp = tl.s * sqrt(tl.area * cti / Fa) * sqrt(lobe);
+            cx<T> ph = cexpj(tl.phase);
             T nE = cnorm(E);
             cx<T> ek = cdot(E, kout);
             c3<T> Ep = E + cscale(kout, -ek);
@@ -596,11 +661,11 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<T> *pr, int n, const v3<T> *
 
 // App. A Eq. doppler_freq: f' = f0 prod_i (c - v_i.k_i) / (c - v_{i-1}.k_i), evaluated without
 // cancellation as f_D = f0 expm1( sum_i log1p(-v_i.k_i / c) - log1p(-v_{i-1}.k_i / c) )
-template <class T> DRT_HD T doppler(int n, const v3<dl<T>> *V, T fc) {
+template <class S, class T = typename ST<S>::R> DRT_HD T doppler(int n, const v3<S> *V, const v3<T> *seg, T fc) {
     T acc = T(0);
     const T ic = T(1) / T(C0);
     for (int i = 1; i <= n + 1; ++i) {
-        v3<T> k = unit(val(V[i]) - val(V[i - 1]));
+        v3<T> k = unit(seg[i]);
         acc += log1p(-dot(der(V[i]), k) * ic) - log1p(-dot(der(V[i - 1]), k) * ic);
     }
     return fc * expm1(acc);
@@ -609,8 +674,8 @@ template <class T> DRT_HD T doppler(int n, const v3<dl<T>> *V, T fc) {
 // ------------------------------------------------------------------------------------------------
 // one (path, time-step) of the FP64 form: geometry, validity, delay, Doppler, angles, amplitude;
 // user outputs at [ti][perm[p]], synthesis record at [ti][p]
-DRT_HD void write_outputs_fp64(const OutD &o, size_t oi, int n, const v3<double> *P, double tau, cx<double> a,
-                               double fd, uint32_t fl) {
+DRT_HD void write_outputs_fp64(const OutD &o, size_t oi, int n, const v3<double> *P, const v3<double> *seg,
+                               double tau, cx<double> a, double fd, uint32_t fl) {
     if (o.tau) o.tau[oi] = tau;
     if (o.amp) {
         double *q = reinterpret_cast<double *>(o.amp) + 2 * oi;
@@ -619,7 +684,7 @@ DRT_HD void write_outputs_fp64(const OutD &o, size_t oi, int n, const v3<double>
     }
     if (o.doppler) reinterpret_cast<double *>(o.doppler)[oi] = fd;
     if (o.angles) {
-        v3<double> kd = unit(P[1] - P[0]), ka = unit(P[n] - P[n + 1]);
+        v3<double> kd = unit(seg[1]), ka = -unit(seg[n + 1]);
         float *q = o.angles + 4 * oi;
         q[0] = (float)atan2(kd.y, kd.x);
         q[1] = (float)atan2(kd.z, hypot(kd.x, kd.y));
@@ -656,19 +721,23 @@ DRT_HD void write_record(const RecD &r, size_t ri, double tau, cx<double> a, uin
     r.rec_b[ri] = (float)(st - hi);
 }
 
-DRT_HD void path_step_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const double *pose, int p,
-                           int ti, const OutD &out, const RecD &rec) {
+// FP64 (path, time-step) core: primitives from `load(j, type, idx)`; FP64 outputs (amp double[2],
+// Doppler double) or, for the FP32-bulk form's redo, FP32 ones (float[2], float)
+template <class Loader>
+DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, int p, int ti,
+                                const OutD &out, const RecD &rec, bool f32out, Loader load,
+                                const double *warm = nullptr) {
     typedef double T;
     const T t = tg.t_start + ti * tg.dt;
     uint32_t code = L.ptypes[p];
     int4 pi = L.pprims[p];
     int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
     int n = 0;
-    Prim<T> pr[MAXI];
+    Prim<dl<T>> pr[MAXI];
     for (int j = 0; j < MAXI; ++j) {
         int ty = (code >> (8 * j)) & 0xff;
         if (ty != T_NONE) {
-            pr[j] = load_prim<T>(L, pose, tg.n_steps, ti, ty, prim[j]);
+            pr[j] = load(ty, prim[j]);
             n = j + 1;
         }
     }
@@ -676,23 +745,432 @@ DRT_HD void path_step_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGrid
     V[0] = terminal<T>(L.tx, t);
     V[n + 1] = terminal<T>(L.rx, t);
     uint32_t fl = 0;
-    solve_geometry(pr, n, V, L.ps0 + (size_t)p * MAXI, fl);
+    double sinit[MAXI];
+    const double *s0 = L.ps0 + (size_t)p * MAXI;
+    if (warm) {
+        // warm start of the Newton solve: edge parameters and their rates at the chunk base
+        const double tau = (ti - (ti / CHUNK) * CHUNK) * tg.dt;
+        for (int j = 0; j < MAXI; ++j) sinit[j] = warm[j] + warm[MAXI + j] * tau;
+        s0 = sinit;
+    }
+    solve_geometry(pr, n, V, s0, fl);
     v3<T> P[MAXI + 2];
     for (int i = 0; i <= n + 1; ++i) P[i] = val(V[i]);
     fl |= validity(pr, n, P);
+    v3<T> seg[MAXI + 2];
     T d = T(0);
-    for (int i = 1; i <= n + 1; ++i) d += norm(P[i] - P[i - 1]);
+    for (int i = 1; i <= n + 1; ++i) {
+        seg[i] = P[i] - P[i - 1];
+        d += norm(seg[i]);
+    }
     T tau = d / T(C0);
-    cx<T> a = (fl & F_DEGEN) ? C<T>(T(0), T(0)) : amplitude(L, pr, n, P, T(fg.fc));
+    cx<T> a = (fl & F_DEGEN) ? C<T>(T(0), T(0)) : amplitude(L, pr, n, seg, T(fg.fc));
     if (out.tau || out.amp || out.doppler || out.angles || out.flags || out.points) {
-        T fd = doppler(n, V, T(fg.fc));
+        T fd = doppler(n, V, seg, T(fg.fc));
         size_t oi = (size_t)ti * L.n_paths + L.perm[p];
-        write_outputs_fp64(out, oi, n, P, tau, a, fd, fl);
+        if (f32out) {
+            OutD o2 = out;
+            o2.amp = nullptr;
+            o2.doppler = nullptr;
+            write_outputs_fp64(o2, oi, n, P, seg, tau, a, fd, fl);
+            if (out.amp) {
+                float *q = reinterpret_cast<float *>(out.amp) + 2 * oi;
+                q[0] = (float)a.re;
+                q[1] = (float)a.im;
+            }
+            if (out.doppler) reinterpret_cast<float *>(out.doppler)[oi] = (float)fd;
+        } else {
+            write_outputs_fp64(out, oi, n, P, seg, tau, a, fd, fl);
+        }
     }
     if (rec.rec_a) {
         double f0 = fg.fc - 0.5 * fg.bandwidth, df = fg.bandwidth / fg.n_bins;
         write_record(rec, (size_t)ti * L.n_paths + p, tau, a, fl, f0, df);
     }
+}
+
+DRT_HD void path_step_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const double *pose, int p,
+                           int ti, const OutD &out, const RecD &rec, bool f32out = false,
+                           const double *warm = nullptr) {
+    path_step_fp64_core(
+        L, tg, fg, p, ti, out, rec, f32out,
+        [&](int ty, int idx) { return load_prim<double>(L, pose, tg.n_steps, ti, ty, idx); }, warm);
+}
+
+// Warm start for the chains with >= 2 diffractions in a segment (paths [n_bulk, n_paths)): per
+// (path, chunk) the FP64 dual-number solve at the chunk base from the t0 edge parameters gives each
+// diffraction vertex's edge parameter s and its rate ds/dt; a step tau later starts its Newton solve
+// at s + tau ds/dt and converges in one or two iterations.  warm is [chunk][path - n_bulk][8].
+// one dual-number FP64 solve of a chain at time t from the edge-parameter start `sin`; writes each
+// diffraction vertex's parameter and rate to sv/sd (sin and 0 where the solve failed)
+template <class Loader>
+DRT_HD void solve_edge_params(const LinkDev &L, int p, double t, const double *sin, double *sv, double *sd,
+                              Loader load) {
+    typedef double T;
+    uint32_t code = L.ptypes[p];
+    int4 pi = L.pprims[p];
+    int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
+    int n = 0;
+    Prim<dl<T>> pr[MAXI];
+    for (int j = 0; j < MAXI; ++j) {
+        int ty = (code >> (8 * j)) & 0xff;
+        if (ty != T_NONE) {
+            pr[j] = load(ty, prim[j]);
+            n = j + 1;
+        }
+    }
+    v3<dl<T>> V[MAXI + 2];
+    V[0] = terminal<T>(L.tx, t);
+    V[n + 1] = terminal<T>(L.rx, t);
+    uint32_t fl = 0;
+    solve_geometry(pr, n, V, sin, fl);
+    for (int j = 0; j < MAXI; ++j) {
+        sv[j] = sin[j];
+        sd[j] = 0.0;
+        if (j < n && pr[j].type == T_D && !(fl & F_NOCONV)) {
+            dl<T> sj = dot(V[j + 1] - pr[j].p, pr[j].a);
+            if (isfinite(sj.v) && isfinite(sj.d)) {
+                sv[j] = sj.v;
+                sd[j] = sj.d;
+            }
+        }
+    }
+}
+
+DRT_HD void path_warm_fp64(const LinkDev &L, const TimeGridD &tg, const double *pose, int p, int chunk,
+                           double *warm) {
+    const int ti = chunk * CHUNK;
+    const double t = tg.t_start + ti * tg.dt;
+    // rates at t0, where the ray-tracing parameters s0 are already the solution (one iteration)
+    double s_t0[MAXI], r_t0[MAXI], start[MAXI];
+    solve_edge_params(L, p, 0.0, L.ps0 + (size_t)p * MAXI, s_t0, r_t0,
+                      [&](int ty, int idx) { return load_prim_direct<double>(L, 0.0, ty, idx); });
+    // chunk-base solve from the linear predictor s(t0) + t ds/dt(t0)
+    for (int j = 0; j < MAXI; ++j) start[j] = s_t0[j] + r_t0[j] * t;
+    double *w = warm + ((size_t)chunk * (L.n_paths - L.n_bulk) + (p - L.n_bulk)) * (2 * MAXI);
+    solve_edge_params(L, p, t, start, w, w + MAXI,
+                      [&](int ty, int idx) { return load_prim<double>(L, pose, tg.n_steps, ti, ty, idx); });
+}
+
+// ------------------------------------------------------------------------------------------------
+// FP32-bulk form.  Time steps are grouped in chunks of CHUNK consecutive steps.  Per
+// (path, chunk) an FP64 base solve at the chunk's first instant t_b gives the path length d_b and
+// the phase anchors frac(f_0 d_b / c), frac(df d_b / c) (k_base_fp64).  Per (path, step) the geometry
+// runs in FP32 delta numbers (dd): base values at t_b, deltas since t_b, time derivatives; the
+// delay is d_b + sum of the segment-length deltas, so the FP32 rounding acts on metre-scale
+// deltas, not on the ~100 m path length.
+
+// per (path, chunk) FP64 anchors
+struct BaseRec {
+    double d;                  // path length at the chunk base (m)
+    float ph0, st_hi, st_lo;   // frac(f_0 d / c); frac(df d / c) = st_hi + st_lo
+    float pad;
+    float seg[MAXI + 1][3];    // segment vectors V_i - V_{i-1} at the chunk base, from FP64 positions
+};
+
+// per (body, chunk) FP32 base pose: rows of R(t_b), O(t_b), v_O(t_b), a, axis k, w(t_b), wdot
+struct PoseB { float R[9], O[3], vO[3], a[3], k[3], w, wdot, pad; };
+
+DRT_HD void body_pose_base(const BodyD &B, double tb, PoseB &q) {
+    double P[POSE_W];
+    body_pose_row(B, tb, P);
+    for (int j = 0; j < 9; ++j) q.R[j] = (float)P[j];
+    for (int j = 0; j < 3; ++j) {
+        q.O[j] = (float)P[9 + j];
+        q.vO[j] = (float)P[12 + j];
+        q.a[j] = (float)B.a[j];
+        q.k[j] = (float)B.k[j];
+    }
+    q.w = (float)(B.w0 + B.wdot * tb);
+    q.wdot = (float)B.wdot;
+    q.pad = 0.f;
+}
+
+DRT_HD void terminal_base(const TermD &m, double tb, PoseB &q) {
+    for (int j = 0; j < 9; ++j) q.R[j] = (j % 4 == 0) ? 1.f : 0.f;
+    for (int j = 0; j < 3; ++j) {
+        q.O[j] = (float)(m.r[j] + m.v[j] * tb + 0.5 * m.a[j] * tb * tb);
+        q.vO[j] = (float)(m.v[j] + m.a[j] * tb);
+        q.a[j] = (float)m.a[j];
+        q.k[j] = j == 2 ? 1.f : 0.f;
+    }
+    q.w = q.wdot = q.pad = 0.f;
+}
+
+// pose of one body tau seconds after its chunk base, as delta numbers: rotation by
+// dth = w tau + wdot tau^2 / 2 about k applied to the base pose, written with sin(dth) and the
+// versine 2 sin^2(dth/2) so that small rotations lose nothing.
+struct PoseDD {
+    v3<float> R0, R1, R2, O, dO, vO, w, k;
+    float sn, vs;   // sin(dth), 1 - cos(dth)
+};
+DRT_HD PoseDD pose_dd(const PoseB &q, float tau) {
+    PoseDD P;
+    P.R0 = V3<float>(q.R[0], q.R[1], q.R[2]);
+    P.R1 = V3<float>(q.R[3], q.R[4], q.R[5]);
+    P.R2 = V3<float>(q.R[6], q.R[7], q.R[8]);
+    P.O = V3<float>(q.O[0], q.O[1], q.O[2]);
+    v3<float> a = V3<float>(q.a[0], q.a[1], q.a[2]), vb = V3<float>(q.vO[0], q.vO[1], q.vO[2]);
+    P.dO = vb * tau + a * (0.5f * tau * tau);
+    P.vO = vb + a * tau;
+    P.k = V3<float>(q.k[0], q.k[1], q.k[2]);
+    P.w = P.k * (q.w + q.wdot * tau);
+    float dth = q.w * tau + 0.5f * q.wdot * tau * tau;
+    float sh = sinf(0.5f * dth);
+    P.sn = sinf(dth);
+    P.vs = 2.f * sh * sh;
+    return P;
+}
+DRT_HD v3<float> rotb(const PoseDD &P, const float *x) {
+    v3<float> v = V3<float>(x[0], x[1], x[2]);
+    return V3<float>(dot(P.R0, v), dot(P.R1, v), dot(P.R2, v));
+}
+// change of a base vector r under the extra rotation: sin(dth) k x r + (1 - cos(dth)) k x (k x r)
+DRT_HD v3<float> drot(const PoseDD &P, v3<float> r) {
+    v3<float> kr = cross(P.k, r);
+    return kr * P.sn + cross(P.k, kr) * P.vs;
+}
+DRT_HD v3<dd> pose_point_dd(const PoseDD &P, const float *rel) {
+    v3<float> rb = rotb(P, rel), dr = drot(P, rb);
+    return ddv(P.O + rb, P.dO + dr, P.vO + cross(P.w, rb + dr));
+}
+DRT_HD v3<dd> pose_dir_dd(const PoseDD &P, const float *d0) {
+    v3<float> nb = rotb(P, d0), dn = drot(P, nb);
+    return ddv(nb, dn, cross(P.w, nb + dn));
+}
+// terminal tau seconds after its chunk base, from its base record (stored like a body pose: O = r,
+// vO = v, a = a at the chunk's first instant)
+DRT_HD v3<dd> terminal_dd(const PoseB &q, float tau) {
+    v3<float> b = V3<float>(q.O[0], q.O[1], q.O[2]), v = V3<float>(q.vO[0], q.vO[1], q.vO[2]);
+    v3<float> a = V3<float>(q.a[0], q.a[1], q.a[2]);
+    return ddv(b, v * tau + a * (0.5f * tau * tau), v + a * tau);
+}
+
+DRT_HD Prim<dd> load_prim_dd(const LinkDev &L, const PoseB *poseb, int n_chunks, int chunk, float tau, int type,
+                             int idx) {
+    Prim<dd> q;
+    q.type = type;
+    q.idx = idx;
+    int body = type == T_R ? L.facesF[idx].body : type == T_D ? L.edgesF[idx].body : L.tilesF[idx].body;
+    PoseDD P = pose_dd(poseb[(size_t)body * n_chunks + chunk], tau);
+    if (type == T_R) {
+        const FaceF &f = L.facesF[idx];
+        q.p = pose_point_dd(P, f.c);
+        q.a = pose_dir_dd(P, f.n);
+        v3<float> ub = rotb(P, f.u);
+        q.b = ub + drot(P, ub);
+        q.h1 = f.hu;
+        q.h2 = f.hw;
+        q.mat = f.mat;
+    } else if (type == T_D) {
+        const EdgeF &e = L.edgesF[idx];
+        q.p = pose_point_dd(P, e.a);
+        q.a = pose_dir_dd(P, e.e);
+        v3<float> tb = rotb(P, e.t0), nb = rotb(P, e.n0);
+        q.b = tb + drot(P, tb);
+        q.c = nb + drot(P, nb);
+        q.h1 = e.len;
+        q.h2 = e.wn;
+        q.mat = e.mat;
+    } else {
+        const TileF &tl = L.tilesF[idx];
+        q.p = pose_point_dd(P, tl.c);
+        q.a = pose_dir_dd(P, tl.n);
+        q.mat = tl.mat;
+    }
+    return q;
+}
+
+// FP64 value-only primitive posed from its body's pose record (chunk-base solve)
+DRT_HD Prim<double> load_prim_value(const LinkDev &L, const double *Pr, int type, int idx) {
+    Pose<double> P = load_pose<double>(Pr);
+    Prim<double> q;
+    q.type = type;
+    q.idx = idx;
+    if (type == T_R) {
+        const FaceD &f = L.faces[idx];
+        q.p = P.O + rot(P, f.c);
+        q.a = rot(P, f.n);
+        q.b = rot(P, f.u);
+        q.h1 = f.hu;
+        q.h2 = f.hw;
+        q.mat = f.mat;
+    } else if (type == T_D) {
+        const EdgeD &e = L.edges[idx];
+        q.p = P.O + rot(P, e.a);
+        q.a = rot(P, e.e);
+        q.b = rot(P, e.t0);
+        q.c = rot(P, e.n0);
+        q.h1 = e.len;
+        q.h2 = e.wn;
+        q.mat = e.mat;
+    } else {
+        const TileD &tl = L.tiles[idx];
+        q.p = P.O + rot(P, tl.c);
+        q.a = rot(P, tl.n);
+        q.mat = tl.mat;
+    }
+    return q;
+}
+
+// (path, chunk) FP64 anchors: path length and segment vectors at the chunk's first instant, phase
+// seed and per-bin step
+DRT_HD void path_base_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const double *pose64, int p,
+                           int chunk, BaseRec *out) {
+    const double tb = tg.t_start + (double)chunk * CHUNK * tg.dt;
+    const int n_chunks = (tg.n_steps + CHUNK - 1) / CHUNK;
+    uint32_t code = L.ptypes[p];
+    int4 pi = L.pprims[p];
+    int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
+    int n = 0;
+    Prim<double> pr[MAXI];
+    for (int j = 0; j < MAXI; ++j) {
+        int ty = (code >> (8 * j)) & 0xff;
+        if (ty != T_NONE) {
+            pr[j] = load_prim_value(L, pose_at(pose64, n_chunks, prim_body(L, ty, prim[j]), chunk), ty, prim[j]);
+            n = j + 1;
+        }
+    }
+    v3<double> V[MAXI + 2];
+    V[0] = val(terminal<double>(L.tx, tb));
+    V[n + 1] = val(terminal<double>(L.rx, tb));
+    uint32_t fl = 0;
+    solve_geometry(pr, n, V, L.ps0 + (size_t)p * MAXI, fl);
+    BaseRec r;
+    double d = 0.0;
+    for (int i = 0; i <= MAXI; ++i) r.seg[i][0] = r.seg[i][1] = r.seg[i][2] = 0.f;
+    for (int i = 1; i <= n + 1; ++i) {
+        v3<double> sg = V[i] - V[i - 1];
+        d += norm(sg);
+        r.seg[i - 1][0] = (float)sg.x;
+        r.seg[i - 1][1] = (float)sg.y;
+        r.seg[i - 1][2] = (float)sg.z;
+    }
+    double f0 = fg.fc - 0.5 * fg.bandwidth, df = fg.bandwidth / fg.n_bins;
+    double x = f0 * d / C0, y = df * d / C0;
+    double st = y - floor(y);
+    double hi = ldexp(rint(ldexp(st, 12)), -12);   // 12 leading bits: k * hi exact in FP32
+    r.d = d;
+    r.ph0 = (float)(x - floor(x));
+    r.st_hi = (float)hi;
+    r.st_lo = (float)(st - hi);
+    r.pad = 0.f;
+    out[(size_t)chunk * L.n_paths + p] = r;
+}
+
+DRT_HD void write_outputs_bulk(const OutD &o, size_t oi, int n, const v3<dd> *V, const v3<float> *seg, double tau,
+                               cx<float> a, float fd, uint32_t fl) {
+    if (o.tau) o.tau[oi] = tau;
+    if (o.amp) {
+        float *q = reinterpret_cast<float *>(o.amp) + 2 * oi;
+        q[0] = a.re;
+        q[1] = a.im;
+    }
+    if (o.doppler) reinterpret_cast<float *>(o.doppler)[oi] = fd;
+    if (o.angles) {
+        v3<float> kd = unit(seg[1]), ka = -unit(seg[n + 1]);
+        float *q = o.angles + 4 * oi;
+        q[0] = atan2f(kd.y, kd.x);
+        q[1] = atan2f(kd.z, hypotf(kd.x, kd.y));
+        q[2] = atan2f(ka.y, ka.x);
+        q[3] = atan2f(ka.z, hypotf(ka.x, ka.y));
+    }
+    if (o.flags) o.flags[oi] = (uint8_t)fl;
+    if (o.points) {
+        double *q = o.points + oi * (MAXI * 3);
+        const double qn = nan("");
+        for (int j = 0; j < MAXI; ++j) {
+            bool in = j < n;
+            q[3 * j + 0] = in ? (double)V[j + 1].x.b + (double)V[j + 1].x.d : qn;
+            q[3 * j + 1] = in ? (double)V[j + 1].y.b + (double)V[j + 1].y.d : qn;
+            q[3 * j + 2] = in ? (double)V[j + 1].z.b + (double)V[j + 1].z.d : qn;
+        }
+    }
+}
+
+// list of (path, step) pairs the FP32-bulk kernel hands to the FP64 redo kernel
+struct RedoList { int *count; int2 *items; int cap; };
+
+DRT_HD void path_step_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const PoseB *poseb,
+                           const BaseRec *base, int p, int ti, const OutD &out, const RecD &rec, const RedoList &redo) {
+    typedef float T;
+    const int n_chunks = (tg.n_steps + CHUNK - 1) / CHUNK;
+    const int chunk = ti / CHUNK;
+    const float tau_t = (float)((ti - chunk * CHUNK) * tg.dt);
+    uint32_t code = L.ptypes[p];
+    int4 pi = L.pprims[p];
+    int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
+    int n = 0;
+    Prim<dd> pr[MAXI];
+    for (int j = 0; j < MAXI; ++j) {
+        int ty = (code >> (8 * j)) & 0xff;
+        if (ty != T_NONE) {
+            pr[j] = load_prim_dd(L, poseb, n_chunks, chunk, tau_t, ty, prim[j]);
+            n = j + 1;
+        }
+    }
+    v3<dd> V[MAXI + 2];
+    V[0] = terminal_dd(poseb[(size_t)L.n_bodies * n_chunks + chunk], tau_t);
+    V[n + 1] = terminal_dd(poseb[(size_t)(L.n_bodies + 1) * n_chunks + chunk], tau_t);
+    uint32_t fl = 0;
+    solve_geometry(pr, n, V, L.ps0 + (size_t)p * MAXI, fl);
+    v3<T> P[MAXI + 2];
+    for (int i = 0; i <= n + 1; ++i) P[i] = val(V[i]);
+    fl |= validity(pr, n, P);
+    {
+        bool finite = true;
+        for (int i = 1; i <= n; ++i) finite = finite && isfinite(P[i].x) && isfinite(P[i].y) && isfinite(P[i].z);
+        if (!finite || (fl & (F_REDO64 | F_NOCONV | F_DEGEN))) {
+            // geometry FP32 cannot resolve: queue this path-step for the FP64 redo kernel (rare,
+            // see F_REDO64); the list holds every path-step in the worst case
+#ifdef __CUDA_ARCH__
+            int k = atomicAdd(redo.count, 1);
+#else
+            int k = (*redo.count)++;
+#endif
+            if (k < redo.cap) redo.items[k] = make_int2(p, ti);
+            return;
+        }
+    }
+    const BaseRec &B = base[(size_t)chunk * L.n_paths + p];
+    float dd_len = 0.f;   // change of the path length since the chunk base
+    v3<float> seg[MAXI + 2];
+    for (int i = 1; i <= n + 1; ++i) {
+        v3<dd> sv = V[i] - V[i - 1];
+        dd_len += norm(sv).d;
+        // segment vector: FP64-accurate base + FP32 delta
+        seg[i] = V3<float>(B.seg[i - 1][0] + sv.x.d, B.seg[i - 1][1] + sv.y.d, B.seg[i - 1][2] + sv.z.d);
+    }
+    cx<T> a = (fl & F_DEGEN) ? C<T>(T(0), T(0)) : amplitude(L, pr, n, seg, T(fg.fc));
+    if (out.tau || out.amp || out.doppler || out.angles || out.flags || out.points) {
+        T fd = doppler(n, V, seg, T(fg.fc));
+        size_t oi = (size_t)ti * L.n_paths + L.perm[p];
+        write_outputs_bulk(out, oi, n, V, seg, (B.d + (double)dd_len) / C0, a, fd, fl);
+    }
+    if (rec.rec_a) {
+        const float f0c = (float)((fg.fc - 0.5 * fg.bandwidth) / C0), dfc = (float)(fg.bandwidth / fg.n_bins / C0);
+        float x = f0c * dd_len;
+        x -= floorf(x);
+        float ph = B.ph0 + x;
+        ph -= floorf(ph);
+        float lo = fmaf(dfc, dd_len, B.st_lo);
+        float4 v;
+        v.x = fl ? 0.f : a.re;
+        v.y = fl ? 0.f : a.im;
+        v.z = ph;
+        v.w = B.st_hi;
+        size_t ri = (size_t)ti * L.n_paths + p;
+        rec.rec_a[ri] = v;
+        rec.rec_b[ri] = lo;
+    }
+}
+
+// FP64 redo of one queued FP32-bulk path-step (FP32 output formats)
+DRT_HD void path_step_redo(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, int p, int ti, const OutD &out,
+                           const RecD &rec) {
+    const double t = tg.t_start + ti * tg.dt;
+    path_step_fp64_core(L, tg, fg, p, ti, out, rec, true,
+                        [&](int ty, int idx) { return load_prim_direct<double>(L, t, ty, idx); });
 }
 
 }  // namespace drt

@@ -186,7 +186,7 @@ class Context:
         counts = (C.c_int64 * 4)()
         ms = (C.c_double * 4)()
         _check(load_library().drt_profile_read(self._h, counts, ms))
-        names = ("pose", "extrapolate", "synth", "other")
+        names = ("pose", "extrapolate", "synth", "base")
         return {names[k]: (int(counts[k]), float(ms[k])) for k in range(4)}
 
     def probe_peak(self, kind: int, blocks: int = 152 * 16) -> float:
