@@ -308,6 +308,50 @@ def scene_canyon(seed: int = 0, n_facades: int = 40, n_vehicles: int = 8, width:
     return b.build(tx, rx)
 
 
+def scene_link(seed: int = 0, n_facades: int = 24, tile_size: float = 3.0) -> Scene:
+    """A link of the batched workload: the tiny 28 GHz scene (fixed TX at (0,0,5), RX from
+    (50,0,1.5) at +10 m/s, concrete ground, one metal 4.5 x 1.8 x 1.5 m box at +15 m/s ahead of RX,
+    its start drawn in [58, 73] m) plus `n_facades` static building facades around the road
+    (8-30 m either side of it, 10-30 m long, 5-20 m high, +-20 deg yaw, eps_r ~ U[3,7],
+    sigma ~ U[0.01,0.1] S/m) with their end and roof wedge edges and ER tiles (S ~ U[0.2,0.5],
+    alpha_R in {2,4}) on which the extra paths of the link are drawn."""
+    rng = np.random.default_rng(5000 + seed)
+    b = _Builder(f"link-seed{seed}")
+    concrete = b.material(5.3, 0.1)
+    metal = b.material(1.0, 0.0, pec=True)
+    b.face(0, concrete, [0, 0, 0], [0, 0, 1], [1, 0, 0], math.inf, math.inf)
+    x0 = rng.uniform(58.0, 73.0)
+    centre = np.array([x0, 0.0, 0.75])
+    body = b.body(centre, [15.0, 0, 0], [0, 0, 0])
+    b.box(body, metal, centre, np.eye(3), (4.5, 1.8, 1.5))
+    for i in range(n_facades):
+        side = 1.0 if i % 2 == 0 else -1.0
+        length, height = rng.uniform(10, 30), rng.uniform(5, 20)
+        yaw = math.radians(rng.uniform(-20, 20))
+        mat = b.material(rng.uniform(3, 7), rng.uniform(0.01, 0.1))
+        R = _rot_z(yaw)
+        u = R @ np.array([1.0, 0, 0])
+        n = R @ np.array([0, -side, 0])          # facing the road
+        up = np.array([0.0, 0.0, 1.0])
+        centre = np.array([rng.uniform(-20, 110), side * rng.uniform(8, 30), 0.5 * height])
+        b.face(0, mat, centre, n, u, 0.5 * length, 0.5 * height)
+        lo, hi = centre - 0.5 * height * up, centre + 0.5 * height * up
+        for s_end in (-1.0, 1.0):
+            off = s_end * 0.5 * length * u
+            b.edge(0, mat, lo + off, hi + off, n, s_end * u)
+        b.edge(0, mat, hi - 0.5 * length * u, hi + 0.5 * length * u, n, up)
+        nu = max(1, int(round(length / tile_size)))
+        nw = max(1, int(round(height / tile_size)))
+        for iu in range(nu):
+            for iw in range(nw):
+                c = centre + ((iu + 0.5) / nu - 0.5) * length * u + ((iw + 0.5) / nw - 0.5) * height * up
+                b.tile(0, mat, c, n, (length / nu) * (height / nw), rng.uniform(0.2, 0.5),
+                       float(rng.choice([2.0, 4.0])), rng.uniform(0, 2 * math.pi))
+    tx = ([0.0, 0.0, 5.0], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0])
+    rx = ([50.0, 0.0, 1.5], [10.0, 0.0, 0.0], [0.0, 0.0, 0.0])
+    return b.build(tx, rx)
+
+
 def draw_chain_types(rng, p_types=(0.6, 0.2, 0.2), lengths=(1, 2, 3)):
     """Interaction types of one chain: length uniform on `lengths`, types i.i.d. R:D:S."""
     n = int(rng.choice(lengths))
@@ -348,6 +392,23 @@ WORKLOADS = {
     "canyon": dict(scene=scene_canyon, fc=60e9, bandwidth=1e9, n_bins=512, dt=0.5e-3,
                    n_steps=2000, n_paths=512),
 }
+
+
+# the batched workload: `n_links` links of scene_link(seed % LINK_SCENES) with the first P paths of
+# that scene's path set, P log-uniform in [8, 2048], horizons uniform in [100, 5000] steps of 1 ms,
+# 256 bins over 400 MHz at 28 GHz
+LINK_SCENES = 4
+BATCH = dict(fc=28e9, bandwidth=400e6, n_bins=256, dt=1e-3, p_range=(8, 2048), t_range=(100, 5000))
+
+
+def batch_links(n_links: int, seed: int = 0, p_range=None, t_range=None):
+    """Per link of the batched workload: (scene index, path count P, horizon T), seeded."""
+    rng = np.random.default_rng(9000 + seed)
+    p_lo, p_hi = p_range or BATCH["p_range"]
+    t_lo, t_hi = t_range or BATCH["t_range"]
+    P = np.exp(rng.uniform(math.log(p_lo), math.log(p_hi), n_links)).astype(np.int64)
+    T = rng.integers(t_lo, t_hi + 1, n_links)
+    return [(i % LINK_SCENES, int(max(p_lo, min(p_hi, P[i]))), int(T[i])) for i in range(n_links)]
 
 
 def grids(workload: str, n_steps: int | None = None, n_bins: int | None = None):

@@ -41,13 +41,21 @@ def keep_valid_at_t0(scene, ps, fc, n_threads=8):
     return out
 
 
-def canyon_pathset(seed, n_paths=512, tries=60000, batch=3000, fc=60e9):
-    scene = I.scene_canyon(seed)
-    rng = np.random.default_rng(77 + seed)
-    kept = [keep_valid_at_t0(scene, I.chains_to_pathset([[]]), fc)]       # line of sight
-    n = 1
+def chain_key(ps, p):
+    return tuple((int(ps.types[p, j]), int(ps.prims[p, j])) for j in range(int(ps.n_int[p])))
+
+
+def drawn_pathset(scene, rng, n_paths, fc, kept=None, tries=60000, batch=3000):
+    """Fill up to n_paths with drawn chains valid at t0; a chain already in the set is not taken
+    again (a ray-tracing run finds each ray once)."""
+    kept = kept or [keep_valid_at_t0(scene, I.chains_to_pathset([[]]), fc)]       # line of sight
+    seen = {chain_key(k, p) for k in kept for p in range(k.n_paths)}
+    n = sum(k.n_paths for k in kept)
+    exhausted = set()
     while n < n_paths:
         types = I.draw_chain_types(rng)
+        if tuple(types) in exhausted:      # no fresh valid chain left for this type sequence
+            continue
         found = None
         for _ in range(tries // batch):
             chains, s0s = [], []
@@ -60,13 +68,32 @@ def canyon_pathset(seed, n_paths=512, tries=60000, batch=3000, fc=60e9):
             for i, s in enumerate(s0s):
                 ps.s0[i, :len(s)] = s
             v = keep_valid_at_t0(scene, ps, fc)
-            if v.n_paths:
-                found = v.subset([0])
+            fresh = [p for p in range(v.n_paths) if chain_key(v, p) not in seen]
+            if fresh:
+                found = v.subset([fresh[0]])
                 break
-        if found is not None:
+        if found is None:
+            exhausted.add(tuple(types))
+        else:
             kept.append(found)
+            seen.add(chain_key(found, 0))
             n += 1
-    return scene, I.PathSet.concat(kept)
+            if n % 256 == 0:
+                print(f"  {n} chains", flush=True)
+    return I.PathSet.concat(kept)
+
+
+def canyon_pathset(seed, n_paths=512, fc=60e9):
+    scene = I.scene_canyon(seed)
+    return scene, drawn_pathset(scene, np.random.default_rng(77 + seed), n_paths, fc)
+
+
+def link_pathset(seed, n_paths=2048, fc=28e9):
+    """Links of the batched workload: LoS and the valid reflections of order <= 2 of the tiny
+    geometry first, then drawn R:D:S chains on the facades.  A link of P paths takes the first P."""
+    scene = I.scene_link(seed)
+    base = keep_valid_at_t0(scene, I.chains_tiny(scene), fc)
+    return scene, drawn_pathset(scene, np.random.default_rng(177 + seed), n_paths, fc, kept=[base])
 
 
 def tiny_pathset(seed, fc=28e9):
@@ -79,6 +106,12 @@ def main():
         scene, ps = tiny_pathset(seed)
         ps.to_npz(os.path.join(HERE, f"pathset_tiny_seed{seed}.npz"))
         print(f"tiny seed {seed}: {ps.n_paths} paths")
+    for seed in range(I.LINK_SCENES):
+        scene, ps = link_pathset(seed)
+        ps.to_npz(os.path.join(HERE, f"pathset_link_seed{seed}.npz"))
+        print(f"link seed {seed}: {ps.n_paths} paths")
+    if "--links-only" in sys.argv:
+        return
     scene, ps = canyon_pathset(0)
     ps.to_npz(os.path.join(HERE, "pathset_canyon_seed0.npz"))
     sig = {}

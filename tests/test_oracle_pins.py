@@ -167,8 +167,11 @@ def test_drt_equals_snapshot_resolve(which):
     assert rel[ok].max() < 1e-12
     dp = np.abs(a["pts"] - b["pts"])[ok]
     assert np.nanmax(dp) < 1e-8
+    # 5-point finite differences of the re-solve (h = 1 ms) truncate at ~1e-5 of the point's own
+    # speed where a diffraction point slides fast (hundreds of m/s near grazing)
     dv = np.abs(a["vel"] - b["vel"])[ok]
-    assert np.nanmax(dv) < 1e-5          # 5-point finite differences of the re-solve, h = 1 ms
+    vmag = np.maximum(1.0, np.abs(b["vel"]))[ok]
+    assert np.nanmax(dv / vmag) < 1e-5
     far = ok & (np.minimum(a["margin"], b["margin"]) > 1e-9)
     assert np.array_equal(a["flags"][far], b["flags"][far])
     va = ok & (a["flags"] == 0)
@@ -320,23 +323,27 @@ def test_reciprocity_of_reflection_and_diffraction_chains():
     diffractions leaves the length, the delay and the complex amplitude unchanged.  (Luebbers'
     lossy-wedge heuristic weights the two reflection terms by face coefficients taken at the source
     and observer angles respectively, so it is not reciprocal; those chains are left out.)"""
-    sc, ps = canyon()
-    keep = [p for p in range(ps.n_paths) if ps.n_int[p] > 0 and T_S_free(ps, p) and pec_wedges(sc, ps, p)]
-    sub = ps.subset(keep)
-    rev = I.empty_paths(sub.n_paths)
-    for p in range(sub.n_paths):
-        n = int(sub.n_int[p])
-        rev.n_int[p] = n
-        rev.types[p, :n] = sub.types[p, :n][::-1]
-        rev.prims[p, :n] = sub.prims[p, :n][::-1]
-        rev.s0[p, :n] = sub.s0[p, :n][::-1]
-    sw = I.Scene(sc.name, sc.rx.copy(), sc.tx.copy(), sc.bodies, sc.materials, sc.faces, sc.edges, sc.tiles)
-    a = O.extrapolate(sc, sub, I.TimeGrid(0.2, 1, 1), 60e9, n_threads=8)
-    b = O.extrapolate(sw, rev, I.TimeGrid(0.2, 1, 1), 60e9, n_threads=8)
-    ok = (a["flags"][0] == 0) & (b["flags"][0] == 0)
-    assert ok.sum() > 150
-    assert np.abs(a["tau"][0] - b["tau"][0])[ok].max() < 1e-12 * a["tau"][0].max()
-    assert (np.abs(a["a"][0] - b["a"][0]) <= 1e-9 * np.abs(a["a"][0]))[ok].all()
+    total = 0
+    cases = [canyon() + (60e9,)] + [(I.scene_link(k), I.PathSet.from_npz(
+        os.path.join(GOLD, f"pathset_link_seed{k}.npz")), 28e9) for k in range(I.LINK_SCENES)]
+    for sc, ps, fc in cases:
+        keep = [p for p in range(ps.n_paths) if ps.n_int[p] > 0 and T_S_free(ps, p) and pec_wedges(sc, ps, p)]
+        sub = ps.subset(keep)
+        rev = I.empty_paths(sub.n_paths)
+        for p in range(sub.n_paths):
+            n = int(sub.n_int[p])
+            rev.n_int[p] = n
+            rev.types[p, :n] = sub.types[p, :n][::-1]
+            rev.prims[p, :n] = sub.prims[p, :n][::-1]
+            rev.s0[p, :n] = sub.s0[p, :n][::-1]
+        sw = I.Scene(sc.name, sc.rx.copy(), sc.tx.copy(), sc.bodies, sc.materials, sc.faces, sc.edges, sc.tiles)
+        a = O.extrapolate(sc, sub, I.TimeGrid(0.2, 1, 1), fc, n_threads=8)
+        b = O.extrapolate(sw, rev, I.TimeGrid(0.2, 1, 1), fc, n_threads=8)
+        ok = (a["flags"][0] == 0) & (b["flags"][0] == 0)
+        total += ok.sum()
+        assert np.abs(a["tau"][0] - b["tau"][0])[ok].max() < 1e-12 * a["tau"][0].max()
+        assert (np.abs(a["a"][0] - b["a"][0]) <= 1e-9 * np.abs(a["a"][0]))[ok].all()
+    assert total > 150
 
 
 def T_S_free(ps, p):
