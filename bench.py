@@ -56,6 +56,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-links", type=int, default=4096, help="links of the batched workload (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="measured serving window (0: skip)")
+    ap.add_argument("--serve-warmup", type=float, default=2.0)
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
     return ap.parse_args()
 
 
@@ -165,6 +170,136 @@ def run_reference(args):
                              "sample": f"{paths.n_paths} paths x {n_sub} consecutive steps per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def run_batched(args, ctx, drt, flush):
+    """The batched FP32-bulk form over `--batch-links` uneven links (log-uniform 8..2048 paths,
+    horizons uniform 100..5000 x 1 ms, 256 bins at 28 GHz): one drt_batch_run per step, replayed
+    from its CUDA graph."""
+    import torch
+    w = I.BATCH
+    spec = I.batch_links(args.batch_links, seed=0)
+    sets = [(I.scene_link(k), I.PathSet.from_npz(os.path.join(ROOT, "tests", "golden", f"pathset_link_seed{k}.npz")))
+            for k in range(I.LINK_SCENES)]
+    t0 = time.perf_counter()
+    loaded, links, tgs, fgs, Hs = {}, [], [], [], []
+    for k, P, T in spec:
+        if (k, P) not in loaded:
+            loaded[(k, P)] = ctx.load(sets[k][0], sets[k][1].subset(np.arange(P)))
+        links.append(loaded[(k, P)])
+        tgs.append(I.TimeGrid(0.0, w["dt"], T))
+        fgs.append(I.FreqGrid(w["fc"], w["bandwidth"], w["n_bins"]))
+        Hs.append(torch.empty((T, w["n_bins"]), dtype=torch.complex64, device="cuda"))
+    load_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b = ctx.batch(links, tgs, fgs, Hs)
+    plan_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup if args.warmup < 3 else 3)):
+        b.run(use_graph=True)
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.batch_steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run(use_graph=True)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    total_s = sum(a.elapsed_time(c) for a, c in evs) * 1e-3
+    info = b.info(redo=True)
+    ps_steps = sum(P * T for _, P, T in spec)
+    h_samples = sum(T for _, _, T in spec) * w["n_bins"]
+    out = {"value": ps_steps * args.batch_steps / total_s, "unit": UNIT,
+           "h_samples_per_s": h_samples * args.batch_steps / total_s,
+           "terms_per_s": ps_steps * w["n_bins"] * args.batch_steps / total_s,
+           "ms_per_step": 1e3 * total_s / args.batch_steps, "steps": args.batch_steps,
+           "workload": f"{len(spec)} links, paths log-U[8,2048] (mean {np.mean([p for _, p, _ in spec]):.0f}), "
+                       f"steps U[100,5000] x 1 ms (mean {np.mean([t for _, _, t in spec]):.0f}), "
+                       f"{w['n_bins']} bins over 400 MHz at 28 GHz",
+           "path_steps_per_step": ps_steps, "precision": "DRT_FP32_BULK", "graph": True,
+           "fused_variant": info["variant"], "scratch_gb": info["scratch_bytes"] / 1e9,
+           "redo_steps_per_step": info["redo_steps"], "load_s": load_s, "plan_and_autotune_s": plan_s,
+           "l2": "flushed by a 256 MB write between timed steps (outside the events)"}
+    b.close()
+    del Hs
+    for lk in loaded.values():
+        lk.unload()
+    return out
+
+
+def run_serving(args, drt):
+    """Poisson-arriving prediction requests on resident canyon links (512, 128 and 32 paths),
+    horizons U{50..500} x 1 ms from random start times, 512 bins at 60 GHz, HBM budget 64 GB."""
+    import torch
+    ctx = drt.Context(torch.cuda.current_device(), hbm_budget=64 << 30)
+    scene = I.scene_canyon(0)
+    paths = I.PathSet.from_npz(PATHSET)
+    links = [ctx.load(scene, paths), ctx.load(scene, paths.subset(np.arange(128))),
+             ctx.load(scene, paths.subset(np.arange(32)))]
+    weights = np.array([0.6, 0.25, 0.15])
+    ctx.serve_start(0, 4, 256)
+    F, ring = 512, 2048
+    bufs = [torch.empty((500, F), dtype=torch.complex64, device="cuda") for _ in range(ring)]
+    rng = np.random.default_rng(11)
+    duration = args.serve_warmup + args.serve_seconds
+    n_req = int(args.serve_rate * duration * 1.2) + 16
+    gaps = rng.exponential(1.0 / args.serve_rate, n_req)
+    arrivals = np.cumsum(gaps)
+    arrivals = arrivals[arrivals < duration]
+    li = rng.choice(len(links), len(arrivals), p=weights)
+    hor = rng.integers(50, 501, len(arrivals))
+    t_starts = rng.integers(0, 1000, len(arrivals)) * 1e-3
+    tickets = [None] * len(arrivals)
+    results = [None] * len(arrivals)
+    fg = I.FreqGrid(60e9, 1e9, F)
+    done_upto = [0]
+
+    def collector():
+        for i in range(len(arrivals)):
+            while tickets[i] is None:
+                time.sleep(1e-4)
+            results[i] = ctx.wait(tickets[i], 60000)
+            done_upto[0] = i + 1
+
+    th = threading.Thread(target=collector, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    for i, ta in enumerate(arrivals):
+        while time.perf_counter() - t0 < ta:
+            pass
+        while i - done_upto[0] >= ring - 1:      # the ring buffer slot is still in use
+            time.sleep(1e-4)
+        H = bufs[i % ring][:hor[i]]
+        tickets[i] = ctx.submit(links[li[i]], I.TimeGrid(float(t_starts[i]), 1e-3, int(hor[i])), fg, H)
+    th.join()
+    t_end = time.perf_counter() - t0
+    stats = ctx.serve_stats()
+    ctx.serve_stop()
+    n_paths = np.array([lk.n_paths for lk in links])
+    sub = np.array([r["t_submit"] for r in results])
+    t_first = sub.min()
+    meas = (sub - t_first) >= args.serve_warmup
+    lat = np.array([r["latency"] for r in results])[meas] * 1e3
+    done_t = np.array([r["t_done"] for r in results])
+    ps = (n_paths[li] * hor)[meas]
+    span = done_t[meas].max() - sub[meas].min()
+    ok = all(r["status"] == 0 for r in results)
+    for lk in links:
+        lk.unload()
+    ctx.close()
+    return {"requests": int(meas.sum()), "offered_req_per_s": args.serve_rate,
+            "achieved_req_per_s": meas.sum() / span, "value": ps.sum() / span, "unit": UNIT,
+            "h_samples_per_s": (hor[meas] * F).sum() / span,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
+                           "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
+            "mean_batch_requests": float(np.mean([r["batch_requests"] for r in results])),
+            "launches": stats["launches"], "arena_peak_gb": stats["arena_peak"] / 1e9, "all_ok": ok,
+            "window_s": args.serve_seconds, "warmup_s": args.serve_warmup, "wall_s": t_end,
+            "workload": "Poisson arrivals; canyon links of 512/128/32 paths (p = 0.6/0.25/0.15); horizons "
+                        "U{50..500} x 1 ms from t_start U[0,1) s; 512 bins over 1 GHz at 60 GHz; FP32-bulk; "
+                        "HBM budget 64 GB"}
 
 
 def run_ours(args):
@@ -296,6 +431,10 @@ def run_ours(args):
                             "traffic": None, "note": "per-path-step FLOP count not yet measured"}
     probe = ctx.probe_peak(0)
     line["roofline"]["probe_fp64_tflops"] = probe / 1e12
+    if args.batch_links > 0:
+        line["batched"] = run_batched(args, ctx, drt, flush)
+    if args.serve_seconds > 0:
+        line["serving"] = run_serving(args, drt)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, paths, tg, fg, n_steps=400)
     link.unload()

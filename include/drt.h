@@ -191,6 +191,80 @@ drt_status drt_synthesize_H_noalloc(drt_ctx *ctx, uint64_t link, const drt_time_
                                     const drt_freq_grid *fgrid, void *H, int32_t precision,
                                     void *stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * a10: batched synthesis over many resident links (FP32-bulk form).  drt_batch_create plans one
+ * batch: link i is synthesised over tgrids[i] x fgrids[i] into the caller's DEVICE buffer H[i]
+ * ([n_steps][n_bins] complex64).  Each stage (base poses, FP64 chunk poses, multi-diffraction warm
+ * starts, FP64 chunk anchors, fused extrapolation + synthesis, FP64 redo) is one persistent launch
+ * over the (link, work unit) pairs of all links, claimed with atomic counters, largest links first,
+ * so uneven links (8 to thousands of paths, 100 to thousands of steps) share one launch per stage.
+ * The chunk length per link comes from a phase-error model and the fused kernel's shape (warps per
+ * block, frequency bins per thread) from timing its variants on the batch (autotuning, done
+ * synchronously inside drt_batch_create).  Scratch is allocated once per batch within the HBM
+ * budget.  The links must stay loaded and the H buffers valid while the batch exists.
+ * drt_batch_run launches the batch on `stream`; with use_graph != 0 the first run is captured into
+ * a CUDA graph (captured on a stream of the batch, so any stream can replay it) and later runs
+ * replay it.  precision must be DRT_FP32_BULK.
+ * Errors: DRT_EINVAL, DRT_ENOTFOUND, DRT_ENOMEM, DRT_ECUDA. */
+typedef struct drt_batch drt_batch;
+drt_status drt_batch_create(drt_ctx *ctx, int32_t n_links, const uint64_t *links,
+                            const drt_time_grid *tgrids, const drt_freq_grid *fgrids, void *const *H,
+                            int32_t precision, drt_batch **out);
+drt_status drt_batch_run(drt_ctx *ctx, drt_batch *batch, int32_t use_graph, void *stream);
+/* chosen fused-kernel variant (0: 8 warps x 32 bins, 1: 8 x 16, 2: 4 x 32, 3: 4 x 16), scratch
+ * bytes, the autotuner's best sample time (ms) and the path-steps of the last run that FP32 could
+ * not resolve and the FP64 redo kernel recomputed (reading it waits for the device); any output
+ * may be NULL */
+drt_status drt_batch_info(drt_ctx *ctx, const drt_batch *batch, int32_t *variant,
+                          uint64_t *scratch_bytes, float *tune_ms, int64_t *redo_steps);
+void drt_batch_destroy(drt_ctx *ctx, drt_batch *batch);
+
+/* ---------------------------------------------------------------------------------------------
+ * a11: serving.  The context runs one serving thread that takes anticipative-prediction requests
+ * (Sec. II: the multipath of a loaded link predicted over [t_start, t_start + n_steps dt)) from
+ * any thread, admits them by HBM footprint into an arena of `pool_bytes` reserved within the
+ * context's budget, and batches whatever is queued whenever one of `n_slots` streams is free
+ * (continuous batching, at most `max_batch` requests per launch), so requests that arrive while
+ * others run start as soon as a slot and arena memory free up and overlap with them on the device.
+ * Requests run the FP32-bulk batched form (drt_batch_create); each result depends only on its own
+ * request, not on the batch it ran in.  drt_serve_start is optional: the first drt_submit starts
+ * the loop with pool_bytes = min(half the free budget, 16 GiB), 4 slots, 256 requests per launch.
+ * Errors: DRT_EINVAL, DRT_EBUSY (already started), DRT_ENOMEM (arena beyond the budget),
+ * DRT_ECUDA. */
+typedef struct {
+    uint64_t link;
+    drt_time_grid tgrid;
+    drt_freq_grid fgrid;
+    void *H;                    /* DEVICE [n_steps][n_bins] complex64, caller-owned, required    */
+    drt_path_outputs records;   /* optional DEVICE records [n_steps][n_paths] in the FP32-bulk    */
+                                /* formats (tau double, amp float[2], doppler float); NULL = skip */
+    int32_t precision;          /* DRT_FP32_BULK                                                  */
+    int32_t reserved;
+} drt_request;
+typedef struct {
+    drt_status status;          /* DRT_OK, DRT_ENOMEM (larger than the arena) or DRT_ECUDA       */
+    int32_t batch_requests;     /* requests in the launch that served this one                    */
+    double t_submit, t_launch, t_done;   /* seconds on the library's steady clock                 */
+} drt_result;
+typedef struct {
+    uint64_t submitted, completed, launches, queued, in_flight;
+    uint64_t arena_bytes, arena_used, arena_peak;
+} drt_serve_stats;
+drt_status drt_serve_start(drt_ctx *ctx, uint64_t pool_bytes, int32_t n_slots, int32_t max_batch);
+/* finishes every submitted request, then ends the loop and frees the arena (drt_destroy calls it) */
+drt_status drt_serve_stop(drt_ctx *ctx);
+/* copies the request and returns a ticket at once; the link must stay loaded (drt_unload answers
+ * DRT_EBUSY while it has pending requests) and H / records valid until the request is done.
+ * Errors: DRT_EINVAL, DRT_ENOTFOUND (link), DRT_ECUDA (the serving loop failed earlier). */
+drt_status drt_submit(drt_ctx *ctx, const drt_request *req, uint64_t *out_ticket);
+/* *done = 1 and *res filled once the request is finished (the ticket is then retired; res may
+ * be NULL); *done = 0 while pending.  Errors: DRT_ENOTFOUND (unknown or retired ticket). */
+drt_status drt_poll(drt_ctx *ctx, uint64_t ticket, int32_t *done, drt_result *res);
+/* blocks until the request is finished (DRT_OK, ticket retired) or timeout_ms passes
+ * (DRT_ETIMEOUT, ticket kept).  Errors: DRT_ENOTFOUND, DRT_ETIMEOUT. */
+drt_status drt_wait(drt_ctx *ctx, uint64_t ticket, uint32_t timeout_ms, drt_result *res);
+drt_status drt_serve_stats_read(drt_ctx *ctx, drt_serve_stats *out);
+
 /* Number of paths of a link (for sizing outputs).  Errors: DRT_ENOTFOUND. */
 drt_status drt_link_info(drt_ctx *ctx, uint64_t link, int32_t *n_paths);
 

@@ -7,7 +7,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -40,6 +42,8 @@ drt_status fail(drt_status code, const char *fmt, ...) {
 
 struct Link {
     LinkDev dev;
+    drt_scene_view view{};
+    std::shared_ptr<std::atomic<int>> inflight = std::make_shared<std::atomic<int>>(0);   // serving
     std::vector<void *> allocs;
     size_t bytes = 0;
     int32_t n_paths = 0;
@@ -69,6 +73,10 @@ struct drt_ctx {
     bool profiling = false;
     struct Mark { int kind; cudaEvent_t a, b; };
     std::vector<Mark> marks;
+    // a11 serving loop and its arena
+    Server *server = nullptr;
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
 };
 
 namespace {
@@ -212,7 +220,9 @@ Link *find_link(drt_ctx *c, uint64_t id) {
     return it == c->links.end() ? nullptr : &it->second;
 }
 
-TimeGridD tgd(const drt_time_grid *g) { return TimeGridD{g->t_start, g->dt, g->n_steps}; }
+// default chunk: 16 steps (FP32-bulk anchors); the batch planner may choose another from its
+// phase-error model
+TimeGridD tgd(const drt_time_grid *g, int chunk = 16) { return TimeGridD{g->t_start, g->dt, g->n_steps, chunk}; }
 FreqGridD fgd(const drt_freq_grid *g) { return FreqGridD{g->fc, g->bandwidth, g->n_bins}; }
 
 // bracket one launch with events when tracing is on
@@ -303,6 +313,17 @@ drt_status synth_into(drt_ctx *c, Link &L, const drt_time_grid *tg, const drt_fr
 // validated host-side structure-of-arrays image of one link (device pointers unset)
 drt_status drt::pack_link(const drt_scene *s, const drt_path_set *ps, PackedLink &H) {
     if (drt_status st = validate(s, ps)) return st;
+    {
+        auto n3 = [](const double *x) { return std::sqrt(dot3(x, x)); };
+        drt_scene_view v{std::max(n3(s->tx.v), n3(s->rx.v)), std::max(n3(s->tx.a), n3(s->rx.a)), 0.0};
+        for (int i = 0; i < s->n_bodies; ++i) {
+            const drt_body &b = s->bodies[i];
+            v.vmax = std::max(v.vmax, n3(b.v));
+            v.amax = std::max(v.amax, n3(b.a));
+            v.wmax = std::max(v.wmax, std::fabs(b.w0) + std::fabs(b.wdot));
+        }
+        H.view = v;
+    }
     LinkDev &d = H.dev;
     d.n_paths = ps->n_paths;
     d.n_bodies = s->n_bodies;
@@ -505,6 +526,7 @@ drt_status drt_create(drt_ctx **out, int32_t device, uint64_t hbm_budget_bytes) 
 
 void drt_destroy(drt_ctx *c) {
     if (!c) return;
+    drt_serve_stop(c);
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     for (auto &kv : c->links)
@@ -532,6 +554,7 @@ drt_status drt_load_paths(drt_ctx *c, const drt_scene *s, const drt_path_set *ps
     CUDA_TRY(cudaSetDevice(c->device));
     Link L;
     L.dev = H.dev;
+    L.view = H.view;
     L.n_paths = ps->n_paths;
     LinkDev &d = L.dev;
     drt_status st = DRT_OK;
@@ -563,6 +586,8 @@ drt_status drt_unload(drt_ctx *c, uint64_t link) {
     std::lock_guard<std::mutex> lk(c->mu);
     Link *L = find_link(c, link);
     if (!L) return fail(DRT_ENOTFOUND, "unknown link %llu", (unsigned long long)link);
+    if (L->inflight->load() > 0)
+        return fail(DRT_EBUSY, "link %llu has %d pending requests", (unsigned long long)link, L->inflight->load());
     CUDA_TRY(cudaSetDevice(c->device));
     CUDA_TRY(cudaDeviceSynchronize());
     for (void *p : L->allocs) cudaFree(p);
@@ -727,5 +752,206 @@ extern "C" drt_status drt_synthesize_H_noalloc(drt_ctx *c, uint64_t link, const 
     CUDA_TRY(launch_pose(L->dev, t, pose, s));
     CUDA_TRY(launch_extrapolate_fp64(L->dev, t, f, pose, none, rec, s));
     CUDA_TRY(launch_synth(rec, L->n_paths, t, f, reinterpret_cast<float2 *>(H), s));
+    return DRT_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// a10: batches of links
+struct drt_batch {
+    drt::BatchPlan *plan = nullptr;
+    size_t bytes = 0;
+    int32_t n_links = 0;
+    float tune_ms = 0.f;
+};
+
+extern "C" drt_status drt_batch_create(drt_ctx *c, int32_t n_links, const uint64_t *links, const drt_time_grid *tgrids,
+                                       const drt_freq_grid *fgrids, void *const *H, int32_t precision,
+                                       drt_batch **out) {
+    if (!c || !out || n_links < 0 || (n_links && (!links || !tgrids || !fgrids || !H)))
+        return fail(DRT_EINVAL, "batch: NULL or negative argument");
+    if (precision != DRT_FP32_BULK)
+        return fail(DRT_EINVAL, "batched synthesis runs the FP32-bulk form (DRT_FP32_BULK); use drt_synthesize_H "
+                                "per link for DRT_FP64");
+    *out = nullptr;
+    std::lock_guard<std::mutex> lk(c->mu);
+    std::vector<const LinkDev *> devs(n_links);
+    std::vector<drt_scene_view> views(n_links);
+    for (int i = 0; i < n_links; ++i) {
+        if (drt_status st = check_grids(&tgrids[i], &fgrids[i], precision)) return st;
+        Link *L = find_link(c, links[i]);
+        if (!L) return fail(DRT_ENOTFOUND, "batch: unknown link %llu", (unsigned long long)links[i]);
+        if (!H[i] && tgrids[i].n_steps > 0) return fail(DRT_EINVAL, "batch: H[%d] is NULL", i);
+        devs[i] = &L->dev;
+        views[i] = L->view;
+    }
+    CUDA_TRY(cudaSetDevice(c->device));
+    BatchPlan *P = nullptr;
+    size_t bytes = 0;
+    CUDA_TRY(batch_build(devs, views, tgrids, fgrids, H, nullptr, &P, &bytes));
+    if (c->budget && c->used + bytes > c->budget) {
+        batch_free(P);
+        return fail(DRT_ENOMEM, "batch needs %zu bytes of scratch; HBM budget %llu, in use %llu", bytes,
+                    (unsigned long long)c->budget, (unsigned long long)c->used);
+    }
+    cudaError_t e = batch_alloc(P);
+    if (e != cudaSuccess) {
+        batch_free(P);
+        return fail(DRT_ENOMEM, "batch allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    }
+    c->used += bytes;
+    drt_batch *b = new drt_batch();
+    b->plan = P;
+    b->bytes = bytes;
+    b->n_links = n_links;
+    e = batch_autotune(P, c->side[0], &b->tune_ms);
+    if (e != cudaSuccess) {
+        c->used -= bytes;
+        batch_free(P);
+        delete b;
+        return fail(DRT_ECUDA, "batch autotune: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return DRT_OK;
+}
+
+extern "C" drt_status drt_batch_run(drt_ctx *c, drt_batch *b, int32_t use_graph, void *stream) {
+    if (!c || !b) return fail(DRT_EINVAL, "ctx and batch must be non-NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    CUDA_TRY(cudaSetDevice(c->device));
+    CUDA_TRY(batch_run(b->plan, (cudaStream_t)stream, use_graph != 0));
+    return DRT_OK;
+}
+
+extern "C" drt_status drt_batch_info(drt_ctx *c, const drt_batch *b, int32_t *variant, uint64_t *scratch_bytes,
+                                     float *tune_ms, int64_t *redo_steps) {
+    if (!c || !b) return fail(DRT_EINVAL, "ctx and batch must be non-NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (variant) *variant = batch_variant(b->plan);
+    if (scratch_bytes) *scratch_bytes = b->bytes;
+    if (tune_ms) *tune_ms = b->tune_ms;
+    if (redo_steps) {
+        long long n = 0;
+        CUDA_TRY(cudaSetDevice(c->device));
+        CUDA_TRY(cudaDeviceSynchronize());
+        CUDA_TRY(batch_redo_count(b->plan, &n));
+        *redo_steps = n;
+    }
+    return DRT_OK;
+}
+
+extern "C" void drt_batch_destroy(drt_ctx *c, drt_batch *b) {
+    if (!c || !b) return;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    batch_free(b->plan);
+    c->used -= b->bytes;
+    delete b;
+}
+
+// ---------------------------------------------------------------------------------------------
+// a11: serving
+static drt_status serve_start_locked(drt_ctx *c, uint64_t pool_bytes, int32_t n_slots, int32_t max_batch) {
+    if (c->server) return fail(DRT_EBUSY, "the serving loop is already running");
+    if (n_slots < 1 || n_slots > 16 || max_batch < 1) return fail(DRT_EINVAL, "1 <= n_slots <= 16, max_batch >= 1");
+    if (!pool_bytes) {   // half of what the budget leaves, at most 16 GiB
+        const uint64_t cap = 16ull << 30;
+        pool_bytes = c->budget ? std::min<uint64_t>(cap, c->budget > c->used ? (c->budget - c->used) / 2 : 0) : cap;
+    }
+    if (pool_bytes < (1u << 20)) return fail(DRT_ENOMEM, "no HBM budget left for the serving arena");
+    CUDA_TRY(cudaSetDevice(c->device));
+    void *arena = nullptr;
+    if (drt_status st = dev_alloc(c, pool_bytes, &arena)) return st;
+    Server *S = server_start(c->device, arena, pool_bytes, n_slots, max_batch);
+    if (!S) {
+        dev_free(c, arena, pool_bytes);
+        return fail(DRT_ECUDA, "serving streams could not be created");
+    }
+    c->server = S;
+    c->arena = arena;
+    c->arena_bytes = pool_bytes;
+    return DRT_OK;
+}
+
+extern "C" drt_status drt_serve_start(drt_ctx *c, uint64_t pool_bytes, int32_t n_slots, int32_t max_batch) {
+    if (!c) return fail(DRT_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    return serve_start_locked(c, pool_bytes, n_slots, max_batch);
+}
+
+extern "C" drt_status drt_serve_stop(drt_ctx *c) {
+    if (!c) return fail(DRT_EINVAL, "ctx is NULL");
+    Server *S;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        S = c->server;
+        c->server = nullptr;
+    }
+    if (!S) return DRT_OK;
+    server_stop(S);   // without the ctx lock: completions need none, waiters may hold none
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    dev_free(c, c->arena, c->arena_bytes);
+    c->arena = nullptr;
+    c->arena_bytes = 0;
+    return DRT_OK;
+}
+
+extern "C" drt_status drt_submit(drt_ctx *c, const drt_request *req, uint64_t *out_ticket) {
+    if (!c || !req || !out_ticket) return fail(DRT_EINVAL, "ctx, req and out_ticket must be non-NULL");
+    if (req->precision != DRT_FP32_BULK) return fail(DRT_EINVAL, "served requests run the FP32-bulk form");
+    if (drt_status st = check_grids(&req->tgrid, &req->fgrid, req->precision)) return st;
+    if (!req->H && req->tgrid.n_steps > 0) return fail(DRT_EINVAL, "request H is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    Link *L = find_link(c, req->link);
+    if (!L) return fail(DRT_ENOTFOUND, "unknown link %llu", (unsigned long long)req->link);
+    if (!c->server)
+        if (drt_status st = serve_start_locked(c, 0, 4, 256)) return st;
+    std::string msg;
+    if (server_failed(c->server, &msg)) return fail(DRT_ECUDA, "serving loop failed: %s", msg.c_str());
+    ServeItem it;
+    it.dev = L->dev;
+    it.view = L->view;
+    it.tg = req->tgrid;
+    it.fg = req->fgrid;
+    it.H = req->H;
+    const drt_path_outputs &o = req->records;
+    it.out = OutD{o.tau, o.amp, o.doppler, o.angles, o.flags, o.points};
+    it.inflight = L->inflight;
+    L->inflight->fetch_add(1);
+    *out_ticket = server_submit(c->server, it);
+    return DRT_OK;
+}
+
+static Server *server_of(drt_ctx *c) {
+    std::lock_guard<std::mutex> lk(c->mu);
+    return c->server;
+}
+
+extern "C" drt_status drt_poll(drt_ctx *c, uint64_t ticket, int32_t *done, drt_result *res) {
+    if (!c || !done) return fail(DRT_EINVAL, "ctx and done must be non-NULL");
+    Server *S = server_of(c);
+    if (!S) return fail(DRT_ENOTFOUND, "no serving loop");
+    int r = server_poll(S, ticket, res);
+    if (r < 0) return fail(DRT_ENOTFOUND, "unknown or retired ticket %llu", (unsigned long long)ticket);
+    *done = r;
+    return DRT_OK;
+}
+
+extern "C" drt_status drt_wait(drt_ctx *c, uint64_t ticket, uint32_t timeout_ms, drt_result *res) {
+    if (!c) return fail(DRT_EINVAL, "ctx is NULL");
+    Server *S = server_of(c);
+    if (!S) return fail(DRT_ENOTFOUND, "no serving loop");
+    int r = server_wait(S, ticket, timeout_ms, res);
+    if (r < 0) return fail(DRT_ENOTFOUND, "unknown or retired ticket %llu", (unsigned long long)ticket);
+    if (r == 0) return fail(DRT_ETIMEOUT, "ticket %llu not done after %u ms", (unsigned long long)ticket, timeout_ms);
+    return DRT_OK;
+}
+
+extern "C" drt_status drt_serve_stats_read(drt_ctx *c, drt_serve_stats *out) {
+    if (!c || !out) return fail(DRT_EINVAL, "ctx and out must be non-NULL");
+    Server *S = server_of(c);
+    if (!S) return fail(DRT_ENOTFOUND, "no serving loop");
+    server_stats(S, out);
     return DRT_OK;
 }

@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <memory>
+#include <string>
 #include <vector>
 
 #include "../../include/drt.h"
@@ -46,7 +49,9 @@ struct LinkDev {
     const int32_t *perm;      // internal index -> caller index
 };
 
-struct TimeGridD { double t_start, dt; int32_t n_steps; };
+// chunk: time steps per chunk (FP32-bulk FP64 anchors and multi-diffraction warm starts are taken
+// at the first step of every chunk); a power of two in [4, 64]
+struct TimeGridD { double t_start, dt; int32_t n_steps, chunk; };
 struct FreqGridD { double fc, bandwidth; int32_t n_bins; };
 
 // user-visible outputs (caller order), any may be null
@@ -66,9 +71,50 @@ struct OutD {
 //   step so that k * dhi is exact in FP32 for k < 4096.
 struct RecD { float4 *rec_a; float *rec_b; };
 
+// kinematic bounds of a link used by the batch planner's chunk model: fastest terminal / body
+// translation speed (m/s), largest acceleration (m/s^2), largest angular speed (rad/s)
+struct drt_scene_view { double vmax, amax, wmax; };
+
+// a10 batch plans (drt_batch.cu)
+struct BatchPlan;
+cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::vector<drt_scene_view> &views,
+                        const drt_time_grid *tgs, const drt_freq_grid *fgs, void *const *H, const OutD *outs,
+                        BatchPlan **out, size_t *bytes);
+cudaError_t batch_bind(BatchPlan *P, void *mem, cudaStream_t s);
+cudaError_t batch_alloc(BatchPlan *P);
+cudaError_t batch_autotune(BatchPlan *P, cudaStream_t s, float *best_ms);
+cudaError_t batch_run(BatchPlan *P, cudaStream_t s, bool use_graph);
+cudaError_t batch_free(BatchPlan *P);
+int batch_variant(const BatchPlan *P);
+void batch_set_variant(BatchPlan *P, int v);
+int batch_chunk(const BatchPlan *P, int k);
+size_t batch_bytes(const BatchPlan *P);
+cudaError_t batch_redo_count(const BatchPlan *P, long long *n);
+int choose_chunk(const drt_scene_view &v, const drt_time_grid &tg, const drt_freq_grid &fg);
+
+// a11 serving loop (drt_serve.cu): one request as the serving thread sees it
+struct ServeItem {
+    LinkDev dev;
+    drt_scene_view view;
+    drt_time_grid tg;
+    drt_freq_grid fg;
+    void *H;
+    OutD out;
+    std::shared_ptr<std::atomic<int>> inflight;   // the link's count of pending requests
+};
+struct Server;
+Server *server_start(int device, void *arena, size_t arena_bytes, int n_slots, int max_batch);
+void server_stop(Server *S);
+bool server_failed(Server *S, std::string *msg);
+uint64_t server_submit(Server *S, const ServeItem &item);
+int server_poll(Server *S, uint64_t ticket, drt_result *res);
+int server_wait(Server *S, uint64_t ticket, uint32_t timeout_ms, drt_result *res);
+void server_stats(Server *S, drt_serve_stats *st);
+
 // validated host image of one link, ready for upload (drt_api.cu)
 struct PackedLink {
     LinkDev dev{};
+    drt_scene_view view{};
     std::vector<BodyD> bodies;
     std::vector<FaceD> faces;
     std::vector<EdgeD> edges;

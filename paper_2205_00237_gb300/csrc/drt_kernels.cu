@@ -14,7 +14,7 @@
 
 namespace drt {
 
-DRT_HD int n_chunks_of(const TimeGridD &tg) { return (tg.n_steps + CHUNK - 1) / CHUNK; }
+DRT_HD int n_chunks_of(const TimeGridD &tg) { return (tg.n_steps + tg.chunk - 1) / tg.chunk; }
 
 // ------------------------------------------------------------------------------------------------
 // a2: poses.  theta(t) = w0 t + wdot t^2 / 2 about the fixed axis k (Rodrigues), O(t) by Eq. Taylor,
@@ -48,7 +48,7 @@ k_extrapolate_fp64(const LinkDev L, const TimeGridD tg, const FreqGridD fg, cons
     if (p >= L.n_paths || ti >= tg.n_steps) return;
     const double *w = nullptr;
     if (warm && p >= L.n_bulk)
-        w = warm + ((size_t)(ti / CHUNK) * (L.n_paths - L.n_bulk) + (p - L.n_bulk)) * (2 * MAXI);
+        w = warm + ((size_t)(ti / tg.chunk) * (L.n_paths - L.n_bulk) + (p - L.n_bulk)) * (2 * MAXI);
     path_step_fp64(L, tg, fg, pose, p, ti, out, rec, f32out != 0, w);
 }
 
@@ -59,7 +59,7 @@ k_warm_fp64(const LinkDev L, const TimeGridD tg, const double *__restrict__ pose
     int p = L.n_bulk + blockIdx.x;
     int c = blockIdx.y * WARM_T + threadIdx.x;
     if (p >= L.n_paths || c >= n_chunks_of(tg)) return;
-    path_warm_fp64(L, tg, pose, p, c, warm);
+    path_warm_fp64(L, tg, pose, tg.n_steps, c * tg.chunk, p, c, warm);
 }
 
 size_t warm_bytes(const LinkDev &L, const TimeGridD &tg) {
@@ -93,11 +93,11 @@ size_t bulk_base_bytes(const LinkDev &L, const TimeGridD &tg) {
 }
 
 __global__ void k_pose_bulk(const BodyD *__restrict__ bodies, int n_bodies, TermD tx, TermD rx, double t_start,
-                            double dt, int n_chunks, PoseB *__restrict__ poseb) {
+                            double dt, int n_chunks, int chunk, PoseB *__restrict__ poseb) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (n_bodies + 2) * n_chunks) return;
     int b = i / n_chunks, c = i - b * n_chunks;
-    double tb = t_start + (double)c * CHUNK * dt;
+    double tb = t_start + (double)c * chunk * dt;
     if (b < n_bodies) body_pose_base(bodies[b], tb, poseb[i]);
     else terminal_base(b == n_bodies ? tx : rx, tb, poseb[i]);
 }
@@ -106,7 +106,7 @@ cudaError_t launch_pose_bulk(const LinkDev &L, const TimeGridD &tg, void *poseb,
     int n = (L.n_bodies + 2) * n_chunks_of(tg);
     if (tg.n_steps == 0) return cudaSuccess;
     k_pose_bulk<<<(n + 127) / 128, 128, 0, s>>>(L.bodies, L.n_bodies, L.tx, L.rx, tg.t_start, tg.dt, n_chunks_of(tg),
-                                                reinterpret_cast<PoseB *>(poseb));
+                                                tg.chunk, reinterpret_cast<PoseB *>(poseb));
     return cudaGetLastError();
 }
 
@@ -114,7 +114,7 @@ size_t bulk_pose64_bytes(const LinkDev &L, const TimeGridD &tg) {
     return (size_t)L.n_bodies * n_chunks_of(tg) * POSE_W * sizeof(double);
 }
 size_t bulk_redo_bytes(const LinkDev &L, const TimeGridD &tg) {
-    return 256 + (size_t)L.n_paths * tg.n_steps * sizeof(int2);
+    return 256 + (size_t)L.n_paths * tg.n_steps * sizeof(int4);
 }
 
 // one block per path, one thread per chunk: lanes share the chain signature; body poses at the
@@ -132,7 +132,7 @@ k_base_fp64(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const doubl
 cudaError_t launch_base_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, double *pose64, void *base,
                              cudaStream_t s) {
     if (L.n_bulk == 0 || tg.n_steps == 0) return cudaSuccess;
-    TimeGridD tc{tg.t_start, tg.dt * CHUNK, n_chunks_of(tg)};   // chunk bases
+    TimeGridD tc{tg.t_start, tg.dt * tg.chunk, n_chunks_of(tg), 1};   // chunk bases
     cudaError_t e = launch_pose(L, tc, pose64, s);
     if (e != cudaSuccess) return e;
     dim3 grid(L.n_bulk, (n_chunks_of(tg) + BASE_T - 1) / BASE_T);
@@ -143,7 +143,7 @@ cudaError_t launch_base_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGr
 static RedoList redo_list(void *redo, const LinkDev &L, const TimeGridD &tg) {
     RedoList r;
     r.count = reinterpret_cast<int *>(redo);
-    r.items = reinterpret_cast<int2 *>(reinterpret_cast<char *>(redo) + 256);
+    r.items = reinterpret_cast<int4 *>(reinterpret_cast<char *>(redo) + 256);
     r.cap = L.n_paths * tg.n_steps;
     return r;
 }
@@ -173,8 +173,8 @@ __global__ void __launch_bounds__(128)
 k_redo(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const OutD out, const RecD rec, const RedoList redo) {
     int n = min(*redo.count, redo.cap);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        int2 it = redo.items[k];
-        path_step_redo(L, tg, fg, it.x, it.y, out, rec);
+        int4 it = redo.items[k];
+        path_step_redo(L, tg, fg, it.y, it.z, out, rec);
     }
 }
 

@@ -18,9 +18,6 @@ enum : uint32_t { F_FACE = 1, F_EDGE = 2, F_SIDE = 4, F_NOCONV = 8, F_DEGEN = 16
 // unconverged Newton, non-finite value); the path-step is redone in FP64.  Never written out.
 constexpr uint32_t F_REDO64 = 128;
 
-// time steps per chunk: the FP32-bulk form's FP64 anchors and the multi-diffraction warm starts
-// are taken at the first step of every chunk
-constexpr int CHUNK = 16;
 enum : int { T_NONE = 0, T_R = 1, T_D = 2, T_S = 3 };
 
 // ------------------------------------------------------------------------------------------------
@@ -264,8 +261,20 @@ template <> DRT_HD void clamp_positive<dd>(dd &x, float eps) {
     }
 }
 
+// Newton start for an edge parameter: value s0 + tau sd0 at the step, rate sd0; for delta numbers
+// the base part is s0 (the chunk-base solution) and the delta tau sd0
+template <class S> DRT_HD S newton_start(double s0, double sd0, double tau);
+template <> DRT_HD double newton_start<double>(double s0, double sd0, double tau) { return s0 + sd0 * tau; }
+template <> DRT_HD dl<double> newton_start<dl<double>>(double s0, double sd0, double tau) {
+    return {s0 + sd0 * tau, sd0};
+}
+template <> DRT_HD dd newton_start<dd>(double s0, double sd0, double tau) {
+    return {(float)s0, (float)(sd0 * tau), (float)sd0};
+}
+
 template <class S>
-DRT_HD void multi_diffraction(const Prim<S> *pr, v3<S> *V, int a, int b, const double *s0, uint32_t &fl) {
+DRT_HD void multi_diffraction(const Prim<S> *pr, v3<S> *V, int a, int b, const double *s0, const double *sd0,
+                              double tau, uint32_t &fl) {
     typedef typename ST<S>::R T;
     // convergence threshold on the Newton step (m): near round-off of the working precision
     const T tol = sizeof(T) == 8 ? T(1e-10) : T(1e-4);
@@ -277,7 +286,7 @@ DRT_HD void multi_diffraction(const Prim<S> *pr, v3<S> *V, int a, int b, const d
     for (int i = a + 1; i < b; ++i)
         if (pr[i - 1].type == T_D) {
             didx[m] = i;
-            s[m] = scst<S>(T(s0[i - 1]));
+            s[m] = newton_start<S>(s0[i - 1], sd0 ? sd0[i - 1] : 0.0, tau);
             step[m] = scst<S>(T(0));
             ++m;
         }
@@ -339,7 +348,8 @@ DRT_HD void multi_diffraction(const Prim<S> *pr, v3<S> *V, int a, int b, const d
 
 // geometry of one path-step: vertices V[0..n+1] (TX, interaction points, RX) with velocities
 template <class S>
-DRT_HD void solve_geometry(const Prim<S> *pr, int n, v3<S> *V, const double *s0, uint32_t &fl) {
+DRT_HD void solve_geometry(const Prim<S> *pr, int n, v3<S> *V, const double *s0, uint32_t &fl,
+                           const double *sd0 = nullptr, double tau = 0.0) {
     for (int i = 1; i <= n; ++i)
         if (pr[i - 1].type == T_S) V[i] = pr[i - 1].p;   // Sec. III-C: tile centroid moves rigidly
     int a = 0;
@@ -362,7 +372,7 @@ DRT_HD void solve_geometry(const Prim<S> *pr, int n, v3<S> *V, const double *s0,
             backtrack(pr, V, a, dpos);
             backtrack(pr, V, dpos, b);
         } else {
-            multi_diffraction(pr, V, a, b, s0, fl);
+            multi_diffraction(pr, V, a, b, s0, sd0, tau, fl);
         }
         a = b;
     }
@@ -726,7 +736,7 @@ DRT_HD void write_record(const RecD &r, size_t ri, double tau, cx<double> a, uin
 template <class Loader>
 DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, int p, int ti,
                                 const OutD &out, const RecD &rec, bool f32out, Loader load,
-                                const double *warm = nullptr) {
+                                const double *warm = nullptr, double *rec64 = nullptr) {
     typedef double T;
     const T t = tg.t_start + ti * tg.dt;
     uint32_t code = L.ptypes[p];
@@ -745,15 +755,13 @@ DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const Fre
     V[0] = terminal<T>(L.tx, t);
     V[n + 1] = terminal<T>(L.rx, t);
     uint32_t fl = 0;
-    double sinit[MAXI];
-    const double *s0 = L.ps0 + (size_t)p * MAXI;
     if (warm) {
         // warm start of the Newton solve: edge parameters and their rates at the chunk base
-        const double tau = (ti - (ti / CHUNK) * CHUNK) * tg.dt;
-        for (int j = 0; j < MAXI; ++j) sinit[j] = warm[j] + warm[MAXI + j] * tau;
-        s0 = sinit;
+        const double tau = (ti - (ti / tg.chunk) * tg.chunk) * tg.dt;
+        solve_geometry(pr, n, V, warm, fl, warm + MAXI, tau);
+    } else {
+        solve_geometry(pr, n, V, L.ps0 + (size_t)p * MAXI, fl);
     }
-    solve_geometry(pr, n, V, s0, fl);
     v3<T> P[MAXI + 2];
     for (int i = 0; i <= n + 1; ++i) P[i] = val(V[i]);
     fl |= validity(pr, n, P);
@@ -786,6 +794,11 @@ DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const Fre
     if (rec.rec_a) {
         double f0 = fg.fc - 0.5 * fg.bandwidth, df = fg.bandwidth / fg.n_bins;
         write_record(rec, (size_t)ti * L.n_paths + p, tau, a, fl, f0, df);
+    }
+    if (rec64) {   // (Re a, Im a, tau), a = 0 when the path does not exist
+        rec64[0] = fl ? 0.0 : a.re;
+        rec64[1] = fl ? 0.0 : a.im;
+        rec64[2] = tau;
     }
 }
 
@@ -837,9 +850,9 @@ DRT_HD void solve_edge_params(const LinkDev &L, int p, double t, const double *s
     }
 }
 
-DRT_HD void path_warm_fp64(const LinkDev &L, const TimeGridD &tg, const double *pose, int p, int chunk,
-                           double *warm) {
-    const int ti = chunk * CHUNK;
+DRT_HD void path_warm_fp64(const LinkDev &L, const TimeGridD &tg, const double *pose, int n_rows, int row, int p,
+                           int chunk, double *warm) {
+    const int ti = chunk * tg.chunk;
     const double t = tg.t_start + ti * tg.dt;
     // rates at t0, where the ray-tracing parameters s0 are already the solution (one iteration)
     double s_t0[MAXI], r_t0[MAXI], start[MAXI];
@@ -849,7 +862,7 @@ DRT_HD void path_warm_fp64(const LinkDev &L, const TimeGridD &tg, const double *
     for (int j = 0; j < MAXI; ++j) start[j] = s_t0[j] + r_t0[j] * t;
     double *w = warm + ((size_t)chunk * (L.n_paths - L.n_bulk) + (p - L.n_bulk)) * (2 * MAXI);
     solve_edge_params(L, p, t, start, w, w + MAXI,
-                      [&](int ty, int idx) { return load_prim<double>(L, pose, tg.n_steps, ti, ty, idx); });
+                      [&](int ty, int idx) { return load_prim<double>(L, pose, n_rows, row, ty, idx); });
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1016,9 +1029,9 @@ DRT_HD Prim<double> load_prim_value(const LinkDev &L, const double *Pr, int type
 // (path, chunk) FP64 anchors: path length and segment vectors at the chunk's first instant, phase
 // seed and per-bin step
 DRT_HD void path_base_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const double *pose64, int p,
-                           int chunk, BaseRec *out) {
-    const double tb = tg.t_start + (double)chunk * CHUNK * tg.dt;
-    const int n_chunks = (tg.n_steps + CHUNK - 1) / CHUNK;
+                           int chunk, BaseRec *out, const double *warm = nullptr) {
+    const double tb = tg.t_start + (double)chunk * tg.chunk * tg.dt;
+    const int n_chunks = (tg.n_steps + tg.chunk - 1) / tg.chunk;
     uint32_t code = L.ptypes[p];
     int4 pi = L.pprims[p];
     int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
@@ -1035,7 +1048,9 @@ DRT_HD void path_base_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGrid
     V[0] = val(terminal<double>(L.tx, tb));
     V[n + 1] = val(terminal<double>(L.rx, tb));
     uint32_t fl = 0;
-    solve_geometry(pr, n, V, L.ps0 + (size_t)p * MAXI, fl);
+    const double *s0 = L.ps0 + (size_t)p * MAXI;
+    if (warm && p >= L.n_bulk) s0 = warm + ((size_t)chunk * (L.n_paths - L.n_bulk) + (p - L.n_bulk)) * (2 * MAXI);
+    solve_geometry(pr, n, V, s0, fl);
     BaseRec r;
     double d = 0.0;
     for (int i = 0; i <= MAXI; ++i) r.seg[i][0] = r.seg[i][1] = r.seg[i][2] = 0.f;
@@ -1088,15 +1103,25 @@ DRT_HD void write_outputs_bulk(const OutD &o, size_t oi, int n, const v3<dd> *V,
     }
 }
 
-// list of (path, step) pairs the FP32-bulk kernel hands to the FP64 redo kernel
-struct RedoList { int *count; int2 *items; int cap; };
+// list of (link, path, step) triples the FP32-bulk kernels hand to the FP64 redo kernel
+struct RedoList { int *count; int4 *items; int cap; };
 
-DRT_HD void path_step_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const PoseB *poseb,
-                           const BaseRec *base, int p, int ti, const OutD &out, const RecD &rec, const RedoList &redo) {
+// synthesis record of one path-step: amplitude (0 if the path does not exist), phase seed and the
+// per-bin phase step split hi + lo (cycles)
+struct Rec5 { float ar, ai, ph, hi, lo; };
+
+// FP32-bulk (path, time-step): geometry in delta numbers on the chunk anchors, field in FP32.
+// Chains with >= 2 diffractions in a segment start their Newton solve from the FP64 chunk-base
+// parameters (warm, may be null for the others).  Returns false when the step was queued for the
+// FP64 redo (its record is then zero).
+DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const PoseB *poseb,
+                      const BaseRec *base, const double *warm, int p, int ti, const OutD &out, Rec5 &rec,
+                      const RedoList &redo, int link) {
     typedef float T;
-    const int n_chunks = (tg.n_steps + CHUNK - 1) / CHUNK;
-    const int chunk = ti / CHUNK;
-    const float tau_t = (float)((ti - chunk * CHUNK) * tg.dt);
+    rec = Rec5{0.f, 0.f, 0.f, 0.f, 0.f};
+    const int n_chunks = (tg.n_steps + tg.chunk - 1) / tg.chunk;
+    const int chunk = ti / tg.chunk;
+    const float tau_t = (float)((ti - chunk * tg.chunk) * tg.dt);
     uint32_t code = L.ptypes[p];
     int4 pi = L.pprims[p];
     int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
@@ -1113,23 +1138,41 @@ DRT_HD void path_step_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGrid
     V[0] = terminal_dd(poseb[(size_t)L.n_bodies * n_chunks + chunk], tau_t);
     V[n + 1] = terminal_dd(poseb[(size_t)(L.n_bodies + 1) * n_chunks + chunk], tau_t);
     uint32_t fl = 0;
-    solve_geometry(pr, n, V, L.ps0 + (size_t)p * MAXI, fl);
+    if (warm && p >= L.n_bulk) {
+        const double *w = warm + ((size_t)chunk * (L.n_paths - L.n_bulk) + (p - L.n_bulk)) * (2 * MAXI);
+        solve_geometry(pr, n, V, w, fl, w + MAXI, (double)tau_t);
+    } else {
+        solve_geometry(pr, n, V, L.ps0 + (size_t)p * MAXI, fl);
+    }
     v3<T> P[MAXI + 2];
     for (int i = 0; i <= n + 1; ++i) P[i] = val(V[i]);
     fl |= validity(pr, n, P);
+    {
+        // The FP32 bases carry rounding errors of ~1 ulp of the coordinates (~1e-5 m at 100 m),
+        // and the delta rules multiply them by the deltas: the phase error grows with how far an
+        // interaction point moved since the chunk base (~6e-4 rad per metre at 60 GHz when a
+        // diffraction point slides fast near grazing).  Steps past 0.8 m at 60 GHz (scaled by
+        // 1/fc) are left to the FP64 redo.
+        float disp2 = 0.f;
+        for (int i = 1; i <= n; ++i) disp2 = fmaxf(disp2, V[i].x.d * V[i].x.d + V[i].y.d * V[i].y.d + V[i].z.d * V[i].z.d);
+        const float lim = (float)(0.8 * 60e9 / fg.fc);
+        if (disp2 > lim * lim) fl |= F_REDO64;
+    }
     {
         bool finite = true;
         for (int i = 1; i <= n; ++i) finite = finite && isfinite(P[i].x) && isfinite(P[i].y) && isfinite(P[i].z);
         if (!finite || (fl & (F_REDO64 | F_NOCONV | F_DEGEN))) {
             // geometry FP32 cannot resolve: queue this path-step for the FP64 redo kernel (rare,
             // see F_REDO64); the list holds every path-step in the worst case
+            if (redo.count) {
 #ifdef __CUDA_ARCH__
-            int k = atomicAdd(redo.count, 1);
+                int k = atomicAdd(redo.count, 1);
 #else
-            int k = (*redo.count)++;
+                int k = (*redo.count)++;
 #endif
-            if (k < redo.cap) redo.items[k] = make_int2(p, ti);
-            return;
+                if (k < redo.cap) redo.items[k] = make_int4(link, p, ti, 0);
+            }
+            return false;
         }
     }
     const BaseRec &B = base[(size_t)chunk * L.n_paths + p];
@@ -1147,21 +1190,27 @@ DRT_HD void path_step_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGrid
         size_t oi = (size_t)ti * L.n_paths + L.perm[p];
         write_outputs_bulk(out, oi, n, V, seg, (B.d + (double)dd_len) / C0, a, fd, fl);
     }
+    const float f0c = (float)((fg.fc - 0.5 * fg.bandwidth) / C0), dfc = (float)(fg.bandwidth / fg.n_bins / C0);
+    float x = f0c * dd_len;
+    x -= floorf(x);
+    float ph = B.ph0 + x;
+    ph -= floorf(ph);
+    rec.ar = fl ? 0.f : a.re;
+    rec.ai = fl ? 0.f : a.im;
+    rec.ph = ph;
+    rec.hi = B.st_hi;
+    rec.lo = fmaf(dfc, dd_len, B.st_lo);
+    return true;
+}
+
+DRT_HD void path_step_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const PoseB *poseb,
+                           const BaseRec *base, int p, int ti, const OutD &out, const RecD &rec, const RedoList &redo) {
+    Rec5 r;
+    bulk_eval(L, tg, fg, poseb, base, nullptr, p, ti, out, r, redo, 0);
     if (rec.rec_a) {
-        const float f0c = (float)((fg.fc - 0.5 * fg.bandwidth) / C0), dfc = (float)(fg.bandwidth / fg.n_bins / C0);
-        float x = f0c * dd_len;
-        x -= floorf(x);
-        float ph = B.ph0 + x;
-        ph -= floorf(ph);
-        float lo = fmaf(dfc, dd_len, B.st_lo);
-        float4 v;
-        v.x = fl ? 0.f : a.re;
-        v.y = fl ? 0.f : a.im;
-        v.z = ph;
-        v.w = B.st_hi;
         size_t ri = (size_t)ti * L.n_paths + p;
-        rec.rec_a[ri] = v;
-        rec.rec_b[ri] = lo;
+        rec.rec_a[ri] = make_float4(r.ar, r.ai, r.ph, r.hi);
+        rec.rec_b[ri] = r.lo;
     }
 }
 

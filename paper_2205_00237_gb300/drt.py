@@ -25,7 +25,9 @@ F_FACE, F_EDGE, F_SIDE, F_NOCONV, F_DEGEN = 1, 2, 4, 8, 16
 # every symbol include/drt.h declares
 EXPORTS = ["drt_create", "drt_destroy", "drt_last_error", "drt_load_paths", "drt_unload", "drt_extrapolate",
            "drt_synthesize_H", "drt_synthesize_H_host", "drt_link_info", "drt_probe_peak", "drt_profile_enable",
-           "drt_profile_read", "drt_synthesize_H_noalloc"]
+           "drt_profile_read", "drt_synthesize_H_noalloc", "drt_batch_create", "drt_batch_run", "drt_batch_info",
+           "drt_batch_destroy", "drt_serve_start", "drt_serve_stop", "drt_submit", "drt_poll", "drt_wait",
+           "drt_serve_stats_read"]
 
 
 class DrtError(RuntimeError):
@@ -61,6 +63,21 @@ class _FreqGrid(C.Structure):
 class _Outputs(C.Structure):
     _fields_ = [("tau", C.c_void_p), ("amp", C.c_void_p), ("doppler", C.c_void_p), ("angles", C.c_void_p),
                 ("flags", C.c_void_p), ("points", C.c_void_p)]
+
+
+class _Request(C.Structure):
+    _fields_ = [("link", C.c_uint64), ("tgrid", _TimeGrid), ("fgrid", _FreqGrid), ("H", C.c_void_p),
+                ("records", _Outputs), ("precision", C.c_int32), ("reserved", C.c_int32)]
+
+
+class _Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("batch_requests", C.c_int32), ("t_submit", C.c_double),
+                ("t_launch", C.c_double), ("t_done", C.c_double)]
+
+
+class _ServeStats(C.Structure):
+    _fields_ = [(k, C.c_uint64) for k in ("submitted", "completed", "launches", "queued", "in_flight",
+                                          "arena_bytes", "arena_used", "arena_peak")]
 
 
 _lib = None
@@ -103,6 +120,28 @@ def load_library(path: str = LIB_PATH):
         L.drt_profile_enable.restype = st
         L.drt_profile_read.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
         L.drt_profile_read.restype = st
+        L.drt_batch_create.argtypes = [vp, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(_TimeGrid),
+                                       C.POINTER(_FreqGrid), C.POINTER(vp), C.c_int32, C.POINTER(vp)]
+        L.drt_batch_create.restype = st
+        L.drt_batch_run.argtypes = [vp, vp, C.c_int32, vp]
+        L.drt_batch_run.restype = st
+        L.drt_batch_info.argtypes = [vp, vp, C.POINTER(C.c_int32), C.POINTER(C.c_uint64), C.POINTER(C.c_float),
+                                     C.POINTER(C.c_int64)]
+        L.drt_batch_info.restype = st
+        L.drt_batch_destroy.argtypes = [vp, vp]
+        L.drt_batch_destroy.restype = None
+        L.drt_serve_start.argtypes = [vp, C.c_uint64, C.c_int32, C.c_int32]
+        L.drt_serve_start.restype = st
+        L.drt_serve_stop.argtypes = [vp]
+        L.drt_serve_stop.restype = st
+        L.drt_submit.argtypes = [vp, C.POINTER(_Request), C.POINTER(C.c_uint64)]
+        L.drt_submit.restype = st
+        L.drt_poll.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int32), C.POINTER(_Result)]
+        L.drt_poll.restype = st
+        L.drt_wait.argtypes = [vp, C.c_uint64, C.c_uint32, C.POINTER(_Result)]
+        L.drt_wait.restype = st
+        L.drt_serve_stats_read.argtypes = [vp, C.POINTER(_ServeStats)]
+        L.drt_serve_stats_read.restype = st
         _lib = L
         return L
 
@@ -189,6 +228,60 @@ class Context:
         names = ("pose", "extrapolate", "synth", "base")
         return {names[k]: (int(counts[k]), float(ms[k])) for k in range(4)}
 
+    def batch(self, links, tgrids, fgrids, Hs, precision: int = FP32_BULK) -> "Batch":
+        """drt_batch_create: one batched synthesis plan over loaded links; Hs are complex64 CUDA
+        tensors [T_i][F_i] (kept referenced by the plan).  Autotunes on the device (synchronous)."""
+        n = len(links)
+        ids = (C.c_uint64 * n)(*[lk.handle for lk in links])
+        tgs = (_TimeGrid * n)(*[_tg(t) for t in tgrids])
+        fgs = (_FreqGrid * n)(*[_fg(f) for f in fgrids])
+        hs = (C.c_void_p * n)(*[h.data_ptr() for h in Hs])
+        out = C.c_void_p()
+        _check(load_library().drt_batch_create(self._h, n, ids, tgs, fgs, hs, int(precision), C.byref(out)))
+        return Batch(self, out, list(Hs))
+
+    def serve_start(self, pool_bytes: int = 0, n_slots: int = 4, max_batch: int = 256):
+        """drt_serve_start: start the serving loop with an arena of pool_bytes (0 = default)."""
+        _check(load_library().drt_serve_start(self._h, int(pool_bytes), int(n_slots), int(max_batch)))
+
+    def serve_stop(self):
+        """drt_serve_stop: finish every submitted request and end the serving loop."""
+        _check(load_library().drt_serve_stop(self._h))
+
+    def submit(self, link: "Link", tg: I.TimeGrid, fg: I.FreqGrid, H, records: dict | None = None,
+               precision: int = FP32_BULK) -> int:
+        """drt_submit: queue one prediction request; H (complex64 CUDA tensor [T][F]) and the optional
+        record tensors must stay alive until the request is done.  Returns the ticket."""
+        rec = records or {}
+        req = _Request(link.handle, _tg(tg), _fg(fg), H.data_ptr(),
+                       _Outputs(*(_dptr(rec.get(k)) for k in ("tau", "amp", "doppler", "angles", "flags", "points"))),
+                       int(precision), 0)
+        t = C.c_uint64()
+        _check(load_library().drt_submit(self._h, C.byref(req), C.byref(t)))
+        return t.value
+
+    @staticmethod
+    def _result(r: _Result) -> dict:
+        return dict(status=r.status, batch_requests=r.batch_requests, t_submit=r.t_submit, t_launch=r.t_launch,
+                    t_done=r.t_done, latency=r.t_done - r.t_submit)
+
+    def poll(self, ticket: int):
+        """drt_poll: None while pending, else the result dict (the ticket is then retired)."""
+        done, r = C.c_int32(), _Result()
+        _check(load_library().drt_poll(self._h, int(ticket), C.byref(done), C.byref(r)))
+        return self._result(r) if done.value else None
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> dict:
+        """drt_wait: block until the request is done (raises DrtError DRT_ETIMEOUT on expiry)."""
+        r = _Result()
+        _check(load_library().drt_wait(self._h, int(ticket), int(timeout_ms), C.byref(r)))
+        return self._result(r)
+
+    def serve_stats(self) -> dict:
+        st = _ServeStats()
+        _check(load_library().drt_serve_stats_read(self._h, C.byref(st)))
+        return {k: int(getattr(st, k)) for k, _ in _ServeStats._fields_}
+
     def probe_peak(self, kind: int, blocks: int = 152 * 16) -> float:
         f = C.c_double()
         _check(load_library().drt_probe_peak(self._h, int(kind), int(blocks), C.byref(f)))
@@ -254,3 +347,34 @@ class Link:
         _check(load_library().drt_synthesize_H_noalloc(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs),
                                                        _dptr(H), int(precision), _stream_ptr(stream)))
         return H
+
+
+class Batch:
+    """A batched synthesis plan (drt_batch_create) over several loaded links."""
+
+    def __init__(self, ctx: Context, handle, Hs):
+        self.ctx, self._h, self.Hs = ctx, handle, Hs
+
+    def run(self, use_graph: bool = True, stream=None):
+        """drt_batch_run: every stage of the batch on `stream` (replayed from a CUDA graph)."""
+        _check(load_library().drt_batch_run(self.ctx._h, self._h, 1 if use_graph else 0, _stream_ptr(stream)))
+
+    def info(self, redo: bool = False) -> dict:
+        v, b, ms, r = C.c_int32(), C.c_uint64(), C.c_float(), C.c_int64()
+        _check(load_library().drt_batch_info(self.ctx._h, self._h, C.byref(v), C.byref(b), C.byref(ms),
+                                             C.byref(r) if redo else None))
+        out = dict(variant=v.value, scratch_bytes=b.value, tune_ms=ms.value)
+        if redo:
+            out["redo_steps"] = r.value
+        return out
+
+    def close(self):
+        if self._h:
+            load_library().drt_batch_destroy(self.ctx._h, self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

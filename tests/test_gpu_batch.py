@@ -1,0 +1,159 @@
+"""Batched FP32-bulk synthesis (drt_batch_create / drt_batch_run) against the FP64 oracle.
+
+A batch runs many loaded links of very different sizes (path counts, horizons, bin counts) through
+one persistent launch per stage, optionally replayed from a CUDA graph.  Every link's H must match
+the oracle's direct FP64 sum within the FP32-bulk bars (complex error <= 1e-3 and magnitude error
+<= 1e-4 of the row RMS, the phase bar of 1e-3 rad carried over to H), and match what the same link
+gives on its own (drt_synthesize_H, FP32-bulk form) and on a repeated or graph-replayed run.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2205_00237_gb300 import inputs as I
+
+from test_gpu_parity import compare_H_band, compare_H_pair
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_00237_gb300 import drt
+    c = drt.Context(0)
+    yield c
+    c.close()
+
+
+def link_set(seed):
+    return I.scene_link(seed), I.PathSet.from_npz(os.path.join(GOLD, f"pathset_link_seed{seed}.npz"))
+
+
+def uneven_cases():
+    canyon = I.scene_canyon(0), I.PathSet.from_npz(os.path.join(GOLD, "pathset_canyon_seed0.npz"))
+    sc_l, ps_l = link_set(0)
+    tiny = [(I.scene_tiny(s), I.PathSet.from_npz(os.path.join(GOLD, f"pathset_tiny_seed{s}.npz"))) for s in (0, 1)]
+    return [
+        (tiny[0][0], tiny[0][1], I.TimeGrid(0.0, 1e-3, 300), I.FreqGrid(28e9, 400e6, 256)),
+        (tiny[1][0], tiny[1][1], I.TimeGrid(0.0, 1e-3, 1000), I.FreqGrid(28e9, 400e6, 256)),
+        (canyon[0], canyon[1].subset(np.arange(64)), I.TimeGrid(0.0123, 0.5e-3, 203), I.FreqGrid(60e9, 1e9, 100)),
+        (canyon[0], canyon[1], I.TimeGrid(0.0, 0.5e-3, 150), I.FreqGrid(60e9, 1e9, 512)),
+        (sc_l, ps_l.subset(np.arange(300)), I.TimeGrid(0.0, 1e-3, 777), I.FreqGrid(28e9, 400e6, 256)),
+        (sc_l, ps_l.subset(np.arange(9)), I.TimeGrid(0.25, 1e-3, 5), I.FreqGrid(28e9, 400e6, 33)),
+    ]
+
+
+def test_uneven_batch_matches_oracle_and_single_link(ctx):
+    import torch
+    from paper_2205_00237_gb300 import drt
+    cases = uneven_cases()
+    links = [ctx.load(sc, ps) for sc, ps, _, _ in cases]
+    Hs = [torch.full((tg.n_steps, fg.n_bins), float("nan"), dtype=torch.complex64, device="cuda")
+          for _, _, tg, fg in cases]
+    with ctx.batch(links, [c[2] for c in cases], [c[3] for c in cases], Hs) as b:
+        b.run(use_graph=False)
+        torch.cuda.synchronize()
+        info = b.info(redo=True)
+        assert 0 <= info["variant"] < 4 and info["scratch_bytes"] > 0
+        got = [h.cpu().numpy() for h in Hs]
+        for (sc, ps, tg, fg), link, H in zip(cases, links, got):
+            assert np.isfinite(H).all()
+            r = O.extrapolate(sc, ps, tg, fg.fc, n_threads=8)
+            compare_H_band(H, r, fg)
+            single = link.synthesize_H(tg, fg, drt.FP32_BULK).cpu().numpy()
+            # the single-link form anchors every 16 steps, the batch at the chunk its planner picks
+            compare_H_pair(H, single, r)
+        # graph capture, then replay: the same H (up to the order of the FP64 redo additions)
+        for h in Hs:
+            h.fill_(float("nan"))
+        b.run(use_graph=True)
+        b.run(use_graph=True)
+        torch.cuda.synchronize()
+        for H0, h in zip(got, Hs):
+            H1 = h.cpu().numpy()
+            rms = np.sqrt(np.mean(np.abs(H0) ** 2, axis=1, keepdims=True)) + 1e-30
+            assert (np.abs(H1 - H0) / rms).max() < 1e-6
+    for lk in links:
+        lk.unload()
+
+
+def test_empty_and_zero_step_links_in_a_batch(ctx):
+    import torch
+    sc, ps = link_set(1)
+    a = ctx.load(sc, ps.subset(np.arange(20)))
+    e = ctx.load(sc, I.empty_paths(0))
+    tg0, tg1 = I.TimeGrid(0.0, 1e-3, 0), I.TimeGrid(0.0, 1e-3, 64)
+    fg = I.FreqGrid(28e9, 400e6, 256)
+    H_a = torch.full((64, 256), float("nan"), dtype=torch.complex64, device="cuda")
+    H_e = torch.full((64, 256), float("nan"), dtype=torch.complex64, device="cuda")
+    H_z = torch.empty((1, 256), dtype=torch.complex64, device="cuda")
+    with ctx.batch([a, e, a], [tg1, tg1, tg0], [fg, fg, fg], [H_a, H_e, H_z]) as b:
+        b.run(use_graph=True)
+        torch.cuda.synchronize()
+    r = O.extrapolate(sc, ps.subset(np.arange(20)), tg1, fg.fc, n_threads=8)
+    compare_H_band(H_a.cpu().numpy(), r, fg)
+    assert (H_e.cpu().numpy() == 0).all()    # a link without paths has H = 0
+    a.unload()
+    e.unload()
+
+
+def test_batch_rejects_bad_arguments(ctx):
+    import torch
+    from paper_2205_00237_gb300 import drt
+    sc, ps = link_set(2)
+    a = ctx.load(sc, ps.subset(np.arange(10)))
+    tg, fg = I.TimeGrid(0.0, 1e-3, 16), I.FreqGrid(28e9, 400e6, 16)
+    H = torch.empty((16, 16), dtype=torch.complex64, device="cuda")
+    with pytest.raises(drt.DrtError) as ei:
+        ctx.batch([a], [tg], [fg], [H], precision=drt.FP64)
+    assert ei.value.code == drt.DRT_EINVAL
+    with pytest.raises(drt.DrtError) as ei:
+        ctx.batch([a], [tg], [I.FreqGrid(28e9, 400e6, 0)], [H])
+    assert ei.value.code == drt.DRT_EINVAL
+    a.unload()
+    with pytest.raises(drt.DrtError) as ei:
+        ctx.batch([a], [tg], [fg], [H])
+    assert ei.value.code == drt.DRT_ENOTFOUND
+
+
+def test_batched_workload_sample_at_scale(ctx):
+    """A slice of the batched workload at its full shape (log-uniform path counts up to 2048,
+    horizons up to 5000 steps, 256 bins): sampled rows of sampled links against the oracle."""
+    import torch
+    w = I.BATCH
+    spec = I.batch_links(192, seed=3)
+    sets = [link_set(k) for k in range(I.LINK_SCENES)]
+    loaded = {}
+    links, tgs, fgs, Hs = [], [], [], []
+    for k, P, T in spec:
+        key = (k, P)
+        if key not in loaded:
+            loaded[key] = ctx.load(sets[k][0], sets[k][1].subset(np.arange(P)))
+        links.append(loaded[key])
+        tgs.append(I.TimeGrid(0.0, w["dt"], T))
+        fgs.append(I.FreqGrid(w["fc"], w["bandwidth"], w["n_bins"]))
+        Hs.append(torch.empty((T, w["n_bins"]), dtype=torch.complex64, device="cuda"))
+    with ctx.batch(links, tgs, fgs, Hs) as b:
+        b.run(use_graph=True)
+        torch.cuda.synchronize()
+        redo = b.info(redo=True)["redo_steps"]
+    total = sum(P * T for _, P, T in spec)
+    assert redo < 1e-3 * total, (redo, total)
+    rng = np.random.default_rng(5)
+    order = np.argsort([P for _, P, _ in spec])
+    pick = [order[-1], order[len(order) // 2], order[0]] + list(rng.choice(len(spec), 2, replace=False))
+    for i in pick:
+        k, P, T = spec[i]
+        rows = np.unique(np.concatenate([[0, T - 1], rng.integers(0, T, 6)]))
+        Hg = Hs[i].cpu().numpy()[rows]
+        sc, ps = sets[k][0], sets[k][1].subset(np.arange(P))
+        for j, t in enumerate(rows):
+            r = O.extrapolate(sc, ps, I.TimeGrid(t * w["dt"], w["dt"], 1), w["fc"], n_threads=8)
+            compare_H_band(Hg[j:j + 1], r, fgs[i])
+    for lk in loaded.values():
+        lk.unload()

@@ -84,6 +84,38 @@ def compare_H(Hg, Href, tol=1e-4, mag_tol=None):
     assert np.all(np.abs(Hg[~nz]) == 0)
 
 
+def compare_H_band(Hg, r, fg, tol=1e-3, mag_tol=1e-4, band=1e-4):
+    """FP32-bulk H against the oracle.  A path-step within `band` m of a validity boundary (face or
+    edge rim, side plane) may be decided either way by FP32 geometry (the flags bar of the form), so
+    the oracle sum leaves those path-steps out and each row may differ from it by at most tol (and
+    mag_tol for |H|) of the row RMS plus the summed magnitude of their amplitudes."""
+    Hg = np.asarray(Hg, np.complex128)
+    near = r["margin"] < band
+    r_far = dict(r)
+    r_far["flags"] = np.where(near, np.uint8(0x80), r["flags"]).astype(np.uint8)
+    Href = O.synthesize_H(r_far, fg, n_threads=8)
+    Hall = O.synthesize_H(r, fg, n_threads=8)
+    rms = np.sqrt(np.mean(np.abs(Hall) ** 2, axis=1))
+    slack = np.where(near, np.abs(r["a"]), 0.0).sum(axis=1)
+    nz = rms > 0
+    err = (np.abs(Hg - Href).max(axis=1) - slack)[nz] / rms[nz]
+    assert err.max() < tol, err.max()
+    emag = (np.abs(np.abs(Hg) - np.abs(Href)).max(axis=1) - slack)[nz] / rms[nz]
+    assert emag.max() < mag_tol, emag.max()
+    assert np.all(np.abs(Hg[~nz]) <= slack[~nz, None] * (1 + 1e-6))
+    return int(near.sum())
+
+
+def compare_H_pair(H1, H2, r, tol=2e-4, band=1e-4):
+    """Two FP32-bulk results of the same link (e.g. different chunk lengths): equal within tol of the
+    row RMS plus the amplitudes of the path-steps either may decide differently (near a boundary)."""
+    H1, H2 = np.asarray(H1, np.complex128), np.asarray(H2, np.complex128)
+    slack = np.where(r["margin"] < band, np.abs(r["a"]), 0.0).sum(axis=1)
+    rms = np.sqrt(np.mean(np.abs(H2) ** 2, axis=1)) + 1e-300
+    err = (np.abs(H1 - H2).max(axis=1) - slack) / rms
+    assert err.max() < tol, err.max()
+
+
 def compare_records_bulk(g, r, fc):
     """FP32-bulk records against the oracle (see the module docstring for the bars)."""
     tau = g["tau"].cpu().numpy()
@@ -100,7 +132,10 @@ def compare_records_bulk(g, r, fc):
     rel = np.abs(tau - r["tau"]) / r["tau"]
     assert rel[valid].max() < 1e-8 and rel[ok].max() < 1e-7
     assert (2 * np.pi * fc * np.abs(tau - r["tau"]))[valid].max() < 1e-3
-    assert (np.abs(a - r["a"]) <= 5e-3 * np.abs(r["a"]))[valid].all()
+    # FP32 coefficients: 5e-3 relative, except near a null of the path's own amplitude (the UTD
+    # terms and the ER lobe cancel there), where the bar is 1e-5 of the path's peak over the horizon
+    peak = np.where(valid, np.abs(r["a"]), 0.0).max(axis=0, keepdims=True)
+    assert (np.abs(a - r["a"]) <= 5e-3 * np.abs(r["a"]) + 1e-5 * peak)[valid].all()
     assert np.abs(fd - r["fd"])[ok].max() < 0.1
     assert np.abs(np.angle(np.exp(1j * (ang - r["ang"]))))[ok].max() < 2e-6
     if g.get("points") is not None and r.get("pts") is not None:
@@ -287,7 +322,7 @@ def test_fp32_bulk_form(ctx, which):
     torch.cuda.synchronize()
     r = O.extrapolate(sc, ps, tg, fg.fc, points=True, n_threads=8)
     compare_records_bulk(g, r, fg.fc)
-    compare_H(H.cpu().numpy(), O.synthesize_H(r, fg, n_threads=8), tol=1e-3, mag_tol=1e-4)
+    compare_H_band(H.cpu().numpy(), r, fg)
     link.unload()
 
 
@@ -304,6 +339,6 @@ def test_fp32_bulk_ragged_grid(ctx):
     torch.cuda.synchronize()
     r = O.extrapolate(sc, ps, tg, fg.fc, n_threads=8)
     compare_records_bulk(g, r, fg.fc)
-    compare_H(H.cpu().numpy(), O.synthesize_H(r, fg), tol=1e-3, mag_tol=1e-4)
+    compare_H_band(H.cpu().numpy(), r, fg)
     link.unload()
 
