@@ -222,8 +222,8 @@ Link *find_link(drt_ctx *c, uint64_t id) {
 
 // default chunk: 16 steps (FP32-bulk anchors); the batch planner may choose another from its
 // phase-error model
-TimeGridD tgd(const drt_time_grid *g, int chunk = 16) { return TimeGridD{g->t_start, g->dt, g->n_steps, chunk}; }
-FreqGridD fgd(const drt_freq_grid *g) { return FreqGridD{g->fc, g->bandwidth, g->n_bins}; }
+TimeGridD tgd(const drt_time_grid *g, int chunk = 16) { return make_tgrid(g->t_start, g->dt, g->n_steps, chunk); }
+FreqGridD fgd(const drt_freq_grid *g) { return make_fgrid(g->fc, g->bandwidth, g->n_bins); }
 
 // bracket one launch with events when tracing is on
 template <class F> drt_status traced(drt_ctx *c, int kind, cudaStream_t s, F &&launch) {
@@ -251,39 +251,24 @@ drt_status run_extrapolation(drt_ctx *c, Link &L, const drt_time_grid *tg, const
         if (drt_status st = ensure(c, c->base, bulk_base_bytes(L.dev, t))) return st;
         if (drt_status st = ensure(c, c->pose64, bulk_pose64_bytes(L.dev, t))) return st;
         if (drt_status st = ensure(c, c->redo, bulk_redo_bytes(L.dev, t))) return st;
+        if (drt_status st = ensure(c, c->warm, warm_bytes(L.dev, t) + 8)) return st;
         void *pb = c->poseb.ptr, *bs = c->base.ptr, *rd = c->redo.ptr;
         double *p64 = reinterpret_cast<double *>(c->pose64.ptr);
-        bool md = L.dev.n_bulk < L.n_paths;
-        double *pose = nullptr;
-        double *warm = nullptr;
-        if (md) {
-            size_t pose_bytes = (size_t)tg->n_steps * L.dev.n_bodies * POSE_W * sizeof(double);
-            if (drt_status st = ensure(c, c->pose, pose_bytes)) return st;
-            if (drt_status st = ensure(c, c->warm, warm_bytes(L.dev, t))) return st;
-            pose = reinterpret_cast<double *>(c->pose.ptr);
-            warm = reinterpret_cast<double *>(c->warm.ptr);
-        }
-        // fork: anchors on side[0], multi-diffraction paths in FP64 on side[1]
-        cudaStream_t sa = c->side[0], sb = c->side[1];
+        double *warm = reinterpret_cast<double *>(c->warm.ptr);
+        // fork: warm starts + FP64 anchors on side[0] beside the FP32 base poses on the caller's stream
+        cudaStream_t sa = c->side[0];
         CUDA_TRY(cudaEventRecord(c->ev_fork, s));
         CUDA_TRY(cudaStreamWaitEvent(sa, c->ev_fork, 0));
-        CUDA_TRY(cudaStreamWaitEvent(sb, c->ev_fork, 0));
-        if (drt_status st = traced(c, 3, sa, [&] { return launch_base_fp64(L.dev, t, f, p64, bs, sa); })) return st;
+        if (drt_status st = traced(c, 3, sa, [&] { return launch_base_fp64(L.dev, t, f, p64, bs, warm, sa); }))
+            return st;
         CUDA_TRY(cudaEventRecord(c->ev_join[0], sa));
-        if (md) {
-            if (drt_status st = traced(c, 0, sb, [&] { return launch_pose(L.dev, t, pose, sb); })) return st;
-            if (drt_status st = traced(c, 1, sb, [&] {
-                    return launch_extrapolate_fp64(L.dev, t, f, pose, out, rec, sb, L.dev.n_bulk, L.n_paths, true, warm);
-                }))
-                return st;
-        }
-        CUDA_TRY(cudaEventRecord(c->ev_join[1], sb));
         if (drt_status st = traced(c, 0, s, [&] { return launch_pose_bulk(L.dev, t, pb, s); })) return st;
         CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[0], 0));
-        if (drt_status st = traced(c, 1, s, [&] { return launch_extrapolate_bulk(L.dev, t, f, pb, bs, out, rec, rd, s); }))
+        if (drt_status st = traced(c, 1, s, [&] {
+                return launch_extrapolate_bulk(L.dev, t, f, pb, bs, warm, out, rec, rd, s);
+            }))
             return st;
-        if (drt_status st = traced(c, 3, s, [&] { return launch_redo(L.dev, t, f, out, rec, rd, s); })) return st;
-        CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[1], 0));
+        if (drt_status st = traced(c, 3, s, [&] { return launch_redo(L.dev, t, f, out, rec, rd, warm, s); })) return st;
         return DRT_OK;
     }
     size_t pose_bytes = (size_t)tg->n_steps * L.dev.n_bodies * POSE_W * sizeof(double);
@@ -380,7 +365,8 @@ drt_status drt::pack_link(const drt_scene *s, const drt_path_set *ps, PackedLink
         g.area = t.area;
         g.s = t.s;
         g.alpha = t.alpha_r;
-        g.phase = t.phase;
+        g.cph = std::cos(t.phase);   // the tile's constant phase factor exp(j phase), once per load
+        g.sph = std::sin(t.phase);
         g.body = t.body;
         g.mat = t.material;
     }
@@ -429,7 +415,8 @@ drt_status drt::pack_link(const drt_scene *s, const drt_path_set *ps, PackedLink
         h.area = (float)g.area;
         h.s = (float)g.s;
         h.alpha = (float)g.alpha;
-        h.phase = (float)g.phase;
+        h.cph = (float)g.cph;
+        h.sph = (float)g.sph;
         h.body = g.body;
         h.mat = g.mat;
     }

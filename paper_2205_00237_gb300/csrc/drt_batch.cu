@@ -6,7 +6,7 @@
 // an atomic counter, so links of very different sizes share the GPU without a launch per link:
 //   stage 0  FP32 base poses              (link, body or terminal, chunk)
 //   stage 1  FP64 chunk-base poses        (link, body, chunk)
-//   stage 2  multi-diffraction warm start (link, path with >= 2 D in a segment, chunk)
+//   stage 2  multi-diffraction warm start (link, path with >= 2 D in a segment, chunk base 0..n)
 //   stage 3  FP64 chunk anchors           (link, path, chunk)
 //   stage 4  fused extrapolation + H      (link, block of 32 time steps)
 // Stage 4 never writes per-path-step records to HBM: WARPS warps compute the records of WARPS
@@ -90,9 +90,9 @@ __global__ void __launch_bounds__(128) k_stage(const BatchDev B) {
             int b = (int)(local / nch), c = (int)(local - (long long)b * nch);
             body_pose_row(BL.L.bodies[b], BL.tg.t_start + (double)c * BL.tg.chunk * BL.tg.dt,
                           BL.pose64 + local * POSE_W);
-        } else if (STAGE == ST_WARM) {
-            int p = BL.L.n_bulk + (int)(local / nch), c = (int)(local % nch);
-            path_warm_fp64(BL.L, BL.tg, BL.pose64, nch, c, p, c, BL.warm);
+        } else if (STAGE == ST_WARM) {   // rows 0..nch
+            int p = BL.L.n_bulk + (int)(local / (nch + 1)), c = (int)(local % (nch + 1));
+            path_warm_fp64(BL.L, BL.tg, p, c, BL.warm);
         } else {
             int p = (int)(local / nch), c = (int)(local % nch);
             path_base_fp64(BL.L, BL.tg, BL.fg, BL.pose64, p, c, BL.base, BL.warm);
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_fused(const BatchDev B) {
 }
 
 // FP64 redo of queued steps; their contribution is added to H (all bins) with atomics
-__global__ void __launch_bounds__(128) k_batch_redo(const BatchDev B) {
+__global__ void __launch_bounds__(32) k_batch_redo(const BatchDev B) {   // one warp per block, spread over SMs
     const int n = min(*B.redo.count, B.redo.cap);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int4 itm = B.redo.items[k];
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(128) k_batch_redo(const BatchDev B) {
         const RecD nor{nullptr, nullptr};
         path_step_fp64_core(
             BL.L, BL.tg, BL.fg, itm.y, itm.z, BL.out, nor, true,
-            [&](int ty, int idx) { return load_prim_direct<double>(BL.L, t, ty, idx); }, nullptr, r);
+            [&](int ty, int idx) { return load_prim_direct<double>(BL.L, t, ty, idx); }, BL.warm, r);
         if (r[0] == 0.0 && r[1] == 0.0) continue;
         const double f0 = BL.fg.fc - 0.5 * BL.fg.bandwidth, df = BL.fg.bandwidth / BL.fg.n_bins;
         float2 *row = BL.H + (size_t)itm.z * BL.fg.n_bins;
@@ -256,7 +256,7 @@ static cudaError_t run_stages(BatchPlan &P, cudaStream_t s, long long fused_limi
     if (e == cudaSuccess && P.n_items[ST_BASE]) k_stage<ST_BASE><<<sms * 4, 128, 0, s>>>(B);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess && B.n_items[ST_FUSED]) e = launch_fused(P.variant < 0 ? 0 : P.variant, B, s);
-    if (e == cudaSuccess && B.n_items[ST_FUSED]) k_batch_redo<<<sms * 2, 128, 0, s>>>(B);
+    if (e == cudaSuccess && B.n_items[ST_FUSED]) k_batch_redo<<<sms * 8, 32, 0, s>>>(B);
     if (e == cudaSuccess) e = cudaGetLastError();
     return e;
 }
@@ -315,17 +315,17 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
         std::memset(&B, 0, sizeof(B));
         B.L = *links[i];
         int chunk = choose_chunk(views[i], tgs[i], fgs[i]);
-        B.tg = TimeGridD{tgs[i].t_start, tgs[i].dt, tgs[i].n_steps, chunk};
-        B.fg = FreqGridD{fgs[i].fc, fgs[i].bandwidth, fgs[i].n_bins};
+        B.tg = make_tgrid(tgs[i].t_start, tgs[i].dt, tgs[i].n_steps, chunk);
+        B.fg = make_fgrid(fgs[i].fc, fgs[i].bandwidth, fgs[i].n_bins);
         B.H = reinterpret_cast<float2 *>(H[i]);
         if (outs) B.out = outs[i];
         long long nch = (tgs[i].n_steps + chunk - 1) / chunk;
         int md = B.L.n_paths - B.L.n_bulk;
         B.poseb = reinterpret_cast<PoseB *>(take((size_t)(B.L.n_bodies + 2) * nch * sizeof(PoseB)));
         B.pose64 = reinterpret_cast<double *>(take((size_t)B.L.n_bodies * nch * POSE_W * sizeof(double)));
-        B.warm = reinterpret_cast<double *>(take((size_t)md * nch * 2 * MAXI * sizeof(double)));
+        B.warm = reinterpret_cast<double *>(take((size_t)md * (nch + 1) * 2 * MAXI * sizeof(double)));
         B.base = reinterpret_cast<BaseRec *>(take((size_t)B.L.n_paths * nch * sizeof(BaseRec)));
-        long long cnt[N_STAGES] = {(B.L.n_bodies + 2) * nch, (long long)B.L.n_bodies * nch, (long long)md * nch,
+        long long cnt[N_STAGES] = {(B.L.n_bodies + 2) * nch, (long long)B.L.n_bodies * nch, (long long)md * (nch + 1),
                                    (long long)B.L.n_paths * nch,
                                    (tgs[i].n_steps + FUSED_T - 1) / FUSED_T};   // a link without paths gets H = 0
         for (int s = 0; s < N_STAGES; ++s) {

@@ -20,12 +20,12 @@ constexpr int POSE_W = 18;   // doubles per (time, body) pose record: R (3x3 row
 // posed position is O(t) + R(t) rel
 struct FaceD { double c[3], n[3], u[3], hu, hw; int32_t body, mat; };                       // 96 B
 struct EdgeD { double a[3], e[3], t0[3], n0[3], len, wn; int32_t body, mat, pad0, pad1; };  // 128 B
-struct TileD { double c[3], n[3], area, s, alpha, phase; int32_t body, mat; };               // 88 B
+struct TileD { double c[3], n[3], area, s, alpha, cph, sph; int32_t body, mat; };          // 96 B: cph + j sph = exp(j phase)
 struct MatD { double eps_r, sigma, rough, pec; float eps_rf, sigmaf, roughf, pecf; };       // 48 B
 // FP32 copies for the FP32-bulk form (same meaning, no FP64 conversions in its kernels)
 struct FaceF { float c[3], n[3], u[3], hu, hw; int32_t body, mat, pad0, pad1, pad2; };          // 64 B
 struct EdgeF { float a[3], e[3], t0[3], n0[3], len, wn; int32_t body, mat; };                 // 64 B
-struct TileF { float c[3], n[3], area, s, alpha, phase; int32_t body, mat; };                 // 48 B
+struct TileF { float c[3], n[3], area, s, alpha, cph, sph; int32_t body, mat; };            // 52 B
 struct TermD { double r[3], v[3], a[3]; };
 struct BodyD { double o[3], v[3], a[3], k[3], w0, wdot; };
 
@@ -51,8 +51,28 @@ struct LinkDev {
 
 // chunk: time steps per chunk (FP32-bulk FP64 anchors and multi-diffraction warm starts are taken
 // at the first step of every chunk); a power of two in [4, 64]
-struct TimeGridD { double t_start, dt; int32_t n_steps, chunk; };
-struct FreqGridD { double fc, bandwidth; int32_t n_bins; };
+// grids as kernels see them, with the FP32 constants of the FP32-bulk form derived once on the host
+// (per-step FP64 divisions of grid constants would occupy the FP64 pipe of the FP32 kernels)
+struct TimeGridD {
+    double t_start, dt;
+    int32_t n_steps, chunk;
+    float dtf;   // dt
+};
+struct FreqGridD {
+    double fc, bandwidth;
+    int32_t n_bins;
+    float fcf;        // fc
+    float f0c, dfc;   // (fc - B/2) / c and B / (n_bins c): first bin and bin step over c (1/m)
+    float disp_lim;   // interaction-point displacement since the chunk base past which a step is redone in FP64 (m)
+};
+inline TimeGridD make_tgrid(double t_start, double dt, int32_t n_steps, int32_t chunk) {
+    return TimeGridD{t_start, dt, n_steps, chunk, (float)dt};
+}
+inline FreqGridD make_fgrid(double fc, double bandwidth, int32_t n_bins) {
+    const double c0 = 299792458.0;
+    return FreqGridD{fc, bandwidth, n_bins, (float)fc, (float)((fc - 0.5 * bandwidth) / c0),
+                     (float)(bandwidth / n_bins / c0), (float)(0.8 * 60e9 / fc)};
+}
 
 // user-visible outputs (caller order), any may be null
 struct OutD {
@@ -147,13 +167,15 @@ size_t bulk_base_bytes(const LinkDev &L, const TimeGridD &tg);
 cudaError_t launch_pose_bulk(const LinkDev &L, const TimeGridD &tg, void *poseb, cudaStream_t s);
 size_t bulk_pose64_bytes(const LinkDev &L, const TimeGridD &tg);
 size_t bulk_redo_bytes(const LinkDev &L, const TimeGridD &tg);
+// warm starts of the multi-diffraction chains (warm, warm_bytes) then the FP64 anchors of every path
 cudaError_t launch_base_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, double *pose64, void *base,
-                             cudaStream_t s);
+                             double *warm, cudaStream_t s);
 // the redo scratch holds an int counter (zeroed here, on the stream) followed by the (path, step) list
 cudaError_t launch_extrapolate_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const void *poseb,
-                                    const void *base, const OutD &out, const RecD &rec, void *redo, cudaStream_t s);
+                                    const void *base, const double *warm, const OutD &out, const RecD &rec,
+                                    void *redo, cudaStream_t s);
 cudaError_t launch_redo(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const OutD &out, const RecD &rec,
-                        void *redo, cudaStream_t s);
+                        void *redo, const double *warm, cudaStream_t s);
 cudaError_t launch_synth(const RecD &rec, int32_t n_paths, const TimeGridD &tg, const FreqGridD &fg,
                          float2 *H, cudaStream_t s);
 cudaError_t launch_probe(int kind, int blocks, double *sink, cudaStream_t s, float *ms);

@@ -46,24 +46,21 @@ k_extrapolate_fp64(const LinkDev L, const TimeGridD tg, const FreqGridD fg, cons
     int p = p0 + blockIdx.x;
     int ti = blockIdx.y * EXT_T + threadIdx.x;
     if (p >= L.n_paths || ti >= tg.n_steps) return;
-    const double *w = nullptr;
-    if (warm && p >= L.n_bulk)
-        w = warm + ((size_t)(ti / tg.chunk) * (L.n_paths - L.n_bulk) + (p - L.n_bulk)) * (2 * MAXI);
-    path_step_fp64(L, tg, fg, pose, p, ti, out, rec, f32out != 0, w);
+    path_step_fp64(L, tg, fg, pose, p, ti, out, rec, f32out != 0, warm);
 }
 
 // warm-start pre-pass over (multi-diffraction path, chunk)
 constexpr int WARM_T = 32;
 __global__ void __launch_bounds__(WARM_T)
-k_warm_fp64(const LinkDev L, const TimeGridD tg, const double *__restrict__ pose, double *__restrict__ warm) {
+k_warm_fp64(const LinkDev L, const TimeGridD tg, double *__restrict__ warm) {
     int p = L.n_bulk + blockIdx.x;
     int c = blockIdx.y * WARM_T + threadIdx.x;
-    if (p >= L.n_paths || c >= n_chunks_of(tg)) return;
-    path_warm_fp64(L, tg, pose, tg.n_steps, c * tg.chunk, p, c, warm);
+    if (p >= L.n_paths || c > n_chunks_of(tg)) return;   // rows 0..n_chunks
+    path_warm_fp64(L, tg, p, c, warm);
 }
 
 size_t warm_bytes(const LinkDev &L, const TimeGridD &tg) {
-    return (size_t)(L.n_paths - L.n_bulk) * n_chunks_of(tg) * 2 * MAXI * sizeof(double);
+    return (size_t)(L.n_paths - L.n_bulk) * (n_chunks_of(tg) + 1) * 2 * MAXI * sizeof(double);
 }
 
 cudaError_t launch_extrapolate_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg,
@@ -72,8 +69,8 @@ cudaError_t launch_extrapolate_fp64(const LinkDev &L, const TimeGridD &tg, const
     if (p1 < 0) p1 = L.n_paths;
     if (p1 <= p0 || tg.n_steps == 0) return cudaSuccess;
     if (warm && L.n_bulk < L.n_paths) {
-        dim3 gw(L.n_paths - L.n_bulk, (n_chunks_of(tg) + WARM_T - 1) / WARM_T);
-        k_warm_fp64<<<gw, WARM_T, 0, s>>>(L, tg, pose, warm);
+        dim3 gw(L.n_paths - L.n_bulk, (n_chunks_of(tg) + 1 + WARM_T - 1) / WARM_T);
+        k_warm_fp64<<<gw, WARM_T, 0, s>>>(L, tg, warm);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -122,21 +119,27 @@ size_t bulk_redo_bytes(const LinkDev &L, const TimeGridD &tg) {
 constexpr int BASE_T = 64;
 __global__ void __launch_bounds__(BASE_T)
 k_base_fp64(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const double *__restrict__ pose64,
-            BaseRec *__restrict__ base) {
+            BaseRec *__restrict__ base, const double *__restrict__ warm) {
     int p = blockIdx.x;
     int c = blockIdx.y * BASE_T + threadIdx.x;
-    if (p >= L.n_bulk || c >= n_chunks_of(tg)) return;
-    path_base_fp64(L, tg, fg, pose64, p, c, base);
+    if (p >= L.n_paths || c >= n_chunks_of(tg)) return;
+    path_base_fp64(L, tg, fg, pose64, p, c, base, warm);
 }
 
 cudaError_t launch_base_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, double *pose64, void *base,
-                             cudaStream_t s) {
-    if (L.n_bulk == 0 || tg.n_steps == 0) return cudaSuccess;
-    TimeGridD tc{tg.t_start, tg.dt * tg.chunk, n_chunks_of(tg), 1};   // chunk bases
+                             double *warm, cudaStream_t s) {
+    if (L.n_paths == 0 || tg.n_steps == 0) return cudaSuccess;
+    if (L.n_bulk < L.n_paths) {   // warm starts of the multi-diffraction chains first (rows 0..n_chunks)
+        dim3 gw(L.n_paths - L.n_bulk, (n_chunks_of(tg) + 1 + WARM_T - 1) / WARM_T);
+        k_warm_fp64<<<gw, WARM_T, 0, s>>>(L, tg, warm);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    TimeGridD tc = make_tgrid(tg.t_start, tg.dt * tg.chunk, n_chunks_of(tg), 1);   // chunk bases
     cudaError_t e = launch_pose(L, tc, pose64, s);
     if (e != cudaSuccess) return e;
-    dim3 grid(L.n_bulk, (n_chunks_of(tg) + BASE_T - 1) / BASE_T);
-    k_base_fp64<<<grid, BASE_T, 0, s>>>(L, tg, fg, pose64, reinterpret_cast<BaseRec *>(base));
+    dim3 grid(L.n_paths, (n_chunks_of(tg) + BASE_T - 1) / BASE_T);
+    k_base_fp64<<<grid, BASE_T, 0, s>>>(L, tg, fg, pose64, reinterpret_cast<BaseRec *>(base), warm);
     return cudaGetLastError();
 }
 
@@ -150,38 +153,43 @@ static RedoList redo_list(void *redo, const LinkDev &L, const TimeGridD &tg) {
 
 __global__ void __launch_bounds__(EXT_T)
 k_extrapolate_bulk(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const PoseB *__restrict__ poseb,
-                   const BaseRec *__restrict__ base, const OutD out, const RecD rec, const RedoList redo) {
+                   const BaseRec *__restrict__ base, const double *__restrict__ warm, const OutD out, const RecD rec,
+                   const RedoList redo) {
     int p = blockIdx.x;
     int ti = blockIdx.y * EXT_T + threadIdx.x;
-    if (p >= L.n_bulk || ti >= tg.n_steps) return;
-    path_step_bulk(L, tg, fg, poseb, base, p, ti, out, rec, redo);
+    if (p >= L.n_paths || ti >= tg.n_steps) return;
+    path_step_bulk(L, tg, fg, poseb, base, warm, p, ti, out, rec, redo);
 }
 
 cudaError_t launch_extrapolate_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const void *poseb,
-                                    const void *base, const OutD &out, const RecD &rec, void *redo, cudaStream_t s) {
+                                    const void *base, const double *warm, const OutD &out, const RecD &rec, void *redo,
+                                    cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(redo, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    if (L.n_bulk == 0 || tg.n_steps == 0) return cudaSuccess;
-    dim3 grid(L.n_bulk, (tg.n_steps + EXT_T - 1) / EXT_T);
+    if (L.n_paths == 0 || tg.n_steps == 0) return cudaSuccess;
+    dim3 grid(L.n_paths, (tg.n_steps + EXT_T - 1) / EXT_T);
     k_extrapolate_bulk<<<grid, EXT_T, 0, s>>>(L, tg, fg, reinterpret_cast<const PoseB *>(poseb),
-                                              reinterpret_cast<const BaseRec *>(base), out, rec, redo_list(redo, L, tg));
+                                              reinterpret_cast<const BaseRec *>(base), warm, out, rec,
+                                              redo_list(redo, L, tg));
     return cudaGetLastError();
 }
 
 // FP64 redo of the queued path-steps: a fixed grid strides over the device-side count
-__global__ void __launch_bounds__(128)
-k_redo(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const OutD out, const RecD rec, const RedoList redo) {
+// one warp per block: the few queued steps spread over all SMs (each is a long FP64 chain)
+__global__ void __launch_bounds__(32)
+k_redo(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const OutD out, const RecD rec, const RedoList redo,
+       const double *__restrict__ warm) {
     int n = min(*redo.count, redo.cap);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         int4 it = redo.items[k];
-        path_step_redo(L, tg, fg, it.y, it.z, out, rec);
+        path_step_redo(L, tg, fg, it.y, it.z, out, rec, warm);
     }
 }
 
 cudaError_t launch_redo(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const OutD &out, const RecD &rec,
-                        void *redo, cudaStream_t s) {
+                        void *redo, const double *warm, cudaStream_t s) {
     if (L.n_paths == 0 || tg.n_steps == 0) return cudaSuccess;
-    k_redo<<<152 * 2, 128, 0, s>>>(L, tg, fg, out, rec, redo_list(redo, L, tg));
+    k_redo<<<152 * 8, 32, 0, s>>>(L, tg, fg, out, rec, redo_list(redo, L, tg), warm);
     return cudaGetLastError();
 }
 

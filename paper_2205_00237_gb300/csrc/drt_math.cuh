@@ -118,18 +118,18 @@ template <class T> DRT_HD cx<T> operator*(cx<T> a, cx<T> b) {
 template <class T> DRT_HD cx<T> operator*(cx<T> a, T s) { return {a.re * s, a.im * s}; }
 template <class T> DRT_HD cx<T> operator*(T s, cx<T> a) { return {a.re * s, a.im * s}; }
 template <class T> DRT_HD cx<T> cdiv(cx<T> a, cx<T> b) {
-    // Smith's algorithm
+    // Smith's algorithm, with one reciprocal of the scaled denominator
     if (fabs(b.re) >= fabs(b.im)) {
-        T r = b.im / b.re, den = b.re + b.im * r;
-        return {(a.re + a.im * r) / den, (a.im - a.re * r) / den};
+        T r = b.im / b.re, inv = T(1) / (b.re + b.im * r);
+        return {(a.re + a.im * r) * inv, (a.im - a.re * r) * inv};
     }
-    T r = b.re / b.im, den = b.re * r + b.im;
-    return {(a.re * r + a.im) / den, (a.im * r - a.re) / den};
+    T r = b.re / b.im, inv = T(1) / (b.re * r + b.im);
+    return {(a.re * r + a.im) * inv, (a.im * r - a.re) * inv};
 }
 template <class T> DRT_HD T cabs2(cx<T> a) { return a.re * a.re + a.im * a.im; }
 // principal square root (Re >= 0)
 template <class T> DRT_HD cx<T> csqrt_(cx<T> z) {
-    T r = hypot(z.re, z.im);
+    T r = sqrt(z.re * z.re + z.im * z.im);   // |z| of relative permittivities: no overflow scaling
     if (r == T(0)) return {T(0), T(0)};
     if (z.re >= T(0)) {
         T t = sqrt(T(0.5) * (r + z.re));

@@ -261,20 +261,20 @@ template <> DRT_HD void clamp_positive<dd>(dd &x, float eps) {
     }
 }
 
-// Newton start for an edge parameter: value s0 + tau sd0 at the step, rate sd0; for delta numbers
-// the base part is s0 (the chunk-base solution) and the delta tau sd0
-template <class S> DRT_HD S newton_start(double s0, double sd0, double tau);
-template <> DRT_HD double newton_start<double>(double s0, double sd0, double tau) { return s0 + sd0 * tau; }
-template <> DRT_HD dl<double> newton_start<dl<double>>(double s0, double sd0, double tau) {
-    return {s0 + sd0 * tau, sd0};
+// Newton start for an edge parameter from its value `base` + `delta` and rate: for delta numbers
+// the base part is `base` (the chunk-base solution) and the delta `delta`
+template <class S> DRT_HD S newton_start(double base, double delta, double rate);
+template <> DRT_HD double newton_start<double>(double base, double delta, double) { return base + delta; }
+template <> DRT_HD dl<double> newton_start<dl<double>>(double base, double delta, double rate) {
+    return {base + delta, rate};
 }
-template <> DRT_HD dd newton_start<dd>(double s0, double sd0, double tau) {
-    return {(float)s0, (float)(sd0 * tau), (float)sd0};
+template <> DRT_HD dd newton_start<dd>(double base, double delta, double rate) {
+    return {(float)base, (float)delta, (float)rate};
 }
 
 template <class S>
-DRT_HD void multi_diffraction(const Prim<S> *pr, v3<S> *V, int a, int b, const double *s0, const double *sd0,
-                              double tau, uint32_t &fl) {
+DRT_HD void multi_diffraction(const Prim<S> *pr, v3<S> *V, int a, int b, const double *s0, const double *ds0,
+                              const double *rate0, uint32_t &fl) {
     typedef typename ST<S>::R T;
     // convergence threshold on the Newton step (m): near round-off of the working precision
     const T tol = sizeof(T) == 8 ? T(1e-10) : T(1e-4);
@@ -286,12 +286,12 @@ DRT_HD void multi_diffraction(const Prim<S> *pr, v3<S> *V, int a, int b, const d
     for (int i = a + 1; i < b; ++i)
         if (pr[i - 1].type == T_D) {
             didx[m] = i;
-            s[m] = newton_start<S>(s0[i - 1], sd0 ? sd0[i - 1] : 0.0, tau);
+            s[m] = newton_start<S>(s0[i - 1], ds0 ? ds0[i - 1] : 0.0, rate0 ? rate0[i - 1] : 0.0);
             step[m] = scst<S>(T(0));
             ++m;
         }
     bool conv = false;
-    int extra = 1, halvings = 0;
+    int halvings = 0;
     T Lprev = T(0), smax_prev = T(0);
     bool have_prev = false;
     for (int it = 0; it < 64; ++it) {
@@ -330,10 +330,14 @@ DRT_HD void multi_diffraction(const Prim<S> *pr, v3<S> *V, int a, int b, const d
             step[j] = dp[j];
         }
         smax_prev = smax;
-        if (conv) {
-            if (--extra < 0) break;
-        } else if (smax < tol) {
-            conv = true;   // one more full step refines the derivative part
+        // On dual numbers one Newton step from a value within smax of the root leaves the
+        // derivative part O(smax) from the implicit-function derivative whatever the start's
+        // derivative was, so FP64 stops at the first step below tol (1e-10 m); FP32, whose tol is
+        // 1e-4 m, takes one more step to refine both parts.
+        if (conv) break;
+        if (smax < tol) {
+            conv = true;
+            if (sizeof(T) == 8) break;
         }
     }
     if (!conv) fl |= F_NOCONV;
@@ -349,7 +353,7 @@ DRT_HD void multi_diffraction(const Prim<S> *pr, v3<S> *V, int a, int b, const d
 // geometry of one path-step: vertices V[0..n+1] (TX, interaction points, RX) with velocities
 template <class S>
 DRT_HD void solve_geometry(const Prim<S> *pr, int n, v3<S> *V, const double *s0, uint32_t &fl,
-                           const double *sd0 = nullptr, double tau = 0.0) {
+                           const double *ds0 = nullptr, const double *rate0 = nullptr) {
     for (int i = 1; i <= n; ++i)
         if (pr[i - 1].type == T_S) V[i] = pr[i - 1].p;   // Sec. III-C: tile centroid moves rigidly
     int a = 0;
@@ -372,7 +376,7 @@ DRT_HD void solve_geometry(const Prim<S> *pr, int n, v3<S> *V, const double *s0,
             backtrack(pr, V, a, dpos);
             backtrack(pr, V, dpos, b);
         } else {
-            multi_diffraction(pr, V, a, b, s0, sd0, tau, fl);
+            multi_diffraction(pr, V, a, b, s0, ds0, rate0, fl);
         }
         a = b;
     }
@@ -426,15 +430,15 @@ template <class T> struct MatV { T eps_r, sigma, rough; bool pec; };
 template <class T> DRT_HD MatV<T> matv(const MatD &m);
 template <> DRT_HD MatV<double> matv<double>(const MatD &m) { return {m.eps_r, m.sigma, m.rough, m.pec != 0.0}; }
 template <> DRT_HD MatV<float> matv<float>(const MatD &m) { return {m.eps_rf, m.sigmaf, m.roughf, m.pecf != 0.f}; }
-template <class T> struct TileV { T area, s, phase; int alpha; };
+template <class T> struct TileV { T area, s, cph, sph; int alpha; };   // cph + j sph = exp(j phase)
 template <class T> DRT_HD TileV<T> tilev(const LinkDev &L, int idx);
 template <> DRT_HD TileV<double> tilev<double>(const LinkDev &L, int idx) {
     const TileD &t = L.tiles[idx];
-    return {t.area, t.s, t.phase, (int)t.alpha};
+    return {t.area, t.s, t.cph, t.sph, (int)t.alpha};
 }
 template <> DRT_HD TileV<float> tilev<float>(const LinkDev &L, int idx) {
     const TileF &t = L.tilesF[idx];
-    return {t.area, t.s, t.phase, (int)t.alpha};
+    return {t.area, t.s, t.cph, t.sph, (int)t.alpha};
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -458,11 +462,19 @@ DRT_HD void fresnel(const MatV<T> &m, T fc, T ct, cx<T> &rte, cx<T> &rtm) {
 // UTD transition function F(X) = 2j sqrt(X) exp(jX) int_sqrt(X)^inf exp(-j u^2) du for X >= 0,
 // written as sqrt(pi X) exp(j pi/4) erfcx(exp(j pi/4) sqrt(X)) (erfcx(z) = exp(z^2) erfc(z)) and
 // evaluated by the Maclaurin series of erf (small X), Laplace's continued fraction for erfc
-// (middle range, evaluated bottom-up with a fixed depth) and the asymptotic series
+// (middle range, evaluated bottom-up to a depth that falls with X) and the asymptotic series
 // F ~ sum_m (2m-1)!! / (-2jX)^m (large X) -- Abramowitz & Stegun 7.1.5, 7.1.14, 7.1.23.
 template <class T> struct TransitionCfg;
-template <> struct TransitionCfg<double> { static constexpr double x_ser = 6.0, x_asy = 100.0; static constexpr int n_cf = 40, n_asy = 12; };
-template <> struct TransitionCfg<float> { static constexpr float x_ser = 3.0f, x_asy = 40.0f; static constexpr int n_cf = 24, n_asy = 8; };
+// The continued fraction's depth follows X: ceil(cf_a + cf_b / X) terms reach the working precision
+// (2e-16 relative in FP64, 3e-8 in FP32, checked against 40-digit erfc on [x_ser, x_asy)).
+template <> struct TransitionCfg<double> {
+    static constexpr double x_ser = 6.0, x_asy = 100.0, cf_a = 6.0, cf_b = 370.0;
+    static constexpr int n_cf = 68, n_asy = 12;
+};
+template <> struct TransitionCfg<float> {
+    static constexpr float x_ser = 3.0f, x_asy = 40.0f, cf_a = 3.0f, cf_b = 84.0f;
+    static constexpr int n_cf = 31, n_asy = 8;
+};
 
 template <class T> DRT_HD cx<T> transition_F(T X) {
     using Cfg = TransitionCfg<T>;
@@ -498,7 +510,8 @@ template <class T> DRT_HD cx<T> transition_F(T X) {
     }
     // erfcx(z) = 1 / (sqrt(pi) (z + (1/2)/(z + 1/(z + (3/2)/(z + ...)))))
     cx<T> f = z;
-    for (int k = Cfg::n_cf; k >= 1; --k) f = z + cdiv(C<T>(T(0.5) * T(k), T(0)), f);
+    const int depth = min(Cfg::n_cf, (int)ceil(T(Cfg::cf_a) + T(Cfg::cf_b) / X));
+    for (int k = depth; k >= 1; --k) f = z + cdiv(C<T>(T(0.5) * T(k), T(0)), f);
     return cdiv(pre, f * sqpi);
 }
 
@@ -516,8 +529,11 @@ template <class T> DRT_HD cx<T> utd_term(T eps, T n, T kL) {
 
 // soft / hard wedge diffraction coefficients: Kouyoumjian-Pathak with the spherical-wave distance
 // parameter L, Luebbers' face-coefficient weights for lossy wedges
+// (sphip = |sin phi'|, snphi = |sin(n pi - phi)|: the incidence sines of the 0-face and n-face
+// reflection coefficients, passed in from the direction components)
 template <class T>
-DRT_HD void utd(T n, T phi, T phip, T sinb0, T L, T k, const MatV<T> &m, T fc, cx<T> &Ds, cx<T> &Dh) {
+DRT_HD void utd(T n, T phi, T phip, T sphip, T snphi, T sinb0, T L, T k, const MatV<T> &m, T fc, cx<T> &Ds,
+                cx<T> &Dh) {
     T kL = k * L;
     T pref = T(1) / (T(2) * n * sqrt(T(2 * PI) * k) * sinb0);
     cx<T> Cc = C<T>(-pref * T(0.70710678118654752440), pref * T(0.70710678118654752440));  // -exp(-j pi/4) pref
@@ -527,8 +543,8 @@ DRT_HD void utd(T n, T phi, T phip, T sinb0, T L, T k, const MatV<T> &m, T fc, c
     cx<T> t3 = utd_term(T(PI) - bp + tpn * round((bp - T(PI)) / tpn), n, kL);   // 0-face
     cx<T> t4 = utd_term(T(PI) + bp - tpn * round((bp + T(PI)) / tpn), n, kL);   // n-face
     cx<T> r0s, r0h, rns, rnh;
-    fresnel(m, fc, fabs(sin(phip)), r0s, r0h);
-    fresnel(m, fc, fabs(sin(n * T(PI) - phi)), rns, rnh);
+    fresnel(m, fc, sphip, r0s, r0h);
+    fresnel(m, fc, snphi, rns, rnh);
     cx<T> base = t1 + t2;
     Ds = Cc * (base + r0s * t3 + rns * t4);
     Dh = Cc * (base + r0h * t3 + rnh * t4);
@@ -539,6 +555,9 @@ DRT_HD void utd(T n, T phi, T phip, T sinb0, T L, T k, const MatV<T> &m, T fc, c
 // I_j = 2 pi / (j+1) cos(ti) sum_{w=0}^{(j-1)/2} C(2w, w) sin^{2w}(ti) / 4^w for odd j.
 template <class T> DRT_HD T er_norm(int alpha, T cti) {
     T s2 = fmax(T(0), T(1) - cti * cti);
+    // the sum written out for the exponents of the workloads
+    if (alpha == 2) return T(2 * PI / 3) + T(PI / 2) * cti;
+    if (alpha == 4) return T(2 * PI / 5) + T(PI / 16) * cti * (T(6) + s2);
     T acc = T(0), binom = T(1);   // C(alpha, j)
     T oddsum = T(0), cw = T(1), s2w = T(1);   // running sum_{w} C(2w,w) s2^w / 4^w
     int wmax = -1;
@@ -633,12 +652,21 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
             v3<T> e = val(q.a);
             v3<T> wi = -kin + e * dot(kin, e);
             v3<T> wo = kout - e * dot(kout, e);
-            T phip = wrap2pi(atan2(dot(wi, q.c), dot(wi, q.b)));
-            T phi = wrap2pi(atan2(dot(wo, q.c), dot(wo, q.b)));
+            const T yi = dot(wi, q.c), xi = dot(wi, q.b), yo = dot(wo, q.c), xo = dot(wo, q.b);
+            T phip = wrap2pi(atan2(yi, xi));
+            T phi = wrap2pi(atan2(yo, xo));
             T sinb0 = norm(cross(kin, e));
             T Lp = sdist[i] * sprime[i] * sinb0 * sinb0 / (sdist[i] + sprime[i]);
+            T sphip = T(0), snphi = T(0);
+            if (!m.pec) {   // Luebbers' face coefficients: sin phi' and sin(n pi - phi) from components
+                T sn, cn;
+                sincospi(q.h2, &sn, &cn);
+                const T ri = sqrt(xi * xi + yi * yi), ro = sqrt(xo * xo + yo * yo);
+                sphip = ri > T(0) ? fabs(yi) / ri : T(0);
+                snphi = ro > T(0) ? fabs(sn * xo - cn * yo) / ro : T(0);
+            }
             cx<T> Ds, Dh;
-            utd(q.h2, phi, phip, sinb0, Lp, k, m, fc, Ds, Dh);
+            utd(q.h2, phi, phip, sphip, snphi, sinb0, Lp, k, m, fc, Ds, Dh);
             v3<T> php = -unit(cross(e, kin)), bpv = cross(php, kin);
             v3<T> ph = unit(cross(e, kout)), bv = cross(ph, kout);
             E = cscale(bv, -(Ds * cdot(E, bpv))) + cscale(ph, -(Dh * cdot(E, php)));
@@ -655,7 +683,7 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
             T hb = T(0.5) * (T(1) + cpsi);
             for (int j = 0; j < alpha; ++j) lobe *= hb;   // ((1 + cos psi)/2)^alpha
             T amp = tl.s * sqrt(tl.area * cti / Fa) * sqrt(lobe);
-            cx<T> ph = cexpj(tl.phase);
+            cx<T> ph = C<T>(tl.cph, tl.sph);
             T nE = cnorm(E);
             cx<T> ek = cdot(E, kout);
             c3<T> Ep = E + cscale(kout, -ek);
@@ -733,6 +761,34 @@ DRT_HD void write_record(const RecD &r, size_t ri, double tau, cx<double> a, uin
 
 // FP64 (path, time-step) core: primitives from `load(j, type, idx)`; FP64 outputs (amp double[2],
 // Doppler double) or, for the FP32-bulk form's redo, FP32 ones (float[2], float)
+// Warm starts of the chains with >= 2 diffractions in a segment (paths [n_bulk, n_paths)).  The
+// table holds, per chunk base c = 0..n_chunks (one past the last chunk) and multi-diffraction path,
+// each diffraction vertex's edge parameter s and rate ds/dt from an FP64 dual-number solve
+// ([row][path - n_bulk][2 * MAXI]).  A step at tau into chunk c starts its Newton solve from the
+// cubic Hermite interpolant of (s, ds/dt) at the bases c and c + 1, which is within ~1e-10 m of the
+// root on these workloads, so one Newton step converges.
+DRT_HD const double *warm_row(const LinkDev &L, const double *warm, int row, int p) {
+    return warm + ((size_t)row * (L.n_paths - L.n_bulk) + (p - L.n_bulk)) * (2 * MAXI);
+}
+struct WarmStart { double s[MAXI], ds[MAXI], rate[MAXI]; };
+DRT_HD void hermite_start(const double *w0, const double *w1, double tau, double Tc, WarmStart &ws) {
+    const double h = tau / Tc, h2 = h * h, h3 = h2 * h;
+    const double h10 = h3 - 2.0 * h2 + h, h01 = 3.0 * h2 - 2.0 * h3, h11 = h3 - h2;
+    const double g00 = 6.0 * h2 - 6.0 * h, g10 = 3.0 * h2 - 4.0 * h + 1.0, g11 = 3.0 * h2 - 2.0 * h;
+    for (int j = 0; j < MAXI; ++j) {
+        const double s0 = w0[j], r0 = w0[MAXI + j], s1 = w1[j], r1 = w1[MAXI + j];
+        ws.s[j] = s0;
+        // s(tau) - s0 = h10 Tc r0 + h01 (s1 - s0) + h11 Tc r1 (h00 + h01 = 1)
+        ws.ds[j] = h10 * Tc * r0 + h01 * (s1 - s0) + h11 * Tc * r1;
+        ws.rate[j] = (-g00 * (s1 - s0)) / Tc + g10 * r0 + g11 * r1;
+    }
+}
+DRT_HD void warm_start_at(const LinkDev &L, const TimeGridD &tg, const double *warm, int p, int ti, WarmStart &ws) {
+    const int c = ti / tg.chunk;
+    hermite_start(warm_row(L, warm, c, p), warm_row(L, warm, c + 1, p), (ti - c * tg.chunk) * tg.dt,
+                  tg.chunk * tg.dt, ws);
+}
+
 template <class Loader>
 DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, int p, int ti,
                                 const OutD &out, const RecD &rec, bool f32out, Loader load,
@@ -755,10 +811,10 @@ DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const Fre
     V[0] = terminal<T>(L.tx, t);
     V[n + 1] = terminal<T>(L.rx, t);
     uint32_t fl = 0;
-    if (warm) {
-        // warm start of the Newton solve: edge parameters and their rates at the chunk base
-        const double tau = (ti - (ti / tg.chunk) * tg.chunk) * tg.dt;
-        solve_geometry(pr, n, V, warm, fl, warm + MAXI, tau);
+    if (warm && p >= L.n_bulk) {
+        WarmStart ws;
+        warm_start_at(L, tg, warm, p, ti, ws);
+        solve_geometry(pr, n, V, ws.s, fl, ws.ds, ws.rate);
     } else {
         solve_geometry(pr, n, V, L.ps0 + (size_t)p * MAXI, fl);
     }
@@ -810,11 +866,7 @@ DRT_HD void path_step_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGrid
         [&](int ty, int idx) { return load_prim<double>(L, pose, tg.n_steps, ti, ty, idx); }, warm);
 }
 
-// Warm start for the chains with >= 2 diffractions in a segment (paths [n_bulk, n_paths)): per
-// (path, chunk) the FP64 dual-number solve at the chunk base from the t0 edge parameters gives each
-// diffraction vertex's edge parameter s and its rate ds/dt; a step tau later starts its Newton solve
-// at s + tau ds/dt and converges in one or two iterations.  warm is [chunk][path - n_bulk][8].
-// one dual-number FP64 solve of a chain at time t from the edge-parameter start `sin`; writes each
+// One dual-number FP64 solve of a chain at time t from the edge-parameter start `sin`; writes each
 // diffraction vertex's parameter and rate to sv/sd (sin and 0 where the solve failed)
 template <class Loader>
 DRT_HD void solve_edge_params(const LinkDev &L, int p, double t, const double *sin, double *sv, double *sd,
@@ -850,19 +902,18 @@ DRT_HD void solve_edge_params(const LinkDev &L, int p, double t, const double *s
     }
 }
 
-DRT_HD void path_warm_fp64(const LinkDev &L, const TimeGridD &tg, const double *pose, int n_rows, int row, int p,
-                           int chunk, double *warm) {
-    const int ti = chunk * tg.chunk;
-    const double t = tg.t_start + ti * tg.dt;
+// one row of the warm-start table: the chunk base `row` solved from the t0 edge parameters
+DRT_HD void path_warm_fp64(const LinkDev &L, const TimeGridD &tg, int p, int row, double *warm) {
+    const double t = tg.t_start + (double)row * tg.chunk * tg.dt;
     // rates at t0, where the ray-tracing parameters s0 are already the solution (one iteration)
     double s_t0[MAXI], r_t0[MAXI], start[MAXI];
     solve_edge_params(L, p, 0.0, L.ps0 + (size_t)p * MAXI, s_t0, r_t0,
                       [&](int ty, int idx) { return load_prim_direct<double>(L, 0.0, ty, idx); });
     // chunk-base solve from the linear predictor s(t0) + t ds/dt(t0)
     for (int j = 0; j < MAXI; ++j) start[j] = s_t0[j] + r_t0[j] * t;
-    double *w = warm + ((size_t)chunk * (L.n_paths - L.n_bulk) + (p - L.n_bulk)) * (2 * MAXI);
+    double *w = warm + ((size_t)row * (L.n_paths - L.n_bulk) + (p - L.n_bulk)) * (2 * MAXI);
     solve_edge_params(L, p, t, start, w, w + MAXI,
-                      [&](int ty, int idx) { return load_prim<double>(L, pose, n_rows, row, ty, idx); });
+                      [&](int ty, int idx) { return load_prim_direct<double>(L, t, ty, idx); });
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1049,7 +1100,7 @@ DRT_HD void path_base_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGrid
     V[n + 1] = val(terminal<double>(L.rx, tb));
     uint32_t fl = 0;
     const double *s0 = L.ps0 + (size_t)p * MAXI;
-    if (warm && p >= L.n_bulk) s0 = warm + ((size_t)chunk * (L.n_paths - L.n_bulk) + (p - L.n_bulk)) * (2 * MAXI);
+    if (warm && p >= L.n_bulk) s0 = warm_row(L, warm, chunk, p);
     solve_geometry(pr, n, V, s0, fl);
     BaseRec r;
     double d = 0.0;
@@ -1121,7 +1172,7 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
     rec = Rec5{0.f, 0.f, 0.f, 0.f, 0.f};
     const int n_chunks = (tg.n_steps + tg.chunk - 1) / tg.chunk;
     const int chunk = ti / tg.chunk;
-    const float tau_t = (float)((ti - chunk * tg.chunk) * tg.dt);
+    const float tau_t = (float)(ti - chunk * tg.chunk) * tg.dtf;
     uint32_t code = L.ptypes[p];
     int4 pi = L.pprims[p];
     int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
@@ -1139,8 +1190,9 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
     V[n + 1] = terminal_dd(poseb[(size_t)(L.n_bodies + 1) * n_chunks + chunk], tau_t);
     uint32_t fl = 0;
     if (warm && p >= L.n_bulk) {
-        const double *w = warm + ((size_t)chunk * (L.n_paths - L.n_bulk) + (p - L.n_bulk)) * (2 * MAXI);
-        solve_geometry(pr, n, V, w, fl, w + MAXI, (double)tau_t);
+        WarmStart ws;
+        warm_start_at(L, tg, warm, p, ti, ws);
+        solve_geometry(pr, n, V, ws.s, fl, ws.ds, ws.rate);
     } else {
         solve_geometry(pr, n, V, L.ps0 + (size_t)p * MAXI, fl);
     }
@@ -1155,8 +1207,7 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
         // 1/fc) are left to the FP64 redo.
         float disp2 = 0.f;
         for (int i = 1; i <= n; ++i) disp2 = fmaxf(disp2, V[i].x.d * V[i].x.d + V[i].y.d * V[i].y.d + V[i].z.d * V[i].z.d);
-        const float lim = (float)(0.8 * 60e9 / fg.fc);
-        if (disp2 > lim * lim) fl |= F_REDO64;
+        if (disp2 > fg.disp_lim * fg.disp_lim) fl |= F_REDO64;
     }
     {
         bool finite = true;
@@ -1184,13 +1235,13 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
         // segment vector: FP64-accurate base + FP32 delta
         seg[i] = V3<float>(B.seg[i - 1][0] + sv.x.d, B.seg[i - 1][1] + sv.y.d, B.seg[i - 1][2] + sv.z.d);
     }
-    cx<T> a = (fl & F_DEGEN) ? C<T>(T(0), T(0)) : amplitude(L, pr, n, seg, T(fg.fc));
+    cx<T> a = (fl & F_DEGEN) ? C<T>(T(0), T(0)) : amplitude(L, pr, n, seg, fg.fcf);
     if (out.tau || out.amp || out.doppler || out.angles || out.flags || out.points) {
-        T fd = doppler(n, V, seg, T(fg.fc));
+        T fd = doppler(n, V, seg, fg.fcf);
         size_t oi = (size_t)ti * L.n_paths + L.perm[p];
         write_outputs_bulk(out, oi, n, V, seg, (B.d + (double)dd_len) / C0, a, fd, fl);
     }
-    const float f0c = (float)((fg.fc - 0.5 * fg.bandwidth) / C0), dfc = (float)(fg.bandwidth / fg.n_bins / C0);
+    const float f0c = fg.f0c, dfc = fg.dfc;
     float x = f0c * dd_len;
     x -= floorf(x);
     float ph = B.ph0 + x;
@@ -1204,9 +1255,10 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
 }
 
 DRT_HD void path_step_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const PoseB *poseb,
-                           const BaseRec *base, int p, int ti, const OutD &out, const RecD &rec, const RedoList &redo) {
+                           const BaseRec *base, const double *warm, int p, int ti, const OutD &out, const RecD &rec,
+                           const RedoList &redo) {
     Rec5 r;
-    bulk_eval(L, tg, fg, poseb, base, nullptr, p, ti, out, r, redo, 0);
+    bulk_eval(L, tg, fg, poseb, base, warm, p, ti, out, r, redo, 0);
     if (rec.rec_a) {
         size_t ri = (size_t)ti * L.n_paths + p;
         rec.rec_a[ri] = make_float4(r.ar, r.ai, r.ph, r.hi);
@@ -1216,10 +1268,10 @@ DRT_HD void path_step_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGrid
 
 // FP64 redo of one queued FP32-bulk path-step (FP32 output formats)
 DRT_HD void path_step_redo(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, int p, int ti, const OutD &out,
-                           const RecD &rec) {
+                           const RecD &rec, const double *warm) {
     const double t = tg.t_start + ti * tg.dt;
     path_step_fp64_core(L, tg, fg, p, ti, out, rec, true,
-                        [&](int ty, int idx) { return load_prim_direct<double>(L, t, ty, idx); });
+                        [&](int ty, int idx) { return load_prim_direct<double>(L, t, ty, idx); }, warm);
 }
 
 }  // namespace drt
