@@ -195,13 +195,14 @@ drt_status drt_synthesize_H_noalloc(drt_ctx *ctx, uint64_t link, const drt_time_
  * a10: batched synthesis over many resident links (FP32-bulk form).  drt_batch_create plans one
  * batch: link i is synthesised over tgrids[i] x fgrids[i] into the caller's DEVICE buffer H[i]
  * ([n_steps][n_bins] complex64).  Each stage (base poses, FP64 chunk poses, multi-diffraction warm
- * starts, FP64 chunk anchors, fused extrapolation + synthesis, FP64 redo) is one persistent launch
- * over the (link, work unit) pairs of all links, claimed with atomic counters, largest links first,
- * so uneven links (8 to thousands of paths, 100 to thousands of steps) share one launch per stage.
- * The chunk length per link comes from a phase-error model and the fused kernel's shape (warps per
- * block, frequency bins per thread) from timing its variants on the batch (autotuning, done
- * synchronously inside drt_batch_create).  Scratch is allocated once per batch within the HBM
- * budget.  The links must stay loaded and the H buffers valid while the batch exists.
+ * starts, FP64 chunk anchors, FP32-bulk extrapolation, H synthesis, FP64 redo) is one persistent
+ * launch over the (link, work unit) pairs of all links, claimed with atomic counters, largest links
+ * first, so uneven links (8 to thousands of paths, 100 to thousands of steps) share one launch per
+ * stage.  Extrapolation and synthesis stream through a record buffer of at most 4 GiB in waves of
+ * links.  The chunk length per link comes from a phase-error model and the synthesis frequency
+ * tile (bins per thread) from timing its variants on the batch (autotuning, done synchronously
+ * inside drt_batch_create).  Scratch is allocated once per batch within the HBM budget.  The links
+ * must stay loaded and the H buffers valid while the batch exists.
  * drt_batch_run launches the batch on `stream`; with use_graph != 0 the first run is captured into
  * a CUDA graph (captured on a stream of the batch, so any stream can replay it) and later runs
  * replay it.  precision must be DRT_FP32_BULK.
@@ -211,7 +212,7 @@ drt_status drt_batch_create(drt_ctx *ctx, int32_t n_links, const uint64_t *links
                             const drt_time_grid *tgrids, const drt_freq_grid *fgrids, void *const *H,
                             int32_t precision, drt_batch **out);
 drt_status drt_batch_run(drt_ctx *ctx, drt_batch *batch, int32_t use_graph, void *stream);
-/* chosen fused-kernel variant (0: 8 warps x 32 bins, 1: 8 x 16, 2: 4 x 32, 3: 4 x 16), scratch
+/* chosen synthesis variant (frequency tile of 0: 8, 1: 16, 2: 32 bins per thread), scratch
  * bytes, the autotuner's best sample time (ms) and the path-steps of the last run that FP32 could
  * not resolve and the FP64 redo kernel recomputed (reading it waits for the device); any output
  * may be NULL */

@@ -1,19 +1,22 @@
 // drt_batch.cu -- a10: many resident links in one call, FP32-bulk form.
 //
 // A batch plan holds, per link, its grids, the caller's H buffer and slices of one scratch
-// allocation (base poses, FP64 chunk poses, multi-diffraction warm starts, FP64 chunk anchors).
-// Each stage is one persistent launch over a flattened list of (link, item) work units claimed with
-// an atomic counter, so links of very different sizes share the GPU without a launch per link:
+// allocation (base poses, FP64 chunk poses, multi-diffraction warm starts, FP64 chunk anchors,
+// synthesis records).  Each stage is one persistent launch over a flattened list of (link, unit)
+// work units claimed with an atomic counter, so links of very different sizes share the GPU without
+// a launch per link:
 //   stage 0  FP32 base poses              (link, body or terminal, chunk)
 //   stage 1  FP64 chunk-base poses        (link, body, chunk)
 //   stage 2  multi-diffraction warm start (link, path with >= 2 D in a segment, chunk base 0..n)
 //   stage 3  FP64 chunk anchors           (link, path, chunk)
-//   stage 4  fused extrapolation + H      (link, block of 32 time steps)
-// Stage 4 never writes per-path-step records to HBM: WARPS warps compute the records of WARPS
-// paths for 32 time steps into shared memory, then every thread rotates and accumulates BPT
-// frequency bins of one time step in registers.  Links are ordered by decreasing path count so the
-// largest units are claimed first.  Steps FP32 cannot resolve go to an FP64 redo kernel, which adds
-// their contribution to H with atomics.  The whole sequence can be captured in a CUDA graph.
+//   stage 4  FP32-bulk extrapolation      (link, path, 32 consecutive steps: one warp)
+//   stage 5  H synthesis                  (link, 128 consecutive (step, bin tile) pairs: one block)
+// Stages 4 and 5 run in waves of links whose per-path-step records (20 B each) fit one record
+// buffer, so a batch of any size streams through a bounded scratch.  Links are ordered by
+// decreasing work so the largest units are claimed first.  Steps FP32 cannot resolve go to an FP64
+// redo kernel at the end, which adds their contribution to H with atomics.  The frequency tile
+// width of stage 5 (8, 16 or 32 bins per thread) is autotuned on the batch.  The whole sequence can
+// be captured in a CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,8 +31,13 @@
 
 namespace drt {
 
-enum { ST_POSEB = 0, ST_POSE64 = 1, ST_WARM = 2, ST_BASE = 3, ST_FUSED = 4, N_STAGES = 5 };
-constexpr int FUSED_T = 32;   // time steps per fused work unit (one warp's lanes)
+// stage slots; the synthesis has one slot per tile variant (its units depend on the tile width)
+enum { ST_POSEB = 0, ST_POSE64 = 1, ST_WARM = 2, ST_BASE = 3, ST_BULK = 4, ST_SYNTH = 5, N_STAGES = 8 };
+constexpr int BULK_W = 32;                // time steps per extrapolation unit (one warp's lanes)
+constexpr int SYNTH_U = 128;              // (step, tile) pairs per synthesis unit (one block)
+constexpr int SYNTH_KT[3] = {8, 16, 32};
+constexpr size_t REC_BYTES = sizeof(float4) + sizeof(float);   // one synthesis record
+constexpr size_t REC_CAP = (size_t)4 << 30;                    // record buffer of one wave (bytes)
 
 struct BatchLink {
     LinkDev L;
@@ -37,23 +45,27 @@ struct BatchLink {
     FreqGridD fg;
     PoseB *poseb;      // [bodies + 2][chunks]
     double *pose64;    // [bodies][chunks]
-    double *warm;      // [chunks][n_paths - n_bulk][2 * MAXI]
+    double *warm;      // [chunks + 1][n_paths - n_bulk][2 * MAXI]
     BaseRec *base;     // [chunks][paths]
     float2 *H;         // caller's [T][F]
     OutD out;          // caller's optional per-path-step records (FP32 formats), [T][P]
-    long long it0[N_STAGES + 1];
+    size_t rec0;       // first record of this link in its wave's record buffer ([T][P])
+    long long it0[N_STAGES];   // first item per stage slot (4 on: counted within the link's wave)
 };
 
+// one launch: the links [l0, l1) of its stage or wave, its item count and claim counter
 struct BatchDev {
-    int n_links;
+    int l0, l1;
     const BatchLink *links;
-    long long n_items[N_STAGES];
-    unsigned long long *counters;   // [N_STAGES]
-    RedoList redo;                  // items (link, path, step)
+    long long n_items;
+    unsigned long long *counter;
+    float4 *rec_a;
+    float *rec_b;
+    RedoList redo;   // items (link, path, step)
 };
 
 __device__ __forceinline__ int find_link(const BatchDev &B, int stage, long long it) {
-    int lo = 0, hi = B.n_links - 1;
+    int lo = B.l0, hi = B.l1 - 1;
     while (lo < hi) {   // last link whose first item is <= it
         int mid = (lo + hi + 1) >> 1;
         if (B.links[mid].it0[stage] <= it) lo = mid;
@@ -68,9 +80,9 @@ __device__ __forceinline__ int chunks_of(const TimeGridD &tg) { return (tg.n_ste
 template <int STAGE>
 __global__ void __launch_bounds__(128) k_stage(const BatchDev B) {
     __shared__ long long s_start;
-    const long long total = B.n_items[STAGE];
+    const long long total = B.n_items;
     for (;;) {
-        if (threadIdx.x == 0) s_start = (long long)atomicAdd(&B.counters[STAGE], (unsigned long long)blockDim.x);
+        if (threadIdx.x == 0) s_start = (long long)atomicAdd(B.counter, (unsigned long long)blockDim.x);
         __syncthreads();
         long long it = s_start + threadIdx.x;
         bool done = s_start >= total;
@@ -100,72 +112,76 @@ __global__ void __launch_bounds__(128) k_stage(const BatchDev B) {
     }
 }
 
-// stage 4: fused extrapolation + synthesis
-template <int WARPS, int BPT>
-__global__ void __launch_bounds__(WARPS * 32) k_fused(const BatchDev B) {
-    __shared__ Rec5 srec[WARPS][32];
-    __shared__ long long s_item;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const long long total = B.n_items[ST_FUSED];
+// stage 4: a warp claims (link, path, 32 steps); the lanes share the chain signature
+__global__ void __launch_bounds__(128) k_batch_bulk(const BatchDev B) {
+    const int lane = threadIdx.x & 31;
     for (;;) {
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(&B.counters[ST_FUSED], 1ull);
-        __syncthreads();
-        const long long it = s_item;
-        __syncthreads();
-        if (it >= total) break;
-        const int li = find_link(B, ST_FUSED, it);
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(B.counter, 1ull);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if ((long long)it >= B.n_items) break;
+        const int li = find_link(B, ST_BULK, (long long)it);
         const BatchLink &BL = B.links[li];
-        const int t = (int)(it - BL.it0[ST_FUSED]) * FUSED_T + lane;
-        const int F = BL.fg.n_bins, P = BL.L.n_paths, T = BL.tg.n_steps;
-        const OutD none{};
-        for (int kp = 0; kp < F; kp += WARPS * BPT) {
-            const int k0 = kp + w * BPT;
-            RedoList rl = B.redo;
-            if (kp > 0) rl.count = nullptr;   // queue and record each step once
-            const OutD &out = kp > 0 ? none : BL.out;
-            float2 acc[BPT];
-#pragma unroll
-            for (int j = 0; j < BPT; ++j) acc[j] = make_float2(0.f, 0.f);
-            const float kf = (float)k0;
-            for (int pb = 0; pb < P; pb += WARPS) {
-                const int p = pb + w;
-                Rec5 r{0.f, 0.f, 0.f, 0.f, 0.f};
-                if (p < P && t < T) bulk_eval(BL.L, BL.tg, BL.fg, BL.poseb, BL.base, BL.warm, p, t, out, r, rl, li);
-                srec[w][lane] = r;
-                __syncthreads();
-                if (t < T && k0 < F) {
-                    for (int j = 0; j < WARPS; ++j) {
-                        const Rec5 q = srec[j][lane];
-                        if (q.ar == 0.f && q.ai == 0.f) continue;
-                        float ph = kf * q.hi;   // exact: hi has 12 significant bits, k0 < 4096
-                        ph -= floorf(ph);
-                        ph += q.ph + kf * q.lo;
-                        ph -= floorf(ph);
-                        float sn, cs, ws, wc;
-                        sincospif(2.f * ph, &sn, &cs);
-                        sincospif(2.f * (q.hi + q.lo), &ws, &wc);
-                        float zr = fmaf(q.ar, cs, q.ai * sn), zi = fmaf(q.ai, cs, -q.ar * sn);
-                        const float wr = wc, wi = -ws;
-#pragma unroll
-                        for (int m = 0; m < BPT; ++m) {
-                            acc[m].x += zr;
-                            acc[m].y += zi;
-                            float nr = fmaf(zr, wr, -zi * wi);
-                            zi = fmaf(zr, wi, zi * wr);
-                            zr = nr;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-            if (t < T) {
-                float2 *out = BL.H + (size_t)t * F + k0;
-#pragma unroll
-                for (int m = 0; m < BPT; ++m)
-                    if (k0 + m < F) out[m] = acc[m];
-            }
+        const long long local = (long long)it - BL.it0[ST_BULK];
+        const int nb = (BL.tg.n_steps + BULK_W - 1) / BULK_W;
+        const int p = (int)(local / nb), t = (int)(local % nb) * BULK_W + lane;
+        if (t < BL.tg.n_steps) {
+            Rec5 r;
+            bulk_eval(BL.L, BL.tg, BL.fg, BL.poseb, BL.base, BL.warm, p, t, BL.out, r, B.redo, li);
+            const size_t ri = BL.rec0 + (size_t)t * BL.L.n_paths + p;
+            B.rec_a[ri] = make_float4(r.ar, r.ai, r.ph, r.hi);
+            B.rec_b[ri] = r.lo;
         }
     }
+}
+
+// stage 5: a block takes (link, 128 consecutive (step, tile of KT bins) pairs), one pair per thread
+// as in the single-link synthesis: exact FP32 seed per tile, complex rotation recurrence across the
+// tile
+template <int VI>
+__global__ void __launch_bounds__(SYNTH_U) k_batch_synth(const BatchDev B) {
+    constexpr int KT = SYNTH_KT[VI];
+    const long long it = blockIdx.x;   // one unit per block (a plain grid: no claim loop needed here)
+    if (it >= B.n_items) return;
+    const int li = find_link(B, ST_SYNTH + VI, it);
+    const BatchLink &BL = B.links[li];
+    const int F = BL.fg.n_bins, P = BL.L.n_paths, T = BL.tg.n_steps;
+    const int ntile = (F + KT - 1) / KT;
+    const long long pair = (it - BL.it0[ST_SYNTH + VI]) * SYNTH_U + threadIdx.x;
+    if (pair >= (long long)T * ntile) return;
+    const int ti = (int)(pair / ntile), k0 = (int)(pair % ntile) * KT;
+    const float kf = (float)k0;
+    float2 acc[KT];
+#pragma unroll
+    for (int j = 0; j < KT; ++j) acc[j] = make_float2(0.f, 0.f);
+    const float4 *__restrict__ ra = B.rec_a + BL.rec0 + (size_t)ti * P;
+    const float *__restrict__ rb = B.rec_b + BL.rec0 + (size_t)ti * P;
+    for (int p = 0; p < P; ++p) {
+        const float4 r = __ldg(ra + p);
+        if (r.x == 0.f && r.y == 0.f) continue;
+        const float lo = __ldg(rb + p);
+        float ph = kf * r.w;   // exact: the step's high part has 12 significant bits, k0 < 4096
+        ph -= floorf(ph);
+        ph += r.z + kf * lo;
+        ph -= floorf(ph);
+        float sn, cs, ws, wc;
+        sincospif(2.f * ph, &sn, &cs);
+        sincospif(2.f * (r.w + lo), &ws, &wc);
+        float zr = fmaf(r.x, cs, r.y * sn), zi = fmaf(r.y, cs, -r.x * sn);
+        const float wr = wc, wi = -ws;
+#pragma unroll
+        for (int j = 0; j < KT; ++j) {
+            acc[j].x += zr;
+            acc[j].y += zi;
+            const float nr = fmaf(zr, wr, -zi * wi);
+            zi = fmaf(zr, wi, zi * wr);
+            zr = nr;
+        }
+    }
+    float2 *out = BL.H + (size_t)ti * F + k0;
+#pragma unroll
+    for (int j = 0; j < KT; ++j)
+        if (k0 + j < F) out[j] = acc[j];
 }
 
 // FP64 redo of queued steps; their contribution is added to H (all bins) with atomics
@@ -181,14 +197,26 @@ __global__ void __launch_bounds__(32) k_batch_redo(const BatchDev B) {   // one 
             BL.L, BL.tg, BL.fg, itm.y, itm.z, BL.out, nor, true,
             [&](int ty, int idx) { return load_prim_direct<double>(BL.L, t, ty, idx); }, BL.warm, r);
         if (r[0] == 0.0 && r[1] == 0.0) continue;
+        // a exp(-j 2 pi f_k tau): FP64-reduced seed per 16-bin tile, FP32 rotation across the tile
         const double f0 = BL.fg.fc - 0.5 * BL.fg.bandwidth, df = BL.fg.bandwidth / BL.fg.n_bins;
-        float2 *row = BL.H + (size_t)itm.z * BL.fg.n_bins;
-        for (int kb = 0; kb < BL.fg.n_bins; ++kb) {
-            double x = (f0 + kb * df) * r[2];
-            double s, c;
-            sincospi(2.0 * (x - floor(x)), &s, &c);
-            atomicAdd(&row[kb].x, (float)(r[0] * c + r[1] * s));
-            atomicAdd(&row[kb].y, (float)(r[1] * c - r[0] * s));
+        const int F = BL.fg.n_bins;
+        float2 *row = BL.H + (size_t)itm.z * F;
+        double xs = df * r[2];
+        float ws, wc;
+        sincospif(2.f * (float)(xs - floor(xs)), &ws, &wc);
+        for (int k0 = 0; k0 < F; k0 += 16) {
+            double x = (f0 + k0 * df) * r[2];
+            float sn, cs;
+            sincospif(2.f * (float)(x - floor(x)), &sn, &cs);
+            const float ar = (float)r[0], ai = (float)r[1];
+            float zr = fmaf(ar, cs, ai * sn), zi = fmaf(ai, cs, -ar * sn);
+            for (int j = 0; j < 16 && k0 + j < F; ++j) {
+                atomicAdd(&row[k0 + j].x, zr);
+                atomicAdd(&row[k0 + j].y, zi);
+                const float nr = fmaf(zr, wc, zi * ws);
+                zi = fmaf(zi, wc, -zr * ws);
+                zr = nr;
+            }
         }
     }
 }
@@ -196,35 +224,25 @@ __global__ void __launch_bounds__(32) k_batch_redo(const BatchDev B) {   // one 
 // ------------------------------------------------------------------------------------------------
 // host side
 //
-// One device block per plan: [counters | link table | redo list | per-link scratch], so that a plan
-// can live in memory its owner provides (the serving loop's arena) or in its own allocation.
+// One device block per plan: [counters | link table | redo list | records | per-link scratch], so
+// that a plan can live in memory its owner provides (the serving loop's arena) or in its own
+// allocation.
+struct Wave { int l0, l1; long long n_bulk, n_synth[3]; };
+
 struct BatchPlan {
     int n_links = 0;
     std::vector<BatchLink> host;
-    size_t off_links = 0, off_redo = 0, off_scratch = 0, redo_bytes = 0, bytes = 0;
+    std::vector<Wave> waves;
+    long long n_items[4] = {};   // stages 0-3 over all links
+    size_t off_links = 0, off_redo = 0, off_rec = 0, off_scratch = 0, redo_bytes = 0, rec_count = 0, bytes = 0;
+    size_t n_counters = 0;
     char *mem = nullptr;
     bool owns = false;
-    long long n_items[N_STAGES] = {};
-    int variant = -1;   // fused kernel variant (autotuner or caller)
+    int variant = -1;   // synthesis tile width index (autotuner or caller)
     cudaGraphExec_t graph = nullptr;
     cudaStream_t capture = nullptr;   // private stream the graph is captured on (any caller stream,
                                       // the legacy default stream included, can then launch it)
 };
-
-static const int VARIANTS[4][2] = {{8, 32}, {8, 16}, {4, 32}, {4, 16}};   // (warps, bins per thread)
-
-static BatchDev dev_view(const BatchPlan &P, long long fused_limit = -1) {
-    BatchDev B;
-    B.n_links = P.n_links;
-    B.links = reinterpret_cast<const BatchLink *>(P.mem + P.off_links);
-    for (int s = 0; s < N_STAGES; ++s) B.n_items[s] = P.n_items[s];
-    if (fused_limit >= 0) B.n_items[ST_FUSED] = std::min(fused_limit, P.n_items[ST_FUSED]);
-    B.counters = reinterpret_cast<unsigned long long *>(P.mem);
-    B.redo.count = reinterpret_cast<int *>(P.mem + P.off_redo);
-    B.redo.items = reinterpret_cast<int4 *>(P.mem + P.off_redo + 256);
-    B.redo.cap = (int)std::min<size_t>((P.redo_bytes - 256) / sizeof(int4), 0x7fffffff);
-    return B;
-}
 
 static int sm_count() {
     int dev = 0, n = 0;
@@ -233,31 +251,74 @@ static int sm_count() {
     return n > 0 ? n : 1;
 }
 
-static cudaError_t launch_fused(int variant, const BatchDev &B, cudaStream_t s) {
-    const int sms = sm_count();
-    switch (variant) {
-    case 0: k_fused<VARIANTS[0][0], VARIANTS[0][1]><<<sms * 2, VARIANTS[0][0] * 32, 0, s>>>(B); break;
-    case 1: k_fused<VARIANTS[1][0], VARIANTS[1][1]><<<sms * 2, VARIANTS[1][0] * 32, 0, s>>>(B); break;
-    case 2: k_fused<VARIANTS[2][0], VARIANTS[2][1]><<<sms * 4, VARIANTS[2][0] * 32, 0, s>>>(B); break;
-    default: k_fused<VARIANTS[3][0], VARIANTS[3][1]><<<sms * 4, VARIANTS[3][0] * 32, 0, s>>>(B); break;
+// the launch description of stage `st` (0-3: all links; 4-5: wave w), counter k
+static BatchDev dev_view(const BatchPlan &P, int l0, int l1, long long n_items, size_t k) {
+    BatchDev B;
+    B.l0 = l0;
+    B.l1 = l1;
+    B.links = reinterpret_cast<const BatchLink *>(P.mem + P.off_links);
+    B.n_items = n_items;
+    B.counter = reinterpret_cast<unsigned long long *>(P.mem) + k;
+    B.rec_a = reinterpret_cast<float4 *>(P.mem + P.off_rec);
+    B.rec_b = reinterpret_cast<float *>(P.mem + P.off_rec + P.rec_count * sizeof(float4));
+    B.redo.count = reinterpret_cast<int *>(P.mem + P.off_redo);
+    B.redo.items = reinterpret_cast<int4 *>(P.mem + P.off_redo + 256);
+    B.redo.cap = (int)std::min<size_t>((P.redo_bytes - 256) / sizeof(int4), 0x7fffffff);
+    return B;
+}
+
+static cudaError_t launch_synth_variant(int v, const BatchDev &B, int grid, cudaStream_t s) {
+    switch (v) {
+    case 0: k_batch_synth<0><<<grid, SYNTH_U, 0, s>>>(B); break;
+    case 2: k_batch_synth<2><<<grid, SYNTH_U, 0, s>>>(B); break;
+    default: k_batch_synth<1><<<grid, SYNTH_U, 0, s>>>(B); break;
     }
     return cudaGetLastError();
 }
 
+// stages 0-3 (all links)
+static cudaError_t run_prep(BatchPlan &P, cudaStream_t s) {
+    const int grid = sm_count() * 4;
+    const int nl = P.n_links;
+    if (P.n_items[ST_POSEB]) k_stage<ST_POSEB><<<grid, 128, 0, s>>>(dev_view(P, 0, nl, P.n_items[ST_POSEB], ST_POSEB));
+    if (P.n_items[ST_POSE64])
+        k_stage<ST_POSE64><<<grid, 128, 0, s>>>(dev_view(P, 0, nl, P.n_items[ST_POSE64], ST_POSE64));
+    if (P.n_items[ST_WARM]) k_stage<ST_WARM><<<grid, 128, 0, s>>>(dev_view(P, 0, nl, P.n_items[ST_WARM], ST_WARM));
+    if (P.n_items[ST_BASE]) k_stage<ST_BASE><<<grid, 128, 0, s>>>(dev_view(P, 0, nl, P.n_items[ST_BASE], ST_BASE));
+    return cudaGetLastError();
+}
+
+static cudaError_t run_wave_bulk(BatchPlan &P, size_t w, cudaStream_t s) {
+    const Wave &W = P.waves[w];
+    if (!W.n_bulk) return cudaSuccess;
+    k_batch_bulk<<<sm_count() * 4, 128, 0, s>>>(dev_view(P, W.l0, W.l1, W.n_bulk, 4 + 2 * w));
+    return cudaGetLastError();
+}
+
+static cudaError_t run_wave_synth(BatchPlan &P, size_t w, cudaStream_t s, long long limit = -1) {
+    const Wave &W = P.waves[w];
+    const int v = P.variant < 0 ? 1 : P.variant;
+    long long n = limit >= 0 ? std::min(limit, W.n_synth[v]) : W.n_synth[v];
+    if (!n) return cudaSuccess;
+    return launch_synth_variant(v, dev_view(P, W.l0, W.l1, n, 5 + 2 * w), (int)n, s);
+}
+
+static cudaError_t run_redo(BatchPlan &P, cudaStream_t s) {
+    if (!P.n_links) return cudaSuccess;
+    k_batch_redo<<<sm_count() * 8, 32, 0, s>>>(dev_view(P, 0, P.n_links, 0, 0));
+    return cudaGetLastError();
+}
+
 // all stages of one run, on one stream
-static cudaError_t run_stages(BatchPlan &P, cudaStream_t s, long long fused_limit = -1) {
-    BatchDev B = dev_view(P, fused_limit);
-    cudaError_t e = cudaMemsetAsync(P.mem, 0, sizeof(unsigned long long) * N_STAGES, s);
+static cudaError_t run_stages(BatchPlan &P, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(P.mem, 0, sizeof(unsigned long long) * P.n_counters, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(P.mem + P.off_redo, 0, sizeof(int), s);
-    const int sms = sm_count();
-    if (e == cudaSuccess && P.n_items[ST_POSEB]) k_stage<ST_POSEB><<<sms * 4, 128, 0, s>>>(B);
-    if (e == cudaSuccess && P.n_items[ST_POSE64]) k_stage<ST_POSE64><<<sms * 4, 128, 0, s>>>(B);
-    if (e == cudaSuccess && P.n_items[ST_WARM]) k_stage<ST_WARM><<<sms * 4, 128, 0, s>>>(B);
-    if (e == cudaSuccess && P.n_items[ST_BASE]) k_stage<ST_BASE><<<sms * 4, 128, 0, s>>>(B);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e == cudaSuccess && B.n_items[ST_FUSED]) e = launch_fused(P.variant < 0 ? 0 : P.variant, B, s);
-    if (e == cudaSuccess && B.n_items[ST_FUSED]) k_batch_redo<<<sms * 8, 32, 0, s>>>(B);
-    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = run_prep(P, s);
+    for (size_t w = 0; w < P.waves.size() && e == cudaSuccess; ++w) {
+        e = run_wave_bulk(P, w, s);
+        if (e == cudaSuccess) e = run_wave_synth(P, w, s);
+    }
+    if (e == cudaSuccess) e = run_redo(P, s);
     return e;
 }
 
@@ -296,7 +357,7 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
     P->n_links = n;
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
-    // largest links first: their fused units are claimed first
+    // largest links first: their units are claimed first
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         return (long long)links[a]->n_paths * tgs[a].n_steps > (long long)links[b]->n_paths * tgs[b].n_steps;
     });
@@ -307,8 +368,10 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
         off += r256(b);
         return o;
     };
-    long long it[N_STAGES] = {};
-    size_t redo_items = 0;
+    long long it[4] = {};
+    size_t redo_items = 0, rec_max = 0;
+    Wave W{0, 0, 0, {0, 0, 0}};
+    size_t wave_rec = 0;
     for (int k = 0; k < n; ++k) {
         int i = order[k];
         BatchLink &B = P->host[k];
@@ -319,27 +382,53 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
         B.fg = make_fgrid(fgs[i].fc, fgs[i].bandwidth, fgs[i].n_bins);
         B.H = reinterpret_cast<float2 *>(H[i]);
         if (outs) B.out = outs[i];
-        long long nch = (tgs[i].n_steps + chunk - 1) / chunk;
+        const long long T = tgs[i].n_steps, Pn = B.L.n_paths;
+        long long nch = (T + chunk - 1) / chunk;
         int md = B.L.n_paths - B.L.n_bulk;
         B.poseb = reinterpret_cast<PoseB *>(take((size_t)(B.L.n_bodies + 2) * nch * sizeof(PoseB)));
         B.pose64 = reinterpret_cast<double *>(take((size_t)B.L.n_bodies * nch * POSE_W * sizeof(double)));
         B.warm = reinterpret_cast<double *>(take((size_t)md * (nch + 1) * 2 * MAXI * sizeof(double)));
         B.base = reinterpret_cast<BaseRec *>(take((size_t)B.L.n_paths * nch * sizeof(BaseRec)));
-        long long cnt[N_STAGES] = {(B.L.n_bodies + 2) * nch, (long long)B.L.n_bodies * nch, (long long)md * (nch + 1),
-                                   (long long)B.L.n_paths * nch,
-                                   (tgs[i].n_steps + FUSED_T - 1) / FUSED_T};   // a link without paths gets H = 0
-        for (int s = 0; s < N_STAGES; ++s) {
-            B.it0[s] = it[s];
-            it[s] += cnt[s];
+        long long cnt[4] = {(B.L.n_bodies + 2) * nch, (long long)B.L.n_bodies * nch, (long long)md * (nch + 1),
+                            Pn * nch};
+        for (int st = 0; st < 4; ++st) {
+            B.it0[st] = it[st];
+            it[st] += cnt[st];
         }
-        redo_items += (size_t)B.L.n_paths * tgs[i].n_steps;
+        // waves: consecutive links whose records fit the record buffer
+        const size_t recs = (size_t)T * Pn;
+        if (k > W.l0 && (wave_rec + recs) * REC_BYTES > REC_CAP) {
+            W.l1 = k;
+            P->waves.push_back(W);
+            rec_max = std::max(rec_max, wave_rec);
+            W = Wave{k, k, 0, {0, 0, 0}};
+            wave_rec = 0;
+        }
+        B.rec0 = wave_rec;
+        wave_rec += recs;
+        B.it0[ST_BULK] = W.n_bulk;
+        W.n_bulk += Pn * ((T + BULK_W - 1) / BULK_W);
+        for (int v = 0; v < 3; ++v) {   // a link without paths gets H = 0
+            const long long pairs = T * ((fgs[i].n_bins + SYNTH_KT[v] - 1) / SYNTH_KT[v]);
+            B.it0[ST_SYNTH + v] = W.n_synth[v];
+            W.n_synth[v] += (pairs + SYNTH_U - 1) / SYNTH_U;
+        }
+        redo_items += recs;
     }
-    for (int s = 0; s < N_STAGES; ++s) P->n_items[s] = it[s];
+    if (n) {
+        W.l1 = n;
+        P->waves.push_back(W);
+        rec_max = std::max(rec_max, wave_rec);
+    }
+    for (int st = 0; st < 4; ++st) P->n_items[st] = it[st];
+    P->rec_count = rec_max;
+    P->n_counters = 4 + 2 * P->waves.size();
     // the redo list is bounded: beyond 2^22 + 1/16 of all steps the surplus is dropped and counted
     P->redo_bytes = 256 + r256(std::min<size_t>(redo_items, ((size_t)1 << 22) + redo_items / 16) * sizeof(int4));
-    P->off_links = 256;
+    P->off_links = r256(sizeof(unsigned long long) * P->n_counters);
     P->off_redo = P->off_links + r256(sizeof(BatchLink) * std::max(n, 1));
-    P->off_scratch = P->off_redo + P->redo_bytes;
+    P->off_rec = P->off_redo + P->redo_bytes;
+    P->off_scratch = P->off_rec + r256(rec_max * REC_BYTES);
     P->bytes = P->off_scratch + off;
     *bytes = P->bytes;
     *out = P;
@@ -376,23 +465,30 @@ cudaError_t batch_alloc(BatchPlan *P) {
     return e;
 }
 
-// autotune: time each fused variant on the first units of the batch (after one run of the
-// preparation stages) and keep the fastest
+// autotune: after the preparation stages and the first wave's extrapolation, time each synthesis
+// tile width on the first units of the first wave and keep the fastest
 cudaError_t batch_autotune(BatchPlan *P, cudaStream_t s, float *best_ms) {
-    const long long sample = std::min<long long>(P->n_items[ST_FUSED], (long long)sm_count() * 4);
-    float best = 1e30f;
-    int pick = 0;
+    *best_ms = 0.f;
+    if (P->waves.empty()) {
+        P->variant = 1;
+        return cudaSuccess;
+    }
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    cudaError_t e = run_stages(*P, s, 0);   // preparation only
+    cudaError_t e = cudaMemsetAsync(P->mem, 0, sizeof(unsigned long long) * P->n_counters, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->mem + P->off_redo, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = run_prep(*P, s);
+    if (e == cudaSuccess) e = run_wave_bulk(*P, 0, s);
+    const long long sample = (long long)sm_count() * 64;   // units of each variant timed
+    float best = 1e30f;
+    int pick = 1;
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep)   // first pass warms up
-        for (int v = 0; v < 4 && e == cudaSuccess; ++v) {
-            BatchDev B = dev_view(*P, sample);
-            e = cudaMemsetAsync(P->mem + ST_FUSED * sizeof(unsigned long long), 0, sizeof(unsigned long long), s);
-            if (e == cudaSuccess) e = cudaMemsetAsync(P->mem + P->off_redo, 0, sizeof(int), s);
+        for (int v = 0; v < 3 && e == cudaSuccess; ++v) {
+            P->variant = v;
+            e = cudaMemsetAsync(P->mem + 5 * sizeof(unsigned long long), 0, sizeof(unsigned long long), s);
             cudaEventRecord(a, s);
-            if (e == cudaSuccess) e = launch_fused(v, B, s);
+            if (e == cudaSuccess) e = run_wave_synth(*P, 0, s, sample);
             cudaEventRecord(b, s);
             if (e == cudaSuccess) e = cudaEventSynchronize(b);
             float ms = 0.f;

@@ -53,7 +53,7 @@ struct Server {
     std::map<size_t, size_t> free_blocks;   // offset -> size, coalesced
     int max_batch = 256;
     std::vector<Slot> slots;
-    std::map<int, int> variant_of_bins;     // fused-kernel variant, tuned once per bin count
+    std::map<int, int> variant_of_bins;     // synthesis tile variant, tuned once per bin count
     std::mutex m;
     std::condition_variable cv, cv_done;
     std::deque<uint64_t> queue;
