@@ -40,12 +40,19 @@ WORKLOAD = "canyon"
 PATHSET = os.path.join(ROOT, "tests", "golden", "pathset_canyon_seed0.npz")
 
 # Roofline of the dominant kernel (k_extrapolate_fp64, FP64-pipe bound).  FP64 FLOPs executed per
-# path-step (DADD + DMUL + 2 DFMA thread-instructions per ncu on this workload, see
-# profiles/k_extrapolate_fp64_canyon.md) and the FP64 peak of the GB300 (1.25 TFLOP/s nominal,
-# 152 SMs, no FP64 tensor path used).  DRAM bytes per launch from the same capture (None until taken).
-FP64_FLOP_PER_PATH_STEP = 2450.0
-FP64_PEAK_FLOPS = 1.25e12
-K1_DRAM_BYTES_PER_LAUNCH = 55.81e6
+# path-step on this workload (DADD + DMUL + 2 DFMA thread-instructions counted by ncu, see
+# profiles/k_extrapolate_fp64_canyon.md) and the FP64 peak of the GB300 derived from its unit counts:
+# 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz = 1.26 TFLOP/s (no FP64 tensor path is used).  DRAM bytes
+# per launch from the same capture (set to None whenever the kernel changes after the capture).
+FP64_FLOP_PER_PATH_STEP = 2700.0
+FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
+K1_DRAM_BYTES_PER_LAUNCH = 69.83e6
+# FP32-bulk form (profiles/k_extrapolate_bulk_canyon.md, profiles/k_synth_canyon.md): FP32 FLOPs per
+# path-step of k_extrapolate_bulk (FADD + FMUL + 2 FFMA, ncu) and 8 FLOP per synthesis term; FP32
+# peak 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz = 80.5 TFLOP/s
+FP32_FLOP_PER_PATH_STEP = 2837.0
+FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9
+SYNTH_FLOP_PER_TERM = 8.0
 
 
 def parse():
@@ -73,6 +80,23 @@ def workload():
 
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def max_over_ranks(seconds: float, world: int, device=None) -> float:
+    """The slowest rank's time (all ranks get it); every rank runs its own link, so the job takes as
+    long as its slowest rank."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Units all ranks processed divided by the slowest rank's time (weak scaling)."""
+    return world * units_per_rank / max_seconds
 
 
 class ClockSampler:
@@ -136,8 +160,8 @@ def cpu_baseline(scene, paths, tg, fg, n_steps):
     O.synthesize_H(rec, fg, n_threads=cores)
     dt = time.perf_counter() - t0
     return {"value": paths.n_paths * n_steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{paths.n_paths} paths x first {n_steps} of {tg.n_steps} steps x {fg.n_bins} bins "
-                      f"(extrapolation + H), {dt:.2f} s wall",
+            "sample": f"{paths.n_paths} paths x {n_steps} of {tg.n_steps} steps x {fg.n_bins} bins "
+                      f"(extrapolation + H), {dt:.2f} s wall on {cores} threads",
             "h_samples_per_s": n_steps * fg.n_bins / dt}
 
 
@@ -354,12 +378,8 @@ def run_ours(args):
     ctx.profile(False)
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_s = sum(step_ms) * 1e-3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * P * T * args.steps / total_s
+    total_s = max_over_ranks(total_s, world, dev)
+    value = whole_job_rate(P * T * args.steps, world, total_s)
     n_launch, k1_ms = prof["extrapolate"]
     k1_avg_s = k1_ms * 1e-3 / max(1, n_launch)
     kernel_launches = sum(v[0] for v in prof.values())
@@ -382,14 +402,19 @@ def run_ours(args):
     profb = ctx.profile_read()
     ctx.profile(False)
     bulk_s = sum(a.elapsed_time(b) for a, b in evb) * 1e-3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([bulk_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        bulk_s = float(t.item())
-    fp32_bulk = {"value": world * P * T * args.steps / bulk_s, "unit": UNIT, "ms_per_step": 1e3 * bulk_s / args.steps,
+    bulk_s = max_over_ranks(bulk_s, world, dev)
+    fp32_bulk = {"value": whole_job_rate(P * T * args.steps, world, bulk_s), "unit": UNIT, "ms_per_step": 1e3 * bulk_s / args.steps,
                  "h_samples_per_s": world * T * F * args.steps / bulk_s, "precision": "DRT_FP32_BULK",
                  "kernel_ms": {k: (v[1] / max(1, v[0])) for k, v in profb.items() if v[0]}}
+    ke, ks = fp32_bulk["kernel_ms"].get("extrapolate"), fp32_bulk["kernel_ms"].get("synth")
+    if ke and ks:
+        a1 = FP32_FLOP_PER_PATH_STEP * P * T / (ke * 1e-3)
+        a3 = SYNTH_FLOP_PER_TERM * P * T * F / (ks * 1e-3)
+        fp32_bulk["rooflines"] = {
+            "k_extrapolate_bulk": {"bound": "alu", "achieved": a1 / 1e12, "peak": FP32_PEAK_FLOPS / 1e12,
+                                   "unit": "TFLOP/s", "frac": a1 / FP32_PEAK_FLOPS},
+            "k_synth": {"bound": "alu", "achieved": a3 / 1e12, "peak": FP32_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                        "frac": a3 / FP32_PEAK_FLOPS, "terms_per_s": P * T * F / (ks * 1e-3)}}
 
     # end to end through the public API with host buffers: load (H2D) + synthesize to host (D2H)
     h2d = sum(np.ascontiguousarray(a).nbytes for a in (scene.bodies, scene.materials, scene.faces, scene.edges,
@@ -423,7 +448,9 @@ def run_ours(args):
         achieved = FP64_FLOP_PER_PATH_STEP * P * T / k1_avg_s
         line["roofline"] = {"bound": "alu", "kernel": "k_extrapolate_fp64", "achieved": achieved / 1e12,
                             "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS,
-                            "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s)",
+                            "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (no FP64 figure in "
+                                           "MEASURED_PEAKS.json)",
+                            "algorithmic": f"{FP64_FLOP_PER_PATH_STEP:.0f} FP64 FLOP per path-step x {P * T} path-steps",
                             "traffic": K1_DRAM_BYTES_PER_LAUNCH}
     else:
         line["roofline"] = {"bound": "alu", "kernel": "k_extrapolate_fp64", "achieved": None,
@@ -436,7 +463,7 @@ def run_ours(args):
     if args.serve_seconds > 0:
         line["serving"] = run_serving(args, drt)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(scene, paths, tg, fg, n_steps=400)
+        line["cpu_baseline"] = cpu_baseline(scene, paths, tg, fg, n_steps=tg.n_steps)
     link.unload()
     ctx.close()
     if rank == 0:

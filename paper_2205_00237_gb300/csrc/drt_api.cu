@@ -277,6 +277,7 @@ drt_status run_extrapolation(drt_ctx *c, Link &L, const drt_time_grid *tg, const
     double *pose = reinterpret_cast<double *>(c->pose.ptr);
     double *warm = reinterpret_cast<double *>(c->warm.ptr);
     if (drt_status st = traced(c, 0, s, [&] { return launch_pose(L.dev, t, pose, s); })) return st;
+    if (drt_status st = traced(c, 3, s, [&] { return launch_warm_fp64(L.dev, t, warm, s); })) return st;
     return traced(c, 1, s, [&] { return launch_extrapolate_fp64(L.dev, t, f, pose, out, rec, s, 0, -1, false, warm); });
 }
 

@@ -160,6 +160,8 @@ cudaError_t launch_extrapolate_fp64(const LinkDev &L, const TimeGridD &tg, const
                                     cudaStream_t s, int p0 = 0, int p1 = -1, bool f32out = false,
                                     double *warm = nullptr);
 size_t warm_bytes(const LinkDev &L, const TimeGridD &tg);
+// the warm-start table of the multi-diffraction chains (FP64 dual-number solves at the chunk bases)
+cudaError_t launch_warm_fp64(const LinkDev &L, const TimeGridD &tg, double *warm, cudaStream_t s);
 // FP32-bulk form (CHUNK consecutive steps share FP64 anchors); see drt_physics.cuh.  Scratch:
 // per-(body or terminal, chunk) FP32 base poses and per-(path, chunk) FP64 anchors.
 size_t bulk_pose_bytes(const LinkDev &L, const TimeGridD &tg);

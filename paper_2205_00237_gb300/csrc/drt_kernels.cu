@@ -59,6 +59,13 @@ k_warm_fp64(const LinkDev L, const TimeGridD tg, double *__restrict__ warm) {
     path_warm_fp64(L, tg, p, c, warm);
 }
 
+cudaError_t launch_warm_fp64(const LinkDev &L, const TimeGridD &tg, double *warm, cudaStream_t s) {
+    if (!warm || L.n_bulk >= L.n_paths || tg.n_steps == 0) return cudaSuccess;
+    dim3 gw(L.n_paths - L.n_bulk, (n_chunks_of(tg) + 1 + WARM_T - 1) / WARM_T);
+    k_warm_fp64<<<gw, WARM_T, 0, s>>>(L, tg, warm);
+    return cudaGetLastError();
+}
+
 size_t warm_bytes(const LinkDev &L, const TimeGridD &tg) {
     return (size_t)(L.n_paths - L.n_bulk) * (n_chunks_of(tg) + 1) * 2 * MAXI * sizeof(double);
 }
@@ -68,12 +75,6 @@ cudaError_t launch_extrapolate_fp64(const LinkDev &L, const TimeGridD &tg, const
                                     int p1, bool f32out, double *warm) {
     if (p1 < 0) p1 = L.n_paths;
     if (p1 <= p0 || tg.n_steps == 0) return cudaSuccess;
-    if (warm && L.n_bulk < L.n_paths) {
-        dim3 gw(L.n_paths - L.n_bulk, (n_chunks_of(tg) + 1 + WARM_T - 1) / WARM_T);
-        k_warm_fp64<<<gw, WARM_T, 0, s>>>(L, tg, warm);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
     dim3 grid(p1 - p0, (tg.n_steps + EXT_T - 1) / EXT_T);
     k_extrapolate_fp64<<<grid, EXT_T, 0, s>>>(L, tg, fg, pose, out, rec, p0, f32out ? 1 : 0, warm);
     return cudaGetLastError();
@@ -129,12 +130,8 @@ k_base_fp64(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const doubl
 cudaError_t launch_base_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, double *pose64, void *base,
                              double *warm, cudaStream_t s) {
     if (L.n_paths == 0 || tg.n_steps == 0) return cudaSuccess;
-    if (L.n_bulk < L.n_paths) {   // warm starts of the multi-diffraction chains first (rows 0..n_chunks)
-        dim3 gw(L.n_paths - L.n_bulk, (n_chunks_of(tg) + 1 + WARM_T - 1) / WARM_T);
-        k_warm_fp64<<<gw, WARM_T, 0, s>>>(L, tg, warm);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
+    // warm starts of the multi-diffraction chains first (rows 0..n_chunks)
+    if (cudaError_t e = launch_warm_fp64(L, tg, warm, s)) return e;
     TimeGridD tc = make_tgrid(tg.t_start, tg.dt * tg.chunk, n_chunks_of(tg), 1);   // chunk bases
     cudaError_t e = launch_pose(L, tc, pose64, s);
     if (e != cudaSuccess) return e;

@@ -221,7 +221,9 @@ class Context:
         _check(load_library().drt_profile_enable(self._h, 1 if on else 0))
 
     def profile_read(self):
-        """drt_profile_read: {kind: (launches, total ms)} for pose / extrapolate / synth since last read."""
+        """drt_profile_read: {kind: (launches, total ms)} since the last read.  Kinds: pose (pose
+        tables), extrapolate (the per-path-step kernel), synth (H synthesis), base (FP64 warm starts,
+        FP32-bulk chunk anchors and FP64 redo)."""
         counts = (C.c_int64 * 4)()
         ms = (C.c_double * 4)()
         _check(load_library().drt_profile_read(self._h, counts, ms))
