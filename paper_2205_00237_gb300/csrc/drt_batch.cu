@@ -10,7 +10,7 @@
 //   stage 2  multi-diffraction warm start (link, path with >= 2 D in a segment, chunk base 0..n)
 //   stage 3  FP64 chunk anchors           (link, path, chunk)
 //   stage 4  FP32-bulk extrapolation      (link, path, 32 consecutive steps: one warp)
-//   stage 5  H synthesis                  (link, 128 consecutive (step, bin tile) pairs: one block)
+//   stage 5  H synthesis                  (link, 32 consecutive (step, bin tile) pairs: one block)
 // Stages 4 and 5 run in waves of links whose per-path-step records (20 B each) fit one record
 // buffer, so a batch of any size streams through a bounded scratch.  Links are ordered by
 // decreasing work so the largest units are claimed first.  Steps FP32 cannot resolve go to an FP64
@@ -34,7 +34,8 @@ namespace drt {
 // stage slots; the synthesis has one slot per tile variant (its units depend on the tile width)
 enum { ST_POSEB = 0, ST_POSE64 = 1, ST_WARM = 2, ST_BASE = 3, ST_BULK = 4, ST_SYNTH = 5, N_STAGES = 8 };
 constexpr int BULK_W = 32;                // time steps per extrapolation unit (one warp's lanes)
-constexpr int SYNTH_U = 128;              // (step, tile) pairs per synthesis unit (one block)
+constexpr int SYNTH_U = 32;               // (step, tile) pairs per synthesis unit (one block) ...
+constexpr int SYNTH_PG = 4;               // ... whose warps split the paths
 constexpr int SYNTH_KT[3] = {8, 16, 32};
 constexpr size_t REC_BYTES = sizeof(float4) + sizeof(float);   // one synthesis record
 constexpr size_t REC_CAP = (size_t)4 << 30;                    // record buffer of one wave (bytes)
@@ -135,53 +136,70 @@ __global__ void __launch_bounds__(128) k_batch_bulk(const BatchDev B) {
     }
 }
 
-// stage 5: a block takes (link, 128 consecutive (step, tile of KT bins) pairs), one pair per thread
-// as in the single-link synthesis: exact FP32 seed per tile, complex rotation recurrence across the
-// tile
+// stage 5: a block takes (link, SYNTH_U consecutive (step, tile of KT bins) pairs), as in the
+// single-link synthesis: lane l owns pair l, the SYNTH_PG warps split the paths and add their
+// partial sums in shared memory; exact FP32 seed per (pair, path), complex rotation across the tile
 template <int VI>
-__global__ void __launch_bounds__(SYNTH_U) k_batch_synth(const BatchDev B) {
+__global__ void __launch_bounds__(SYNTH_U * SYNTH_PG) k_batch_synth(const BatchDev B) {
     constexpr int KT = SYNTH_KT[VI];
+    __shared__ float2 part[SYNTH_PG][KT][SYNTH_U + 1];
     const long long it = blockIdx.x;   // one unit per block (a plain grid: no claim loop needed here)
     if (it >= B.n_items) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int li = find_link(B, ST_SYNTH + VI, it);
     const BatchLink &BL = B.links[li];
     const int F = BL.fg.n_bins, P = BL.L.n_paths, T = BL.tg.n_steps;
     const int ntile = (F + KT - 1) / KT;
-    const long long pair = (it - BL.it0[ST_SYNTH + VI]) * SYNTH_U + threadIdx.x;
-    if (pair >= (long long)T * ntile) return;
-    const int ti = (int)(pair / ntile), k0 = (int)(pair % ntile) * KT;
+    const long long pair = (it - BL.it0[ST_SYNTH + VI]) * SYNTH_U + lane;
+    const bool live = pair < (long long)T * ntile;
+    const int ti = live ? (int)(pair / ntile) : 0, k0 = live ? (int)(pair % ntile) * KT : 0;
     const float kf = (float)k0;
     float2 acc[KT];
 #pragma unroll
     for (int j = 0; j < KT; ++j) acc[j] = make_float2(0.f, 0.f);
-    const float4 *__restrict__ ra = B.rec_a + BL.rec0 + (size_t)ti * P;
-    const float *__restrict__ rb = B.rec_b + BL.rec0 + (size_t)ti * P;
-    for (int p = 0; p < P; ++p) {
-        const float4 r = __ldg(ra + p);
-        if (r.x == 0.f && r.y == 0.f) continue;
-        const float lo = __ldg(rb + p);
-        float ph = kf * r.w;   // exact: the step's high part has 12 significant bits, k0 < 4096
-        ph -= floorf(ph);
-        ph += r.z + kf * lo;
-        ph -= floorf(ph);
-        float sn, cs, ws, wc;
-        sincospif(2.f * ph, &sn, &cs);
-        sincospif(2.f * (r.w + lo), &ws, &wc);
-        float zr = fmaf(r.x, cs, r.y * sn), zi = fmaf(r.y, cs, -r.x * sn);
-        const float wr = wc, wi = -ws;
+    if (live) {
+        const float4 *__restrict__ ra = B.rec_a + BL.rec0 + (size_t)ti * P;
+        const float *__restrict__ rb = B.rec_b + BL.rec0 + (size_t)ti * P;
+        for (int p = w; p < P; p += SYNTH_PG) {
+            const float4 r = __ldg(ra + p);
+            if (r.x == 0.f && r.y == 0.f) continue;
+            const float lo = __ldg(rb + p);
+            float ph = kf * r.w;   // exact: the step's high part has 12 significant bits, k0 < 4096
+            ph -= floorf(ph);
+            ph += r.z + kf * lo;
+            ph -= rintf(ph);       // cycles in [-1/2, 1/2]
+            float st = r.w + lo;
+            st -= rintf(st);
+            float sn, cs, ws, wc;   // hardware sine / cosine on [-pi, pi] (abs. error ~4e-7)
+            __sincosf(6.28318530717958648f * ph, &sn, &cs);
+            __sincosf(6.28318530717958648f * st, &ws, &wc);
+            float zr = fmaf(r.x, cs, r.y * sn), zi = fmaf(r.y, cs, -r.x * sn);
+            const float wr = wc, wi = -ws;
 #pragma unroll
-        for (int j = 0; j < KT; ++j) {
-            acc[j].x += zr;
-            acc[j].y += zi;
-            const float nr = fmaf(zr, wr, -zi * wi);
-            zi = fmaf(zr, wi, zi * wr);
-            zr = nr;
+            for (int j = 0; j < KT; ++j) {
+                acc[j].x += zr;
+                acc[j].y += zi;
+                const float nr = fmaf(zr, wr, -zi * wi);
+                zi = fmaf(zr, wi, zi * wr);
+                zr = nr;
+            }
         }
     }
+#pragma unroll
+    for (int j = 0; j < KT; ++j) part[w][j][lane] = acc[j];
+    __syncthreads();
+    if (!live) return;
     float2 *out = BL.H + (size_t)ti * F + k0;
 #pragma unroll
-    for (int j = 0; j < KT; ++j)
-        if (k0 + j < F) out[j] = acc[j];
+    for (int j = w; j < KT; j += SYNTH_PG) {
+        float2 v = part[0][j][lane];
+#pragma unroll
+        for (int g = 1; g < SYNTH_PG; ++g) {
+            v.x += part[g][j][lane].x;
+            v.y += part[g][j][lane].y;
+        }
+        if (k0 + j < F) out[j] = v;
+    }
 }
 
 // FP64 redo of queued steps; their contribution is added to H (all bins) with atomics
@@ -269,9 +287,9 @@ static BatchDev dev_view(const BatchPlan &P, int l0, int l1, long long n_items, 
 
 static cudaError_t launch_synth_variant(int v, const BatchDev &B, int grid, cudaStream_t s) {
     switch (v) {
-    case 0: k_batch_synth<0><<<grid, SYNTH_U, 0, s>>>(B); break;
-    case 2: k_batch_synth<2><<<grid, SYNTH_U, 0, s>>>(B); break;
-    default: k_batch_synth<1><<<grid, SYNTH_U, 0, s>>>(B); break;
+    case 0: k_batch_synth<0><<<grid, SYNTH_U * SYNTH_PG, 0, s>>>(B); break;
+    case 2: k_batch_synth<2><<<grid, SYNTH_U * SYNTH_PG, 0, s>>>(B); break;
+    default: k_batch_synth<1><<<grid, SYNTH_U * SYNTH_PG, 0, s>>>(B); break;
     }
     return cudaGetLastError();
 }
@@ -480,7 +498,7 @@ cudaError_t batch_autotune(BatchPlan *P, cudaStream_t s, float *best_ms) {
     if (e == cudaSuccess) e = cudaMemsetAsync(P->mem + P->off_redo, 0, sizeof(int), s);
     if (e == cudaSuccess) e = run_prep(*P, s);
     if (e == cudaSuccess) e = run_wave_bulk(*P, 0, s);
-    const long long sample = (long long)sm_count() * 64;   // units of each variant timed
+    const long long sample = (long long)sm_count() * 256;   // units of each variant timed
     float best = 1e30f;
     int pick = 1;
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep)   // first pass warms up

@@ -2,12 +2,15 @@
 //   k_pose           a2: per (time-step, body) pose table R(t), O(t), v_O(t), omega(t) (FP64)
 //   k_extrapolate    a3-a8: one thread per (path, time-step); a warp covers 32 consecutive time
 //                    steps of one path, so all its lanes run the same chain signature
-//   k_pose_bulk, k_base_fp64, k_extrapolate_bulk
+//   k_warm_fp64      warm starts of the multi-diffraction chains at the chunk bases (FP64)
+//   k_pose_bulk, k_base_fp64, k_extrapolate_bulk, k_redo
 //                    FP32-bulk form: FP32 base poses and FP64 path-length / phase anchors per
-//                    32-step chunk, then FP32 delta-number geometry and field per (path, step)
+//                    16-step chunk, FP32 delta-number geometry and field per (path, step), FP64
+//                    redo of the steps FP32 cannot resolve
 //   k_synth          a9: H(t, f) = sum_p a_p exp(-j 2 pi f tau_p); one thread per (time-step,
-//                    16-bin frequency tile), sincos seed per tile and a complex rotation
-//                    recurrence inside it, FP32 FMA accumulation
+//                    16-bin frequency tile, path group), sincos seed per tile and a complex
+//                    rotation recurrence inside it, FP32 FMA accumulation, groups added in
+//                    shared memory
 //   k_probe          FMA issue-rate probe for the roofline denominators
 #include "drt_internal.h"
 #include "drt_physics.cuh"
@@ -191,62 +194,82 @@ cudaError_t launch_redo(const LinkDev &L, const TimeGridD &tg, const FreqGridD &
 }
 
 // ------------------------------------------------------------------------------------------------
-// a9: H synthesis.  Thread (t, tile) owns bins k0 .. k0+15 of one time step and loops over the
-// paths of that step; all threads of the step read the same record (broadcast).  Seed
+// a9: H synthesis.  A block owns SYN_PAIRS consecutive (step, tile of KT bins) pairs; its PG warps
+// split the paths of those steps (warp w takes paths w, w + PG, ...), lane l owns pair l, so the
+// lanes of a warp that share a step read the same record (broadcast).  Per (pair, path): seed
 // exp(-j 2 pi frac(phi0 + k0 step)) by sincospi with the step split so k0 * hi is exact, then a
-// complex rotation by exp(-j 2 pi step) per bin.
-constexpr int KT = 16;
+// complex rotation by exp(-j 2 pi step) per bin; the PG partial sums are added through shared memory.
+constexpr int KT = 16, PG = 4, SYN_PAIRS = 32;
 
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(SYN_PAIRS * PG)
 k_synth(const float4 *__restrict__ rec_a, const float *__restrict__ rec_b, int n_paths, int n_steps, int n_bins,
         float2 *__restrict__ H) {
-    int ntile = (n_bins + KT - 1) / KT;
-    int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    int ti = gid / ntile, tile = gid - ti * ntile;
-    if (ti >= n_steps) return;
-    int k0 = tile * KT;
-    float kf = (float)k0;
+    __shared__ float2 part[PG][KT][SYN_PAIRS + 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int ntile = (n_bins + KT - 1) / KT;
+    const long long pair = (long long)blockIdx.x * SYN_PAIRS + lane;
+    const bool live = pair < (long long)n_steps * ntile;
+    const int ti = live ? (int)(pair / ntile) : 0, k0 = live ? (int)(pair % ntile) * KT : 0;
+    const float kf = (float)k0;
     float2 acc[KT];
 #pragma unroll
     for (int j = 0; j < KT; ++j) acc[j] = make_float2(0.f, 0.f);
-    const float4 *ra = rec_a + (size_t)ti * n_paths;
-    const float *rb = rec_b + (size_t)ti * n_paths;
-    for (int p = 0; p < n_paths; ++p) {
-        float4 r = __ldg(ra + p);
-        if (r.x == 0.f && r.y == 0.f) continue;
-        float lo = __ldg(rb + p);
-        float ph = kf * r.w;               // exact
-        ph -= floorf(ph);
-        ph += r.z + kf * lo;
-        ph -= floorf(ph);
-        float sn, cs, ws, wc;
-        sincospif(2.f * ph, &sn, &cs);
-        sincospif(2.f * (r.w + lo), &ws, &wc);
-        // z = a exp(-j 2 pi ph), w = exp(-j 2 pi step)
-        float zr = fmaf(r.x, cs, r.y * sn), zi = fmaf(r.y, cs, -r.x * sn);
-        float wr = wc, wi = -ws;
+    if (live) {
+        const float4 *ra = rec_a + (size_t)ti * n_paths;
+        const float *rb = rec_b + (size_t)ti * n_paths;
+        for (int p = w; p < n_paths; p += PG) {
+            float4 r = __ldg(ra + p);
+            if (r.x == 0.f && r.y == 0.f) continue;
+            float lo = __ldg(rb + p);
+            float ph = kf * r.w;   // exact
+            ph -= floorf(ph);
+            ph += r.z + kf * lo;
+            ph -= rintf(ph);       // cycles in [-1/2, 1/2]
+            float st = r.w + lo;
+            st -= rintf(st);
+            // the hardware sine / cosine on [-pi, pi] (absolute error ~4e-7: far below the
+            // synthesis tolerance of 1e-4 of the row RMS)
+            float sn, cs, ws, wc;
+            __sincosf(6.28318530717958648f * ph, &sn, &cs);
+            __sincosf(6.28318530717958648f * st, &ws, &wc);
+            // z = a exp(-j 2 pi ph), w = exp(-j 2 pi step)
+            float zr = fmaf(r.x, cs, r.y * sn), zi = fmaf(r.y, cs, -r.x * sn);
+            float wr = wc, wi = -ws;
 #pragma unroll
-        for (int j = 0; j < KT; ++j) {
-            acc[j].x += zr;
-            acc[j].y += zi;
-            float nr = fmaf(zr, wr, -zi * wi);
-            zi = fmaf(zr, wi, zi * wr);
-            zr = nr;
+            for (int j = 0; j < KT; ++j) {
+                acc[j].x += zr;
+                acc[j].y += zi;
+                float nr = fmaf(zr, wr, -zi * wi);
+                zi = fmaf(zr, wi, zi * wr);
+                zr = nr;
+            }
         }
     }
+#pragma unroll
+    for (int j = 0; j < KT; ++j) part[w][j][lane] = acc[j];
+    __syncthreads();
+    // warp w adds and writes bins j = w, w + PG, ... of every pair of the block
+    if (!live) return;
     float2 *out = H + (size_t)ti * n_bins + k0;
 #pragma unroll
-    for (int j = 0; j < KT; ++j)
-        if (k0 + j < n_bins) out[j] = acc[j];
+    for (int j = w; j < KT; j += PG) {
+        float2 v = part[0][j][lane];
+#pragma unroll
+        for (int g = 1; g < PG; ++g) {
+            v.x += part[g][j][lane].x;
+            v.y += part[g][j][lane].y;
+        }
+        if (k0 + j < n_bins) out[j] = v;
+    }
 }
 
 cudaError_t launch_synth(const RecD &rec, int32_t n_paths, const TimeGridD &tg, const FreqGridD &fg, float2 *H,
                          cudaStream_t s) {
     int ntile = (fg.n_bins + KT - 1) / KT;
-    long long threads = (long long)tg.n_steps * ntile;
-    if (threads == 0) return cudaSuccess;
-    k_synth<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(rec.rec_a, rec.rec_b, n_paths, tg.n_steps, fg.n_bins,
-                                                               H);
+    long long pairs = (long long)tg.n_steps * ntile;
+    if (pairs == 0) return cudaSuccess;
+    k_synth<<<(unsigned)((pairs + SYN_PAIRS - 1) / SYN_PAIRS), SYN_PAIRS * PG, 0, s>>>(rec.rec_a, rec.rec_b, n_paths,
+                                                                                     tg.n_steps, fg.n_bins, H);
     return cudaGetLastError();
 }
 
