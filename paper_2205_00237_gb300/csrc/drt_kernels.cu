@@ -151,7 +151,9 @@ static RedoList redo_list(void *redo, const LinkDev &L, const TimeGridD &tg) {
     return r;
 }
 
-__global__ void __launch_bounds__(EXT_T)
+// at most 128 registers (4 blocks of 4 warps per SM): the latency-bound FP32 step gains more from
+// the extra warps than it loses to spills (2048-path link 1.47 -> 1.12 ms, canyon within 3 %)
+__global__ void __launch_bounds__(EXT_T, 4)
 k_extrapolate_bulk(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const PoseB *__restrict__ poseb,
                    const BaseRec *__restrict__ base, const double *__restrict__ warm, const OutD out, const RecD rec,
                    const RedoList redo) {
