@@ -352,6 +352,8 @@ drt_status drt::pack_link(const drt_scene *s, const drt_path_set *ps, PackedLink
         std::memcpy(g.n0, e.n0, 24);
         g.len = L0;
         g.wn = e.wedge_n;
+        g.snp = std::sin(M_PI * e.wedge_n);   // direction of the n-face in the edge frame, once per load
+        g.cnp = std::cos(M_PI * e.wedge_n);
         g.body = e.body;
         g.mat = e.material;
         g.pad0 = g.pad1 = 0;
@@ -404,6 +406,8 @@ drt_status drt::pack_link(const drt_scene *s, const drt_path_set *ps, PackedLink
         f3(h.n0, g.n0);
         h.len = (float)g.len;
         h.wn = (float)g.wn;
+        h.snp = (float)g.snp;
+        h.cnp = (float)g.cnp;
         h.body = g.body;
         h.mat = g.mat;
     }

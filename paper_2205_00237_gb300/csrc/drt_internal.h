@@ -19,12 +19,12 @@ constexpr int POSE_W = 18;   // doubles per (time, body) pose record: R (3x3 row
 // primitives, positions relative to the owning body's rotation centre o (world axes at t0), so a
 // posed position is O(t) + R(t) rel
 struct FaceD { double c[3], n[3], u[3], hu, hw; int32_t body, mat; };                       // 96 B
-struct EdgeD { double a[3], e[3], t0[3], n0[3], len, wn; int32_t body, mat, pad0, pad1; };  // 128 B
+struct EdgeD { double a[3], e[3], t0[3], n0[3], len, wn, snp, cnp; int32_t body, mat, pad0, pad1; };  // 144 B: snp, cnp = sin, cos(wn pi)
 struct TileD { double c[3], n[3], area, s, alpha, cph, sph; int32_t body, mat; };          // 96 B: cph + j sph = exp(j phase)
 struct MatD { double eps_r, sigma, rough, pec; float eps_rf, sigmaf, roughf, pecf; };       // 48 B
 // FP32 copies for the FP32-bulk form (same meaning, no FP64 conversions in its kernels)
 struct FaceF { float c[3], n[3], u[3], hu, hw; int32_t body, mat, pad0, pad1, pad2; };          // 64 B
-struct EdgeF { float a[3], e[3], t0[3], n0[3], len, wn; int32_t body, mat; };                 // 64 B
+struct EdgeF { float a[3], e[3], t0[3], n0[3], len, wn, snp, cnp; int32_t body, mat; };      // 72 B
 struct TileF { float c[3], n[3], area, s, alpha, cph, sph; int32_t body, mat; };            // 52 B
 struct TermD { double r[3], v[3], a[3]; };
 struct BodyD { double o[3], v[3], a[3], k[3], w0, wdot; };

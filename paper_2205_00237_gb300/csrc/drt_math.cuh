@@ -20,13 +20,17 @@ template <class T> DRT_HD dl<T> operator-(dl<T> a) { return {-a.v, -a.d}; }
 template <class T> DRT_HD dl<T> operator*(dl<T> a, dl<T> b) { return {a.v * b.v, fma(a.d, b.v, a.v * b.d)}; }
 template <class T> DRT_HD dl<T> operator*(dl<T> a, T s) { return {a.v * s, a.d * s}; }
 template <class T> DRT_HD dl<T> operator*(T s, dl<T> a) { return {a.v * s, a.d * s}; }
+// one reciprocal per quotient and one reciprocal square root per root: division and square root
+// are multi-instruction sequences on the FP64 pipe, which bounds the FP64 form
 template <class T> DRT_HD dl<T> operator/(dl<T> a, dl<T> b) {
-    T q = a.v / b.v;
-    return {q, (a.d - q * b.d) / b.v};
+    const T inv = T(1) / b.v;
+    const T q = a.v * inv;
+    return {q, (a.d - q * b.d) * inv};
 }
 template <class T> DRT_HD dl<T> dsqrt(dl<T> a) {
-    T r = sqrt(a.v);
-    return {r, a.d / (T(2) * r)};
+    if (!(a.v > T(0))) return {sqrt(a.v), a.d / T(0)};   // zero length: value 0, rate undefined
+    const T rs = rsqrt(a.v);
+    return {a.v * rs, T(0.5) * a.d * rs};
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -103,7 +107,16 @@ DRT_HD double norm(v3<double> a) { return sqrt(dot(a, a)); }
 DRT_HD float norm(v3<float> a) { return sqrtf(dot(a, a)); }
 template <class T> DRT_HD dl<T> norm(v3<dl<T>> a) { return dsqrt(dot(a, a)); }
 DRT_HD dd norm(v3<dd> a) { return dsqrt(dot(a, a)); }
-template <class T> DRT_HD v3<T> unit(v3<T> a) { return a * (T(1) / norm(a)); }
+DRT_HD v3<double> unit(v3<double> a) { return a * rsqrt(dot(a, a)); }
+DRT_HD v3<float> unit(v3<float> a) { return a * (1.f / norm(a)); }
+// x^(-1/2) of a dual number: value rsqrt(x), rate -x'/2 x^(-3/2)
+template <class T> DRT_HD v3<dl<T>> unit(v3<dl<T>> a) {
+    const dl<T> q = dot(a, a);
+    const T rs = rsqrt(q.v);
+    const dl<T> inv = {rs, T(-0.5) * q.d * rs * rs * rs};
+    return a * inv;
+}
+DRT_HD v3<dd> unit(v3<dd> a) { return a * (scst<dd>(1.f) / norm(a)); }
 
 // ------------------------------------------------------------------------------------------------
 // complex numbers and complex 3-vectors (polarisation tracking)
@@ -118,13 +131,10 @@ template <class T> DRT_HD cx<T> operator*(cx<T> a, cx<T> b) {
 template <class T> DRT_HD cx<T> operator*(cx<T> a, T s) { return {a.re * s, a.im * s}; }
 template <class T> DRT_HD cx<T> operator*(T s, cx<T> a) { return {a.re * s, a.im * s}; }
 template <class T> DRT_HD cx<T> cdiv(cx<T> a, cx<T> b) {
-    // Smith's algorithm, with one reciprocal of the scaled denominator
-    if (fabs(b.re) >= fabs(b.im)) {
-        T r = b.im / b.re, inv = T(1) / (b.re + b.im * r);
-        return {(a.re + a.im * r) * inv, (a.im - a.re * r) * inv};
-    }
-    T r = b.re / b.im, inv = T(1) / (b.re * r + b.im);
-    return {(a.re * r + a.im) * inv, (a.im * r - a.re) * inv};
+    // a conj(b) / |b|^2 with one reciprocal (the magnitudes here, permittivities and continued-
+    // fraction terms, are far from the exponent range where Smith's scaling would be needed)
+    const T inv = T(1) / fma(b.re, b.re, b.im * b.im);
+    return {fma(a.re, b.re, a.im * b.im) * inv, fma(a.im, b.re, -a.re * b.im) * inv};
 }
 template <class T> DRT_HD T cabs2(cx<T> a) { return a.re * a.re + a.im * a.im; }
 // principal square root (Re >= 0)

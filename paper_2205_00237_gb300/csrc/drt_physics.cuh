@@ -100,6 +100,7 @@ template <class S> struct Prim {
     v3<T> b;        // R: face axis u, D: 0-face tangent t0 = n0 x e
     v3<T> c;        // D: 0-face normal n0
     T h1, h2;       // R: hu, hw; D: length, wedge n
+    T h3, h4;       // D: sin(n pi), cos(n pi) (the n-face direction in the (t0, n0) plane)
     int idx;
 };
 
@@ -132,6 +133,8 @@ DRT_HD Prim<dl<T>> load_prim_row(const LinkDev &L, const double *Prow, int type,
         q.c = rot(P, e.n0);
         q.h1 = T(e.len);
         q.h2 = T(e.wn);
+        q.h3 = T(e.snp);
+        q.h4 = T(e.cnp);
         q.mat = e.mat;
     } else {
         const TileD &tl = L.tiles[idx];
@@ -411,10 +414,19 @@ DRT_HD uint32_t validity(const Prim<S> *pr, int n, const v3<typename ST<S>::R> *
             T s = dot(P[i] - A, e);
             if (s < T(0) || s > q.h1) fl |= F_EDGE;
             for (int side = -1; side <= 1; side += 2) {
+                // the neighbour's direction about the edge, at angle phi from the 0-face tangent
+                // towards the 0-face normal, must lie in the exterior (0, n pi), 1 <= n <= 2: phi in
+                // (0, pi) when y > 0; otherwise phi in [pi, 2 pi) lies below n pi iff
+                // sin(n pi - phi) > 0 (or phi = pi < n pi = 2 pi) -- no arctangent needed
                 v3<T> r = P[i + side] - P[i];
                 v3<T> rp = r - e * dot(r, e);
-                T ph = wrap2pi(atan2(dot(rp, q.c), dot(rp, q.b)));
-                if (!(ph > T(0) && ph < q.h2 * T(PI))) fl |= F_SIDE;
+                const T y = dot(rp, q.c), x = dot(rp, q.b);
+                bool in = y > T(0);
+                if (!in && !(y == T(0) && x >= T(0))) {
+                    const T sn = q.h3 * x - q.h4 * y, cs = q.h4 * x + q.h3 * y;   // r sin, r cos of (n pi - phi)
+                    in = sn > T(0) || (sn == T(0) && cs < T(0));
+                }
+                if (!in) fl |= F_SIDE;
             }
         } else {
             v3<T> nn = val(q.a);
@@ -517,14 +529,15 @@ template <class T> DRT_HD cx<T> transition_F(T X) {
 
 // one Kouyoumjian-Pathak term cot((pi +- beta)/2n) F(kL a+-(beta)) with eps = (pi +- beta) - 2 pi n N:
 // cot(eps/2n) F(2 kL sin^2(eps/2)), -> n sqrt(2 pi kL) sgn(eps) exp(j pi/4) as eps -> 0
-template <class T> DRT_HD cx<T> utd_term(T eps, T n, T kL) {
+template <class T> DRT_HD cx<T> utd_term(T eps, T n, T inv2n, T kL) {
     if (fabs(eps) < T(1e-9)) {
         T m = n * sqrt(T(2 * PI) * kL) * (eps >= T(0) ? T(1) : T(-1)) * T(0.70710678118654752440);
         return C<T>(m, m);
     }
     T sh = sin(T(0.5) * eps);
-    T ct = T(1) / tan(eps / (T(2) * n));
-    return transition_F(T(2) * kL * sh * sh) * ct;
+    T s2, c2;
+    sincos(eps * inv2n, &s2, &c2);   // cot(eps / 2n)
+    return transition_F(T(2) * kL * sh * sh) * (c2 / s2);
 }
 
 // soft / hard wedge diffraction coefficients: Kouyoumjian-Pathak with the spherical-wave distance
@@ -538,10 +551,11 @@ DRT_HD void utd(T n, T phi, T phip, T sphip, T snphi, T sinb0, T L, T k, const M
     T pref = T(1) / (T(2) * n * sqrt(T(2 * PI) * k) * sinb0);
     cx<T> Cc = C<T>(-pref * T(0.70710678118654752440), pref * T(0.70710678118654752440));  // -exp(-j pi/4) pref
     T bm = phi - phip, bp = phi + phip, tpn = T(2 * PI) * n;
-    cx<T> t1 = utd_term(T(PI) + bm - tpn * round((bm + T(PI)) / tpn), n, kL);
-    cx<T> t2 = utd_term(T(PI) - bm + tpn * round((bm - T(PI)) / tpn), n, kL);
-    cx<T> t3 = utd_term(T(PI) - bp + tpn * round((bp - T(PI)) / tpn), n, kL);   // 0-face
-    cx<T> t4 = utd_term(T(PI) + bp - tpn * round((bp + T(PI)) / tpn), n, kL);   // n-face
+    const T inv2n = T(1) / (T(2) * n), itpn = inv2n * T(1 / PI);   // 1/(2n), 1/(2 pi n)
+    cx<T> t1 = utd_term(T(PI) + bm - tpn * round((bm + T(PI)) * itpn), n, inv2n, kL);
+    cx<T> t2 = utd_term(T(PI) - bm + tpn * round((bm - T(PI)) * itpn), n, inv2n, kL);
+    cx<T> t3 = utd_term(T(PI) - bp + tpn * round((bp - T(PI)) * itpn), n, inv2n, kL);   // 0-face
+    cx<T> t4 = utd_term(T(PI) + bp - tpn * round((bp + T(PI)) * itpn), n, inv2n, kL);   // n-face
     cx<T> r0s, r0h, rns, rnh;
     fresnel(m, fc, sphip, r0s, r0h);
     fresnel(m, fc, snphi, rns, rnh);
@@ -596,8 +610,9 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
     v3<T> kd[MAXI + 2];
     T len[MAXI + 2];
     for (int i = 1; i <= n + 1; ++i) {
-        len[i] = norm(seg[i]);
-        kd[i] = seg[i] * (T(1) / len[i]);
+        const T q = dot(seg[i], seg[i]), rs = rsqrt(q);   // one reciprocal square root per segment
+        len[i] = q * rs;
+        kd[i] = seg[i] * rs;
     }
     T spread = T(1), sprime[MAXI + 1], sdist[MAXI + 1];
     int a = 0;
@@ -659,11 +674,9 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
             T Lp = sdist[i] * sprime[i] * sinb0 * sinb0 / (sdist[i] + sprime[i]);
             T sphip = T(0), snphi = T(0);
             if (!m.pec) {   // Luebbers' face coefficients: sin phi' and sin(n pi - phi) from components
-                T sn, cn;
-                sincospi(q.h2, &sn, &cn);
                 const T ri = sqrt(xi * xi + yi * yi), ro = sqrt(xo * xo + yo * yo);
                 sphip = ri > T(0) ? fabs(yi) / ri : T(0);
-                snphi = ro > T(0) ? fabs(sn * xo - cn * yo) / ro : T(0);
+                snphi = ro > T(0) ? fabs(q.h3 * xo - q.h4 * yo) / ro : T(0);
             }
             cx<T> Ds, Dh;
             utd(q.h2, phi, phip, sphip, snphi, sinb0, Lp, k, m, fc, Ds, Dh);
@@ -1035,6 +1048,8 @@ DRT_HD Prim<dd> load_prim_dd(const LinkDev &L, const PoseB *poseb, int n_chunks,
         q.c = nb + drot(P, nb);
         q.h1 = e.len;
         q.h2 = e.wn;
+        q.h3 = e.snp;
+        q.h4 = e.cnp;
         q.mat = e.mat;
     } else {
         const TileF &tl = L.tilesF[idx];
@@ -1067,6 +1082,8 @@ DRT_HD Prim<double> load_prim_value(const LinkDev &L, const double *Pr, int type
         q.c = rot(P, e.n0);
         q.h1 = e.len;
         q.h2 = e.wn;
+        q.h3 = e.snp;
+        q.h4 = e.cnp;
         q.mat = e.mat;
     } else {
         const TileD &tl = L.tiles[idx];
