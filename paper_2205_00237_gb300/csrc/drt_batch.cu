@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(128) k_stage(const BatchDev B) {
 
 // stage 4: a warp claims (link, path, 32 steps); the lanes share the chain signature
 // at most 128 registers: 16 warps per SM instead of 8 (4096-link batch +26 %)
+template <bool DUAL>
 __global__ void __launch_bounds__(128, 4) k_batch_bulk(const BatchDev B) {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -129,7 +130,8 @@ __global__ void __launch_bounds__(128, 4) k_batch_bulk(const BatchDev B) {
         const int p = (int)(local / nb), t = (int)(local % nb) * BULK_W + lane;
         if (t < BL.tg.n_steps) {
             Rec5 r;
-            bulk_eval(BL.L, BL.tg, BL.fg, BL.poseb, BL.base, BL.warm, p, t, BL.out, r, B.redo, li);
+            if constexpr (DUAL) bulk_eval<dd>(BL.L, BL.tg, BL.fg, BL.poseb, BL.base, BL.warm, p, t, BL.out, r, B.redo, li);
+            else bulk_eval<de>(BL.L, BL.tg, BL.fg, BL.poseb, BL.base, BL.warm, p, t, BL.out, r, B.redo, li);
             const size_t ri = BL.rec0 + (size_t)t * BL.L.n_paths + p;
             B.rec_a[ri] = make_float4(r.ar, r.ai, r.ph, r.hi);
             B.rec_b[ri] = r.lo;
@@ -258,6 +260,7 @@ struct BatchPlan {
     char *mem = nullptr;
     bool owns = false;
     int variant = -1;   // synthesis tile width index (autotuner or caller)
+    bool dual = false;  // some link asks for Doppler outputs: carry the rates
     cudaGraphExec_t graph = nullptr;
     cudaStream_t capture = nullptr;   // private stream the graph is captured on (any caller stream,
                                       // the legacy default stream included, can then launch it)
@@ -310,7 +313,8 @@ static cudaError_t run_prep(BatchPlan &P, cudaStream_t s) {
 static cudaError_t run_wave_bulk(BatchPlan &P, size_t w, cudaStream_t s) {
     const Wave &W = P.waves[w];
     if (!W.n_bulk) return cudaSuccess;
-    k_batch_bulk<<<sm_count() * 4, 128, 0, s>>>(dev_view(P, W.l0, W.l1, W.n_bulk, 4 + 2 * w));
+    if (P.dual) k_batch_bulk<true><<<sm_count() * 4, 128, 0, s>>>(dev_view(P, W.l0, W.l1, W.n_bulk, 4 + 2 * w));
+    else k_batch_bulk<false><<<sm_count() * 4, 128, 0, s>>>(dev_view(P, W.l0, W.l1, W.n_bulk, 4 + 2 * w));
     return cudaGetLastError();
 }
 
@@ -401,6 +405,7 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
         B.fg = make_fgrid(fgs[i].fc, fgs[i].bandwidth, fgs[i].n_bins);
         B.H = reinterpret_cast<float2 *>(H[i]);
         if (outs) B.out = outs[i];
+        P->dual = P->dual || B.out.doppler != nullptr;
         const long long T = tgs[i].n_steps, Pn = B.L.n_paths;
         long long nch = (T + chunk - 1) / chunk;
         int md = B.L.n_paths - B.L.n_bulk;

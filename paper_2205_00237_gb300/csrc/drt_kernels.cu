@@ -43,13 +43,14 @@ cudaError_t launch_pose(const LinkDev &L, const TimeGridD &tg, double *pose, cud
 // iteration counts, transition-function ranges) are correlated between neighbouring instants.
 constexpr int EXT_T = 128;
 
+template <bool DUAL>
 __global__ void __launch_bounds__(EXT_T)
 k_extrapolate_fp64(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const double *__restrict__ pose,
                    const OutD out, const RecD rec, int p0, int f32out, const double *__restrict__ warm) {
     int p = p0 + blockIdx.x;
     int ti = blockIdx.y * EXT_T + threadIdx.x;
     if (p >= L.n_paths || ti >= tg.n_steps) return;
-    path_step_fp64(L, tg, fg, pose, p, ti, out, rec, f32out != 0, warm);
+    path_step_fp64<DUAL>(L, tg, fg, pose, p, ti, out, rec, f32out != 0, warm);
 }
 
 // warm-start pre-pass over (multi-diffraction path, chunk)
@@ -79,7 +80,9 @@ cudaError_t launch_extrapolate_fp64(const LinkDev &L, const TimeGridD &tg, const
     if (p1 < 0) p1 = L.n_paths;
     if (p1 <= p0 || tg.n_steps == 0) return cudaSuccess;
     dim3 grid(p1 - p0, (tg.n_steps + EXT_T - 1) / EXT_T);
-    k_extrapolate_fp64<<<grid, EXT_T, 0, s>>>(L, tg, fg, pose, out, rec, p0, f32out ? 1 : 0, warm);
+    // the Doppler shift needs the interaction points' velocities (dual numbers); nothing else does
+    if (out.doppler) k_extrapolate_fp64<true><<<grid, EXT_T, 0, s>>>(L, tg, fg, pose, out, rec, p0, f32out ? 1 : 0, warm);
+    else k_extrapolate_fp64<false><<<grid, EXT_T, 0, s>>>(L, tg, fg, pose, out, rec, p0, f32out ? 1 : 0, warm);
     return cudaGetLastError();
 }
 
@@ -153,6 +156,7 @@ static RedoList redo_list(void *redo, const LinkDev &L, const TimeGridD &tg) {
 
 // at most 128 registers (4 blocks of 4 warps per SM): the latency-bound FP32 step gains more from
 // the extra warps than it loses to spills (2048-path link 1.47 -> 1.12 ms, canyon within 3 %)
+template <bool DUAL>
 __global__ void __launch_bounds__(EXT_T, 4)
 k_extrapolate_bulk(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const PoseB *__restrict__ poseb,
                    const BaseRec *__restrict__ base, const double *__restrict__ warm, const OutD out, const RecD rec,
@@ -160,7 +164,8 @@ k_extrapolate_bulk(const LinkDev L, const TimeGridD tg, const FreqGridD fg, cons
     int p = blockIdx.x;
     int ti = blockIdx.y * EXT_T + threadIdx.x;
     if (p >= L.n_paths || ti >= tg.n_steps) return;
-    path_step_bulk(L, tg, fg, poseb, base, warm, p, ti, out, rec, redo);
+    if constexpr (DUAL) path_step_bulk<dd>(L, tg, fg, poseb, base, warm, p, ti, out, rec, redo);
+    else path_step_bulk<de>(L, tg, fg, poseb, base, warm, p, ti, out, rec, redo);
 }
 
 cudaError_t launch_extrapolate_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const void *poseb,
@@ -170,9 +175,11 @@ cudaError_t launch_extrapolate_bulk(const LinkDev &L, const TimeGridD &tg, const
     if (e != cudaSuccess) return e;
     if (L.n_paths == 0 || tg.n_steps == 0) return cudaSuccess;
     dim3 grid(L.n_paths, (tg.n_steps + EXT_T - 1) / EXT_T);
-    k_extrapolate_bulk<<<grid, EXT_T, 0, s>>>(L, tg, fg, reinterpret_cast<const PoseB *>(poseb),
-                                              reinterpret_cast<const BaseRec *>(base), warm, out, rec,
-                                              redo_list(redo, L, tg));
+    const PoseB *pb = reinterpret_cast<const PoseB *>(poseb);
+    const BaseRec *bs = reinterpret_cast<const BaseRec *>(base);
+    // rates (dual parts) only when the Doppler shift is asked for
+    if (out.doppler) k_extrapolate_bulk<true><<<grid, EXT_T, 0, s>>>(L, tg, fg, pb, bs, warm, out, rec, redo_list(redo, L, tg));
+    else k_extrapolate_bulk<false><<<grid, EXT_T, 0, s>>>(L, tg, fg, pb, bs, warm, out, rec, redo_list(redo, L, tg));
     return cudaGetLastError();
 }
 

@@ -60,6 +60,25 @@ DRT_HD dd dsqrt(dd a) {
     return {r, den > 0.f ? a.d / den : 0.f, rf > 0.f ? a.v / (2.f * rf) : 0.f};
 }
 
+// delta numbers without the rate part, for steps that need no Doppler shift: same rules as dd
+struct de { float b, d; };
+DRT_HD de operator+(de a, de c) { return {a.b + c.b, a.d + c.d}; }
+DRT_HD de operator-(de a, de c) { return {a.b - c.b, a.d - c.d}; }
+DRT_HD de operator-(de a) { return {-a.b, -a.d}; }
+DRT_HD de operator*(de a, de c) { return {a.b * c.b, fmaf(a.b, c.d, a.d * (c.b + c.d))}; }
+DRT_HD de operator*(de a, float s) { return {a.b * s, a.d * s}; }
+DRT_HD de operator*(float s, de a) { return {a.b * s, a.d * s}; }
+DRT_HD de operator/(de a, de c) {
+    float q = a.b / c.b;
+    return {q, (a.d - q * c.d) / (c.b + c.d)};
+}
+DRT_HD de dsqrt(de a) {
+    float r = sqrtf(fmaxf(a.b, 0.f)), rf = sqrtf(fmaxf(a.b + a.d, 0.f));
+    float den = rf + r;
+    return {r, den > 0.f ? a.d / den : 0.f};
+}
+DRT_HD de strip(dd a) { return {a.b, a.d}; }
+
 // scalar traits: real type, full value, time derivative, constants
 template <class S> struct ST;
 template <class T> struct ST<dl<T>> {
@@ -73,6 +92,12 @@ template <> struct ST<dd> {
     static DRT_HD float val(dd x) { return x.b + x.d; }
     static DRT_HD float rate(dd x) { return x.v; }
     static DRT_HD dd cst(float x) { return {x, 0.f, 0.f}; }
+};
+template <> struct ST<de> {
+    typedef float R;
+    static DRT_HD float val(de x) { return x.b + x.d; }
+    static DRT_HD float rate(de) { return 0.f; }
+    static DRT_HD de cst(float x) { return {x, 0.f}; }
 };
 template <> struct ST<double> {   // plain values (FP64 chunk-base solve: no derivative needed)
     typedef double R;
@@ -107,6 +132,7 @@ DRT_HD double norm(v3<double> a) { return sqrt(dot(a, a)); }
 DRT_HD float norm(v3<float> a) { return sqrtf(dot(a, a)); }
 template <class T> DRT_HD dl<T> norm(v3<dl<T>> a) { return dsqrt(dot(a, a)); }
 DRT_HD dd norm(v3<dd> a) { return dsqrt(dot(a, a)); }
+DRT_HD de norm(v3<de> a) { return dsqrt(dot(a, a)); }
 DRT_HD v3<double> unit(v3<double> a) { return a * rsqrt(dot(a, a)); }
 DRT_HD v3<float> unit(v3<float> a) { return a * (1.f / norm(a)); }
 // x^(-1/2) of a dual number: value rsqrt(x), rate -x'/2 x^(-3/2)
@@ -117,6 +143,8 @@ template <class T> DRT_HD v3<dl<T>> unit(v3<dl<T>> a) {
     return a * inv;
 }
 DRT_HD v3<dd> unit(v3<dd> a) { return a * (scst<dd>(1.f) / norm(a)); }
+DRT_HD v3<de> unit(v3<de> a) { return a * (scst<de>(1.f) / norm(a)); }
+DRT_HD v3<de> strip(v3<dd> a) { return {strip(a.x), strip(a.y), strip(a.z)}; }
 
 // ------------------------------------------------------------------------------------------------
 // complex numbers and complex 3-vectors (polarisation tracking)

@@ -4,6 +4,7 @@
 // coefficients.  Templated on the working precision T; positions carry their time derivative as
 // dual numbers so interaction-point velocities come out of the same arithmetic.
 #pragma once
+#include <type_traits>
 #include "drt_internal.h"
 #include "drt_math.cuh"
 
@@ -257,6 +258,12 @@ template <> DRT_HD void clamp_positive<dl<double>>(dl<double> &x, double eps) {
 template <> DRT_HD void clamp_positive<double>(double &x, double eps) {
     if (!(x > eps)) x = eps;
 }
+template <> DRT_HD void clamp_positive<de>(de &x, float eps) {
+    if (!(x.b + x.d > eps)) {
+        x.b = eps;
+        x.d = 0.f;
+    }
+}
 template <> DRT_HD void clamp_positive<dd>(dd &x, float eps) {
     if (!(x.b + x.d > eps)) {
         x.b = eps;
@@ -271,6 +278,7 @@ template <> DRT_HD double newton_start<double>(double base, double delta, double
 template <> DRT_HD dl<double> newton_start<dl<double>>(double base, double delta, double rate) {
     return {base + delta, rate};
 }
+template <> DRT_HD de newton_start<de>(double base, double delta, double) { return {(float)base, (float)delta}; }
 template <> DRT_HD dd newton_start<dd>(double base, double delta, double rate) {
     return {(float)base, (float)delta, (float)rate};
 }
@@ -802,7 +810,15 @@ DRT_HD void warm_start_at(const LinkDev &L, const TimeGridD &tg, const double *w
                   tg.chunk * tg.dt, ws);
 }
 
-template <class Loader>
+// terminal position (and velocity on dual numbers) at time t
+template <class S> DRT_HD v3<S> terminal_as(const TermD &m, double t);
+template <> DRT_HD v3<dl<double>> terminal_as<dl<double>>(const TermD &m, double t) { return terminal<double>(m, t); }
+template <> DRT_HD v3<double> terminal_as<double>(const TermD &m, double t) { return val(terminal<double>(m, t)); }
+
+// S = dl<double> carries every position with its time derivative (the interaction points' sliding
+// velocities, which only the Doppler shift needs); S = double runs the same geometry on values
+// alone, for calls that ask for no Doppler output (H synthesis), at about half the FP64 work
+template <class S = dl<double>, class Loader>
 DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, int p, int ti,
                                 const OutD &out, const RecD &rec, bool f32out, Loader load,
                                 const double *warm = nullptr, double *rec64 = nullptr) {
@@ -812,7 +828,7 @@ DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const Fre
     int4 pi = L.pprims[p];
     int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
     int n = 0;
-    Prim<dl<T>> pr[MAXI];
+    Prim<S> pr[MAXI];
     for (int j = 0; j < MAXI; ++j) {
         int ty = (code >> (8 * j)) & 0xff;
         if (ty != T_NONE) {
@@ -820,9 +836,9 @@ DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const Fre
             n = j + 1;
         }
     }
-    v3<dl<T>> V[MAXI + 2];
-    V[0] = terminal<T>(L.tx, t);
-    V[n + 1] = terminal<T>(L.rx, t);
+    v3<S> V[MAXI + 2];
+    V[0] = terminal_as<S>(L.tx, t);
+    V[n + 1] = terminal_as<S>(L.rx, t);
     uint32_t fl = 0;
     if (warm && p >= L.n_bulk) {
         WarmStart ws;
@@ -843,7 +859,8 @@ DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const Fre
     T tau = d / T(C0);
     cx<T> a = (fl & F_DEGEN) ? C<T>(T(0), T(0)) : amplitude(L, pr, n, seg, T(fg.fc));
     if (out.tau || out.amp || out.doppler || out.angles || out.flags || out.points) {
-        T fd = doppler(n, V, seg, T(fg.fc));
+        T fd = 0;
+        if constexpr (!std::is_same<S, double>::value) fd = doppler(n, V, seg, T(fg.fc));
         size_t oi = (size_t)ti * L.n_paths + L.perm[p];
         if (f32out) {
             OutD o2 = out;
@@ -869,14 +886,6 @@ DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const Fre
         rec64[1] = fl ? 0.0 : a.im;
         rec64[2] = tau;
     }
-}
-
-DRT_HD void path_step_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const double *pose, int p,
-                           int ti, const OutD &out, const RecD &rec, bool f32out = false,
-                           const double *warm = nullptr) {
-    path_step_fp64_core(
-        L, tg, fg, p, ti, out, rec, f32out,
-        [&](int ty, int idx) { return load_prim<double>(L, pose, tg.n_steps, ti, ty, idx); }, warm);
 }
 
 // One dual-number FP64 solve of a chain at time t from the edge-parameter start `sin`; writes each
@@ -1141,7 +1150,34 @@ DRT_HD void path_base_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGrid
     out[(size_t)chunk * L.n_paths + p] = r;
 }
 
-DRT_HD void write_outputs_bulk(const OutD &o, size_t oi, int n, const v3<dd> *V, const v3<float> *seg, double tau,
+// a delta-number primitive without its rates
+DRT_HD Prim<de> strip(const Prim<dd> &q) {
+    Prim<de> r;
+    r.type = q.type;
+    r.mat = q.mat;
+    r.idx = q.idx;
+    r.p = strip(q.p);
+    r.a = strip(q.a);
+    r.b = q.b;
+    r.c = q.c;
+    r.h1 = q.h1;
+    r.h2 = q.h2;
+    r.h3 = q.h3;
+    r.h4 = q.h4;
+    return r;
+}
+template <class S> DRT_HD Prim<S> load_prim_as(const LinkDev &L, const PoseB *poseb, int n_chunks, int chunk,
+                                               float tau, int type, int idx) {
+    if constexpr (std::is_same<S, dd>::value) return load_prim_dd(L, poseb, n_chunks, chunk, tau, type, idx);
+    else return strip(load_prim_dd(L, poseb, n_chunks, chunk, tau, type, idx));
+}
+template <class S> DRT_HD v3<S> terminal_as(const PoseB &q, float tau) {
+    if constexpr (std::is_same<S, dd>::value) return terminal_dd(q, tau);
+    else return strip(terminal_dd(q, tau));
+}
+
+template <class S>
+DRT_HD void write_outputs_bulk(const OutD &o, size_t oi, int n, const v3<S> *V, const v3<float> *seg, double tau,
                                cx<float> a, float fd, uint32_t fl) {
     if (o.tau) o.tau[oi] = tau;
     if (o.amp) {
@@ -1181,7 +1217,9 @@ struct Rec5 { float ar, ai, ph, hi, lo; };
 // FP32-bulk (path, time-step): geometry in delta numbers on the chunk anchors, field in FP32.
 // Chains with >= 2 diffractions in a segment start their Newton solve from the FP64 chunk-base
 // parameters (warm, may be null for the others).  Returns false when the step was queued for the
-// FP64 redo (its record is then zero).
+// FP64 redo (its record is then zero).  S = dd carries the rates the Doppler shift needs, S = de
+// (calls without Doppler output) leaves them out.
+template <class S = dd>
 DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const PoseB *poseb,
                       const BaseRec *base, const double *warm, int p, int ti, const OutD &out, Rec5 &rec,
                       const RedoList &redo, int link) {
@@ -1194,17 +1232,17 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
     int4 pi = L.pprims[p];
     int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
     int n = 0;
-    Prim<dd> pr[MAXI];
+    Prim<S> pr[MAXI];
     for (int j = 0; j < MAXI; ++j) {
         int ty = (code >> (8 * j)) & 0xff;
         if (ty != T_NONE) {
-            pr[j] = load_prim_dd(L, poseb, n_chunks, chunk, tau_t, ty, prim[j]);
+            pr[j] = load_prim_as<S>(L, poseb, n_chunks, chunk, tau_t, ty, prim[j]);
             n = j + 1;
         }
     }
-    v3<dd> V[MAXI + 2];
-    V[0] = terminal_dd(poseb[(size_t)L.n_bodies * n_chunks + chunk], tau_t);
-    V[n + 1] = terminal_dd(poseb[(size_t)(L.n_bodies + 1) * n_chunks + chunk], tau_t);
+    v3<S> V[MAXI + 2];
+    V[0] = terminal_as<S>(poseb[(size_t)L.n_bodies * n_chunks + chunk], tau_t);
+    V[n + 1] = terminal_as<S>(poseb[(size_t)(L.n_bodies + 1) * n_chunks + chunk], tau_t);
     uint32_t fl = 0;
     if (warm && p >= L.n_bulk) {
         WarmStart ws;
@@ -1247,14 +1285,15 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
     float dd_len = 0.f;   // change of the path length since the chunk base
     v3<float> seg[MAXI + 2];
     for (int i = 1; i <= n + 1; ++i) {
-        v3<dd> sv = V[i] - V[i - 1];
+        v3<S> sv = V[i] - V[i - 1];
         dd_len += norm(sv).d;
         // segment vector: FP64-accurate base + FP32 delta
         seg[i] = V3<float>(B.seg[i - 1][0] + sv.x.d, B.seg[i - 1][1] + sv.y.d, B.seg[i - 1][2] + sv.z.d);
     }
     cx<T> a = (fl & F_DEGEN) ? C<T>(T(0), T(0)) : amplitude(L, pr, n, seg, fg.fcf);
     if (out.tau || out.amp || out.doppler || out.angles || out.flags || out.points) {
-        T fd = doppler(n, V, seg, fg.fcf);
+        T fd = 0.f;
+        if constexpr (std::is_same<S, dd>::value) fd = doppler(n, V, seg, fg.fcf);
         size_t oi = (size_t)ti * L.n_paths + L.perm[p];
         write_outputs_bulk(out, oi, n, V, seg, (B.d + (double)dd_len) / C0, a, fd, fl);
     }
@@ -1271,11 +1310,12 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
     return true;
 }
 
+template <class S = dd>
 DRT_HD void path_step_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const PoseB *poseb,
                            const BaseRec *base, const double *warm, int p, int ti, const OutD &out, const RecD &rec,
                            const RedoList &redo) {
     Rec5 r;
-    bulk_eval(L, tg, fg, poseb, base, warm, p, ti, out, r, redo, 0);
+    bulk_eval<S>(L, tg, fg, poseb, base, warm, p, ti, out, r, redo, 0);
     if (rec.rec_a) {
         size_t ri = (size_t)ti * L.n_paths + p;
         rec.rec_a[ri] = make_float4(r.ar, r.ai, r.ph, r.hi);
@@ -1289,6 +1329,26 @@ DRT_HD void path_step_redo(const LinkDev &L, const TimeGridD &tg, const FreqGrid
     const double t = tg.t_start + ti * tg.dt;
     path_step_fp64_core(L, tg, fg, p, ti, out, rec, true,
                         [&](int ty, int idx) { return load_prim_direct<double>(L, t, ty, idx); }, warm);
+}
+
+// one (path, step) of the FP64 form from the per-step pose table; DUAL = false when no Doppler
+// output is asked for (values only)
+template <bool DUAL>
+DRT_HD void path_step_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const double *pose, int p,
+                           int ti, const OutD &out, const RecD &rec, bool f32out = false,
+                           const double *warm = nullptr) {
+    if constexpr (DUAL) {
+        path_step_fp64_core<dl<double>>(
+            L, tg, fg, p, ti, out, rec, f32out,
+            [&](int ty, int idx) { return load_prim<double>(L, pose, tg.n_steps, ti, ty, idx); }, warm);
+    } else {
+        path_step_fp64_core<double>(
+            L, tg, fg, p, ti, out, rec, f32out,
+            [&](int ty, int idx) {
+                return load_prim_value(L, pose_at(pose, tg.n_steps, prim_body(L, ty, idx), ti), ty, idx);
+            },
+            warm);
+    }
 }
 
 }  // namespace drt
