@@ -211,12 +211,9 @@ __global__ void __launch_bounds__(32) k_batch_redo(const BatchDev B) {   // one 
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int4 itm = B.redo.items[k];
         const BatchLink &BL = B.links[itm.x];
-        const double t = BL.tg.t_start + itm.z * BL.tg.dt;
         double r[3];
         const RecD nor{nullptr, nullptr};
-        path_step_fp64_core(
-            BL.L, BL.tg, BL.fg, itm.y, itm.z, BL.out, nor, true,
-            [&](int ty, int idx) { return load_prim_direct<double>(BL.L, t, ty, idx); }, BL.warm, r);
+        path_step_redo(BL.L, BL.tg, BL.fg, itm.y, itm.z, BL.out, nor, BL.warm, r);
         if (r[0] == 0.0 && r[1] == 0.0) continue;
         // a exp(-j 2 pi f_k tau): FP64-reduced seed per 16-bin tile, FP32 rotation across the tile
         const double f0 = BL.fg.fc - 0.5 * BL.fg.bandwidth, df = BL.fg.bandwidth / BL.fg.n_bins;

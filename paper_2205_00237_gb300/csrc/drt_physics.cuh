@@ -1150,6 +1150,23 @@ DRT_HD void path_base_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGrid
     out[(size_t)chunk * L.n_paths + p] = r;
 }
 
+// an FP64 dual-number primitive without its rates
+DRT_HD Prim<double> val_prim(const Prim<dl<double>> &q) {
+    Prim<double> r;
+    r.type = q.type;
+    r.mat = q.mat;
+    r.idx = q.idx;
+    r.p = val(q.p);
+    r.a = val(q.a);
+    r.b = q.b;
+    r.c = q.c;
+    r.h1 = q.h1;
+    r.h2 = q.h2;
+    r.h3 = q.h3;
+    r.h4 = q.h4;
+    return r;
+}
+
 // a delta-number primitive without its rates
 DRT_HD Prim<de> strip(const Prim<dd> &q) {
     Prim<de> r;
@@ -1272,7 +1289,13 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
             // see F_REDO64); the list holds every path-step in the worst case
             if (redo.count) {
 #ifdef __CUDA_ARCH__
-                int k = atomicAdd(redo.count, 1);
+                // one claim per warp: the queued steps of a warp (consecutive steps of one path)
+                // stay adjacent in the list, so the redo warps run one chain signature each
+                const unsigned m = __activemask();
+                const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+                int k0 = 0;
+                if (lane == leader) k0 = atomicAdd(redo.count, __popc(m));
+                const int k = __shfl_sync(m, k0, leader) + __popc(m & ((1u << lane) - 1u));
 #else
                 int k = (*redo.count)++;
 #endif
@@ -1325,10 +1348,17 @@ DRT_HD void path_step_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGrid
 
 // FP64 redo of one queued FP32-bulk path-step (FP32 output formats)
 DRT_HD void path_step_redo(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, int p, int ti, const OutD &out,
-                           const RecD &rec, const double *warm) {
+                           const RecD &rec, const double *warm, double *rec64 = nullptr) {
     const double t = tg.t_start + ti * tg.dt;
-    path_step_fp64_core(L, tg, fg, p, ti, out, rec, true,
-                        [&](int ty, int idx) { return load_prim_direct<double>(L, t, ty, idx); }, warm);
+    if (out.doppler) {
+        path_step_fp64_core<dl<double>>(
+            L, tg, fg, p, ti, out, rec, true, [&](int ty, int idx) { return load_prim_direct<double>(L, t, ty, idx); },
+            warm, rec64);
+    } else {   // no Doppler output: values only
+        path_step_fp64_core<double>(
+            L, tg, fg, p, ti, out, rec, true,
+            [&](int ty, int idx) { return val_prim(load_prim_direct<double>(L, t, ty, idx)); }, warm, rec64);
+    }
 }
 
 // one (path, step) of the FP64 form from the per-step pose table; DUAL = false when no Doppler
