@@ -464,15 +464,15 @@ template <> DRT_HD TileV<float> tilev<float>(const LinkDev &L, int idx) {
 // ------------------------------------------------------------------------------------------------
 // field coefficients
 // Fresnel reflection coefficients for the perpendicular (TE) and parallel (TM) components;
-// eps_c = eps_r - j sigma / (2 pi f eps0); a perfect conductor gives -1 and +1.
+// eps_c = eps_r - j sigma ieps with ieps = 1 / (2 pi f eps0); a perfect conductor gives -1 and +1.
 template <class T>
-DRT_HD void fresnel(const MatV<T> &m, T fc, T ct, cx<T> &rte, cx<T> &rtm) {
+DRT_HD void fresnel(const MatV<T> &m, T ieps, T ct, cx<T> &rte, cx<T> &rtm) {
     if (m.pec) {
         rte = C<T>(T(-1), T(0));
         rtm = C<T>(T(1), T(0));
         return;
     }
-    cx<T> ec = C<T>(m.eps_r, -m.sigma / (T(2 * PI) * fc * T(EPS0)));
+    cx<T> ec = C<T>(m.eps_r, -m.sigma * ieps);
     cx<T> sq = csqrt_(C<T>(ec.re - T(1) + ct * ct, ec.im));
     rte = cdiv(C<T>(ct - sq.re, -sq.im), C<T>(ct + sq.re, sq.im));
     cx<T> ecct = ec * ct;
@@ -542,9 +542,17 @@ template <class T> DRT_HD cx<T> utd_term(T eps, T n, T inv2n, T kL) {
         T m = n * sqrt(T(2 * PI) * kL) * (eps >= T(0) ? T(1) : T(-1)) * T(0.70710678118654752440);
         return C<T>(m, m);
     }
-    T sh = sin(T(0.5) * eps);
-    T s2, c2;
-    sincos(eps * inv2n, &s2, &c2);   // cot(eps / 2n)
+    T sh, s2, c2;
+    if (n == T(1.5)) {   // right-angled wedge: eps/2 = 3u and eps/2n = 2u with u = eps/6, one sincos
+        T su, cu;
+        sincos(eps * T(1.0 / 6.0), &su, &cu);
+        sh = su * (T(3) - T(4) * su * su);
+        s2 = T(2) * su * cu;
+        c2 = T(1) - T(2) * su * su;
+    } else {
+        sh = sin(T(0.5) * eps);
+        sincos(eps * inv2n, &s2, &c2);   // cot(eps / 2n)
+    }
     return transition_F(T(2) * kL * sh * sh) * (c2 / s2);
 }
 
@@ -553,7 +561,7 @@ template <class T> DRT_HD cx<T> utd_term(T eps, T n, T inv2n, T kL) {
 // (sphip = |sin phi'|, snphi = |sin(n pi - phi)|: the incidence sines of the 0-face and n-face
 // reflection coefficients, passed in from the direction components)
 template <class T>
-DRT_HD void utd(T n, T phi, T phip, T sphip, T snphi, T sinb0, T L, T k, const MatV<T> &m, T fc, cx<T> &Ds,
+DRT_HD void utd(T n, T phi, T phip, T sphip, T snphi, T sinb0, T L, T k, const MatV<T> &m, T ieps, cx<T> &Ds,
                 cx<T> &Dh) {
     T kL = k * L;
     T pref = T(1) / (T(2) * n * sqrt(T(2 * PI) * k) * sinb0);
@@ -565,8 +573,8 @@ DRT_HD void utd(T n, T phi, T phip, T sphip, T snphi, T sinb0, T L, T k, const M
     cx<T> t3 = utd_term(T(PI) - bp + tpn * round((bp - T(PI)) * itpn), n, inv2n, kL);   // 0-face
     cx<T> t4 = utd_term(T(PI) + bp - tpn * round((bp + T(PI)) * itpn), n, inv2n, kL);   // n-face
     cx<T> r0s, r0h, rns, rnh;
-    fresnel(m, fc, sphip, r0s, r0h);
-    fresnel(m, fc, snphi, rns, rnh);
+    fresnel(m, ieps, sphip, r0s, r0h);
+    fresnel(m, ieps, snphi, rns, rnh);
     cx<T> base = t1 + t2;
     Ds = Cc * (base + r0s * t3 + rns * t4);
     Dh = Cc * (base + r0h * t3 + rnh * t4);
@@ -647,6 +655,7 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
         a = b;
     }
     const T k = T(2 * PI) * fc / T(C0);
+    const T ieps = T(1) / (T(2 * PI) * fc * T(EPS0));   // eps_c = eps_r - j sigma ieps
     c3<T> E = {C<T>(T(0), T(0)), C<T>(T(0), T(0)), C<T>(T(0), T(0))};
     {
         v3<T> e0 = vertical_pol(kd[1]);
@@ -668,7 +677,7 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
             ep = unit(ep);
             v3<T> epin = cross(ep, kin), epout = cross(ep, kout);
             cx<T> rte, rtm;
-            fresnel(m, fc, ct, rte, rtm);
+            fresnel(m, ieps, ct, rte, rtm);
             T rough = sqrt(fmax(T(0), T(1) - m.rough * m.rough));
             E = cscale(ep, rte * cdot(E, ep) * rough) + cscale(epout, rtm * cdot(E, epin) * rough);
         } else if (q.type == T_D) {
@@ -687,7 +696,7 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
                 snphi = ro > T(0) ? fabs(q.h3 * xo - q.h4 * yo) / ro : T(0);
             }
             cx<T> Ds, Dh;
-            utd(q.h2, phi, phip, sphip, snphi, sinb0, Lp, k, m, fc, Ds, Dh);
+            utd(q.h2, phi, phip, sphip, snphi, sinb0, Lp, k, m, ieps, Ds, Dh);
             v3<T> php = -unit(cross(e, kin)), bpv = cross(php, kin);
             v3<T> ph = unit(cross(e, kout)), bv = cross(ph, kout);
             E = cscale(bv, -(Ds * cdot(E, bpv))) + cscale(ph, -(Dh * cdot(E, php)));
