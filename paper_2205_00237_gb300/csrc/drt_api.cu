@@ -377,8 +377,8 @@ drt_status drt::pack_link(const drt_scene *s, const drt_path_set *ps, PackedLink
     mats.resize(s->n_materials);
     for (int i = 0; i < s->n_materials; ++i) {
         const drt_material &m = s->materials[i];
-        mats[i] = MatD{m.eps_r, m.sigma, m.rough_s, m.pec, (float)m.eps_r, (float)m.sigma, (float)m.rough_s,
-                       (float)m.pec};
+        const double spec = std::sqrt(std::max(0.0, 1.0 - m.rough_s * m.rough_s));   // specular scale of a rough face
+        mats[i] = MatD{m.eps_r, m.sigma, spec, m.pec, (float)m.eps_r, (float)m.sigma, (float)spec, (float)m.pec};
     }
     auto f3 = [](float *d, const double *x) {
         for (int j = 0; j < 3; ++j) d[j] = (float)x[j];

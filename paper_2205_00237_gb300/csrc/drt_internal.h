@@ -21,7 +21,7 @@ constexpr int POSE_W = 18;   // doubles per (time, body) pose record: R (3x3 row
 struct FaceD { double c[3], n[3], u[3], hu, hw; int32_t body, mat; };                       // 96 B
 struct EdgeD { double a[3], e[3], t0[3], n0[3], len, wn, snp, cnp; int32_t body, mat, pad0, pad1; };  // 144 B: snp, cnp = sin, cos(wn pi)
 struct TileD { double c[3], n[3], area, s, alpha, cph, sph; int32_t body, mat; };          // 96 B: cph + j sph = exp(j phase)
-struct MatD { double eps_r, sigma, rough, pec; float eps_rf, sigmaf, roughf, pecf; };       // 48 B
+struct MatD { double eps_r, sigma, spec, pec; float eps_rf, sigmaf, specf, pecf; };         // 48 B: spec = sqrt(1 - S^2)
 // FP32 copies for the FP32-bulk form (same meaning, no FP64 conversions in its kernels)
 struct FaceF { float c[3], n[3], u[3], hu, hw; int32_t body, mat, pad0, pad1, pad2; };          // 64 B
 struct EdgeF { float a[3], e[3], t0[3], n0[3], len, wn, snp, cnp; int32_t body, mat; };      // 72 B

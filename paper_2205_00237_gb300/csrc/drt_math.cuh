@@ -169,12 +169,13 @@ template <class T> DRT_HD T cabs2(cx<T> a) { return a.re * a.re + a.im * a.im; }
 template <class T> DRT_HD cx<T> csqrt_(cx<T> z) {
     T r = sqrt(z.re * z.re + z.im * z.im);   // |z| of relative permittivities: no overflow scaling
     if (r == T(0)) return {T(0), T(0)};
+    // one reciprocal square root gives both t = sqrt(h) and 1/t
     if (z.re >= T(0)) {
-        T t = sqrt(T(0.5) * (r + z.re));
-        return {t, z.im / (T(2) * t)};
+        const T h = T(0.5) * (r + z.re), rs = rsqrt(h);
+        return {h * rs, T(0.5) * z.im * rs};
     }
-    T t = sqrt(T(0.5) * (r - z.re));
-    return {fabs(z.im) / (T(2) * t), copysign(t, z.im)};
+    const T h = T(0.5) * (r - z.re), rs = rsqrt(h);
+    return {T(0.5) * fabs(z.im) * rs, copysign(h * rs, z.im)};
 }
 template <class T> DRT_HD cx<T> cexpj(T ph) {   // exp(j ph)
     T s, c;

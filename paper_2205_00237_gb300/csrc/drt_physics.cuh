@@ -446,10 +446,10 @@ DRT_HD uint32_t validity(const Prim<S> *pr, int n, const v3<typename ST<S>::R> *
 
 // ------------------------------------------------------------------------------------------------
 // material and tile parameters in the working precision
-template <class T> struct MatV { T eps_r, sigma, rough; bool pec; };
+template <class T> struct MatV { T eps_r, sigma, spec; bool pec; };   // spec = sqrt(1 - S^2)
 template <class T> DRT_HD MatV<T> matv(const MatD &m);
-template <> DRT_HD MatV<double> matv<double>(const MatD &m) { return {m.eps_r, m.sigma, m.rough, m.pec != 0.0}; }
-template <> DRT_HD MatV<float> matv<float>(const MatD &m) { return {m.eps_rf, m.sigmaf, m.roughf, m.pecf != 0.f}; }
+template <> DRT_HD MatV<double> matv<double>(const MatD &m) { return {m.eps_r, m.sigma, m.spec, m.pec != 0.0}; }
+template <> DRT_HD MatV<float> matv<float>(const MatD &m) { return {m.eps_rf, m.sigmaf, m.specf, m.pecf != 0.f}; }
 template <class T> struct TileV { T area, s, cph, sph; int alpha; };   // cph + j sph = exp(j phase)
 template <class T> DRT_HD TileV<T> tilev(const LinkDev &L, int idx);
 template <> DRT_HD TileV<double> tilev<double>(const LinkDev &L, int idx) {
@@ -488,11 +488,11 @@ template <class T> struct TransitionCfg;
 // The continued fraction's depth follows X: ceil(cf_a + cf_b / X) terms reach the working precision
 // (2e-16 relative in FP64, 3e-8 in FP32, checked against 40-digit erfc on [x_ser, x_asy)).
 template <> struct TransitionCfg<double> {
-    static constexpr double x_ser = 6.0, x_asy = 100.0, cf_a = 6.0, cf_b = 370.0;
+    static constexpr double x_ser = 6.0, x_asy = 100.0, cf_a = 6.0, cf_b = 370.0, asy_eps = 1e-17;
     static constexpr int n_cf = 68, n_asy = 12;
 };
 template <> struct TransitionCfg<float> {
-    static constexpr float x_ser = 3.0f, x_asy = 40.0f, cf_a = 3.0f, cf_b = 84.0f;
+    static constexpr float x_ser = 3.0f, x_asy = 40.0f, cf_a = 3.0f, cf_b = 84.0f, asy_eps = 1e-8f;
     static constexpr int n_cf = 31, n_asy = 8;
 };
 
@@ -503,11 +503,15 @@ template <class T> DRT_HD cx<T> transition_F(T X) {
     const T r2 = T(0.70710678118654752440);
     if (X >= T(Cfg::x_asy)) {
         // 1 + sum_{m>=1} prod_{i<=m} (-(2i-1)) / (2jX) ; 1/(2jX) = -j/(2X)
+        // each factor -(2m - 1) / (2jX) is purely imaginary: one real multiply per part; stop once
+        // the terms fall below the working precision
         cx<T> acc = C<T>(T(1), T(0)), term = C<T>(T(1), T(0));
-        cx<T> inv = C<T>(T(0), T(-0.5) / X);
+        const T a = T(-0.5) / X;   // 1/(2jX) = j a
         for (int mm = 1; mm <= Cfg::n_asy; ++mm) {
-            term = term * inv * T(-(2 * mm - 1));
+            const T sm = a * T(-(2 * mm - 1));   // term *= j sm
+            term = C<T>(-term.im * sm, term.re * sm);
             acc = acc + term;
+            if (fabs(term.re) + fabs(term.im) < T(Cfg::asy_eps)) break;
         }
         return acc;
     }
@@ -678,8 +682,7 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
             v3<T> epin = cross(ep, kin), epout = cross(ep, kout);
             cx<T> rte, rtm;
             fresnel(m, ieps, ct, rte, rtm);
-            T rough = sqrt(fmax(T(0), T(1) - m.rough * m.rough));
-            E = cscale(ep, rte * cdot(E, ep) * rough) + cscale(epout, rtm * cdot(E, epin) * rough);
+            E = cscale(ep, rte * cdot(E, ep) * m.spec) + cscale(epout, rtm * cdot(E, epin) * m.spec);
         } else if (q.type == T_D) {
             v3<T> e = val(q.a);
             v3<T> wi = -kin + e * dot(kin, e);
