@@ -486,14 +486,16 @@ DRT_HD void fresnel(const MatV<T> &m, T ieps, T ct, cx<T> &rte, cx<T> &rtm) {
 // F ~ sum_m (2m-1)!! / (-2jX)^m (large X) -- Abramowitz & Stegun 7.1.5, 7.1.14, 7.1.23.
 template <class T> struct TransitionCfg;
 // The continued fraction's depth follows X: ceil(cf_a + cf_b / X) terms reach the working precision
-// (2e-16 relative in FP64, 3e-8 in FP32, checked against 40-digit erfc on [x_ser, x_asy)).
+// (2e-16 relative in FP64, 3e-8 in FP32, checked against 40-digit erfc on [x_ser, x_asy)); the
+// asymptotic series, stopped once a term falls below asy_eps, reaches it from x_asy on (2.2e-16
+// at X = 40 after 34 terms in FP64, 4.5e-9 at X = 20 after 14 terms in FP32).
 template <> struct TransitionCfg<double> {
-    static constexpr double x_ser = 6.0, x_asy = 100.0, cf_a = 6.0, cf_b = 370.0, asy_eps = 1e-17;
-    static constexpr int n_cf = 68, n_asy = 12;
+    static constexpr double x_ser = 6.0, x_asy = 40.0, cf_a = 6.0, cf_b = 370.0, asy_eps = 1e-17;
+    static constexpr int n_cf = 68, n_asy = 40;
 };
 template <> struct TransitionCfg<float> {
-    static constexpr float x_ser = 3.0f, x_asy = 40.0f, cf_a = 3.0f, cf_b = 84.0f, asy_eps = 1e-8f;
-    static constexpr int n_cf = 31, n_asy = 8;
+    static constexpr float x_ser = 3.0f, x_asy = 20.0f, cf_a = 3.0f, cf_b = 84.0f, asy_eps = 1e-8f;
+    static constexpr int n_cf = 31, n_asy = 16;
 };
 
 template <class T> DRT_HD cx<T> transition_F(T X) {
