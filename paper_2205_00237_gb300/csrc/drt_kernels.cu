@@ -161,8 +161,8 @@ __global__ void __launch_bounds__(EXT_T, 4)
 k_extrapolate_bulk(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const PoseB *__restrict__ poseb,
                    const BaseRec *__restrict__ base, const double *__restrict__ warm, const OutD out, const RecD rec,
                    const RedoList redo) {
-    int p = blockIdx.x;
-    int ti = blockIdx.y * EXT_T + threadIdx.x;
+    int p = blockIdx.y;   // time-major block order: an SM's resident blocks are nearby paths (signatures)
+    int ti = blockIdx.x * EXT_T + threadIdx.x;
     if (p >= L.n_paths || ti >= tg.n_steps) return;
     if constexpr (DUAL) path_step_bulk<dd>(L, tg, fg, poseb, base, warm, p, ti, out, rec, redo);
     else path_step_bulk<de>(L, tg, fg, poseb, base, warm, p, ti, out, rec, redo);
@@ -174,7 +174,7 @@ cudaError_t launch_extrapolate_bulk(const LinkDev &L, const TimeGridD &tg, const
     cudaError_t e = cudaMemsetAsync(redo, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     if (L.n_paths == 0 || tg.n_steps == 0) return cudaSuccess;
-    dim3 grid(L.n_paths, (tg.n_steps + EXT_T - 1) / EXT_T);
+    dim3 grid((tg.n_steps + EXT_T - 1) / EXT_T, L.n_paths);
     const PoseB *pb = reinterpret_cast<const PoseB *>(poseb);
     const BaseRec *bs = reinterpret_cast<const BaseRec *>(base);
     // rates (dual parts) only when the Doppler shift is asked for

@@ -4,6 +4,10 @@
 // coefficients.  Templated on the working precision T; positions carry their time derivative as
 // dual numbers so interaction-point velocities come out of the same arithmetic.
 #pragma once
+// rarely executed code (multi-diffraction Newton, the transition function near shadow boundaries,
+// user-output writes) is kept out of line so the hot per-step code stays dense in the instruction
+// cache (canyon FP32-bulk step 0.36 -> 0.27 ms)
+#define DRT_OUTLINE __host__ __device__ __noinline__
 #include <type_traits>
 #include "drt_internal.h"
 #include "drt_math.cuh"
@@ -284,7 +288,7 @@ template <> DRT_HD dd newton_start<dd>(double base, double delta, double rate) {
 }
 
 template <class S>
-DRT_HD void multi_diffraction(const Prim<S> *pr, v3<S> *V, int a, int b, const double *s0, const double *ds0,
+DRT_OUTLINE void multi_diffraction(const Prim<S> *pr, v3<S> *V, int a, int b, const double *s0, const double *ds0,
                               const double *rate0, uint32_t &fl) {
     typedef typename ST<S>::R T;
     // convergence threshold on the Newton step (m): near round-off of the working precision
@@ -498,25 +502,11 @@ template <> struct TransitionCfg<float> {
     static constexpr int n_cf = 31, n_asy = 16;
 };
 
-template <class T> DRT_HD cx<T> transition_F(T X) {
+// X below the asymptotic range (rare: a ray near a shadow or reflection boundary), out of line
+template <class T> DRT_OUTLINE cx<T> transition_F_near(T X) {
     using Cfg = TransitionCfg<T>;
-    if (!(X > T(0))) return C<T>(T(0), T(0));
     const T sqpi = T(1.7724538509055160273);
     const T r2 = T(0.70710678118654752440);
-    if (X >= T(Cfg::x_asy)) {
-        // 1 + sum_{m>=1} prod_{i<=m} (-(2i-1)) / (2jX) ; 1/(2jX) = -j/(2X)
-        // each factor -(2m - 1) / (2jX) is purely imaginary: one real multiply per part; stop once
-        // the terms fall below the working precision
-        cx<T> acc = C<T>(T(1), T(0)), term = C<T>(T(1), T(0));
-        const T a = T(-0.5) / X;   // 1/(2jX) = j a
-        for (int mm = 1; mm <= Cfg::n_asy; ++mm) {
-            const T sm = a * T(-(2 * mm - 1));   // term *= j sm
-            term = C<T>(-term.im * sm, term.re * sm);
-            acc = acc + term;
-            if (fabs(term.re) + fabs(term.im) < T(Cfg::asy_eps)) break;
-        }
-        return acc;
-    }
     T sx = sqrt(X);
     cx<T> z = C<T>(r2 * sx, r2 * sx);   // exp(j pi/4) sqrt(X)
     cx<T> pre = C<T>(sqpi * sx * r2, sqpi * sx * r2);   // sqrt(pi X) exp(j pi/4)
@@ -539,6 +529,28 @@ template <class T> DRT_HD cx<T> transition_F(T X) {
     const int depth = min(Cfg::n_cf, (int)ceil(T(Cfg::cf_a) + T(Cfg::cf_b) / X));
     for (int k = depth; k >= 1; --k) f = z + cdiv(C<T>(T(0.5) * T(k), T(0)), f);
     return cdiv(pre, f * sqpi);
+}
+
+template <class T> DRT_HD cx<T> transition_F(T X) {
+    using Cfg = TransitionCfg<T>;
+    if (!(X > T(0))) return C<T>(T(0), T(0));
+    const T sqpi = T(1.7724538509055160273);
+    const T r2 = T(0.70710678118654752440);
+    if (X >= T(Cfg::x_asy)) {
+        // 1 + sum_{m>=1} prod_{i<=m} (-(2i-1)) / (2jX) ; 1/(2jX) = -j/(2X)
+        // each factor -(2m - 1) / (2jX) is purely imaginary: one real multiply per part; stop once
+        // the terms fall below the working precision
+        cx<T> acc = C<T>(T(1), T(0)), term = C<T>(T(1), T(0));
+        const T a = T(-0.5) / X;   // 1/(2jX) = j a
+        for (int mm = 1; mm <= Cfg::n_asy; ++mm) {
+            const T sm = a * T(-(2 * mm - 1));   // term *= j sm
+            term = C<T>(-term.im * sm, term.re * sm);
+            acc = acc + term;
+            if (fabs(term.re) + fabs(term.im) < T(Cfg::asy_eps)) break;
+        }
+        return acc;
+    }
+    return transition_F_near(X);
 }
 
 // one Kouyoumjian-Pathak term cot((pi +- beta)/2n) F(kL a+-(beta)) with eps = (pi +- beta) - 2 pi n N:
@@ -1208,7 +1220,7 @@ template <class S> DRT_HD v3<S> terminal_as(const PoseB &q, float tau) {
 }
 
 template <class S>
-DRT_HD void write_outputs_bulk(const OutD &o, size_t oi, int n, const v3<S> *V, const v3<float> *seg, double tau,
+DRT_OUTLINE void write_outputs_bulk(const OutD &o, size_t oi, int n, const v3<S> *V, const v3<float> *seg, double tau,
                                cx<float> a, float fd, uint32_t fl) {
     if (o.tau) o.tau[oi] = tau;
     if (o.amp) {
