@@ -63,7 +63,7 @@ struct drt_ctx {
     std::mutex mu;
     std::map<uint64_t, Link> links;
     uint64_t next_link = 1;
-    Scratch pose, rec_a, rec_b, h, poseb, base, pose64, redo, warm;
+    Scratch pose, rec_a, rec_b, h, poseb, base, pose64, redo, warm, redo3;
     double *probe_sink = nullptr;
     // side streams for work that overlaps within one call (FP32-bulk: anchors and the FP64
     // multi-diffraction paths run beside the FP32 kernel), joined back with events
@@ -220,8 +220,8 @@ Link *find_link(drt_ctx *c, uint64_t id) {
     return it == c->links.end() ? nullptr : &it->second;
 }
 
-// default chunk: 16 steps (FP32-bulk anchors); the batch planner may choose another from its
-// phase-error model
+// chunk of 16 steps (FP64 warm starts); the FP32-bulk form takes its chunk from the phase-error
+// model (choose_chunk)
 TimeGridD tgd(const drt_time_grid *g, int chunk = 16) { return make_tgrid(g->t_start, g->dt, g->n_steps, chunk); }
 FreqGridD fgd(const drt_freq_grid *g) { return make_fgrid(g->fc, g->bandwidth, g->n_bins); }
 
@@ -243,8 +243,10 @@ template <class F> drt_status traced(drt_ctx *c, int kind, cudaStream_t s, F &&l
 
 // pose table + extrapolation (+ records) for one link
 drt_status run_extrapolation(drt_ctx *c, Link &L, const drt_time_grid *tg, const drt_freq_grid *fg,
-                             const OutD &out, const RecD &rec, int32_t precision, cudaStream_t s) {
-    TimeGridD t = tgd(tg);
+                             const OutD &out, const RecD &rec, int32_t precision, cudaStream_t s,
+                             bool defer_redo = false) {
+    // FP32-bulk chunk length from the same phase-error model as the batch planner
+    TimeGridD t = precision == DRT_FP32_BULK ? tgd(tg, choose_chunk(L.view, *tg, *fg)) : tgd(tg);
     FreqGridD f = fgd(fg);
     if (precision == DRT_FP32_BULK) {
         if (drt_status st = ensure(c, c->poseb, bulk_pose_bytes(L.dev, t))) return st;
@@ -268,7 +270,9 @@ drt_status run_extrapolation(drt_ctx *c, Link &L, const drt_time_grid *tg, const
                 return launch_extrapolate_bulk(L.dev, t, f, pb, bs, warm, out, rec, rd, s);
             }))
             return st;
-        if (drt_status st = traced(c, 3, s, [&] { return launch_redo(L.dev, t, f, out, rec, rd, warm, s); })) return st;
+        if (!defer_redo)   // else the caller runs the redo beside the synthesis (synth_into)
+            if (drt_status st = traced(c, 3, s, [&] { return launch_redo(L.dev, t, f, out, rec, rd, warm, s); }))
+                return st;
         return DRT_OK;
     }
     size_t pose_bytes = (size_t)tg->n_steps * L.dev.n_bodies * POSE_W * sizeof(double);
@@ -288,9 +292,26 @@ drt_status synth_into(drt_ctx *c, Link &L, const drt_time_grid *tg, const drt_fr
     if (drt_status st = ensure(c, c->rec_b, n * sizeof(float))) return st;
     RecD rec{reinterpret_cast<float4 *>(c->rec_a.ptr), reinterpret_cast<float *>(c->rec_b.ptr)};
     OutD none{};
-    if (drt_status st = run_extrapolation(c, L, tg, fg, none, rec, precision, s)) return st;
-    TimeGridD t = tgd(tg);
+    TimeGridD t = precision == DRT_FP32_BULK ? tgd(tg, choose_chunk(L.view, *tg, *fg)) : tgd(tg);
     FreqGridD f = fgd(fg);
+    if (precision == DRT_FP32_BULK) {
+        // the FP64 redo of the few steps FP32 cannot resolve runs beside the synthesis (their records
+        // stay zero) and adds its contributions to H afterwards
+        if (drt_status st = ensure(c, c->redo3, (size_t)L.n_paths * tg->n_steps * 3 * sizeof(double) + 8)) return st;
+        if (drt_status st = run_extrapolation(c, L, tg, fg, none, rec, precision, s, true)) return st;
+        double *r3 = reinterpret_cast<double *>(c->redo3.ptr);
+        void *rd = c->redo.ptr;
+        const double *warm = reinterpret_cast<const double *>(c->warm.ptr);
+        cudaStream_t sb = c->side[1];
+        CUDA_TRY(cudaEventRecord(c->ev_fork, s));
+        CUDA_TRY(cudaStreamWaitEvent(sb, c->ev_fork, 0));
+        if (drt_status st = traced(c, 3, sb, [&] { return launch_redo_rec(L.dev, t, f, rd, warm, r3, sb); })) return st;
+        CUDA_TRY(cudaEventRecord(c->ev_join[1], sb));
+        if (drt_status st = traced(c, 2, s, [&] { return launch_synth(rec, L.n_paths, t, f, H, s); })) return st;
+        CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[1], 0));
+        return traced(c, 3, s, [&] { return launch_redo_add(L.dev, t, f, rd, r3, H, s); });
+    }
+    if (drt_status st = run_extrapolation(c, L, tg, fg, none, rec, precision, s)) return st;
     return traced(c, 2, s, [&] { return launch_synth(rec, L.n_paths, t, f, H, s); });
 }
 
@@ -523,7 +544,7 @@ void drt_destroy(drt_ctx *c) {
     cudaDeviceSynchronize();
     for (auto &kv : c->links)
         for (void *p : kv.second.allocs) cudaFree(p);
-    for (Scratch *s : {&c->pose, &c->rec_a, &c->rec_b, &c->h, &c->poseb, &c->base, &c->pose64, &c->redo, &c->warm})
+    for (Scratch *s : {&c->pose, &c->rec_a, &c->rec_b, &c->h, &c->poseb, &c->base, &c->pose64, &c->redo, &c->warm, &c->redo3})
         if (s->ptr) cudaFree(s->ptr);
     cudaFree(c->probe_sink);
     for (int i = 0; i < 2; ++i) {

@@ -178,6 +178,12 @@ cudaError_t launch_extrapolate_bulk(const LinkDev &L, const TimeGridD &tg, const
                                     void *redo, cudaStream_t s);
 cudaError_t launch_redo(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const OutD &out, const RecD &rec,
                         void *redo, const double *warm, cudaStream_t s);
+// the redo for an H synthesis: (Re a, Im a, tau) per queued step into out3 ([cap][3] doubles), then
+// added into H after the synthesis
+cudaError_t launch_redo_rec(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, void *redo, const double *warm,
+                            double *out3, cudaStream_t s);
+cudaError_t launch_redo_add(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, void *redo, const double *in3,
+                            float2 *H, cudaStream_t s);
 cudaError_t launch_synth(const RecD &rec, int32_t n_paths, const TimeGridD &tg, const FreqGridD &fg,
                          float2 *H, cudaStream_t s);
 cudaError_t launch_probe(int kind, int blocks, double *sink, cudaStream_t s, float *ms);
