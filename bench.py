@@ -45,13 +45,13 @@ PATHSET = os.path.join(ROOT, "tests", "golden", "pathset_canyon_seed0.npz")
 # profiles/k_extrapolate_fp64_canyon.md) and the FP64 peak of the GB300 derived from its unit counts:
 # 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz = 1.26 TFLOP/s (no FP64 tensor path is used).  DRAM bytes
 # per launch from the same capture (set to None whenever the kernel changes after the capture).
-FP64_FLOP_PER_PATH_STEP = 2090.0
+FP64_FLOP_PER_PATH_STEP = 1756.0
 FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
-K1_DRAM_BYTES_PER_LAUNCH = 29.83e6
+K1_DRAM_BYTES_PER_LAUNCH = 126.71e6
 # FP32-bulk form (profiles/k_extrapolate_bulk_canyon.md, profiles/k_synth_canyon.md): FP32 FLOPs per
 # path-step of k_extrapolate_bulk (FADD + FMUL + 2 FFMA, ncu) and 8 FLOP per synthesis term; FP32
 # peak 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz = 80.5 TFLOP/s
-FP32_FLOP_PER_PATH_STEP = 1928.0
+FP32_FLOP_PER_PATH_STEP = 1733.0
 FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9
 SYNTH_FLOP_PER_TERM = 8.0
 
