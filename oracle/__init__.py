@@ -147,6 +147,29 @@ def synthesize_H(rec, fgrid, n_threads=1):
 
 
 # ---------------------------------------------------------------------------- unit-level calls
+PP_DOPPLER, PP_DELAY = 0, 1
+
+
+def power_profile(rec, steps_per_bin, x0, dx, n_bins, kind=PP_DOPPLER):
+    """Power-Doppler (PDfP, Sec. IV-A) or power-delay (PDP, Sec. IV-B) profile of an extrapolate()
+    record: the incoherent sum of |a_p(t)|^2 over the valid path-steps whose instant falls in time
+    bin i (steps_per_bin consecutive steps) and whose Doppler shift (Hz) or delay (s) falls in bin
+    j = floor((x - x0) / dx), 0 <= j < n_bins.  Returns P[n_time_bins][n_bins] (FP64)."""
+    T, P = rec["tau"].shape
+    n_t = -(-T // steps_per_bin)
+    out = np.zeros((n_t, n_bins))
+    x = rec["fd"] if kind == PP_DOPPLER else rec["tau"]
+    pw = np.abs(rec["a"]) ** 2
+    for t in range(T):                      # plain loops: the definition, nothing fused
+        for p in range(P):
+            if rec["flags"][t, p] != 0:
+                continue
+            j = int(np.floor((x[t, p] - x0) / dx))
+            if 0 <= j < n_bins:
+                out[t // steps_per_bin, j] += pw[t, p]
+    return out
+
+
 def fresnel(eps_r, sigma, pec, fc, cos_theta):
     o = np.empty(4)
     lib().or_fresnel_coeffs(eps_r, sigma, float(pec), fc, cos_theta, _dp(o))

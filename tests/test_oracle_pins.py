@@ -610,3 +610,61 @@ def test_reflection_plus_diffraction_continuous_at_path_level(edge_kind):
     assert r_m["flags"][0, 0] == 0 and r_p["flags"][0, 0] & O.F_FACE
     assert abs(s_m - s_p) < 1e-4 * a_r
     assert np.abs(r_m["a"][0, 1:]).max() > 0.1 * a_r      # the diffracted path is a real contribution
+
+
+# ------------------------------------------------------------------------------------------------
+# Power-Doppler and power-delay profiles (Sec. IV-A, IV-B)
+# ------------------------------------------------------------------------------------------------
+def _los_run(fc=5.9e9):
+    """LoS only: TX fixed at (0, 0, 5), RX from (50, 0, 5) receding along +x at 20 m/s, so the
+    delay is (50 + 20 t)/c, the Doppler shift -20 fc / c and |a| = lambda / (4 pi d) (Friis)."""
+    sc = wall_scene([0, 0, 5], [50, 0, 5], vrx=(20.0, 0, 0))
+    ps = I.chains_to_pathset([[]])
+    tg = I.TimeGrid(0.0, 0.01, 100)
+    return O.extrapolate(sc, ps, tg, fc), tg, fc
+
+
+def test_power_doppler_profile_closed_form():
+    rec, tg, fc = _los_run()
+    lam = C0 / fc
+    t = tg.t_start + tg.dt * np.arange(tg.n_steps)
+    pw = (lam / (4 * np.pi * (50 + 20 * t))) ** 2
+    fd = -20 * fc / C0
+    x0, dx, nb = -1000.0, 14.34, 100
+    P = O.power_profile(rec, 20, x0, dx, nb, O.PP_DOPPLER)
+    j = int(np.floor((fd - x0) / dx))
+    want = np.zeros_like(P)
+    want[:, j] = pw.reshape(5, 20).sum(axis=1)
+    assert P.shape == (5, nb)
+    assert np.allclose(P, want, rtol=1e-9, atol=0)
+
+
+def test_power_delay_profile_closed_form():
+    rec, tg, fc = _los_run()
+    lam = C0 / fc
+    t = tg.t_start + tg.dt * np.arange(tg.n_steps)
+    d = 50 + 20 * t
+    x0, dx, nb = 1.0e-7, 1.0e-9, 200
+    P = O.power_profile(rec, 7, x0, dx, nb, O.PP_DELAY)   # a ragged last time bin (100 = 14 x 7 + 2)
+    want = np.zeros((15, nb))
+    for k in range(tg.n_steps):
+        want[k // 7, int(np.floor((d[k] / C0 - x0) / dx))] += (lam / (4 * np.pi * d[k])) ** 2
+    assert np.allclose(P, want, rtol=1e-9, atol=0)
+
+
+def test_power_profile_keeps_only_valid_path_steps_in_range():
+    """Total power equals the sum of |a|^2 over valid path-steps whose Doppler is in range; a path
+    that leaves its face (tiny scene, seed 0: ground-then-box point from t = 0.6 s) stops counting."""
+    sc = I.scene_tiny(0)
+    ps = I.PathSet.from_npz(os.path.join(GOLD, "pathset_tiny_seed0.npz"))
+    tg = I.TimeGrid(0.0, 1e-3, 1000)
+    rec = O.extrapolate(sc, ps, tg, 28e9, n_threads=8)
+    x0, dx, nb = -3000.0, 14.34, 420
+    P = O.power_profile(rec, 200, x0, dx, nb, O.PP_DOPPLER)
+    valid = rec["flags"] == 0
+    inr = (rec["fd"] >= x0) & (rec["fd"] < x0 + dx * nb)
+    pw = np.abs(rec["a"]) ** 2
+    assert np.isclose(P.sum(), pw[valid & inr].sum(), rtol=1e-12)
+    assert (~valid).any() and (pw[~valid] > 0).any()        # invalid path-steps carry power, excluded
+    per_bin = np.where(valid & inr, pw, 0).reshape(5, 200, -1).sum(axis=(1, 2))
+    assert np.allclose(P.sum(axis=1), per_bin, rtol=1e-12)
