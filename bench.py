@@ -254,6 +254,36 @@ def run_batched(args, ctx, drt, flush):
     return out
 
 
+def run_power(args, link, tg, fg, drt, flush):
+    """Power-Doppler (200 ms windows x 14.34 Hz bins over +-8 kHz) and power-delay (200 ms x 1 ns
+    over 4.096 us) profiles of the canyon link, each one drt_power_profile call (extrapolation with
+    Doppler and records, then the binning kernel)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    spb = max(1, int(round(0.2 / tg.dt)))
+    cases = {"pdfp": (-8000.0, 14.34, 1116, drt.PP_DOPPLER), "pdp": (0.0, 1e-9, 4096, drt.PP_DELAY)}
+    out = {"windows_steps": spb, "l2": "flushed between timed calls"}
+    for prec, pname in ((drt.FP64, "fp64"), (drt.FP32_BULK, "fp32_bulk")):
+        for name, (x0, dx, nb, kind) in cases.items():
+            P = link.power_profile(tg, fg, spb, x0, dx, nb, kind, prec)
+            for _ in range(2):
+                link.power_profile(tg, fg, spb, x0, dx, nb, kind, prec, P=P)
+            torch.cuda.synchronize()
+            evs = []
+            for _ in range(max(1, args.steps)):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                link.power_profile(tg, fg, spb, x0, dx, nb, kind, prec, P=P)
+                e1.record(stream)
+                evs.append((e0, e1))
+            torch.cuda.synchronize()
+            ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+            out[f"{name}_{pname}"] = {"ms": ms, "path_steps_per_s": link.n_paths * tg.n_steps / (ms * 1e-3),
+                                      "bins": nb}
+    return out
+
+
 def run_serving(args, drt):
     """Poisson-arriving prediction requests on resident canyon links (512, 128 and 32 paths),
     horizons U{50..500} x 1 ms from random start times, 512 bins at 60 GHz, HBM budget 64 GB."""
@@ -459,6 +489,7 @@ def run_ours(args):
                             "traffic": None, "note": "per-path-step FLOP count not yet measured"}
     probe = ctx.probe_peak(0)
     line["roofline"]["probe_fp64_tflops"] = probe / 1e12
+    line["power_profiles"] = run_power(args, link, tg, fg, drt, flush)
     if args.batch_links > 0:
         line["batched"] = run_batched(args, ctx, drt, flush)
     if args.serve_seconds > 0:

@@ -192,6 +192,24 @@ drt_status drt_synthesize_H_noalloc(drt_ctx *ctx, uint64_t link, const drt_time_
                                     void *stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Power-Doppler profile (PDfP, Sec. IV-A) and power-delay profile (PDP, Sec. IV-B) of a link:
+ * P[i][j] = sum of |a_p(t)|^2 over the valid path-steps whose instant t_n falls in time bin
+ * i = n / steps_per_bin (the last bin may be ragged) and whose Doppler shift f' - fc (Hz, App. A
+ * Eq. doppler_freq; kind DRT_PP_DOPPLER) or delay tau (s; kind DRT_PP_DELAY) falls in bin
+ * j = floor((x - x0) / dx), 0 <= j < n_bins (the paper bins 200 ms x 14.34 Hz).  The whole path
+ * runs on the device: extrapolation with records into context scratch, then one block per time bin
+ * adds its path-steps into a shared-memory histogram.  P is a caller-owned DEVICE buffer of
+ * ceil(n_steps / steps_per_bin) x n_bins doubles, written whole (may be NULL when n_steps is 0);
+ * 1 <= n_bins <= 4096, dx > 0.
+ * Errors: DRT_EINVAL (grids), DRT_ENOTFOUND, DRT_ENOMEM, DRT_ECUDA. */
+#define DRT_PP_DOPPLER 0
+#define DRT_PP_DELAY 1
+typedef struct { int32_t steps_per_bin, n_bins; double x0, dx; int32_t kind, reserved; } drt_power_grid;
+drt_status drt_power_profile(drt_ctx *ctx, uint64_t link, const drt_time_grid *tgrid,
+                             const drt_freq_grid *fgrid, const drt_power_grid *grid, double *P,
+                             int32_t precision, void *stream);
+
+/* ---------------------------------------------------------------------------------------------
  * a10: batched synthesis over many resident links (FP32-bulk form).  drt_batch_create plans one
  * batch: link i is synthesised over tgrids[i] x fgrids[i] into the caller's DEVICE buffer H[i]
  * ([n_steps][n_bins] complex64).  Each stage (base poses, FP64 chunk poses, multi-diffraction warm

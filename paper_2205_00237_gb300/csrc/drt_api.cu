@@ -63,7 +63,7 @@ struct drt_ctx {
     std::mutex mu;
     std::map<uint64_t, Link> links;
     uint64_t next_link = 1;
-    Scratch pose, rec_a, rec_b, h, poseb, base, pose64, redo, warm, redo3;
+    Scratch pose, rec_a, rec_b, h, poseb, base, pose64, redo, warm, redo3, pp_tau, pp_amp, pp_fd, pp_fl;
     double *probe_sink = nullptr;
     // side streams for work that overlaps within one call (FP32-bulk: anchors and the FP64
     // multi-diffraction paths run beside the FP32 kernel), joined back with events
@@ -544,7 +544,8 @@ void drt_destroy(drt_ctx *c) {
     cudaDeviceSynchronize();
     for (auto &kv : c->links)
         for (void *p : kv.second.allocs) cudaFree(p);
-    for (Scratch *s : {&c->pose, &c->rec_a, &c->rec_b, &c->h, &c->poseb, &c->base, &c->pose64, &c->redo, &c->warm, &c->redo3})
+    for (Scratch *s : {&c->pose, &c->rec_a, &c->rec_b, &c->h, &c->poseb, &c->base, &c->pose64, &c->redo, &c->warm, &c->redo3, &c->pp_tau,
+                       &c->pp_amp, &c->pp_fd, &c->pp_fl})
         if (s->ptr) cudaFree(s->ptr);
     cudaFree(c->probe_sink);
     for (int i = 0; i < 2; ++i) {
@@ -656,6 +657,35 @@ drt_status drt_synthesize_H_host(drt_ctx *c, uint64_t link, const drt_time_grid 
     if (drt_status st = synth_into(c, *L, tg, fg, reinterpret_cast<float2 *>(c->h.ptr), precision, s)) return st;
     CUDA_TRY(cudaMemcpyAsync(H_host, c->h.ptr, bytes, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
+    return DRT_OK;
+}
+
+drt_status drt_power_profile(drt_ctx *c, uint64_t link, const drt_time_grid *tg, const drt_freq_grid *fg,
+                             const drt_power_grid *g, double *P, int32_t precision, void *stream) {
+    if (!c || !g) return fail(DRT_EINVAL, "ctx and power grid must be non-NULL");
+    if (drt_status st = check_grids(tg, fg, precision)) return st;
+    if (!P && tg->n_steps > 0) return fail(DRT_EINVAL, "P must be non-NULL");
+    if (g->steps_per_bin < 1 || g->n_bins < 1 || g->n_bins > 4096 || !(g->dx > 0) || !std::isfinite(g->x0) ||
+        (g->kind != DRT_PP_DOPPLER && g->kind != DRT_PP_DELAY))
+        return fail(DRT_EINVAL, "power grid: steps_per_bin >= 1, 1 <= n_bins <= 4096, dx > 0, finite x0, kind "
+                                "DRT_PP_DOPPLER or DRT_PP_DELAY required");
+    std::lock_guard<std::mutex> lk(c->mu);
+    Link *L = find_link(c, link);
+    if (!L) return fail(DRT_ENOTFOUND, "unknown link %llu", (unsigned long long)link);
+    CUDA_TRY(cudaSetDevice(c->device));
+    const size_t n = (size_t)tg->n_steps * L->n_paths;
+    const size_t fsz = precision == DRT_FP64 ? sizeof(double) : sizeof(float);
+    if (drt_status st = ensure(c, c->pp_tau, n * sizeof(double) + 8)) return st;
+    if (drt_status st = ensure(c, c->pp_amp, 2 * n * fsz + 8)) return st;
+    if (drt_status st = ensure(c, c->pp_fd, n * fsz + 8)) return st;
+    if (drt_status st = ensure(c, c->pp_fl, n + 8)) return st;
+    OutD o{reinterpret_cast<double *>(c->pp_tau.ptr), c->pp_amp.ptr, c->pp_fd.ptr, nullptr,
+           reinterpret_cast<uint8_t *>(c->pp_fl.ptr), nullptr};
+    cudaStream_t s = (cudaStream_t)stream;
+    RecD none{nullptr, nullptr};
+    if (drt_status st = run_extrapolation(c, *L, tg, fg, o, none, precision, s)) return st;
+    CUDA_TRY(launch_power_bin(precision == DRT_FP64, o, tg->n_steps, L->n_paths, g->steps_per_bin, g->x0, g->dx,
+                              g->n_bins, g->kind, P, s));
     return DRT_OK;
 }
 

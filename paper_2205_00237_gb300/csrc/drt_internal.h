@@ -184,6 +184,10 @@ cudaError_t launch_redo_rec(const LinkDev &L, const TimeGridD &tg, const FreqGri
                             double *out3, cudaStream_t s);
 cudaError_t launch_redo_add(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, void *redo, const double *in3,
                             float2 *H, cudaStream_t s);
+// histogram of |a|^2 over (time bin, Doppler (kind 0) or delay (kind 1) bin) from [T][P] records;
+// out[n_time_bins][n_bins] is written whole (FP64)
+cudaError_t launch_power_bin(bool fp64, const OutD &rec, int n_steps, int n_paths, int steps_per_bin, double x0,
+                             double dx, int n_bins, int kind, double *out, cudaStream_t s);
 cudaError_t launch_synth(const RecD &rec, int32_t n_paths, const TimeGridD &tg, const FreqGridD &fg,
                          float2 *H, cudaStream_t s);
 cudaError_t launch_probe(int kind, int blocks, double *sink, cudaStream_t s, float *ms);

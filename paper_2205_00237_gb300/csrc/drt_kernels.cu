@@ -12,6 +12,7 @@
 //                    rotation recurrence inside it, FP32 FMA accumulation, groups added in
 //                    shared memory
 //   k_probe          FMA issue-rate probe for the roofline denominators
+#include <algorithm>
 #include "drt_internal.h"
 #include "drt_physics.cuh"
 
@@ -254,6 +255,66 @@ cudaError_t launch_redo_add(const LinkDev &L, const TimeGridD &tg, const FreqGri
                             float2 *H, cudaStream_t s) {
     if (L.n_paths == 0 || tg.n_steps == 0) return cudaSuccess;
     k_redo_add<<<152 * 4, 128, 0, s>>>(fg, redo_list(redo, L, tg), in3, H);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// Power-Doppler / power-delay profiles (Sec. IV-A, IV-B): incoherent sum of |a|^2 of the valid
+// path-steps per (time bin, Doppler or delay bin).  Block x takes PB_ITEMS path-steps of time
+// bin x / per_t, adds them into a shared-memory histogram (FP64 shared atomics) and adds its non-zero bins
+// into the zeroed output, so a window of any length spreads over the whole GPU.
+constexpr int PB_T = 256, PB_ITEMS = 16 * PB_T;
+
+template <class A>
+__global__ void __launch_bounds__(PB_T)
+k_power_bin(const double *__restrict__ tau, const A *__restrict__ amp, const A *__restrict__ fd,
+            const uint8_t *__restrict__ flags, int n_steps, int n_paths, int steps_per_bin, double x0, double dx,
+            int n_bins, int kind, unsigned per_t, double *__restrict__ out) {
+    extern __shared__ double hist[];
+    const int tb = blockIdx.x / per_t;
+    const int t0 = tb * steps_per_bin, t1 = min(n_steps, t0 + steps_per_bin);
+    const long long n = (long long)(t1 - t0) * n_paths;
+    const long long q0 = (long long)(blockIdx.x % per_t) * PB_ITEMS;
+    if (q0 >= n) return;
+    for (int j = threadIdx.x; j < n_bins; j += PB_T) hist[j] = 0.0;
+    __syncthreads();
+    const long long q1 = min(n, q0 + PB_ITEMS);
+    const size_t base = (size_t)t0 * n_paths;
+    for (long long q = q0 + threadIdx.x; q < q1; q += PB_T) {
+        const size_t i = base + q;
+        if (flags[i]) continue;
+        const double x = kind == 0 ? (double)fd[i] : tau[i];
+        const double u = floor((x - x0) / dx);
+        if (!(u >= 0.0 && u < (double)n_bins)) continue;
+        const double ar = (double)amp[2 * i], ai = (double)amp[2 * i + 1];
+        atomicAdd(&hist[(int)u], ar * ar + ai * ai);
+    }
+    __syncthreads();
+    double *row = out + (size_t)tb * n_bins;
+    for (int j = threadIdx.x; j < n_bins; j += PB_T)
+        if (hist[j] != 0.0) atomicAdd(&row[j], hist[j]);
+}
+
+cudaError_t launch_power_bin(bool fp64, const OutD &rec, int n_steps, int n_paths, int steps_per_bin, double x0,
+                             double dx, int n_bins, int kind, double *out, cudaStream_t s) {
+    const int n_t = (n_steps + steps_per_bin - 1) / steps_per_bin;
+    if (n_t == 0) return cudaSuccess;
+    if (cudaError_t e = cudaMemsetAsync(out, 0, (size_t)n_t * n_bins * sizeof(double), s)) return e;
+    const long long per_bin = (long long)std::min(steps_per_bin, n_steps) * n_paths;
+    if (per_bin == 0) return cudaSuccess;
+    const long long per_t = (per_bin + PB_ITEMS - 1) / PB_ITEMS;
+    if (per_t * n_t > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)(per_t * n_t);
+    const size_t sh = (size_t)n_bins * sizeof(double);
+    if (fp64)
+        k_power_bin<double><<<grid, PB_T, sh, s>>>(rec.tau, reinterpret_cast<const double *>(rec.amp),
+                                                   reinterpret_cast<const double *>(rec.doppler), rec.flags,
+                                                   n_steps, n_paths, steps_per_bin, x0, dx, n_bins, kind, (unsigned)per_t, out);
+    else
+        k_power_bin<float><<<grid, PB_T, sh, s>>>(rec.tau, reinterpret_cast<const float *>(rec.amp),
+                                                  reinterpret_cast<const float *>(rec.doppler), rec.flags,
+                                                  n_steps, n_paths, steps_per_bin, x0, dx, n_bins, kind,
+                                                  (unsigned)per_t, out);
     return cudaGetLastError();
 }
 

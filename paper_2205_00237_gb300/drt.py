@@ -27,7 +27,8 @@ EXPORTS = ["drt_create", "drt_destroy", "drt_last_error", "drt_load_paths", "drt
            "drt_synthesize_H", "drt_synthesize_H_host", "drt_link_info", "drt_probe_peak", "drt_profile_enable",
            "drt_profile_read", "drt_synthesize_H_noalloc", "drt_batch_create", "drt_batch_run", "drt_batch_info",
            "drt_batch_destroy", "drt_serve_start", "drt_serve_stop", "drt_submit", "drt_poll", "drt_wait",
-           "drt_serve_stats_read"]
+           "drt_serve_stats_read", "drt_power_profile"]
+PP_DOPPLER, PP_DELAY = 0, 1
 
 
 class DrtError(RuntimeError):
@@ -63,6 +64,11 @@ class _FreqGrid(C.Structure):
 class _Outputs(C.Structure):
     _fields_ = [("tau", C.c_void_p), ("amp", C.c_void_p), ("doppler", C.c_void_p), ("angles", C.c_void_p),
                 ("flags", C.c_void_p), ("points", C.c_void_p)]
+
+
+class _PowerGrid(C.Structure):
+    _fields_ = [("steps_per_bin", C.c_int32), ("n_bins", C.c_int32), ("x0", C.c_double), ("dx", C.c_double),
+                ("kind", C.c_int32), ("reserved", C.c_int32)]
 
 
 class _Request(C.Structure):
@@ -142,6 +148,8 @@ def load_library(path: str = LIB_PATH):
         L.drt_wait.restype = st
         L.drt_serve_stats_read.argtypes = [vp, C.POINTER(_ServeStats)]
         L.drt_serve_stats_read.restype = st
+        L.drt_power_profile.argtypes = [vp, C.c_uint64, vp, vp, C.POINTER(_PowerGrid), vp, C.c_int32, vp]
+        L.drt_power_profile.restype = st
         _lib = L
         return L
 
@@ -341,6 +349,20 @@ class Link:
         _check(load_library().drt_synthesize_H_host(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs),
                                                     _dptr(H), int(precision), _stream_ptr(stream)))
         return H
+
+    def power_profile(self, tg: I.TimeGrid, fg: I.FreqGrid, steps_per_bin: int, x0: float, dx: float, n_bins: int,
+                      kind: int = PP_DOPPLER, precision: int = FP64, P=None, stream=None):
+        """drt_power_profile: power-Doppler (kind PP_DOPPLER) or power-delay (PP_DELAY) profile into a
+        float64 CUDA tensor [ceil(T / steps_per_bin)][n_bins]."""
+        import torch
+        n_t = -(-int(tg.n_steps) // int(steps_per_bin)) if int(steps_per_bin) > 0 else 0   # the call rejects < 1
+        if P is None:
+            P = torch.empty((n_t, int(n_bins)), dtype=torch.float64, device=torch.device("cuda", self.ctx.device))
+        g = _PowerGrid(int(steps_per_bin), int(n_bins), float(x0), float(dx), int(kind), 0)
+        tgs, fgs = _tg(tg), _fg(fg)
+        _check(load_library().drt_power_profile(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs), C.byref(g),
+                                                _dptr(P), int(precision), _stream_ptr(stream)))
+        return P
 
     def synthesize_H_noalloc(self, tg: I.TimeGrid, fg: I.FreqGrid, H, precision: int = FP64, stream=None):
         """drt_synthesize_H_noalloc: the same H as synthesize_H without any device allocation, for

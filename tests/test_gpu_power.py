@@ -1,0 +1,133 @@
+"""Power-Doppler (Sec. IV-A) and power-delay (Sec. IV-B) profiles on the GPU against the oracle.
+
+The profile sums |a|^2 of the valid path-steps into (time bin, Doppler or delay bin).  A path-step
+is decided the same way on both sides except where its validity sits within the flags band of a
+face or edge boundary, or its Doppler shift / delay sits within the record tolerance of a bin edge.
+Those path-steps are left out of the oracle's sum and bound the difference per time bin instead
+(their |a|^2, widened to the neighbouring instants); every other bin must match within the
+amplitude bar of the form (FP64: 1e-9 relative on a, FP32-bulk: 5e-3).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2205_00237_gb300 import inputs as I
+
+from test_gpu_parity import band_amplitude
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+# per form: flags band (m), Doppler tolerance (Hz), delay tolerance (relative), amplitude bar
+BARS = {"fp64": (1e-9, 1e-3, 1e-12, 1e-9), "fp32": (1e-4, 0.1, 1e-8, 5e-3)}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_00237_gb300 import drt
+    c = drt.Context(0)
+    yield c
+    c.close()
+
+
+def compare_profile(Pg, r, spb, x0, dx, nb, kind, form):
+    band, fd_tol, tau_tol, a_tol = BARS[form]
+    x = r["fd"] if kind == O.PP_DOPPLER else r["tau"]
+    tol = fd_tol if kind == O.PP_DOPPLER else tau_tol * np.abs(r["tau"])
+    u = (x - x0) / dx
+    edge = np.abs(u - np.round(u)) * dx <= tol
+    amb = (r["margin"] < band) | ((r["flags"] == 0) & edge)
+    r_u = dict(r)
+    r_u["flags"] = np.where(amb, np.uint8(0x80), r["flags"]).astype(np.uint8)
+    Pu = O.power_profile(r_u, spb, x0, dx, nb, kind)
+    Pall = O.power_profile(r, spb, x0, dx, nb, kind)
+    T = x.shape[0]
+    w = band_amplitude(r) ** 2 * (1 + 2 * a_tol) ** 2
+    slack_t = np.where(amb, w, 0.0).sum(axis=1)
+    slack = np.add.reduceat(slack_t, np.arange(0, T, spb))[:, None]
+    assert Pg.shape == Pall.shape
+    assert np.isfinite(Pg).all() and (Pg >= 0).all()
+    d = np.abs(Pg - Pu) - slack
+    bar = 2.5 * a_tol * Pu + 1e-30
+    assert (d <= bar).all(), (d - bar).max()
+    # the comparison is not carried by the slack alone (a path whose Doppler shift stays within the
+    # tolerance of one bin edge for many steps is ambiguous for all of them: tiny scenes, 3 paths)
+    assert Pu.sum() >= 0.5 * Pall.sum() > 0
+    return int(amb.sum())
+
+
+def tiny(seed):
+    return I.scene_tiny(seed), I.PathSet.from_npz(os.path.join(GOLD, f"pathset_tiny_seed{seed}.npz"))
+
+
+@pytest.mark.parametrize("form", ["fp64", "fp32"])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_tiny_power_doppler_and_delay(ctx, seed, form):
+    from paper_2205_00237_gb300 import drt
+    import torch
+    sc, ps = tiny(seed)
+    tg, fg = I.TimeGrid(0.0, 1e-3, 1000), I.FreqGrid(28e9, 400e6, 256)
+    prec = drt.FP64 if form == "fp64" else drt.FP32_BULK
+    link = ctx.load(sc, ps)
+    r = O.extrapolate(sc, ps, tg, fg.fc, n_threads=8)
+    # 200-step windows (200 ms), Doppler bins of 14.34 Hz over +-3 kHz; one 7-step ragged case
+    for spb in (200, 7):
+        Pd = link.power_profile(tg, fg, spb, -3011.4, 14.34, 420, drt.PP_DOPPLER, prec)
+        torch.cuda.synchronize()
+        compare_profile(Pd.cpu().numpy(), r, spb, -3011.4, 14.34, 420, O.PP_DOPPLER, form)
+    Pt = link.power_profile(tg, fg, 200, 0.0, 1e-9, 2000, drt.PP_DELAY, prec)
+    torch.cuda.synchronize()
+    compare_profile(Pt.cpu().numpy(), r, 200, 0.0, 1e-9, 2000, O.PP_DELAY, form)
+    link.unload()
+
+
+@pytest.mark.parametrize("form", ["fp64", "fp32"])
+def test_canyon_power_profiles(ctx, form):
+    """Canyon (512 paths, 60 GHz, 0.5 ms steps) over 600 steps: 400-step windows, the last ragged."""
+    from paper_2205_00237_gb300 import drt
+    import torch
+    sc = I.scene_canyon(0)
+    ps = I.PathSet.from_npz(os.path.join(GOLD, "pathset_canyon_seed0.npz"))
+    tg, fg = I.TimeGrid(0.0, 0.5e-3, 600), I.FreqGrid(60e9, 1e9, 512)
+    prec = drt.FP64 if form == "fp64" else drt.FP32_BULK
+    link = ctx.load(sc, ps)
+    r = O.extrapolate(sc, ps, tg, fg.fc, n_threads=8)
+    Pd = link.power_profile(tg, fg, 400, -8000.0, 14.34, 1116, drt.PP_DOPPLER, prec)
+    Pt = link.power_profile(tg, fg, 400, 0.0, 1e-9, 4096, drt.PP_DELAY, prec)
+    torch.cuda.synchronize()
+    compare_profile(Pd.cpu().numpy(), r, 400, -8000.0, 14.34, 1116, O.PP_DOPPLER, form)
+    compare_profile(Pt.cpu().numpy(), r, 400, 0.0, 1e-9, 4096, O.PP_DELAY, form)
+    link.unload()
+
+
+def test_power_profile_edges(ctx):
+    """No paths, no steps, one bin, and rejected grids."""
+    from paper_2205_00237_gb300 import drt
+    import torch
+    sc, ps = tiny(0)
+    tg, fg = I.TimeGrid(0.0, 1e-3, 50), I.FreqGrid(28e9, 400e6, 16)
+    e = ctx.load(sc, I.empty_paths(0))
+    P = e.power_profile(tg, fg, 10, -1e4, 1e2, 200)
+    torch.cuda.synchronize()
+    assert P.shape == (5, 200) and (P.cpu().numpy() == 0).all()
+    e.unload()
+    link = ctx.load(sc, ps)
+    P0 = link.power_profile(I.TimeGrid(0.0, 1e-3, 0), fg, 10, -1e4, 1e2, 200)
+    assert P0.shape == (0, 200)
+    # one bin holding every Doppler shift: the total received power per window
+    r = O.extrapolate(sc, ps, tg, fg.fc, n_threads=4)
+    P1 = link.power_profile(tg, fg, 50, -1e6, 2e6, 1).cpu().numpy()
+    want = np.where(r["flags"] == 0, np.abs(r["a"]) ** 2, 0.0).sum()
+    slack = np.where(r["margin"] < 1e-9, band_amplitude(r) ** 2, 0.0).sum()
+    assert abs(P1[0, 0] - want) <= 1e-8 * want + slack
+    for bad in [dict(spb=0), dict(nb=0), dict(nb=5000), dict(dx=0.0), dict(dx=-1.0), dict(kind=2)]:
+        a = dict(spb=10, x0=0.0, dx=1.0, nb=10, kind=drt.PP_DOPPLER)
+        a.update(bad)
+        with pytest.raises(drt.DrtError) as ei:
+            link.power_profile(tg, fg, a["spb"], a["x0"], a["dx"], a["nb"], a["kind"])
+        assert ei.value.code == drt.DRT_EINVAL
+    link.unload()
