@@ -170,6 +170,67 @@ def power_profile(rec, steps_per_bin, x0, dx, n_bins, kind=PP_DOPPLER):
     return out
 
 
+def lifetime_toggles(rec, share):
+    """Expiry criterion of the multipath lifetime T_C (Sec. II: the time during which no major path
+    appears or disappears).  major[n] (n >= 1) is True when some path is valid at one of the instants
+    n - 1, n and not at the other while, at the instant where it is valid, its |a|^2 is at least
+    `share` of the total |a|^2 of the valid paths of that instant."""
+    T, P = rec["flags"].shape
+    valid = rec["flags"] == 0
+    pw = np.abs(rec["a"]) ** 2
+    tot = np.zeros(T)
+    for n in range(T):
+        for p in range(P):
+            if valid[n, p]:
+                tot[n] += pw[n, p]
+    major = np.zeros(T, dtype=bool)
+    for n in range(1, T):
+        for p in range(P):
+            if valid[n, p] != valid[n - 1, p]:
+                m = n if valid[n, p] else n - 1
+                if pw[m, p] >= share * tot[m]:
+                    major[n] = True
+    return major
+
+
+def plan_windows(major, min_steps, max_steps):
+    """Segmentation of the span into T_C windows (Sec. IV-B divides its span into T_C windows, longer
+    where the multipath is stable, shorter near LoS/NLoS transitions): a window starting at step s
+    ends at the first major change n with s + min_steps <= n <= s + max_steps, else after max_steps
+    steps.  Returns the first step of every window, starting with 0."""
+    T = len(major)
+    starts = [0]
+    s = 0
+    while True:
+        nxt = s + max_steps
+        for n in range(s + min_steps, min(s + max_steps, T - 1) + 1):
+            if major[n]:
+                nxt = n
+                break
+        if nxt >= T:
+            return starts
+        starts.append(nxt)
+        s = nxt
+
+
+def synthesize_H_windows(rec, starts, fgrid, n_threads=1):
+    """H(t, f) of DRT over a span divided into T_C windows: every window re-initialises the multipath
+    at its first instant (the chains valid there, as a ray-tracing run at that instant returns them)
+    and extrapolates only those chains until the next window; a chain that appears inside a window is
+    not seen until the next one (Sec. II, Sec. IV-B)."""
+    T, P = rec["flags"].shape
+    flags = rec["flags"].copy()
+    bounds = list(starts) + [T]
+    for k in range(len(starts)):
+        s0, s1 = bounds[k], bounds[k + 1]
+        for p in range(P):
+            if rec["flags"][s0, p] != 0:        # not in the chain set of this window
+                flags[s0:s1, p] |= np.uint8(0x80)
+    r = dict(rec)
+    r["flags"] = flags
+    return synthesize_H(r, fgrid, n_threads=n_threads)
+
+
 def fresnel(eps_r, sigma, pec, fc, cos_theta):
     o = np.empty(4)
     lib().or_fresnel_coeffs(eps_r, sigma, float(pec), fc, cos_theta, _dp(o))
