@@ -284,6 +284,43 @@ def run_power(args, link, tg, fg, drt, flush):
     return out
 
 
+def run_lifetime(args, link, tg, fg, drt, flush):
+    """Multipath-lifetime management on the canyon link: the window plan (drt_lifetime_windows, share
+    1e-5 of the power, windows of 10 to 150 ms) and H over those windows (drt_synthesize_H_windows),
+    beside the plain H of the same form."""
+    import torch
+    stream = torch.cuda.current_stream()
+    mn, mx = max(1, int(round(0.01 / tg.dt))), max(1, int(round(0.15 / tg.dt)))
+    out = {"share": 1e-5, "min_steps": mn, "max_steps": mx, "l2": "flushed between timed calls"}
+    H = torch.empty((tg.n_steps, fg.n_bins), dtype=torch.complex64, device="cuda")
+    for prec, pname in ((drt.FP64, "fp64"), (drt.FP32_BULK, "fp32_bulk")):
+        starts, major = link.lifetime_windows(tg, fg, 1e-5, mn, mx, prec)
+        plan_ms = []
+        for _ in range(max(1, args.steps)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            link.lifetime_windows(tg, fg, 1e-5, mn, mx, prec)
+            plan_ms.append(1e3 * (time.perf_counter() - t0))
+        for _ in range(2):
+            link.synthesize_H_windows(tg, fg, starts, prec, H=H)
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(max(1, args.steps)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            link.synthesize_H_windows(tg, fg, starts, prec, H=H)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        out[pname] = {"windows": len(starts), "major_changes": int(major.sum()),
+                      "plan_ms_wall": statistics.median(plan_ms), "windowed_H_ms": ms,
+                      "path_steps_per_s": link.n_paths * tg.n_steps / (ms * 1e-3)}
+    return out
+
+
 def run_serving(args, drt):
     """Poisson-arriving prediction requests on resident canyon links (512, 128 and 32 paths),
     horizons U{50..500} x 1 ms from random start times, 512 bins at 60 GHz, HBM budget 64 GB."""
@@ -490,6 +527,7 @@ def run_ours(args):
     probe = ctx.probe_peak(0)
     line["roofline"]["probe_fp64_tflops"] = probe / 1e12
     line["power_profiles"] = run_power(args, link, tg, fg, drt, flush)
+    line["lifetime"] = run_lifetime(args, link, tg, fg, drt, flush)
     if args.batch_links > 0:
         line["batched"] = run_batched(args, ctx, drt, flush)
     if args.serve_seconds > 0:

@@ -210,6 +210,40 @@ drt_status drt_power_profile(drt_ctx *ctx, uint64_t link, const drt_time_grid *t
                              int32_t precision, void *stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Multipath lifetime T_C management (Sec. II: extrapolation holds while no major path appears or
+ * disappears; Sec. IV-B divides a span into T_C windows, long where the multipath is stable and short
+ * near LoS/NLoS transitions, and re-initialises the multipath at every window start).
+ *
+ * drt_lifetime_windows: expiry criterion and window plan of `link` over the time grid.  Step n >= 1
+ * is a major change when some path is valid at one of the instants n - 1, n and not at the other
+ * while, at the instant where it is valid, its |a|^2 is at least params->share of the total |a|^2 of
+ * the valid paths of that instant.  A window starting at step w ends at the first major change in
+ * [w + min_steps, w + max_steps], else after max_steps steps.  Writes the window starts (steps,
+ * starts[0] = 0) to the HOST array `starts` (cap entries), their count to *n_windows (0 when
+ * n_steps = 0) and, if `major` is non-NULL, the per-step major flags to the HOST array major[n_steps].
+ * Runs the extrapolation (amplitudes and flags, `precision` form) and two reduction kernels on
+ * `stream`, then waits for it.  Errors: DRT_EINVAL (params: finite share >= 0,
+ * 1 <= min_steps <= max_steps; or cap smaller than the window count, which is then in *n_windows),
+ * DRT_ENOTFOUND, DRT_ENOMEM, DRT_ECUDA. */
+typedef struct { double share; int32_t min_steps, max_steps; } drt_lifetime_params;
+drt_status drt_lifetime_windows(drt_ctx *ctx, uint64_t link, const drt_time_grid *tgrid,
+                                const drt_freq_grid *fgrid, const drt_lifetime_params *params,
+                                int32_t precision, uint8_t *major, int32_t *starts, int32_t cap,
+                                int32_t *n_windows, void *stream);
+
+/* drt_synthesize_H_windows: H(t, f) of DRT over the span divided into T_C windows that start at the
+ * HOST steps starts[0..n_windows) (starts[0] = 0, strictly increasing, < n_steps).  Each window's
+ * multipath is the set of paths valid at its first instant (FP64 validity at that instant, as a
+ * ray-tracing run there would return it); a path outside that set contributes nothing until the next
+ * window, even where it becomes valid inside this one.  One window at every step gives
+ * drt_synthesize_H.  H: caller-owned DEVICE buffer [n_steps][n_bins] complex64, as drt_synthesize_H.
+ * Asynchronous on `stream` (starts is copied before the call returns).
+ * Errors: DRT_EINVAL (grids, starts), DRT_ENOTFOUND, DRT_ENOMEM, DRT_ECUDA. */
+drt_status drt_synthesize_H_windows(drt_ctx *ctx, uint64_t link, const drt_time_grid *tgrid,
+                                    const drt_freq_grid *fgrid, const int32_t *starts,
+                                    int32_t n_windows, void *H, int32_t precision, void *stream);
+
+/* ---------------------------------------------------------------------------------------------
  * a10: batched synthesis over many resident links (FP32-bulk form).  drt_batch_create plans one
  * batch: link i is synthesised over tgrids[i] x fgrids[i] into the caller's DEVICE buffer H[i]
  * ([n_steps][n_bins] complex64).  Each stage (base poses, FP64 chunk poses, multi-diffraction warm

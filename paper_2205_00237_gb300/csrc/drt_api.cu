@@ -63,7 +63,8 @@ struct drt_ctx {
     std::mutex mu;
     std::map<uint64_t, Link> links;
     uint64_t next_link = 1;
-    Scratch pose, rec_a, rec_b, h, poseb, base, pose64, redo, warm, redo3, pp_tau, pp_amp, pp_fd, pp_fl;
+    Scratch pose, rec_a, rec_b, h, poseb, base, pose64, redo, warm, redo3, pp_tau, pp_amp, pp_fd, pp_fl, lt_tot,
+        lt_major, win_sel, win_starts;
     double *probe_sink = nullptr;
     // side streams for work that overlaps within one call (FP32-bulk: anchors and the FP64
     // multi-diffraction paths run beside the FP32 kernel), joined back with events
@@ -286,7 +287,7 @@ drt_status run_extrapolation(drt_ctx *c, Link &L, const drt_time_grid *tg, const
 }
 
 drt_status synth_into(drt_ctx *c, Link &L, const drt_time_grid *tg, const drt_freq_grid *fg, float2 *H,
-                      int32_t precision, cudaStream_t s) {
+                      int32_t precision, cudaStream_t s, const WinMask *wm = nullptr) {
     size_t n = (size_t)tg->n_steps * L.n_paths;
     if (drt_status st = ensure(c, c->rec_a, n * sizeof(float4))) return st;
     if (drt_status st = ensure(c, c->rec_b, n * sizeof(float))) return st;
@@ -302,16 +303,23 @@ drt_status synth_into(drt_ctx *c, Link &L, const drt_time_grid *tg, const drt_fr
         double *r3 = reinterpret_cast<double *>(c->redo3.ptr);
         void *rd = c->redo.ptr;
         const double *warm = reinterpret_cast<const double *>(c->warm.ptr);
+        if (wm) CUDA_TRY(launch_select(L.dev, t, f, *wm, warm, s));
         cudaStream_t sb = c->side[1];
         CUDA_TRY(cudaEventRecord(c->ev_fork, s));
         CUDA_TRY(cudaStreamWaitEvent(sb, c->ev_fork, 0));
         if (drt_status st = traced(c, 3, sb, [&] { return launch_redo_rec(L.dev, t, f, rd, warm, r3, sb); })) return st;
+        if (wm) CUDA_TRY(launch_redo_window_mask(L.dev, t, rd, *wm, r3, sb));
         CUDA_TRY(cudaEventRecord(c->ev_join[1], sb));
+        if (wm) CUDA_TRY(launch_window_mask(L.dev, t, rec, *wm, s));
         if (drt_status st = traced(c, 2, s, [&] { return launch_synth(rec, L.n_paths, t, f, H, s); })) return st;
         CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[1], 0));
         return traced(c, 3, s, [&] { return launch_redo_add(L.dev, t, f, rd, r3, H, s); });
     }
     if (drt_status st = run_extrapolation(c, L, tg, fg, none, rec, precision, s)) return st;
+    if (wm) {
+        CUDA_TRY(launch_select(L.dev, t, f, *wm, reinterpret_cast<const double *>(c->warm.ptr), s));
+        CUDA_TRY(launch_window_mask(L.dev, t, rec, *wm, s));
+    }
     return traced(c, 2, s, [&] { return launch_synth(rec, L.n_paths, t, f, H, s); });
 }
 
@@ -545,7 +553,7 @@ void drt_destroy(drt_ctx *c) {
     for (auto &kv : c->links)
         for (void *p : kv.second.allocs) cudaFree(p);
     for (Scratch *s : {&c->pose, &c->rec_a, &c->rec_b, &c->h, &c->poseb, &c->base, &c->pose64, &c->redo, &c->warm, &c->redo3, &c->pp_tau,
-                       &c->pp_amp, &c->pp_fd, &c->pp_fl})
+                       &c->pp_amp, &c->pp_fd, &c->pp_fl, &c->lt_tot, &c->lt_major, &c->win_sel, &c->win_starts})
         if (s->ptr) cudaFree(s->ptr);
     cudaFree(c->probe_sink);
     for (int i = 0; i < 2; ++i) {
@@ -687,6 +695,88 @@ drt_status drt_power_profile(drt_ctx *c, uint64_t link, const drt_time_grid *tg,
     CUDA_TRY(launch_power_bin(precision == DRT_FP64, o, tg->n_steps, L->n_paths, g->steps_per_bin, g->x0, g->dx,
                               g->n_bins, g->kind, P, s));
     return DRT_OK;
+}
+
+drt_status drt_lifetime_windows(drt_ctx *c, uint64_t link, const drt_time_grid *tg, const drt_freq_grid *fg,
+                                const drt_lifetime_params *lp, int32_t precision, uint8_t *major, int32_t *starts,
+                                int32_t cap, int32_t *n_windows, void *stream) {
+    if (!c || !lp || !n_windows) return fail(DRT_EINVAL, "ctx, params and n_windows must be non-NULL");
+    if (drt_status st = check_grids(tg, fg, precision)) return st;
+    if (!(lp->share >= 0.0) || !std::isfinite(lp->share) || lp->min_steps < 1 || lp->max_steps < lp->min_steps)
+        return fail(DRT_EINVAL, "lifetime params: finite share >= 0, 1 <= min_steps <= max_steps required");
+    if (cap < 0 || (cap > 0 && !starts)) return fail(DRT_EINVAL, "starts must hold cap >= 0 entries");
+    std::lock_guard<std::mutex> lk(c->mu);
+    Link *L = find_link(c, link);
+    if (!L) return fail(DRT_ENOTFOUND, "unknown link %llu", (unsigned long long)link);
+    CUDA_TRY(cudaSetDevice(c->device));
+    const int T = tg->n_steps;
+    *n_windows = 0;
+    if (T == 0) return DRT_OK;
+    const size_t n = (size_t)T * L->n_paths;
+    const size_t fsz = precision == DRT_FP64 ? sizeof(double) : sizeof(float);
+    if (drt_status st = ensure(c, c->pp_amp, 2 * n * fsz + 8)) return st;
+    if (drt_status st = ensure(c, c->pp_fl, n + 8)) return st;
+    if (drt_status st = ensure(c, c->lt_tot, (size_t)T * sizeof(double))) return st;
+    if (drt_status st = ensure(c, c->lt_major, (size_t)T)) return st;
+    OutD o{nullptr, c->pp_amp.ptr, nullptr, nullptr, reinterpret_cast<uint8_t *>(c->pp_fl.ptr), nullptr};
+    cudaStream_t s = (cudaStream_t)stream;
+    RecD none{nullptr, nullptr};
+    if (drt_status st = run_extrapolation(c, *L, tg, fg, o, none, precision, s)) return st;
+    uint8_t *mj = reinterpret_cast<uint8_t *>(c->lt_major.ptr);
+    CUDA_TRY(launch_lifetime(precision == DRT_FP64, o, T, L->n_paths, lp->share,
+                             reinterpret_cast<double *>(c->lt_tot.ptr), mj, s));
+    std::vector<uint8_t> m(T);
+    CUDA_TRY(cudaMemcpyAsync(m.data(), mj, T, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (major) std::memcpy(major, m.data(), T);
+    // windows: from start w, the first major change in [w + min_steps, w + max_steps], else w + max_steps
+    std::vector<int32_t> w{0};
+    for (long long s0 = 0;;) {
+        long long nxt = s0 + lp->max_steps;
+        for (long long k = s0 + lp->min_steps; k <= std::min<long long>(s0 + lp->max_steps, T - 1); ++k)
+            if (m[k]) {
+                nxt = k;
+                break;
+            }
+        if (nxt >= T) break;
+        w.push_back((int32_t)nxt);
+        s0 = nxt;
+    }
+    *n_windows = (int32_t)w.size();
+    if ((int32_t)w.size() > cap)
+        return fail(DRT_EINVAL, "starts holds %d entries, %d windows found (n_windows)", cap, (int)w.size());
+    std::memcpy(starts, w.data(), w.size() * sizeof(int32_t));
+    return DRT_OK;
+}
+
+drt_status drt_synthesize_H_windows(drt_ctx *c, uint64_t link, const drt_time_grid *tg, const drt_freq_grid *fg,
+                                    const int32_t *starts, int32_t n_windows, void *H, int32_t precision,
+                                    void *stream) {
+    if (!c) return fail(DRT_EINVAL, "ctx must be non-NULL");
+    if (drt_status st = check_grids(tg, fg, precision)) return st;
+    const int T = tg->n_steps;
+    if (T > 0) {
+        if (!H || !starts || n_windows < 1 || starts[0] != 0)
+            return fail(DRT_EINVAL, "H, starts and n_windows >= 1 with starts[0] = 0 required");
+        for (int k = 1; k < n_windows; ++k)
+            if (starts[k] <= starts[k - 1] || starts[k] >= T)
+                return fail(DRT_EINVAL, "window starts must increase strictly and stay below n_steps");
+    }
+    std::lock_guard<std::mutex> lk(c->mu);
+    Link *L = find_link(c, link);
+    if (!L) return fail(DRT_ENOTFOUND, "unknown link %llu", (unsigned long long)link);
+    CUDA_TRY(cudaSetDevice(c->device));
+    if (T == 0) return DRT_OK;
+    const int P = L->n_paths;
+    cudaStream_t s = (cudaStream_t)stream;
+    // re-initialisation at every window start: the paths valid there (FP64 flags of that instant,
+    // one selection launch inside the synthesis)
+    if (drt_status st = ensure(c, c->win_sel, (size_t)T * P + 8)) return st;
+    if (drt_status st = ensure(c, c->win_starts, (size_t)n_windows * sizeof(int32_t))) return st;
+    int32_t *sd = reinterpret_cast<int32_t *>(c->win_starts.ptr);
+    CUDA_TRY(cudaMemcpyAsync(sd, starts, (size_t)n_windows * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    WinMask wm{sd, n_windows, reinterpret_cast<uint8_t *>(c->win_sel.ptr)};
+    return synth_into(c, *L, tg, fg, reinterpret_cast<float2 *>(H), precision, s, &wm);
 }
 
 drt_status drt_profile_enable(drt_ctx *c, int32_t on) {

@@ -184,6 +184,24 @@ cudaError_t launch_redo_rec(const LinkDev &L, const TimeGridD &tg, const FreqGri
                             double *out3, cudaStream_t s);
 cudaError_t launch_redo_add(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, void *redo, const double *in3,
                             float2 *H, cudaStream_t s);
+// multipath lifetime: per-instant total |a|^2 of the valid paths (tot[T]) and major validity changes
+// (major[T], 1 at instant n when a path with >= share of the power at its valid side changes validity)
+cudaError_t launch_lifetime(bool fp64, const OutD &rec, int n_steps, int n_paths, double share, double *tot,
+                            uint8_t *major, cudaStream_t s);
+// T_C windows: window w starts at step starts[w] (starts[0] = 0, increasing); sel is [T][P] (caller
+// path order) and holds, in the rows of the window starts, the path's FP64 flags at that instant
+// (0: in the window's multipath); launch_select writes those rows
+struct WinMask {
+    const int32_t *starts;
+    int32_t n_w;
+    uint8_t *sel;
+};
+cudaError_t launch_select(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const WinMask &wm,
+                          const double *warm, cudaStream_t s);
+cudaError_t launch_window_mask(const LinkDev &L, const TimeGridD &tg, const RecD &rec, const WinMask &wm,
+                               cudaStream_t s);
+cudaError_t launch_redo_window_mask(const LinkDev &L, const TimeGridD &tg, void *redo, const WinMask &wm, double *in3,
+                                    cudaStream_t s);
 // histogram of |a|^2 over (time bin, Doppler (kind 0) or delay (kind 1) bin) from [T][P] records;
 // out[n_time_bins][n_bins] is written whole (FP64)
 cudaError_t launch_power_bin(bool fp64, const OutD &rec, int n_steps, int n_paths, int steps_per_bin, double x0,

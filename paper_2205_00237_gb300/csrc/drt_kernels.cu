@@ -319,6 +319,134 @@ cudaError_t launch_power_bin(bool fp64, const OutD &rec, int n_steps, int n_path
 }
 
 // ------------------------------------------------------------------------------------------------
+// Multipath lifetime T_C (Sec. II): the multipath structure expires at an instant where a path with a
+// non-negligible share of the power appears or disappears.  k_step_power sums |a|^2 of the valid paths
+// of every instant (one warp per instant); k_toggle marks instant n when some path's validity differs
+// between n - 1 and n while, at the instant where it is valid, it carries >= `share` of that total.
+template <class A>
+__global__ void __launch_bounds__(256)
+k_step_power(const A *__restrict__ amp, const uint8_t *__restrict__ flags, int n_steps, int n_paths,
+             double *__restrict__ tot) {
+    const int n = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (n >= n_steps) return;   // warp-uniform
+    double acc = 0.0;
+    for (int p = lane; p < n_paths; p += 32) {
+        const size_t i = (size_t)n * n_paths + p;
+        if (flags[i]) continue;
+        const double ar = (double)amp[2 * i], ai = (double)amp[2 * i + 1];
+        acc += ar * ar + ai * ai;
+    }
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) tot[n] = acc;
+}
+
+template <class A>
+__global__ void __launch_bounds__(256)
+k_toggle(const A *__restrict__ amp, const uint8_t *__restrict__ flags, const double *__restrict__ tot, int n_steps,
+         int n_paths, double share, uint8_t *__restrict__ major) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= (long long)(n_steps - 1) * n_paths) return;
+    const int n = 1 + (int)(q / n_paths);
+    const size_t i1 = (size_t)n * n_paths + (size_t)(q % n_paths), i0 = i1 - n_paths;
+    const bool v1 = flags[i1] == 0, v0 = flags[i0] == 0;
+    if (v1 == v0) return;
+    const size_t im = v1 ? i1 : i0;
+    const double ar = (double)amp[2 * im], ai = (double)amp[2 * im + 1];
+    if (ar * ar + ai * ai >= share * tot[v1 ? n : n - 1]) major[n] = 1;
+}
+
+cudaError_t launch_lifetime(bool fp64, const OutD &rec, int n_steps, int n_paths, double share, double *tot,
+                            uint8_t *major, cudaStream_t s) {
+    if (n_steps == 0) return cudaSuccess;
+    if (cudaError_t e = cudaMemsetAsync(major, 0, n_steps, s)) return e;
+    if (n_paths == 0) return cudaSuccess;
+    const unsigned gp = (unsigned)((n_steps + 7) / 8);
+    const long long nq = (long long)(n_steps - 1) * n_paths;
+    const unsigned gt = (unsigned)((nq + 255) / 256);
+    if (fp64) {
+        const double *a = reinterpret_cast<const double *>(rec.amp);
+        k_step_power<double><<<gp, 256, 0, s>>>(a, rec.flags, n_steps, n_paths, tot);
+        if (nq) k_toggle<double><<<gt, 256, 0, s>>>(a, rec.flags, tot, n_steps, n_paths, share, major);
+    } else {
+        const float *a = reinterpret_cast<const float *>(rec.amp);
+        k_step_power<float><<<gp, 256, 0, s>>>(a, rec.flags, n_steps, n_paths, tot);
+        if (nq) k_toggle<float><<<gt, 256, 0, s>>>(a, rec.flags, tot, n_steps, n_paths, share, major);
+    }
+    return cudaGetLastError();
+}
+
+// DRT over T_C windows: a path that is not valid at the first instant of its window is outside that
+// window's multipath (sel[start][caller index] != 0, its FP64 flags at the window start) and its
+// records carry a = 0; the same holds for the FP64 redo contributions of the FP32-bulk form.
+// k_select evaluates the FP64 flags of every (window start, path) in one launch (poses computed at the
+// instant, multi-diffraction warm starts from the grid's table).
+__device__ __forceinline__ int window_of(const int32_t *__restrict__ starts, int n_w, int n) {
+    int lo = 0, hi = n_w - 1;   // the last window starting at or before n (starts[0] = 0)
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (starts[mid] <= n) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(32)
+k_select(const LinkDev L, const TimeGridD tg, const FreqGridD fg, WinMask wm, const double *__restrict__ warm) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= (long long)wm.n_w * L.n_paths) return;
+    const int w = (int)(q / L.n_paths), p = (int)(q % L.n_paths);
+    OutD o{};
+    o.flags = wm.sel;   // written at [starts[w]][caller index]
+    const RecD none{nullptr, nullptr};
+    path_step_redo(L, tg, fg, p, wm.starts[w], o, none, warm);
+}
+
+cudaError_t launch_select(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const WinMask &wm,
+                          const double *warm, cudaStream_t s) {
+    const long long n = (long long)wm.n_w * L.n_paths;
+    if (n == 0) return cudaSuccess;
+    k_select<<<(unsigned)((n + 31) / 32), 32, 0, s>>>(L, tg, fg, wm, warm);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256)
+k_window_mask(float4 *__restrict__ rec_a, int n_steps, int n_paths, const int32_t *__restrict__ perm,
+              WinMask wm) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= (long long)n_steps * n_paths) return;
+    const int n = (int)(q / n_paths), p = (int)(q % n_paths);
+    const int w = window_of(wm.starts, wm.n_w, n);
+    if (wm.sel[(size_t)wm.starts[w] * n_paths + perm[p]])
+        reinterpret_cast<float2 *>(rec_a + q)[0] = make_float2(0.f, 0.f);
+}
+
+__global__ void __launch_bounds__(128)
+k_redo_window_mask(const RedoList redo, const int32_t *__restrict__ perm, int n_paths, WinMask wm,
+                   double *__restrict__ in3) {
+    const int n = min(*redo.count, redo.cap);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int4 it = redo.items[k];
+        const int w = window_of(wm.starts, wm.n_w, it.z);
+        if (wm.sel[(size_t)wm.starts[w] * n_paths + perm[it.y]]) in3[3 * (size_t)k] = in3[3 * (size_t)k + 1] = 0.0;
+    }
+}
+
+cudaError_t launch_window_mask(const LinkDev &L, const TimeGridD &tg, const RecD &rec, const WinMask &wm,
+                               cudaStream_t s) {
+    const long long n = (long long)tg.n_steps * L.n_paths;
+    if (n == 0) return cudaSuccess;
+    k_window_mask<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rec.rec_a, tg.n_steps, L.n_paths, L.perm, wm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_redo_window_mask(const LinkDev &L, const TimeGridD &tg, void *redo, const WinMask &wm, double *in3,
+                                    cudaStream_t s) {
+    if (L.n_paths == 0 || tg.n_steps == 0) return cudaSuccess;
+    k_redo_window_mask<<<152 * 2, 128, 0, s>>>(redo_list(redo, L, tg), L.perm, L.n_paths, wm, in3);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
 // a9: H synthesis.  A block owns SYN_PAIRS consecutive (step, tile of KT bins) pairs; its PG warps
 // split the paths of those steps (warp w takes paths w, w + PG, ...), lane l owns pair l, so the
 // lanes of a warp that share a step read the same record (broadcast).  Per (pair, path): seed

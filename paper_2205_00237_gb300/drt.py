@@ -27,7 +27,7 @@ EXPORTS = ["drt_create", "drt_destroy", "drt_last_error", "drt_load_paths", "drt
            "drt_synthesize_H", "drt_synthesize_H_host", "drt_link_info", "drt_probe_peak", "drt_profile_enable",
            "drt_profile_read", "drt_synthesize_H_noalloc", "drt_batch_create", "drt_batch_run", "drt_batch_info",
            "drt_batch_destroy", "drt_serve_start", "drt_serve_stop", "drt_submit", "drt_poll", "drt_wait",
-           "drt_serve_stats_read", "drt_power_profile"]
+           "drt_serve_stats_read", "drt_power_profile", "drt_lifetime_windows", "drt_synthesize_H_windows"]
 PP_DOPPLER, PP_DELAY = 0, 1
 
 
@@ -69,6 +69,10 @@ class _Outputs(C.Structure):
 class _PowerGrid(C.Structure):
     _fields_ = [("steps_per_bin", C.c_int32), ("n_bins", C.c_int32), ("x0", C.c_double), ("dx", C.c_double),
                 ("kind", C.c_int32), ("reserved", C.c_int32)]
+
+
+class _LifetimeParams(C.Structure):
+    _fields_ = [("share", C.c_double), ("min_steps", C.c_int32), ("max_steps", C.c_int32)]
 
 
 class _Request(C.Structure):
@@ -150,6 +154,11 @@ def load_library(path: str = LIB_PATH):
         L.drt_serve_stats_read.restype = st
         L.drt_power_profile.argtypes = [vp, C.c_uint64, vp, vp, C.POINTER(_PowerGrid), vp, C.c_int32, vp]
         L.drt_power_profile.restype = st
+        L.drt_lifetime_windows.argtypes = [vp, C.c_uint64, vp, vp, C.POINTER(_LifetimeParams), C.c_int32, vp, vp,
+                                           C.c_int32, C.POINTER(C.c_int32), vp]
+        L.drt_lifetime_windows.restype = st
+        L.drt_synthesize_H_windows.argtypes = [vp, C.c_uint64, vp, vp, vp, C.c_int32, vp, C.c_int32, vp]
+        L.drt_synthesize_H_windows.restype = st
         _lib = L
         return L
 
@@ -363,6 +372,36 @@ class Link:
         _check(load_library().drt_power_profile(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs), C.byref(g),
                                                 _dptr(P), int(precision), _stream_ptr(stream)))
         return P
+
+    def lifetime_windows(self, tg: I.TimeGrid, fg: I.FreqGrid, share: float, min_steps: int = 1,
+                         max_steps: int | None = None, precision: int = FP64, stream=None):
+        """drt_lifetime_windows: (window starts as a list of steps, per-step major-change flags as a
+        numpy bool array) of the multipath-lifetime plan."""
+        T = int(tg.n_steps)
+        lp = _LifetimeParams(float(share), int(min_steps), int(max_steps if max_steps is not None else max(T, 1)))
+        major = np.zeros(max(T, 1), dtype=np.uint8)
+        cap = max(T, 1)
+        starts = np.zeros(cap, dtype=np.int32)
+        nw = C.c_int32(0)
+        tgs, fgs = _tg(tg), _fg(fg)
+        _check(load_library().drt_lifetime_windows(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs), C.byref(lp),
+                                                   int(precision), major.ctypes.data, starts.ctypes.data, cap,
+                                                   C.byref(nw), _stream_ptr(stream)))
+        return [int(x) for x in starts[:nw.value]], major[:T].astype(bool)
+
+    def synthesize_H_windows(self, tg: I.TimeGrid, fg: I.FreqGrid, starts, precision: int = FP64, H=None,
+                             stream=None):
+        """drt_synthesize_H_windows: H over the T_C windows starting at `starts` (steps)."""
+        import torch
+        if H is None:
+            H = torch.empty((int(tg.n_steps), int(fg.n_bins)), dtype=torch.complex64,
+                            device=torch.device("cuda", self.ctx.device))
+        st_ = np.ascontiguousarray(np.asarray(starts, dtype=np.int32))
+        tgs, fgs = _tg(tg), _fg(fg)
+        _check(load_library().drt_synthesize_H_windows(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs),
+                                                       st_.ctypes.data if st_.size else None, int(st_.size),
+                                                       _dptr(H), int(precision), _stream_ptr(stream)))
+        return H
 
     def synthesize_H_noalloc(self, tg: I.TimeGrid, fg: I.FreqGrid, H, precision: int = FP64, stream=None):
         """drt_synthesize_H_noalloc: the same H as synthesize_H without any device allocation, for
