@@ -170,6 +170,29 @@ def power_profile(rec, steps_per_bin, x0, dx, n_bins, kind=PP_DOPPLER):
     return out
 
 
+def subbands(n_bins, n_sub):
+    """Bin ranges [k0, k1) of n_sub near-equal sub-bands: k0 = s N / n_sub (integer division)."""
+    return [(s * n_bins // n_sub, (s + 1) * n_bins // n_sub) for s in range(n_sub)]
+
+
+def synthesize_H_wideband(scene, paths, tgrid, fgrid, n_sub, n_threads=1):
+    """H(t, f) with the field coefficients (Fresnel, UTD, ER, lambda / 4 pi) evaluated per sub-band
+    instead of once at fc: sub-band [k0, k1) spans [f_k0, f_k0 + (k1 - k0) df) of the grid
+    f_k = fc - B/2 + k B/N and its coefficients are taken at the centre of that interval (one
+    sub-band is the narrowband case, coefficients at fc).  Each sub-band is a plain extrapolation
+    at its centre frequency and a direct sum over its own bins."""
+    from types import SimpleNamespace
+    T, N = int(tgrid.n_steps), int(fgrid.n_bins)
+    df = fgrid.bandwidth / N
+    H = np.empty((T, N), dtype=np.complex128)
+    for k0, k1 in subbands(N, n_sub):
+        n = k1 - k0
+        fs = SimpleNamespace(fc=fgrid.fc - fgrid.bandwidth / 2 + (k0 + n / 2) * df, bandwidth=n * df, n_bins=n)
+        rec = extrapolate(scene, paths, tgrid, fs.fc, n_threads=n_threads)
+        H[:, k0:k1] = synthesize_H(rec, fs, n_threads=n_threads)
+    return H
+
+
 def lifetime_toggles(rec, share):
     """Expiry criterion of the multipath lifetime T_C (Sec. II: the time during which no major path
     appears or disappears).  major[n] (n >= 1) is True when some path is valid at one of the instants
