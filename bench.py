@@ -321,6 +321,31 @@ def run_lifetime(args, link, tg, fg, drt, flush):
     return out
 
 
+def run_wideband(args, link, tg, fg, drt, flush, n_sub=4):
+    """H with field coefficients per sub-band (drt_synthesize_H_wideband, 4 sub-bands) on the canyon
+    link, both forms: one extrapolation and one synthesis per sub-band."""
+    import torch
+    stream = torch.cuda.current_stream()
+    H = torch.empty((tg.n_steps, fg.n_bins), dtype=torch.complex64, device="cuda")
+    out = {"n_sub": n_sub, "l2": "flushed between timed calls"}
+    for prec, pname in ((drt.FP64, "fp64"), (drt.FP32_BULK, "fp32_bulk")):
+        for _ in range(2):
+            link.synthesize_H_wideband(tg, fg, n_sub, prec, H=H)
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(max(1, args.steps)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            link.synthesize_H_wideband(tg, fg, n_sub, prec, H=H)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        out[pname] = {"ms": ms, "path_steps_per_s": link.n_paths * tg.n_steps / (ms * 1e-3)}
+    return out
+
+
 def run_serving(args, drt):
     """Poisson-arriving prediction requests on resident canyon links (512, 128 and 32 paths),
     horizons U{50..500} x 1 ms from random start times, 512 bins at 60 GHz, HBM budget 64 GB."""
@@ -528,6 +553,7 @@ def run_ours(args):
     line["roofline"]["probe_fp64_tflops"] = probe / 1e12
     line["power_profiles"] = run_power(args, link, tg, fg, drt, flush)
     line["lifetime"] = run_lifetime(args, link, tg, fg, drt, flush)
+    line["wideband"] = run_wideband(args, link, tg, fg, drt, flush)
     if args.batch_links > 0:
         line["batched"] = run_batched(args, ctx, drt, flush)
     if args.serve_seconds > 0:

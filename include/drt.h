@@ -210,6 +210,20 @@ drt_status drt_power_profile(drt_ctx *ctx, uint64_t link, const drt_time_grid *t
                              int32_t precision, void *stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Wideband coefficients: H(t, f) with the field coefficients (Fresnel with eps_c(f), UTD with k(f),
+ * ER, lambda / 4 pi; Sec. III-A to III-C) evaluated per sub-band instead of once at fc.  The n_bins
+ * bins split into n_sub sub-bands of near-equal size, [k0, k1) with k0 = s n_bins / n_sub (integer
+ * division); sub-band s spans [f_k0, f_k0 + (k1 - k0) df) of the grid f_k = fc - B/2 + k B/n_bins,
+ * df = B / n_bins, and its coefficients are taken at the centre of that span (n_sub = 1 is
+ * drt_synthesize_H).  Each sub-band runs its own extrapolation (the geometry is repeated) and
+ * synthesis into its columns of H.  H: caller-owned DEVICE buffer [n_steps][n_bins] complex64.
+ * Asynchronous on `stream`.  Errors: DRT_EINVAL (grids, 1 <= n_sub <= n_bins), DRT_ENOTFOUND,
+ * DRT_ENOMEM, DRT_ECUDA. */
+drt_status drt_synthesize_H_wideband(drt_ctx *ctx, uint64_t link, const drt_time_grid *tgrid,
+                                     const drt_freq_grid *fgrid, int32_t n_sub, void *H,
+                                     int32_t precision, void *stream);
+
+/* ---------------------------------------------------------------------------------------------
  * Multipath lifetime T_C management (Sec. II: extrapolation holds while no major path appears or
  * disappears; Sec. IV-B divides a span into T_C windows, long where the multipath is stable and short
  * near LoS/NLoS transitions, and re-initialises the multipath at every window start).

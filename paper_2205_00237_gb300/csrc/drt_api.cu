@@ -287,7 +287,7 @@ drt_status run_extrapolation(drt_ctx *c, Link &L, const drt_time_grid *tg, const
 }
 
 drt_status synth_into(drt_ctx *c, Link &L, const drt_time_grid *tg, const drt_freq_grid *fg, float2 *H,
-                      int32_t precision, cudaStream_t s, const WinMask *wm = nullptr) {
+                      int32_t precision, cudaStream_t s, const WinMask *wm = nullptr, int ld = -1) {
     size_t n = (size_t)tg->n_steps * L.n_paths;
     if (drt_status st = ensure(c, c->rec_a, n * sizeof(float4))) return st;
     if (drt_status st = ensure(c, c->rec_b, n * sizeof(float))) return st;
@@ -311,16 +311,16 @@ drt_status synth_into(drt_ctx *c, Link &L, const drt_time_grid *tg, const drt_fr
         if (wm) CUDA_TRY(launch_redo_window_mask(L.dev, t, rd, *wm, r3, sb));
         CUDA_TRY(cudaEventRecord(c->ev_join[1], sb));
         if (wm) CUDA_TRY(launch_window_mask(L.dev, t, rec, *wm, s));
-        if (drt_status st = traced(c, 2, s, [&] { return launch_synth(rec, L.n_paths, t, f, H, s); })) return st;
+        if (drt_status st = traced(c, 2, s, [&] { return launch_synth(rec, L.n_paths, t, f, H, s, ld); })) return st;
         CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[1], 0));
-        return traced(c, 3, s, [&] { return launch_redo_add(L.dev, t, f, rd, r3, H, s); });
+        return traced(c, 3, s, [&] { return launch_redo_add(L.dev, t, f, rd, r3, H, s, ld); });
     }
     if (drt_status st = run_extrapolation(c, L, tg, fg, none, rec, precision, s)) return st;
     if (wm) {
         CUDA_TRY(launch_select(L.dev, t, f, *wm, reinterpret_cast<const double *>(c->warm.ptr), s));
         CUDA_TRY(launch_window_mask(L.dev, t, rec, *wm, s));
     }
-    return traced(c, 2, s, [&] { return launch_synth(rec, L.n_paths, t, f, H, s); });
+    return traced(c, 2, s, [&] { return launch_synth(rec, L.n_paths, t, f, H, s, ld); });
 }
 
 }  // namespace
@@ -777,6 +777,28 @@ drt_status drt_synthesize_H_windows(drt_ctx *c, uint64_t link, const drt_time_gr
     CUDA_TRY(cudaMemcpyAsync(sd, starts, (size_t)n_windows * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     WinMask wm{sd, n_windows, reinterpret_cast<uint8_t *>(c->win_sel.ptr)};
     return synth_into(c, *L, tg, fg, reinterpret_cast<float2 *>(H), precision, s, &wm);
+}
+
+drt_status drt_synthesize_H_wideband(drt_ctx *c, uint64_t link, const drt_time_grid *tg, const drt_freq_grid *fg,
+                                     int32_t n_sub, void *H, int32_t precision, void *stream) {
+    if (!c || !H) return fail(DRT_EINVAL, "ctx and H must be non-NULL");
+    if (drt_status st = check_grids(tg, fg, precision)) return st;
+    if (n_sub < 1 || n_sub > fg->n_bins) return fail(DRT_EINVAL, "1 <= n_sub <= n_bins required");
+    std::lock_guard<std::mutex> lk(c->mu);
+    Link *L = find_link(c, link);
+    if (!L) return fail(DRT_ENOTFOUND, "unknown link %llu", (unsigned long long)link);
+    CUDA_TRY(cudaSetDevice(c->device));
+    const int N = fg->n_bins;
+    const double df = fg->bandwidth / N;
+    float2 *h = reinterpret_cast<float2 *>(H);
+    for (int sb = 0; sb < n_sub; ++sb) {
+        // sub-band [k0, k1) spans [f_k0, f_k0 + (k1 - k0) df); coefficients at its centre
+        const int k0 = (int)((long long)sb * N / n_sub), k1 = (int)((long long)(sb + 1) * N / n_sub);
+        const int n = k1 - k0;
+        drt_freq_grid fs{fg->fc - 0.5 * fg->bandwidth + (k0 + 0.5 * n) * df, n * df, n, 0};
+        if (drt_status st = synth_into(c, *L, tg, &fs, h + k0, precision, (cudaStream_t)stream, nullptr, N)) return st;
+    }
+    return DRT_OK;
 }
 
 drt_status drt_profile_enable(drt_ctx *c, int32_t on) {

@@ -183,7 +183,7 @@ cudaError_t launch_redo(const LinkDev &L, const TimeGridD &tg, const FreqGridD &
 cudaError_t launch_redo_rec(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, void *redo, const double *warm,
                             double *out3, cudaStream_t s);
 cudaError_t launch_redo_add(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, void *redo, const double *in3,
-                            float2 *H, cudaStream_t s);
+                            float2 *H, cudaStream_t s, int ld = -1);
 // multipath lifetime: per-instant total |a|^2 of the valid paths (tot[T]) and major validity changes
 // (major[T], 1 at instant n when a path with >= share of the power at its valid side changes validity)
 cudaError_t launch_lifetime(bool fp64, const OutD &rec, int n_steps, int n_paths, double share, double *tot,
@@ -206,8 +206,9 @@ cudaError_t launch_redo_window_mask(const LinkDev &L, const TimeGridD &tg, void 
 // out[n_time_bins][n_bins] is written whole (FP64)
 cudaError_t launch_power_bin(bool fp64, const OutD &rec, int n_steps, int n_paths, int steps_per_bin, double x0,
                              double dx, int n_bins, int kind, double *out, cudaStream_t s);
+// H rows of ld elements (ld < 0: n_bins), bins written at H[t * ld + k]
 cudaError_t launch_synth(const RecD &rec, int32_t n_paths, const TimeGridD &tg, const FreqGridD &fg,
-                         float2 *H, cudaStream_t s);
+                         float2 *H, cudaStream_t s, int ld = -1);
 cudaError_t launch_probe(int kind, int blocks, double *sink, cudaStream_t s, float *ms);
 
 }  // namespace drt

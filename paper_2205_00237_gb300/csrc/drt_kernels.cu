@@ -219,7 +219,7 @@ k_redo_rec(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const RedoLi
 
 // one thread per (queued step, 16-bin tile): FP64-reduced seed, FP32 rotation across the tile
 __global__ void __launch_bounds__(128)
-k_redo_add(const FreqGridD fg, const RedoList redo, const double *__restrict__ in3, float2 *__restrict__ H) {
+k_redo_add(const FreqGridD fg, const RedoList redo, const double *__restrict__ in3, float2 *__restrict__ H, int ld) {
     const int n = min(*redo.count, redo.cap);
     const int F = fg.n_bins, ntile = (F + 15) / 16;
     const double f0 = fg.fc - 0.5 * fg.bandwidth, df = fg.bandwidth / F;
@@ -228,7 +228,7 @@ k_redo_add(const FreqGridD fg, const RedoList redo, const double *__restrict__ i
         const int k = (int)(q / ntile), k0 = (int)(q % ntile) * 16;
         const double ar = in3[3 * (size_t)k], ai = in3[3 * (size_t)k + 1], tau = in3[3 * (size_t)k + 2];
         if (ar == 0.0 && ai == 0.0) continue;
-        float2 *row = H + (size_t)redo.items[k].z * F;
+        float2 *row = H + (size_t)redo.items[k].z * ld;
         double x = (f0 + k0 * df) * tau, xs = df * tau;
         float sn, cs, ws, wc;
         sincospif(2.f * (float)(x - floor(x)), &sn, &cs);
@@ -252,9 +252,10 @@ cudaError_t launch_redo_rec(const LinkDev &L, const TimeGridD &tg, const FreqGri
 }
 
 cudaError_t launch_redo_add(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, void *redo, const double *in3,
-                            float2 *H, cudaStream_t s) {
+                            float2 *H, cudaStream_t s, int ld) {
     if (L.n_paths == 0 || tg.n_steps == 0) return cudaSuccess;
-    k_redo_add<<<152 * 4, 128, 0, s>>>(fg, redo_list(redo, L, tg), in3, H);
+    if (ld < 0) ld = fg.n_bins;
+    k_redo_add<<<152 * 4, 128, 0, s>>>(fg, redo_list(redo, L, tg), in3, H, ld);
     return cudaGetLastError();
 }
 
@@ -456,7 +457,7 @@ constexpr int KT = 16, PG = 4, SYN_PAIRS = 32;
 
 __global__ void __launch_bounds__(SYN_PAIRS * PG)
 k_synth(const float4 *__restrict__ rec_a, const float *__restrict__ rec_b, int n_paths, int n_steps, int n_bins,
-        float2 *__restrict__ H) {
+        float2 *__restrict__ H, int ld) {
     __shared__ float2 part[PG][KT][SYN_PAIRS + 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int ntile = (n_bins + KT - 1) / KT;
@@ -503,7 +504,7 @@ k_synth(const float4 *__restrict__ rec_a, const float *__restrict__ rec_b, int n
     __syncthreads();
     // warp w adds and writes bins j = w, w + PG, ... of every pair of the block
     if (!live) return;
-    float2 *out = H + (size_t)ti * n_bins + k0;
+    float2 *out = H + (size_t)ti * ld + k0;
 #pragma unroll
     for (int j = w; j < KT; j += PG) {
         float2 v = part[0][j][lane];
@@ -517,12 +518,13 @@ k_synth(const float4 *__restrict__ rec_a, const float *__restrict__ rec_b, int n
 }
 
 cudaError_t launch_synth(const RecD &rec, int32_t n_paths, const TimeGridD &tg, const FreqGridD &fg, float2 *H,
-                         cudaStream_t s) {
+                         cudaStream_t s, int ld) {
+    if (ld < 0) ld = fg.n_bins;
     int ntile = (fg.n_bins + KT - 1) / KT;
     long long pairs = (long long)tg.n_steps * ntile;
     if (pairs == 0) return cudaSuccess;
     k_synth<<<(unsigned)((pairs + SYN_PAIRS - 1) / SYN_PAIRS), SYN_PAIRS * PG, 0, s>>>(rec.rec_a, rec.rec_b, n_paths,
-                                                                                     tg.n_steps, fg.n_bins, H);
+                                                                                     tg.n_steps, fg.n_bins, H, ld);
     return cudaGetLastError();
 }
 

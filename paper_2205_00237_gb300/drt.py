@@ -27,7 +27,8 @@ EXPORTS = ["drt_create", "drt_destroy", "drt_last_error", "drt_load_paths", "drt
            "drt_synthesize_H", "drt_synthesize_H_host", "drt_link_info", "drt_probe_peak", "drt_profile_enable",
            "drt_profile_read", "drt_synthesize_H_noalloc", "drt_batch_create", "drt_batch_run", "drt_batch_info",
            "drt_batch_destroy", "drt_serve_start", "drt_serve_stop", "drt_submit", "drt_poll", "drt_wait",
-           "drt_serve_stats_read", "drt_power_profile", "drt_lifetime_windows", "drt_synthesize_H_windows"]
+           "drt_serve_stats_read", "drt_power_profile", "drt_lifetime_windows", "drt_synthesize_H_windows",
+           "drt_synthesize_H_wideband"]
 PP_DOPPLER, PP_DELAY = 0, 1
 
 
@@ -159,6 +160,8 @@ def load_library(path: str = LIB_PATH):
         L.drt_lifetime_windows.restype = st
         L.drt_synthesize_H_windows.argtypes = [vp, C.c_uint64, vp, vp, vp, C.c_int32, vp, C.c_int32, vp]
         L.drt_synthesize_H_windows.restype = st
+        L.drt_synthesize_H_wideband.argtypes = [vp, C.c_uint64, vp, vp, C.c_int32, vp, C.c_int32, vp]
+        L.drt_synthesize_H_wideband.restype = st
         _lib = L
         return L
 
@@ -401,6 +404,18 @@ class Link:
         _check(load_library().drt_synthesize_H_windows(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs),
                                                        st_.ctypes.data if st_.size else None, int(st_.size),
                                                        _dptr(H), int(precision), _stream_ptr(stream)))
+        return H
+
+    def synthesize_H_wideband(self, tg: I.TimeGrid, fg: I.FreqGrid, n_sub: int, precision: int = FP64, H=None,
+                              stream=None):
+        """drt_synthesize_H_wideband: H with field coefficients per sub-band (n_sub sub-bands)."""
+        import torch
+        if H is None:
+            H = torch.empty((int(tg.n_steps), int(fg.n_bins)), dtype=torch.complex64,
+                            device=torch.device("cuda", self.ctx.device))
+        tgs, fgs = _tg(tg), _fg(fg)
+        _check(load_library().drt_synthesize_H_wideband(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs),
+                                                        int(n_sub), _dptr(H), int(precision), _stream_ptr(stream)))
         return H
 
     def synthesize_H_noalloc(self, tg: I.TimeGrid, fg: I.FreqGrid, H, precision: int = FP64, stream=None):
