@@ -11,10 +11,11 @@
 //   stage 3  FP64 chunk anchors           (link, path, chunk)
 //   stage 4  FP32-bulk extrapolation      (link, path, 32 consecutive steps: one warp)
 //   stage 5  H synthesis                  (link, 32 consecutive (step, bin tile) pairs: one block)
-// Stages 4 and 5 run in waves of links whose per-path-step records (20 B each) fit one record
-// buffer, so a batch of any size streams through a bounded scratch.  Links are ordered by
-// decreasing work so the largest units are claimed first.  Steps FP32 cannot resolve go to an FP64
-// redo kernel at the end, which adds their contribution to H with atomics.  The frequency tile
+// All stages run in waves of links whose per-path-step records (20 B each) fit one record buffer and
+// whose poses, warm starts and anchors fit one scratch region, both reused by the next wave, so a
+// batch of any size streams through a bounded scratch.  Links are ordered by decreasing work so the
+// largest units are claimed first.  Steps FP32 cannot resolve go to an FP64 redo kernel at the end
+// of their wave, which adds their contribution to H with atomics.  The frequency tile
 // width of stage 5 (8, 16 or 32 bins per thread) is autotuned on the batch.  The whole sequence can
 // be captured in a CUDA graph.
 #include <cuda_runtime.h>
@@ -39,6 +40,7 @@ constexpr int SYNTH_PG = 4;               // ... whose warps split the paths
 constexpr int SYNTH_KT[3] = {8, 16, 32};
 constexpr size_t REC_BYTES = sizeof(float4) + sizeof(float);   // one synthesis record
 constexpr size_t REC_CAP = (size_t)4 << 30;                    // record buffer of one wave (bytes)
+constexpr size_t SCRATCH_CAP = (size_t)8 << 30;                // poses, warm starts, anchors of one wave
 
 struct BatchLink {
     LinkDev L;
@@ -59,6 +61,7 @@ struct BatchDev {
     int l0, l1;
     const BatchLink *links;
     long long n_items;
+    long long it_base;   // stages 0-3: item of the wave's first link
     unsigned long long *counter;
     float4 *rec_a;
     float *rec_b;
@@ -85,11 +88,12 @@ __global__ void __launch_bounds__(128) k_stage(const BatchDev B) {
     for (;;) {
         if (threadIdx.x == 0) s_start = (long long)atomicAdd(B.counter, (unsigned long long)blockDim.x);
         __syncthreads();
-        long long it = s_start + threadIdx.x;
+        long long q = s_start + threadIdx.x;
         bool done = s_start >= total;
         __syncthreads();
         if (done) break;
-        if (it >= total) continue;
+        if (q >= total) continue;
+        const long long it = B.it_base + q;
         int li = find_link(B, STAGE, it);
         const BatchLink &BL = B.links[li];
         long long local = it - BL.it0[STAGE];
@@ -207,6 +211,8 @@ __global__ void __launch_bounds__(SYNTH_U * SYNTH_PG) k_batch_synth(const BatchD
 
 // FP64 redo of queued steps; their contribution is added to H (all bins) with atomics
 __global__ void __launch_bounds__(32) k_batch_redo(const BatchDev B) {   // one warp per block, spread over SMs
+    if (blockIdx.x == 0 && threadIdx.x == 0)   // the run's total (the wave's count may exceed the list)
+        atomicAdd(reinterpret_cast<unsigned long long *>(B.redo.count) + 1, (unsigned long long)*B.redo.count);
     const int n = min(*B.redo.count, B.redo.cap);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int4 itm = B.redo.items[k];
@@ -245,7 +251,9 @@ __global__ void __launch_bounds__(32) k_batch_redo(const BatchDev B) {   // one 
 // One device block per plan: [counters | link table | redo list | records | per-link scratch], so
 // that a plan can live in memory its owner provides (the serving loop's arena) or in its own
 // allocation.
-struct Wave { int l0, l1; long long n_bulk, n_synth[3]; };
+// a wave: consecutive links whose records and scratch fit their buffers; its preparation items
+// [prep0, prep0 + n_prep) per stage 0-3, its bulk units and synthesis units per tile variant
+struct Wave { int l0, l1; long long prep0[4], n_prep[4], n_bulk, n_synth[3]; };
 
 struct BatchPlan {
     int n_links = 0;
@@ -277,6 +285,7 @@ static BatchDev dev_view(const BatchPlan &P, int l0, int l1, long long n_items, 
     B.l1 = l1;
     B.links = reinterpret_cast<const BatchLink *>(P.mem + P.off_links);
     B.n_items = n_items;
+    B.it_base = 0;
     B.counter = reinterpret_cast<unsigned long long *>(P.mem) + k;
     B.rec_a = reinterpret_cast<float4 *>(P.mem + P.off_rec);
     B.rec_b = reinterpret_cast<float *>(P.mem + P.off_rec + P.rec_count * sizeof(float4));
@@ -295,23 +304,31 @@ static cudaError_t launch_synth_variant(int v, const BatchDev &B, int grid, cuda
     return cudaGetLastError();
 }
 
-// stages 0-3 (all links)
-static cudaError_t run_prep(BatchPlan &P, cudaStream_t s) {
+// counters: 6 per wave (stages 0-3, bulk, synthesis)
+static size_t counter_of(size_t w, int slot) { return 6 * w + slot; }
+
+// stages 0-3 of wave w
+static cudaError_t run_prep(BatchPlan &P, size_t w, cudaStream_t s) {
     const int grid = sm_count() * 4;
-    const int nl = P.n_links;
-    if (P.n_items[ST_POSEB]) k_stage<ST_POSEB><<<grid, 128, 0, s>>>(dev_view(P, 0, nl, P.n_items[ST_POSEB], ST_POSEB));
-    if (P.n_items[ST_POSE64])
-        k_stage<ST_POSE64><<<grid, 128, 0, s>>>(dev_view(P, 0, nl, P.n_items[ST_POSE64], ST_POSE64));
-    if (P.n_items[ST_WARM]) k_stage<ST_WARM><<<grid, 128, 0, s>>>(dev_view(P, 0, nl, P.n_items[ST_WARM], ST_WARM));
-    if (P.n_items[ST_BASE]) k_stage<ST_BASE><<<grid, 128, 0, s>>>(dev_view(P, 0, nl, P.n_items[ST_BASE], ST_BASE));
+    const Wave &W = P.waves[w];
+    auto view = [&](int st) {
+        BatchDev B = dev_view(P, W.l0, W.l1, W.n_prep[st], counter_of(w, st));
+        B.it_base = W.prep0[st];
+        return B;
+    };
+    if (W.n_prep[ST_POSEB]) k_stage<ST_POSEB><<<grid, 128, 0, s>>>(view(ST_POSEB));
+    if (W.n_prep[ST_POSE64]) k_stage<ST_POSE64><<<grid, 128, 0, s>>>(view(ST_POSE64));
+    if (W.n_prep[ST_WARM]) k_stage<ST_WARM><<<grid, 128, 0, s>>>(view(ST_WARM));
+    if (W.n_prep[ST_BASE]) k_stage<ST_BASE><<<grid, 128, 0, s>>>(view(ST_BASE));
     return cudaGetLastError();
 }
 
 static cudaError_t run_wave_bulk(BatchPlan &P, size_t w, cudaStream_t s) {
     const Wave &W = P.waves[w];
     if (!W.n_bulk) return cudaSuccess;
-    if (P.dual) k_batch_bulk<true><<<sm_count() * 4, 128, 0, s>>>(dev_view(P, W.l0, W.l1, W.n_bulk, 4 + 2 * w));
-    else k_batch_bulk<false><<<sm_count() * 4, 128, 0, s>>>(dev_view(P, W.l0, W.l1, W.n_bulk, 4 + 2 * w));
+    const BatchDev B = dev_view(P, W.l0, W.l1, W.n_bulk, counter_of(w, 4));
+    if (P.dual) k_batch_bulk<true><<<sm_count() * 4, 128, 0, s>>>(B);
+    else k_batch_bulk<false><<<sm_count() * 4, 128, 0, s>>>(B);
     return cudaGetLastError();
 }
 
@@ -320,25 +337,28 @@ static cudaError_t run_wave_synth(BatchPlan &P, size_t w, cudaStream_t s, long l
     const int v = P.variant < 0 ? 1 : P.variant;
     long long n = limit >= 0 ? std::min(limit, W.n_synth[v]) : W.n_synth[v];
     if (!n) return cudaSuccess;
-    return launch_synth_variant(v, dev_view(P, W.l0, W.l1, n, 5 + 2 * w), (int)n, s);
+    return launch_synth_variant(v, dev_view(P, W.l0, W.l1, n, counter_of(w, 5)), (int)n, s);
 }
 
-static cudaError_t run_redo(BatchPlan &P, cudaStream_t s) {
-    if (!P.n_links) return cudaSuccess;
-    k_batch_redo<<<sm_count() * 8, 32, 0, s>>>(dev_view(P, 0, P.n_links, 0, 0));
-    return cudaGetLastError();
+// the wave's queued FP64 steps (before the next wave reuses its scratch), then an empty list
+static cudaError_t run_redo(BatchPlan &P, size_t w, cudaStream_t s) {
+    const Wave &W = P.waves[w];
+    k_batch_redo<<<sm_count() * 8, 32, 0, s>>>(dev_view(P, W.l0, W.l1, 0, 0));
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(P.mem + P.off_redo, 0, sizeof(int), s);
+    return e;
 }
 
-// all stages of one run, on one stream
+// all stages of one run, on one stream: per wave, preparation, extrapolation, synthesis, redo
 static cudaError_t run_stages(BatchPlan &P, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(P.mem, 0, sizeof(unsigned long long) * P.n_counters, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(P.mem + P.off_redo, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = run_prep(P, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P.mem + P.off_redo, 0, 16, s);   // count, run total
     for (size_t w = 0; w < P.waves.size() && e == cudaSuccess; ++w) {
-        e = run_wave_bulk(P, w, s);
+        e = run_prep(P, w, s);
+        if (e == cudaSuccess) e = run_wave_bulk(P, w, s);
         if (e == cudaSuccess) e = run_wave_synth(P, w, s);
+        if (e == cudaSuccess) e = run_redo(P, w, s);
     }
-    if (e == cudaSuccess) e = run_redo(P, s);
     return e;
 }
 
@@ -389,9 +409,16 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
         return o;
     };
     long long it[4] = {};
-    size_t redo_items = 0, rec_max = 0;
-    Wave W{0, 0, 0, {0, 0, 0}};
+    size_t rec_max = 0, scratch_max = 0;
+    Wave W{0, 0, {0, 0, 0, 0}, {0, 0, 0, 0}, 0, {0, 0, 0}};
     size_t wave_rec = 0;
+    auto close_wave = [&](int l1) {
+        W.l1 = l1;
+        for (int st = 0; st < 4; ++st) W.n_prep[st] = it[st] - W.prep0[st];
+        P->waves.push_back(W);
+        rec_max = std::max(rec_max, wave_rec);
+        scratch_max = std::max(scratch_max, off);
+    };
     for (int k = 0; k < n; ++k) {
         int i = order[k];
         BatchLink &B = P->host[k];
@@ -406,24 +433,28 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
         const long long T = tgs[i].n_steps, Pn = B.L.n_paths;
         long long nch = (T + chunk - 1) / chunk;
         int md = B.L.n_paths - B.L.n_bulk;
-        B.poseb = reinterpret_cast<PoseB *>(take((size_t)(B.L.n_bodies + 2) * nch * sizeof(PoseB)));
-        B.pose64 = reinterpret_cast<double *>(take((size_t)B.L.n_bodies * nch * POSE_W * sizeof(double)));
-        B.warm = reinterpret_cast<double *>(take((size_t)md * (nch + 1) * 2 * MAXI * sizeof(double)));
-        B.base = reinterpret_cast<BaseRec *>(take((size_t)B.L.n_paths * nch * sizeof(BaseRec)));
+        const size_t sz[4] = {(size_t)(B.L.n_bodies + 2) * nch * sizeof(PoseB),
+                              (size_t)B.L.n_bodies * nch * POSE_W * sizeof(double),
+                              (size_t)md * (nch + 1) * 2 * MAXI * sizeof(double), (size_t)B.L.n_paths * nch * sizeof(BaseRec)};
+        const size_t sbytes = r256(sz[0]) + r256(sz[1]) + r256(sz[2]) + r256(sz[3]);
+        // waves: consecutive links whose records fit the record buffer and whose scratch fits its cap
+        // (the scratch of a wave is reused by the next one)
+        const size_t recs = (size_t)T * Pn;
+        if (k > W.l0 && ((wave_rec + recs) * REC_BYTES > REC_CAP || off + sbytes > SCRATCH_CAP)) {
+            close_wave(k);
+            W = Wave{k, k, {it[0], it[1], it[2], it[3]}, {0, 0, 0, 0}, 0, {0, 0, 0}};
+            wave_rec = 0;
+            off = 0;
+        }
+        B.poseb = reinterpret_cast<PoseB *>(take(sz[0]));
+        B.pose64 = reinterpret_cast<double *>(take(sz[1]));
+        B.warm = reinterpret_cast<double *>(take(sz[2]));
+        B.base = reinterpret_cast<BaseRec *>(take(sz[3]));
         long long cnt[4] = {(B.L.n_bodies + 2) * nch, (long long)B.L.n_bodies * nch, (long long)md * (nch + 1),
                             Pn * nch};
         for (int st = 0; st < 4; ++st) {
             B.it0[st] = it[st];
             it[st] += cnt[st];
-        }
-        // waves: consecutive links whose records fit the record buffer
-        const size_t recs = (size_t)T * Pn;
-        if (k > W.l0 && (wave_rec + recs) * REC_BYTES > REC_CAP) {
-            W.l1 = k;
-            P->waves.push_back(W);
-            rec_max = std::max(rec_max, wave_rec);
-            W = Wave{k, k, 0, {0, 0, 0}};
-            wave_rec = 0;
         }
         B.rec0 = wave_rec;
         wave_rec += recs;
@@ -434,23 +465,19 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
             B.it0[ST_SYNTH + v] = W.n_synth[v];
             W.n_synth[v] += (pairs + SYNTH_U - 1) / SYNTH_U;
         }
-        redo_items += recs;
     }
-    if (n) {
-        W.l1 = n;
-        P->waves.push_back(W);
-        rec_max = std::max(rec_max, wave_rec);
-    }
+    if (n) close_wave(n);
     for (int st = 0; st < 4; ++st) P->n_items[st] = it[st];
     P->rec_count = rec_max;
-    P->n_counters = 4 + 2 * P->waves.size();
-    // the redo list is bounded: beyond 2^22 + 1/16 of all steps the surplus is dropped and counted
-    P->redo_bytes = 256 + r256(std::min<size_t>(redo_items, ((size_t)1 << 22) + redo_items / 16) * sizeof(int4));
+    P->n_counters = 6 * std::max<size_t>(P->waves.size(), 1);
+    // the redo list of a wave is bounded: beyond 2^22 + 1/128 of the wave's steps the surplus is
+    // dropped and counted (measured redo rates stay below 1e-3 of the steps)
+    P->redo_bytes = 256 + r256(std::min<size_t>(rec_max, ((size_t)1 << 22) + rec_max / 128) * sizeof(int4));
     P->off_links = r256(sizeof(unsigned long long) * P->n_counters);
     P->off_redo = P->off_links + r256(sizeof(BatchLink) * std::max(n, 1));
     P->off_rec = P->off_redo + P->redo_bytes;
     P->off_scratch = P->off_rec + r256(rec_max * REC_BYTES);
-    P->bytes = P->off_scratch + off;
+    P->bytes = P->off_scratch + scratch_max;
     *bytes = P->bytes;
     *out = P;
     return cudaSuccess;
@@ -498,8 +525,8 @@ cudaError_t batch_autotune(BatchPlan *P, cudaStream_t s, float *best_ms) {
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     cudaError_t e = cudaMemsetAsync(P->mem, 0, sizeof(unsigned long long) * P->n_counters, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(P->mem + P->off_redo, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = run_prep(*P, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->mem + P->off_redo, 0, 16, s);
+    if (e == cudaSuccess) e = run_prep(*P, 0, s);
     if (e == cudaSuccess) e = run_wave_bulk(*P, 0, s);
     const long long sample = (long long)sm_count() * 256;   // units of each variant timed
     float best = 1e30f;
@@ -507,7 +534,8 @@ cudaError_t batch_autotune(BatchPlan *P, cudaStream_t s, float *best_ms) {
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep)   // first pass warms up
         for (int v = 0; v < 3 && e == cudaSuccess; ++v) {
             P->variant = v;
-            e = cudaMemsetAsync(P->mem + 5 * sizeof(unsigned long long), 0, sizeof(unsigned long long), s);
+            e = cudaMemsetAsync(P->mem + counter_of(0, 5) * sizeof(unsigned long long), 0,
+                                sizeof(unsigned long long), s);
             cudaEventRecord(a, s);
             if (e == cudaSuccess) e = run_wave_synth(*P, 0, s, sample);
             cudaEventRecord(b, s);
@@ -548,11 +576,12 @@ void batch_set_variant(BatchPlan *P, int v) { P->variant = v; }
 int batch_chunk(const BatchPlan *P, int k) { return P->host[k].tg.chunk; }
 size_t batch_bytes(const BatchPlan *P) { return P->bytes; }
 
-// queued FP64 redo steps of the last completed run (the count may exceed the list's capacity)
+// queued FP64 redo steps of the last completed run, all waves (a wave's count may exceed its list's
+// capacity; the total counts every queued step)
 cudaError_t batch_redo_count(const BatchPlan *P, long long *n) {
-    int c = 0;
-    cudaError_t e = cudaMemcpy(&c, P->mem + P->off_redo, sizeof(int), cudaMemcpyDeviceToHost);
-    *n = c;
+    unsigned long long c = 0;
+    cudaError_t e = cudaMemcpy(&c, P->mem + P->off_redo + 8, sizeof(c), cudaMemcpyDeviceToHost);
+    *n = (long long)c;
     return e;
 }
 

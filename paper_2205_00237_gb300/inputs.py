@@ -82,7 +82,7 @@ class PathSet:
                        np.concatenate([s.prims for s in sets]), np.concatenate([s.s0 for s in sets]))
 
     def to_npz(self, path):
-        np.savez(path, n_int=self.n_int, types=self.types, prims=self.prims, s0=self.s0)
+        np.savez_compressed(path, n_int=self.n_int, types=self.types, prims=self.prims, s0=self.s0)
 
     @staticmethod
     def from_npz(path) -> "PathSet":
@@ -350,6 +350,115 @@ def scene_link(seed: int = 0, n_facades: int = 24, tile_size: float = 3.0) -> Sc
     tx = ([0.0, 0.0, 5.0], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0])
     rx = ([50.0, 0.0, 1.5], [10.0, 0.0, 0.0], [0.0, 0.0, 0.0])
     return b.build(tx, rx)
+
+
+HIGHWAY = dict(n_links=64, n_tiles=20000, n_rd=300, carriers=(28e9, 60e9), bandwidth=400e6, n_bins=1024,
+               dt=1e-4, n_steps=20000)
+
+
+def _highway_base(seed: int):
+    """Static part and vehicles of the highway scene (see scene_highway)."""
+    rng = np.random.default_rng(3000 + seed)
+    b = _Builder(f"highway-seed{seed}")
+    concrete = b.material(5.3, 0.1)
+    metal = b.material(1.0, 0.0, pec=True)
+    b.face(0, concrete, [0, 0, 0], [0, 0, 1], [1, 0, 0], math.inf, math.inf)
+    # noise barriers along both road sides, 4 m high, in 50 m panels with top wedge edges; ER tiles
+    # of 0.6 m x 0.8 m (2000 x 5 per side) on their road-facing sides
+    half, n_panel, panel, height = 600.0, 24, 50.0, 4.0
+    n_col, n_row = HIGHWAY["n_tiles"] // 10, 5
+    up = np.array([0.0, 0.0, 1.0])
+    for side in (+1.0, -1.0):
+        mat = b.material(rng.uniform(4, 6), rng.uniform(0.01, 0.05))
+        n = np.array([0.0, -side, 0.0])                      # facing the road
+        u = np.array([1.0, 0.0, 0.0])
+        for k in range(n_panel):
+            centre = np.array([-half + (k + 0.5) * panel, side * 13.0, 0.5 * height])
+            b.face(0, mat, centre, n, u, 0.5 * panel, 0.5 * height)
+            top = centre + 0.5 * height * up
+            b.edge(0, mat, top - 0.5 * panel * u, top + 0.5 * panel * u, n, up)
+        w, h = 2 * half / n_col, height / n_row
+        for i in range(n_col):
+            for j in range(n_row):
+                c = np.array([-half + (i + 0.5) * w, side * 13.0, (j + 0.5) * h])
+                b.tile(0, mat, c, n, w * h, rng.uniform(0.2, 0.5), float(rng.choice([2.0, 4.0])),
+                       rng.uniform(0, 2 * math.pi))
+    # 60 vehicles, 10 per lane (3 lanes each way, 3.5 m wide): 3 in 4 cars (4.5 x 1.8 x 1.5 m), the
+    # rest trucks (12 x 2.5 x 3.8 m); speeds U[20, 36] m/s, yaw rates U[-0.02, 0.02] rad/s,
+    # accelerations U[-1, 1] m/s^2 along the heading
+    veh = []
+    for lane in range(6):
+        y = (-8.75, -5.25, -1.75, 1.75, 5.25, 8.75)[lane]
+        dirn = 1.0 if y < 0 else -1.0
+        for i in range(10):
+            truck = rng.uniform() < 0.25
+            dims = (12.0, 2.5, 3.8) if truck else (4.5, 1.8, 1.5)
+            centre = np.array([-300.0 + 60.0 * i + rng.uniform(0, 30), y, 0.3 + 0.5 * dims[2]])
+            heading = np.array([dirn, 0.0, 0.0])
+            speed, acc = rng.uniform(20, 36), rng.uniform(-1, 1)
+            body = b.body(centre, speed * heading, acc * heading, [0, 0, 1], rng.uniform(-0.02, 0.02), 0.0)
+            b.box(body, metal, centre, np.eye(3), dims)
+            veh.append((centre + [0, 0, 0.5 * dims[2] + 0.25], speed * heading, acc * heading))
+    return b, veh
+
+
+def scene_highway(seed: int = 0, link: int = 0) -> Scene:
+    """Large vehicular highway: 6 lanes, 60 translating and yawing vehicles (metal boxes), a
+    concrete ground plane and two 4 m noise barriers 13 m either side of the centre line carrying
+    20000 ER tiles (S ~ U[0.2,0.5], alpha_R in {2,4}) that face the road.  Link `link` puts TX and
+    RX 0.25 m above the roofs of two distinct vehicles drawn near the middle of the road (seeded),
+    with those vehicles' velocity and acceleration.  The tiles face every terminal on the road, so
+    every single-scatter chain is a ray at t0."""
+    if seed not in _HIGHWAY_CACHE:
+        b, veh = _highway_base(seed)
+        _HIGHWAY_CACHE[seed] = (b.build(veh[0], veh[1]), veh)
+    base, veh = _HIGHWAY_CACHE[seed]
+    rng = np.random.default_rng(7000 + 100 * seed + link)
+    mid = [i for i, (c, _, _) in enumerate(veh) if abs(c[0]) < 200.0]
+    i, j = rng.choice(mid, size=2, replace=False)
+    tx, rx = np.zeros((), TERMINAL), np.zeros((), TERMINAL)
+    tx[()], rx[()] = veh[int(i)], veh[int(j)]
+    return dataclasses.replace(base, name=f"{base.name}-link{link}", tx=tx, rx=rx)
+
+
+_HIGHWAY_CACHE: dict = {}   # seed -> (scene with the static part and vehicles, vehicle terminals)
+
+
+def highway_tile_chains(n_tiles: int):
+    """The single-scatter chains of the highway links, one per tile."""
+    ps = PathSet(np.ones(n_tiles, np.uint8), np.zeros((n_tiles, 4), np.uint8), np.full((n_tiles, 4), -1, np.int32),
+                 np.zeros((n_tiles, 4)))
+    ps.types[:, 0] = T_S
+    ps.prims[:, 0] = np.arange(n_tiles, dtype=np.int32)
+    return ps
+
+
+def highway_pathset(rd: PathSet, link: int, n_tiles: int | None = None, n_rd: int | None = None) -> PathSet:
+    """Path set of highway link `link`: its reflection / diffraction chains (rows
+    [link n_rd, (link + 1) n_rd) of the committed set `rd`) and one single-scatter chain per tile."""
+    n_tiles = HIGHWAY["n_tiles"] if n_tiles is None else n_tiles
+    n_rd = HIGHWAY["n_rd"] if n_rd is None else n_rd
+    return PathSet.concat([rd.subset(np.arange(link * n_rd, (link + 1) * n_rd)), highway_tile_chains(n_tiles)])
+
+
+def draw_chains_batch(rng, scene: Scene, n: int, p_r: float = 0.75, lengths=(1, 2)) -> PathSet:
+    """n candidate reflection / diffraction chains at once: length uniform on `lengths`, each vertex R
+    with probability p_r else D, uniform faces / edges, a vertex never repeating its predecessor's
+    primitive (the next index is taken instead), D edge parameters at the edge midpoint."""
+    nf, ne = len(scene.faces), len(scene.edges)
+    L = rng.choice(np.asarray(lengths), size=n)
+    is_r = rng.uniform(size=(n, MAX_INT)) < p_r
+    u = rng.uniform(size=(n, MAX_INT))
+    prim = np.where(is_r, (u * nf).astype(np.int64), (u * ne).astype(np.int64))
+    for j in range(1, MAX_INT):
+        same = (is_r[:, j] == is_r[:, j - 1]) & (prim[:, j] == prim[:, j - 1])
+        prim[same, j] = (prim[same, j] + 1) % np.where(is_r[same, j], nf, ne)
+    live = np.arange(MAX_INT)[None, :] < L[:, None]
+    types = np.where(live, np.where(is_r, T_R, T_D), T_NONE).astype(np.uint8)
+    prims = np.where(live, prim, -1).astype(np.int32)
+    half = 0.5 * np.linalg.norm(scene.edges["b"] - scene.edges["a"], axis=1) if ne else np.zeros(1)
+    s0 = np.where(live & ~is_r, half[np.clip(prim, 0, max(ne - 1, 0))], 0.0)
+    return PathSet(L.astype(np.uint8), types, prims, s0)
 
 
 def draw_chain_types(rng, p_types=(0.6, 0.2, 0.2), lengths=(1, 2, 3)):

@@ -6,7 +6,8 @@ chains from the seeded generators of ``paper_2205_00237_gb300.inputs`` and keeps
 oracle finds valid at t0 (every point on its face or edge, every neighbour on the correct side).  It
 calls only ``oracle/`` and the input generators, never the CUDA library.
 
-  python tests/golden/make_pathsets.py        # rewrites tests/golden/pathset_*.npz
+  python tests/golden/make_pathsets.py        # rewrites tests/golden/pathset_*.npz (--all: and the
+                                              # highway chains; --highway-only: those alone)
 
 Chain draws for the canyon follow the stated recipe: LoS plus chains of length uniform on {1,2,3}
 with i.i.d. types R:D:S = 0.6:0.2:0.2 and uniform primitives; a drawn type sequence gets up to
@@ -96,12 +97,44 @@ def link_pathset(seed, n_paths=2048, fc=28e9):
     return scene, drawn_pathset(scene, np.random.default_rng(177 + seed), n_paths, fc, kept=[base])
 
 
+def highway_rd_pathsets(seed=0, fc=28e9, batch=20000):
+    """Reflection / diffraction chains of the highway links: LoS, then candidate chains of length
+    uniform on {1, 2} with i.i.d. types R:D = 3:1 and uniform faces / edges, kept in draw order when
+    valid at t0 and not yet taken, until `n_rd` chains per link.  The tile chains of a link are implicit
+    (one per tile, every tile faces the road: inputs.highway_tile_chains)."""
+    hw = I.HIGHWAY
+    rng = np.random.default_rng(4000 + seed)
+    out = []
+    for link in range(hw["n_links"]):
+        scene = I.scene_highway(seed, link)
+        kept = [keep_valid_at_t0(scene, I.chains_to_pathset([[]]), fc)]
+        seen = {()}
+        n = 1
+        while n < hw["n_rd"]:
+            v = keep_valid_at_t0(scene, I.draw_chains_batch(rng, scene, batch), fc)
+            for p in range(v.n_paths):
+                k = chain_key(v, p)
+                if k not in seen and n < hw["n_rd"]:
+                    seen.add(k)
+                    kept.append(v.subset([p]))
+                    n += 1
+        out.append(I.PathSet.concat(kept))
+        print(f"  highway link {link}: {n} chains", flush=True)
+    return I.PathSet.concat(out)
+
+
 def tiny_pathset(seed, fc=28e9):
     scene = I.scene_tiny(seed)
     return scene, keep_valid_at_t0(scene, I.chains_tiny(scene), fc)
 
 
 def main():
+    if "--highway-only" in sys.argv or "--all" in sys.argv:
+        ps = highway_rd_pathsets(0)
+        ps.to_npz(os.path.join(HERE, "pathset_highway_rd_seed0.npz"))
+        print(f"highway seed 0: {ps.n_paths} reflection / diffraction chains over {I.HIGHWAY['n_links']} links")
+        if "--highway-only" in sys.argv:
+            return
     for seed in (0, 1):
         scene, ps = tiny_pathset(seed)
         ps.to_npz(os.path.join(HERE, f"pathset_tiny_seed{seed}.npz"))
@@ -112,6 +145,7 @@ def main():
         print(f"link seed {seed}: {ps.n_paths} paths")
     if "--links-only" in sys.argv:
         return
+
     scene, ps = canyon_pathset(0)
     ps.to_npz(os.path.join(HERE, "pathset_canyon_seed0.npz"))
     sig = {}
