@@ -281,7 +281,9 @@ drt_status drt_batch_run(drt_ctx *ctx, drt_batch *batch, int32_t use_graph, void
 /* chosen synthesis variant (frequency tile of 0: 8, 1: 16, 2: 32 bins per thread), scratch
  * bytes, the autotuner's best sample time (ms) and the path-steps of the last run that FP32 could
  * not resolve and the FP64 redo kernel recomputed (reading it waits for the device); any output
- * may be NULL */
+ * may be NULL.  With redo_steps non-NULL the call returns DRT_ENOMEM when a wave of the last run
+ * queued more redo steps than its list holds (2^22 + 1/128 of the wave's path-steps): that run's H
+ * is then incomplete. */
 drt_status drt_batch_info(drt_ctx *ctx, const drt_batch *batch, int32_t *variant,
                           uint64_t *scratch_bytes, float *tune_ms, int64_t *redo_steps);
 void drt_batch_destroy(drt_ctx *ctx, drt_batch *batch);

@@ -988,8 +988,12 @@ extern "C" drt_status drt_batch_info(drt_ctx *c, const drt_batch *b, int32_t *va
         long long n = 0;
         CUDA_TRY(cudaSetDevice(c->device));
         CUDA_TRY(cudaDeviceSynchronize());
-        CUDA_TRY(batch_redo_count(b->plan, &n));
+        bool over = false;
+        CUDA_TRY(batch_redo_count(b->plan, &n, &over));
         *redo_steps = n;
+        if (over)
+            return fail(DRT_ENOMEM, "%lld steps went to the FP64 redo, more than a wave's redo list holds: "
+                                    "H of the last run is incomplete", n);
     }
     return DRT_OK;
 }

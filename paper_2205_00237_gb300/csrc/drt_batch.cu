@@ -211,8 +211,11 @@ __global__ void __launch_bounds__(SYNTH_U * SYNTH_PG) k_batch_synth(const BatchD
 
 // FP64 redo of queued steps; their contribution is added to H (all bins) with atomics
 __global__ void __launch_bounds__(32) k_batch_redo(const BatchDev B) {   // one warp per block, spread over SMs
-    if (blockIdx.x == 0 && threadIdx.x == 0)   // the run's total (the wave's count may exceed the list)
-        atomicAdd(reinterpret_cast<unsigned long long *>(B.redo.count) + 1, (unsigned long long)*B.redo.count);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {   // the run's total; a wave whose count exceeds the list
+        unsigned long long *hdr = reinterpret_cast<unsigned long long *>(B.redo.count);   // marks the run
+        atomicAdd(hdr + 1, (unsigned long long)*B.redo.count);
+        if (*B.redo.count > B.redo.cap) atomicOr(hdr + 2, 1ull);
+    }
     const int n = min(*B.redo.count, B.redo.cap);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int4 itm = B.redo.items[k];
@@ -352,7 +355,7 @@ static cudaError_t run_redo(BatchPlan &P, size_t w, cudaStream_t s) {
 // all stages of one run, on one stream: per wave, preparation, extrapolation, synthesis, redo
 static cudaError_t run_stages(BatchPlan &P, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(P.mem, 0, sizeof(unsigned long long) * P.n_counters, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(P.mem + P.off_redo, 0, 16, s);   // count, run total
+    if (e == cudaSuccess) e = cudaMemsetAsync(P.mem + P.off_redo, 0, 24, s);   // count, run total, overflow
     for (size_t w = 0; w < P.waves.size() && e == cudaSuccess; ++w) {
         e = run_prep(P, w, s);
         if (e == cudaSuccess) e = run_wave_bulk(P, w, s);
@@ -525,7 +528,7 @@ cudaError_t batch_autotune(BatchPlan *P, cudaStream_t s, float *best_ms) {
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     cudaError_t e = cudaMemsetAsync(P->mem, 0, sizeof(unsigned long long) * P->n_counters, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(P->mem + P->off_redo, 0, 16, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->mem + P->off_redo, 0, 24, s);
     if (e == cudaSuccess) e = run_prep(*P, 0, s);
     if (e == cudaSuccess) e = run_wave_bulk(*P, 0, s);
     const long long sample = (long long)sm_count() * 256;   // units of each variant timed
@@ -578,10 +581,11 @@ size_t batch_bytes(const BatchPlan *P) { return P->bytes; }
 
 // queued FP64 redo steps of the last completed run, all waves (a wave's count may exceed its list's
 // capacity; the total counts every queued step)
-cudaError_t batch_redo_count(const BatchPlan *P, long long *n) {
-    unsigned long long c = 0;
-    cudaError_t e = cudaMemcpy(&c, P->mem + P->off_redo + 8, sizeof(c), cudaMemcpyDeviceToHost);
-    *n = (long long)c;
+cudaError_t batch_redo_count(const BatchPlan *P, long long *n, bool *overflow) {
+    unsigned long long c[2] = {0, 0};
+    cudaError_t e = cudaMemcpy(c, P->mem + P->off_redo + 8, sizeof(c), cudaMemcpyDeviceToHost);
+    *n = (long long)c[0];
+    if (overflow) *overflow = c[1] != 0;
     return e;
 }
 

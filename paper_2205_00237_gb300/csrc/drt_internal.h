@@ -109,7 +109,7 @@ int batch_variant(const BatchPlan *P);
 void batch_set_variant(BatchPlan *P, int v);
 int batch_chunk(const BatchPlan *P, int k);
 size_t batch_bytes(const BatchPlan *P);
-cudaError_t batch_redo_count(const BatchPlan *P, long long *n);
+cudaError_t batch_redo_count(const BatchPlan *P, long long *n, bool *overflow = nullptr);
 int choose_chunk(const drt_scene_view &v, const drt_time_grid &tg, const drt_freq_grid &fg);
 
 // a11 serving loop (drt_serve.cu): one request as the serving thread sees it
