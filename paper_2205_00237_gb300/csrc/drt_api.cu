@@ -258,11 +258,25 @@ drt_status run_extrapolation(drt_ctx *c, Link &L, const drt_time_grid *tg, const
         void *pb = c->poseb.ptr, *bs = c->base.ptr, *rd = c->redo.ptr;
         double *p64 = reinterpret_cast<double *>(c->pose64.ptr);
         double *warm = reinterpret_cast<double *>(c->warm.ptr);
-        // fork: warm starts + FP64 anchors on side[0] beside the FP32 base poses on the caller's stream
-        cudaStream_t sa = c->side[0];
+        // fork: the multi-diffraction warm starts (a few latency-bound solves) on side[1] beside the
+        // FP64 anchors of the other paths on side[0], the FP32 base poses on the caller's stream;
+        // the multi-diffraction anchors follow their warm starts
+        cudaStream_t sa = c->side[0], sw = c->side[1];
+        const int nb = L.dev.n_bulk;
         CUDA_TRY(cudaEventRecord(c->ev_fork, s));
         CUDA_TRY(cudaStreamWaitEvent(sa, c->ev_fork, 0));
-        if (drt_status st = traced(c, 3, sa, [&] { return launch_base_fp64(L.dev, t, f, p64, bs, warm, sa); }))
+        CUDA_TRY(cudaStreamWaitEvent(sw, c->ev_fork, 0));
+        if (drt_status st = traced(c, 3, sw, [&] { return launch_warm_fp64(L.dev, t, warm, sw); })) return st;
+        CUDA_TRY(cudaEventRecord(c->ev_join[1], sw));
+        if (drt_status st = traced(c, 3, sa, [&] {
+                cudaError_t e = launch_base_pose64(L.dev, t, p64, sa);
+                return e != cudaSuccess ? e : launch_base_paths(L.dev, t, f, p64, bs, warm, 0, nb, sa);
+            }))
+            return st;
+        CUDA_TRY(cudaStreamWaitEvent(sa, c->ev_join[1], 0));
+        if (drt_status st = traced(c, 3, sa, [&] {
+                return launch_base_paths(L.dev, t, f, p64, bs, warm, nb, L.dev.n_paths, sa);
+            }))
             return st;
         CUDA_TRY(cudaEventRecord(c->ev_join[0], sa));
         if (drt_status st = traced(c, 0, s, [&] { return launch_pose_bulk(L.dev, t, pb, s); })) return st;

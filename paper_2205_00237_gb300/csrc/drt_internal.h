@@ -169,9 +169,11 @@ size_t bulk_base_bytes(const LinkDev &L, const TimeGridD &tg);
 cudaError_t launch_pose_bulk(const LinkDev &L, const TimeGridD &tg, void *poseb, cudaStream_t s);
 size_t bulk_pose64_bytes(const LinkDev &L, const TimeGridD &tg);
 size_t bulk_redo_bytes(const LinkDev &L, const TimeGridD &tg);
-// warm starts of the multi-diffraction chains (warm, warm_bytes) then the FP64 anchors of every path
-cudaError_t launch_base_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, double *pose64, void *base,
-                             double *warm, cudaStream_t s);
+// FP32-bulk anchors in parts: FP64 poses at the chunk bases, then the anchors of paths [p0, p1) (the
+// multi-diffraction paths [n_bulk, n_paths) need their warm starts, launch_warm_fp64, first)
+cudaError_t launch_base_pose64(const LinkDev &L, const TimeGridD &tg, double *pose64, cudaStream_t s);
+cudaError_t launch_base_paths(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const double *pose64,
+                              void *base, const double *warm, int p0, int p1, cudaStream_t s);
 // the redo scratch holds an int counter (zeroed here, on the stream) followed by the (path, step) list
 cudaError_t launch_extrapolate_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const void *poseb,
                                     const void *base, const double *warm, const OutD &out, const RecD &rec,
