@@ -180,16 +180,8 @@ __global__ void __launch_bounds__(SYNTH_U * SYNTH_PG) k_batch_synth(const BatchD
             float sn, cs, ws, wc;   // hardware sine / cosine on [-pi, pi] (abs. error ~4e-7)
             __sincosf(6.28318530717958648f * ph, &sn, &cs);
             __sincosf(6.28318530717958648f * st, &ws, &wc);
-            float zr = fmaf(r.x, cs, r.y * sn), zi = fmaf(r.y, cs, -r.x * sn);
-            const float wr = wc, wi = -ws;
-#pragma unroll
-            for (int j = 0; j < KT; ++j) {
-                acc[j].x += zr;
-                acc[j].y += zi;
-                const float nr = fmaf(zr, wr, -zi * wi);
-                zi = fmaf(zr, wi, zi * wr);
-                zr = nr;
-            }
+            const float zr = fmaf(r.x, cs, r.y * sn), zi = fmaf(r.y, cs, -r.x * sn);
+            add_geometric<KT>(acc, zr, zi, wc, -ws);
         }
     }
 #pragma unroll

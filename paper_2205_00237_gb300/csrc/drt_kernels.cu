@@ -490,15 +490,7 @@ k_synth(const float4 *__restrict__ rec_a, const float *__restrict__ rec_b, int n
             __sincosf(6.28318530717958648f * st, &ws, &wc);
             // z = a exp(-j 2 pi ph), w = exp(-j 2 pi step)
             float zr = fmaf(r.x, cs, r.y * sn), zi = fmaf(r.y, cs, -r.x * sn);
-            float wr = wc, wi = -ws;
-#pragma unroll
-            for (int j = 0; j < KT; ++j) {
-                acc[j].x += zr;
-                acc[j].y += zi;
-                float nr = fmaf(zr, wr, -zi * wi);
-                zi = fmaf(zr, wi, zi * wr);
-                zr = nr;
-            }
+            add_geometric<KT>(acc, zr, zi, wc, -ws);
         }
     }
 #pragma unroll

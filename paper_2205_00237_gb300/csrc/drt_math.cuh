@@ -190,4 +190,41 @@ template <class T> DRT_HD c3<T> cscale(c3<T> E, cx<T> s) { return {E.x * s, E.y 
 template <class T> DRT_HD cx<T> cdot(c3<T> E, v3<T> e) { return E.x * e.x + E.y * e.y + E.z * e.z; }
 template <class T> DRT_HD T cnorm(c3<T> E) { return sqrt(cabs2(E.x) + cabs2(E.y) + cabs2(E.z)); }
 
+// acc[j] += z w^j, j < KT, for |w| = 1 (one path's terms across a frequency tile).  Where |Im w| >= 1/4
+// the three-term recurrence z_{j+1} = 2 Re(w) z_j - z_{j-1} (w + 1/w = 2 Re w on the unit circle)
+// costs 2 FMA per term instead of the 4 of a complex rotation; a rounding error made at one term
+// reaches a later one scaled by at most 1 / |Im w| <= 4, so the error stays below 4 j eps.  Near
+// w = +-1 the rotation, whose error grows like j eps, is kept.
+#ifdef __CUDACC__
+template <int KT>
+__device__ __forceinline__ void add_geometric(float2 (&acc)[KT], float zr, float zi, float wr, float wi) {
+    if (fabsf(wi) >= 0.25f) {
+        const float c2 = 2.f * wr;
+        float ar = zr, ai = zi;
+        float br = fmaf(zr, wr, -zi * wi), bi = fmaf(zr, wi, zi * wr);
+        acc[0].x += ar;
+        acc[0].y += ai;
+#pragma unroll
+        for (int j = 1; j < KT; ++j) {
+            acc[j].x += br;
+            acc[j].y += bi;
+            const float cr = fmaf(c2, br, -ar), ci = fmaf(c2, bi, -ai);
+            ar = br;
+            ai = bi;
+            br = cr;
+            bi = ci;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < KT; ++j) {
+            acc[j].x += zr;
+            acc[j].y += zi;
+            const float nr = fmaf(zr, wr, -zi * wi);
+            zi = fmaf(zr, wi, zi * wr);
+            zr = nr;
+        }
+    }
+}
+#endif
+
 }  // namespace drt
