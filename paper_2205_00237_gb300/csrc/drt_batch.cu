@@ -167,10 +167,17 @@ __global__ void __launch_bounds__(SYNTH_U * SYNTH_PG) k_batch_synth(const BatchD
     if (live) {
         const float4 *__restrict__ ra = B.rec_a + BL.rec0 + (size_t)ti * P;
         const float *__restrict__ rb = B.rec_b + BL.rec0 + (size_t)ti * P;
+        // the next path's record is loaded one iteration ahead (its latency hides behind the terms)
+        float4 rn = w < P ? __ldg(ra + w) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float lon = w < P ? __ldg(rb + w) : 0.f;
         for (int p = w; p < P; p += SYNTH_PG) {
-            const float4 r = __ldg(ra + p);
+            const float4 r = rn;
+            const float lo = lon;
+            if (p + SYNTH_PG < P) {
+                rn = __ldg(ra + p + SYNTH_PG);
+                lon = __ldg(rb + p + SYNTH_PG);
+            }
             if (r.x == 0.f && r.y == 0.f) continue;
-            const float lo = __ldg(rb + p);
             float ph = kf * r.w;   // exact: the step's high part has 12 significant bits, k0 < 4096
             ph -= floorf(ph);
             ph += r.z + kf * lo;

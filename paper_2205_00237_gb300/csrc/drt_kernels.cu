@@ -473,10 +473,17 @@ k_synth(const float4 *__restrict__ rec_a, const float *__restrict__ rec_b, int n
     if (live) {
         const float4 *ra = rec_a + (size_t)ti * n_paths;
         const float *rb = rec_b + (size_t)ti * n_paths;
+        // the next path's record is loaded one iteration ahead (its latency hides behind the terms)
+        float4 rn = w < n_paths ? __ldg(ra + w) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float lon = w < n_paths ? __ldg(rb + w) : 0.f;
         for (int p = w; p < n_paths; p += PG) {
-            float4 r = __ldg(ra + p);
+            const float4 r = rn;
+            const float lo = lon;
+            if (p + PG < n_paths) {
+                rn = __ldg(ra + p + PG);
+                lon = __ldg(rb + p + PG);
+            }
             if (r.x == 0.f && r.y == 0.f) continue;
-            float lo = __ldg(rb + p);
             float ph = kf * r.w;   // exact
             ph -= floorf(ph);
             ph += r.z + kf * lo;
