@@ -606,6 +606,16 @@ drt_status drt_load_paths(drt_ctx *c, const drt_scene *s, const drt_path_set *ps
     if (!st) st = upload(c, L, H.pprims, &d.pprims);
     if (!st) st = upload(c, L, H.ps0, &d.ps0);
     if (!st) st = upload(c, L, H.perm, &d.perm);
+    if (!st) {   // multi-diffraction edge parameters and rates at t = 0 (warm-start predictor)
+        const size_t n = (size_t)(d.n_paths - d.n_bulk) * 2 * MAXI;
+        std::vector<double> zero(n, 0.0);
+        st = upload(c, L, zero, &d.t0par);
+        if (!st && n) {
+            cudaError_t e = launch_t0par(d, const_cast<double *>(d.t0par), 0);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+            if (e != cudaSuccess) st = fail(DRT_ECUDA, "t0 edge parameters: %s", cudaGetErrorString(e));
+        }
+    }
     if (st) {
         for (void *p : L.allocs) cudaFree(p);
         c->used -= L.bytes;

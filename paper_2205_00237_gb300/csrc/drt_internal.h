@@ -47,6 +47,9 @@ struct LinkDev {
     const int4 *pprims;       // primitive index of vertex j
     const double *ps0;        // [P][4] Newton start for segments with >= 2 diffractions
     const int32_t *perm;      // internal index -> caller index
+    // per path with >= 2 diffractions in a segment ([n_bulk, n_paths)): its edge parameters and their
+    // rates at the scene's reference instant t = 0, solved once when the link is loaded
+    const double *t0par;      // [n_paths - n_bulk][2 * MAXI]
 };
 
 // chunk: time steps per chunk (FP32-bulk FP64 anchors and multi-diffraction warm starts are taken
@@ -161,6 +164,8 @@ cudaError_t launch_extrapolate_fp64(const LinkDev &L, const TimeGridD &tg, const
                                     double *warm = nullptr);
 size_t warm_bytes(const LinkDev &L, const TimeGridD &tg);
 // the warm-start table of the multi-diffraction chains (FP64 dual-number solves at the chunk bases)
+// edge parameters and rates at t = 0 of the multi-diffraction paths (LinkDev::t0par), at load
+cudaError_t launch_t0par(const LinkDev &L, double *t0par, cudaStream_t s);
 cudaError_t launch_warm_fp64(const LinkDev &L, const TimeGridD &tg, double *warm, cudaStream_t s);
 // FP32-bulk form (CHUNK consecutive steps share FP64 anchors); see drt_physics.cuh.  Scratch:
 // per-(body or terminal, chunk) FP32 base poses and per-(path, chunk) FP64 anchors.

@@ -64,6 +64,19 @@ k_warm_fp64(const LinkDev L, const TimeGridD tg, double *__restrict__ warm) {
     path_warm_fp64(L, tg, p, c, warm);
 }
 
+__global__ void __launch_bounds__(32) k_t0par(const LinkDev L, double *__restrict__ t0par) {
+    const int p = L.n_bulk + blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= L.n_paths) return;
+    path_t0par_fp64(L, p, t0par + (size_t)(p - L.n_bulk) * (2 * MAXI));
+}
+
+cudaError_t launch_t0par(const LinkDev &L, double *t0par, cudaStream_t s) {
+    const int n = L.n_paths - L.n_bulk;
+    if (n <= 0) return cudaSuccess;
+    k_t0par<<<(n + 31) / 32, 32, 0, s>>>(L, t0par);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_warm_fp64(const LinkDev &L, const TimeGridD &tg, double *warm, cudaStream_t s) {
     if (!warm || L.n_bulk >= L.n_paths || tg.n_steps == 0) return cudaSuccess;
     dim3 gw(L.n_paths - L.n_bulk, (n_chunks_of(tg) + 1 + WARM_T - 1) / WARM_T);

@@ -951,14 +951,19 @@ DRT_HD void solve_edge_params(const LinkDev &L, int p, double t, const double *s
 }
 
 // one row of the warm-start table: the chunk base `row` solved from the t0 edge parameters
+// edge parameters and their rates at t = 0, where the ray-tracing parameters s0 are already the
+// solution (one iteration); written to out[2 * MAXI]
+DRT_HD void path_t0par_fp64(const LinkDev &L, int p, double *out) {
+    solve_edge_params(L, p, 0.0, L.ps0 + (size_t)p * MAXI, out, out + MAXI,
+                      [&](int ty, int idx) { return load_prim_direct<double>(L, 0.0, ty, idx); });
+}
+
 DRT_HD void path_warm_fp64(const LinkDev &L, const TimeGridD &tg, int p, int row, double *warm) {
     const double t = tg.t_start + (double)row * tg.chunk * tg.dt;
-    // rates at t0, where the ray-tracing parameters s0 are already the solution (one iteration)
-    double s_t0[MAXI], r_t0[MAXI], start[MAXI];
-    solve_edge_params(L, p, 0.0, L.ps0 + (size_t)p * MAXI, s_t0, r_t0,
-                      [&](int ty, int idx) { return load_prim_direct<double>(L, 0.0, ty, idx); });
-    // chunk-base solve from the linear predictor s(t0) + t ds/dt(t0)
-    for (int j = 0; j < MAXI; ++j) start[j] = s_t0[j] + r_t0[j] * t;
+    // chunk-base solve from the linear predictor s(0) + t ds/dt(0) (solved at load: LinkDev::t0par)
+    const double *q = L.t0par + (size_t)(p - L.n_bulk) * (2 * MAXI);
+    double start[MAXI];
+    for (int j = 0; j < MAXI; ++j) start[j] = q[j] + q[MAXI + j] * t;
     double *w = warm + ((size_t)row * (L.n_paths - L.n_bulk) + (p - L.n_bulk)) * (2 * MAXI);
     solve_edge_params(L, p, t, start, w, w + MAXI,
                       [&](int ty, int idx) { return load_prim_direct<double>(L, t, ty, idx); });
