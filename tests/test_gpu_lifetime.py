@@ -165,3 +165,19 @@ def test_lifetime_edges_and_errors(ctx):
             link.synthesize_H_windows(tg, fg, bad, H=H)
         assert ei.value.code == drt.DRT_EINVAL
     link.unload()
+
+
+def test_canyon_full_size_plan(ctx):
+    """The benchmarked configuration (canyon, 2000 x 0.5 ms, share 1e-5, windows of 10-150 ms), FP64."""
+    from paper_2205_00237_gb300 import drt
+    sc = I.scene_canyon(0)
+    ps = I.PathSet.from_npz(os.path.join(GOLD, "pathset_canyon_seed0.npz"))
+    tg, fg = I.grids("canyon")
+    link = ctx.load(sc, ps)
+    starts, major = link.lifetime_windows(tg, fg, 1e-5, 20, 300, precision=drt.FP64)
+    r = O.extrapolate(sc, ps, tg, fg.fc, n_threads=16)
+    want = O.lifetime_toggles(r, 1e-5)
+    amb = ambiguous_changes(r, 1e-5, BAND["fp64"], A_TOL["fp64"])
+    assert np.array_equal(major[~amb], want[~amb])
+    assert starts == O.plan_windows(major, 20, 300) and len(starts) > 2
+    link.unload()

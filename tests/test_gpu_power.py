@@ -169,3 +169,24 @@ def test_power_doppler_error_against_snapshot_resolve(ctx, form):
     # every other bin is empty on both sides or touched by an ambiguous path-step
     assert ((Pg > 0) == (Prt > 0))[~touched].all()
     link.unload()
+
+
+@pytest.mark.parametrize("form", ["fp64", "fp32"])
+def test_canyon_full_size_last_window(ctx, form):
+    """The benchmarked configuration (canyon, 2000 x 0.5 ms, 200 ms windows, 14.34 Hz bins over
+    +-8 kHz): the last window of the GPU profile against the oracle over that window's 400 steps."""
+    from paper_2205_00237_gb300 import drt
+    import torch
+    sc = I.scene_canyon(0)
+    ps = I.PathSet.from_npz(os.path.join(GOLD, "pathset_canyon_seed0.npz"))
+    tg, fg = I.grids("canyon")
+    prec = drt.FP64 if form == "fp64" else drt.FP32_BULK
+    link = ctx.load(sc, ps)
+    spb, x0, dx, nb = 400, -8000.0, 14.34, 1116
+    P = link.power_profile(tg, fg, spb, x0, dx, nb, drt.PP_DOPPLER, prec)
+    torch.cuda.synchronize()
+    last = P.cpu().numpy()[-1:]
+    t0 = tg.n_steps - spb
+    r = O.extrapolate(sc, ps, I.TimeGrid(tg.t_start + t0 * tg.dt, tg.dt, spb), fg.fc, n_threads=16)
+    compare_profile(last, r, spb, x0, dx, nb, O.PP_DOPPLER, form)
+    link.unload()

@@ -104,3 +104,24 @@ def test_wideband_rejects_bad_subband_counts(ctx):
             link.synthesize_H_wideband(tg, fg, n_sub)
         assert ei.value.code == drt.DRT_EINVAL
     link.unload()
+
+
+@pytest.mark.parametrize("form", ["fp64", "fp32"])
+def test_canyon_full_size_sampled_rows(ctx, form):
+    """The benchmarked configuration (canyon, 2000 x 0.5 ms, 512 bins over 1 GHz, 4 sub-bands):
+    sampled rows of the GPU result against the oracle's per-sub-band sums at those instants."""
+    from paper_2205_00237_gb300 import drt
+    import torch
+    sc = I.scene_canyon(0)
+    ps = I.PathSet.from_npz(os.path.join(GOLD, "pathset_canyon_seed0.npz"))
+    tg, fg = I.grids("canyon")
+    prec = drt.FP64 if form == "fp64" else drt.FP32_BULK
+    link = ctx.load(sc, ps)
+    H = link.synthesize_H_wideband(tg, fg, 4, prec)
+    torch.cuda.synchronize()
+    rows = [0, 777, 1500, tg.n_steps - 1]
+    Hg = H[torch.as_tensor(rows, device="cuda")].cpu().numpy().astype(np.complex128)
+    for j, t in enumerate(rows):
+        compare_wideband(Hg[j:j + 1], sc, ps, I.TimeGrid(tg.t_start + t * tg.dt, tg.dt, 1), fg, 4,
+                         tol=1e-4 if form == "fp64" else 1e-3, band=BAND[form])
+    link.unload()
