@@ -45,9 +45,12 @@ PATHSET = os.path.join(ROOT, "tests", "golden", "pathset_canyon_seed0.npz")
 # profiles/k_extrapolate_fp64_canyon.md) and the FP64 peak of the GB300 derived from its unit counts:
 # 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz = 1.26 TFLOP/s (no FP64 tensor path is used).  DRAM bytes
 # per launch from the same capture (set to None whenever the kernel changes after the capture).
-FP64_FLOP_PER_PATH_STEP = 1756.0
+FP64_FLOP_PER_PATH_STEP = 1747.0
 FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
-K1_DRAM_BYTES_PER_LAUNCH = 126.71e6
+K1_DRAM_BYTES_PER_LAUNCH = 28.32e6
+# the same capture: the FP64 pipe was busy this fraction of the launch (conversions, compares and the
+# division / square-root sequences occupy it without counting as DADD / DMUL / DFMA FLOPs)
+K1_FP64_PIPE_ACTIVE = 0.869
 # FP32-bulk form (profiles/k_extrapolate_bulk_canyon.md, profiles/k_synth_canyon.md): FP32 FLOPs per
 # path-step of k_extrapolate_bulk (FADD + FMUL + 2 FFMA, ncu) and 8 FLOP per synthesis term; FP32
 # peak 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz = 80.5 TFLOP/s
@@ -595,7 +598,8 @@ def run_ours(args):
                             "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (no FP64 figure in "
                                            "MEASURED_PEAKS.json)",
                             "algorithmic": f"{FP64_FLOP_PER_PATH_STEP:.0f} FP64 FLOP per path-step x {P * T} path-steps",
-                            "traffic": K1_DRAM_BYTES_PER_LAUNCH}
+                            "traffic": K1_DRAM_BYTES_PER_LAUNCH,
+                            "ncu_fp64_pipe_active": K1_FP64_PIPE_ACTIVE}
     else:
         line["roofline"] = {"bound": "alu", "kernel": "k_extrapolate_fp64", "achieved": None,
                             "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s", "frac": None,
