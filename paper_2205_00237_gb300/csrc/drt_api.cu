@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <atomic>
 #include <map>
 #include <memory>
@@ -113,17 +114,27 @@ drt_status ensure(drt_ctx *c, Scratch &s, size_t bytes) {
     return DRT_OK;
 }
 
-template <class X> drt_status upload(drt_ctx *c, Link &L, const std::vector<X> &v, const X **dst) {
-    void *p = nullptr;
-    size_t bytes = v.size() * sizeof(X);
-    drt_status st = dev_alloc(c, bytes, &p);
-    if (st) return st;
-    L.allocs.push_back(p);
-    L.bytes += bytes;
-    if (bytes) CUDA_TRY(cudaMemcpy(p, v.data(), bytes, cudaMemcpyHostToDevice));
-    *dst = reinterpret_cast<const X *>(p);
-    return DRT_OK;
-}
+// the arrays of one link packed at 256-byte offsets into one host image, uploaded as one device
+// allocation with one copy (separate allocations cost a cudaMalloc / cudaFree per array per link)
+struct LinkImage {
+    std::vector<char> host;
+    std::vector<std::function<void(char *)>> bind;
+    template <class X> void add(const std::vector<X> &v, const X **dst) {
+        const size_t off = (host.size() + 255) & ~(size_t)255;
+        host.resize(off + v.size() * sizeof(X));
+        if (!v.empty()) std::memcpy(host.data() + off, v.data(), v.size() * sizeof(X));
+        bind.push_back([dst, off](char *base) { *dst = reinterpret_cast<const X *>(base + off); });
+    }
+    drt_status upload(drt_ctx *c, Link &L) {
+        void *p = nullptr;
+        if (drt_status st = dev_alloc(c, host.size(), &p)) return st;
+        L.allocs.push_back(p);
+        L.bytes += host.size();
+        if (!host.empty()) CUDA_TRY(cudaMemcpy(p, host.data(), host.size(), cudaMemcpyHostToDevice));
+        for (auto &b : bind) b(reinterpret_cast<char *>(p));
+        return DRT_OK;
+    }
+};
 
 bool finite3(const double *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
 double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
@@ -593,28 +604,28 @@ drt_status drt_load_paths(drt_ctx *c, const drt_scene *s, const drt_path_set *ps
     L.view = H.view;
     L.n_paths = ps->n_paths;
     LinkDev &d = L.dev;
-    drt_status st = DRT_OK;
-    if (!st) st = upload(c, L, H.bodies, &d.bodies);
-    if (!st) st = upload(c, L, H.faces, &d.faces);
-    if (!st) st = upload(c, L, H.edges, &d.edges);
-    if (!st) st = upload(c, L, H.tiles, &d.tiles);
-    if (!st) st = upload(c, L, H.mats, &d.mats);
-    if (!st) st = upload(c, L, H.facesF, &d.facesF);
-    if (!st) st = upload(c, L, H.edgesF, &d.edgesF);
-    if (!st) st = upload(c, L, H.tilesF, &d.tilesF);
-    if (!st) st = upload(c, L, H.ptypes, &d.ptypes);
-    if (!st) st = upload(c, L, H.pprims, &d.pprims);
-    if (!st) st = upload(c, L, H.ps0, &d.ps0);
-    if (!st) st = upload(c, L, H.perm, &d.perm);
-    if (!st) {   // multi-diffraction edge parameters and rates at t = 0 (warm-start predictor)
-        const size_t n = (size_t)(d.n_paths - d.n_bulk) * 2 * MAXI;
-        std::vector<double> zero(n, 0.0);
-        st = upload(c, L, zero, &d.t0par);
-        if (!st && n) {
-            cudaError_t e = launch_t0par(d, const_cast<double *>(d.t0par), 0);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(0);
-            if (e != cudaSuccess) st = fail(DRT_ECUDA, "t0 edge parameters: %s", cudaGetErrorString(e));
-        }
+    LinkImage img;
+    img.add(H.bodies, &d.bodies);
+    img.add(H.faces, &d.faces);
+    img.add(H.edges, &d.edges);
+    img.add(H.tiles, &d.tiles);
+    img.add(H.mats, &d.mats);
+    img.add(H.facesF, &d.facesF);
+    img.add(H.edgesF, &d.edgesF);
+    img.add(H.tilesF, &d.tilesF);
+    img.add(H.ptypes, &d.ptypes);
+    img.add(H.pprims, &d.pprims);
+    img.add(H.ps0, &d.ps0);
+    img.add(H.perm, &d.perm);
+    // multi-diffraction edge parameters and rates at t = 0 (warm-start predictor), solved below
+    const size_t n_t0 = (size_t)(d.n_paths - d.n_bulk) * 2 * MAXI;
+    std::vector<double> t0par(n_t0, 0.0);
+    img.add(t0par, &d.t0par);
+    drt_status st = img.upload(c, L);
+    if (!st && n_t0) {
+        cudaError_t e = launch_t0par(d, const_cast<double *>(d.t0par), 0);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+        if (e != cudaSuccess) st = fail(DRT_ECUDA, "t0 edge parameters: %s", cudaGetErrorString(e));
     }
     if (st) {
         for (void *p : L.allocs) cudaFree(p);
