@@ -728,8 +728,8 @@ static double complex utd_term(double eps, double n, double kL) {
     return (cos(eps / (2 * n)) / sin(eps / (2 * n))) * or_transition_F(2.0 * kL * sh * sh);
 }
 
-/* Soft and hard UTD wedge diffraction coefficients (Kouyoumjian-Pathak, spherical-wave distance
- * parameter L = s s' sin^2 b0 / (s + s')), with Luebbers' heuristic for lossy wedges: the two
+/* Soft and hard UTD wedge diffraction coefficients (Kouyoumjian-Pathak; the distance parameter L is
+ * the caller's, see path_amplitude), with Luebbers' heuristic for lossy wedges: the two
  * reflection-type terms are weighted by the 0-face and n-face Fresnel coefficients (-1 / +1 for a
  * perfect conductor recovers the "-/+" of the PEC form). */
 void or_utd(double n, double phi, double phip, double sinb0, double L, double k, const or_mat *m, double fc,
@@ -806,31 +806,60 @@ static double complex path_amplitude(const or_scene *S, const or_path *pa, doubl
         len[i] = nrm(d);
         kd[i] = scl(d, 1.0 / len[i]);
     }
-    /* spreading per anchor segment (a tile re-radiates as a point source): 1/length without
-     * diffraction, else 1/s'_1 x prod_j sqrt(s'_j / (s_j (s'_j + s_j))) with s'_{j+1} = s_j */
+    /* Ray spreading (Sec. III-A "ray divergence factor") and the UTD distance parameters
+     * (Sec. III-B, Kouyoumjian-Pathak), per anchor segment between point sources (TX, tiles, RX):
+     *  - from a point source the wave is spherical, principal radii rho1 = rho2 = distance; without
+     *    diffraction the segment spreads as 1 / (unfolded length);
+     *  - a planar reflection keeps the principal radii and mirrors their directions;
+     *  - at an edge the incident wavefront's radius of curvature rho_e in the plane of the incident ray
+     *    and the edge follows from its principal radii (Euler: 1/rho_e = cos^2 g / rho1 + sin^2 g / rho2,
+     *    g the angle between that plane and the first principal direction); for a straight edge the
+     *    diffracted ray's second caustic lies rho_e behind the edge, so it spreads as
+     *    sqrt(rho_e / (s (rho_e + s))) up to the next diffraction or point source at distance s, and
+     *    its wavefront has one caustic on the edge (principal direction e x k_out, radius s) and the
+     *    other radius rho_e + s;
+     *  - the distance parameter of the transition function is
+     *    L = s (rho_e + s) rho1 rho2 sin^2 b0 / (rho_e (rho1 + s) (rho2 + s)),
+     *    which for a spherical incident wave is s s' sin^2 b0 / (s + s'). */
     double spread = 1.0;
-    double sprime[OR_MAXI + 1], sdist[OR_MAXI + 1];
+    double rho1[OR_MAXI + 1], rho2[OR_MAXI + 1], rhoe[OR_MAXI + 1], snext[OR_MAXI + 1];
     int a = 0;
     for (int b = 1; b <= n + 1; ++b) {
         if (b <= n && pa->type[b - 1] != OR_T_S) continue;
-        int prev = a;
-        double acc = 0.0, sp = -1.0;
+        int last = a;            /* the point source or the latest diffraction */
+        double d = 0.0;          /* distance travelled since `last` */
+        v3 X1 = mk(0, 0, 0);     /* after a diffraction: principal direction of its caustic on the edge */
         for (int i = a + 1; i <= b; ++i) {
-            acc += len[i];
-            if (i == b || pa->type[i - 1] == OR_T_D) {
-                if (prev == a) {
-                    if (i == b) spread *= 1.0 / acc;
-                    else { spread *= 1.0 / acc; sp = acc; }
-                } else {
-                    double s_ = acc;
-                    sdist[prev] = s_;
-                    sprime[prev] = sp;
-                    spread *= sqrt(sp / (s_ * (sp + s_)));
-                    sp = s_;
+            d += len[i];
+            if (i < b && pa->type[i - 1] == OR_T_R) {
+                if (last != a) {
+                    or_frame F;
+                    face_frame(S, pa->prim[i - 1], t, &F);
+                    X1 = sub(X1, scl(F.ey, 2.0 * dot(X1, F.ey)));
                 }
-                prev = i;
-                acc = 0.0;
+                continue;
             }
+            if (last == a) spread *= 1.0 / d;
+            else {
+                snext[last] = d;
+                spread *= sqrt(rhoe[last] / (d * (rhoe[last] + d)));
+            }
+            if (i == b) break;
+            or_frame F;
+            double elen, wn;
+            edge_frame(S, pa->prim[i - 1], t, &F, &elen, &wn);
+            if (last == a) {
+                rho1[i] = rho2[i] = rhoe[i] = d;
+            } else {
+                rho1[i] = d;
+                rho2[i] = rhoe[last] + d;
+                v3 u = sub(F.ez, scl(kd[i], dot(F.ez, kd[i])));
+                double cg = nrm(u) > 1e-12 ? dot(unit(u), X1) : 0.0;
+                rhoe[i] = 1.0 / (cg * cg / rho1[i] + (1.0 - cg * cg) / rho2[i]);
+            }
+            X1 = unit(crs(F.ez, kd[i + 1]));
+            last = i;
+            d = 0.0;
         }
         a = b;
     }
@@ -866,7 +895,8 @@ static double complex path_amplitude(const or_scene *S, const or_path *pa, doubl
             double phip = wrap2pi(atan2(dot(wi, F.ey), dot(wi, F.ex)));
             double phi = wrap2pi(atan2(dot(wo, F.ey), dot(wo, F.ex)));
             double sinb0 = nrm(crs(kin, e));
-            double L = sdist[i] * sprime[i] * sinb0 * sinb0 / (sdist[i] + sprime[i]);
+            double sd = snext[i];
+            double L = sd * (rhoe[i] + sd) * rho1[i] * rho2[i] * sinb0 * sinb0 / (rhoe[i] * (rho1[i] + sd) * (rho2[i] + sd));
             double complex Ds, Dh;
             or_utd(wn, phi, phip, sinb0, L, k, m, fc, &Ds, &Dh);
             v3 php = unit(scl(crs(e, kin), -1.0)), bp = crs(php, kin);
