@@ -174,18 +174,21 @@ drt_status drt_synthesize_H_host(drt_ctx *ctx, uint64_t link, const drt_time_gri
  * that cannot allocate device memory at call time: latency-bound anticipative-prediction loops,
  * where cudaMalloc / cudaFree may synchronise the device and stall for milliseconds, and processes
  * whose device memory is already fully reserved by another allocator).  Same inputs, output and
- * result as drt_synthesize_H, but the pose table and the synthesis records live in one static
- * device array of DRT_NOALLOC_SCRATCH_BYTES (32 MiB) that the library reserves on every device
- * that loads it, until the process exits; the call makes no cudaMalloc, cudaFree or other
+ * result as drt_synthesize_H's FP64 form (the same launches), but the pose table, the warm-start
+ * table of the chains with several diffractions in one segment and the synthesis records live in one
+ * static device array of DRT_NOALLOC_SCRATCH_BYTES (32 MiB) that the library reserves on every
+ * device that loads it, until the process exits; the call makes no cudaMalloc, cudaFree or other
  * allocating call.  `precision` is checked, and the synthesis runs the FP64 form, whose result
- * meets the tolerances of both forms.  It needs 144 n_steps n_bodies + 20 n_steps n_paths bytes (each part rounded
- * up to 256 B) and fails with DRT_EINVAL when that exceeds the array.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  Every call on a device shares the array and nothing in it
- * needs to start at zero (each call writes the pose table and records before reading them); calls
- * whose device work overlaps (different streams, or different contexts on the same device) race on
- * it, so order them on one stream or serialise them.  Errors: DRT_EINVAL, DRT_ENOTFOUND,
- * DRT_ECUDA. */
+ * meets the tolerances of both forms.  It needs 144 n_steps n_bodies + 64 n_multi (ceil(n_steps / 16)
+ * + 1) + 20 n_steps n_paths bytes (n_multi = chains with two or more diffractions in a segment;
+ * each part rounded up to 256 B) and fails with DRT_EINVAL when that exceeds the array.  Every call
+ * looks up the array's device address (cudaGetSymbolAddress) with the context's device current,
+ * which allocates nothing; make the first call on a device before any stream capture, since the
+ * runtime may load the library's device code there.  Every call on a device shares the array and
+ * nothing in it needs to start at zero (each call writes the pose table, warm starts and records
+ * before reading them); calls whose device work overlaps (different streams, or different contexts
+ * on the same device) race on it, so order them on one stream or serialise them.
+ * Errors: DRT_EINVAL, DRT_ENOTFOUND, DRT_ECUDA. */
 #define DRT_NOALLOC_SCRATCH_BYTES (32u << 20)
 drt_status drt_synthesize_H_noalloc(drt_ctx *ctx, uint64_t link, const drt_time_grid *tgrid,
                                     const drt_freq_grid *fgrid, void *H, int32_t precision,
@@ -282,8 +285,9 @@ drt_status drt_batch_run(drt_ctx *ctx, drt_batch *batch, int32_t use_graph, void
  * bytes, the autotuner's best sample time (ms) and the path-steps of the last run that FP32 could
  * not resolve and the FP64 redo kernel recomputed (reading it waits for the device); any output
  * may be NULL.  With redo_steps non-NULL the call returns DRT_ENOMEM when a wave of the last run
- * queued more redo steps than its list holds (2^22 + 1/128 of the wave's path-steps): that run's H
- * is then incomplete. */
+ * queued more redo steps than its list holds (2^22 + 1/128 of the wave's path-steps, or the value
+ * of the environment variable DRT_BATCH_REDO_CAP when that is smaller, read when a plan is built):
+ * that run's H is then incomplete. */
 drt_status drt_batch_info(drt_ctx *ctx, const drt_batch *batch, int32_t *variant,
                           uint64_t *scratch_bytes, float *tune_ms, int64_t *redo_steps);
 void drt_batch_destroy(drt_ctx *ctx, drt_batch *batch);
@@ -311,7 +315,10 @@ typedef struct {
     int32_t reserved;
 } drt_request;
 typedef struct {
-    drt_status status;          /* DRT_OK, DRT_ENOMEM (larger than the arena) or DRT_ECUDA       */
+    drt_status status;          /* DRT_OK; DRT_ENOMEM when the request is larger than the arena, */
+                                /* or when its batch queued more FP64 redo steps than the redo    */
+                                /* list holds (H then misses them); DRT_EINVAL when the batch     */
+                                /* could not be planned; DRT_ECUDA                                */
     int32_t batch_requests;     /* requests in the launch that served this one                    */
     double t_submit, t_launch, t_done;   /* seconds on the library's steady clock                 */
 } drt_result;

@@ -253,6 +253,21 @@ template <class F> drt_status traced(drt_ctx *c, int kind, cudaStream_t s, F &&l
     return DRT_OK;
 }
 
+// the chains that run the generic code (several diffractions in a segment, 4 vertices) get a launch of
+// their own on side[1], beside the launches of the other chains on s: fork after the work queued on s
+// so far, join before anything after it
+template <class F> cudaError_t split_multi(drt_ctx *c, const LinkDev &L, cudaStream_t s, F &&launch) {
+    const bool split = L.len_start[MAXI] > 0 && L.len_start[MAXI] < L.n_paths;
+    if (!split) return launch(s);
+    cudaStream_t sm = c->side[1];
+    cudaError_t e = cudaEventRecord(c->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sm, c->ev_fork, 0);
+    if (e == cudaSuccess) e = launch(sm);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_join[1], sm);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join[1], 0);
+    return e;
+}
+
 // pose table + extrapolation (+ records) for one link
 drt_status run_extrapolation(drt_ctx *c, Link &L, const drt_time_grid *tg, const drt_freq_grid *fg,
                              const OutD &out, const RecD &rec, int32_t precision, cudaStream_t s,
@@ -293,7 +308,9 @@ drt_status run_extrapolation(drt_ctx *c, Link &L, const drt_time_grid *tg, const
         if (drt_status st = traced(c, 0, s, [&] { return launch_pose_bulk(L.dev, t, pb, s); })) return st;
         CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[0], 0));
         if (drt_status st = traced(c, 1, s, [&] {
-                return launch_extrapolate_bulk(L.dev, t, f, pb, bs, warm, out, rec, rd, s);
+                return split_multi(c, L.dev, s, [&](cudaStream_t sm) {
+                    return launch_extrapolate_bulk(L.dev, t, f, pb, bs, warm, out, rec, rd, s, sm);
+                });
             }))
             return st;
         if (!defer_redo)   // else the caller runs the redo beside the synthesis (synth_into)
@@ -308,7 +325,11 @@ drt_status run_extrapolation(drt_ctx *c, Link &L, const drt_time_grid *tg, const
     double *warm = reinterpret_cast<double *>(c->warm.ptr);
     if (drt_status st = traced(c, 0, s, [&] { return launch_pose(L.dev, t, pose, s); })) return st;
     if (drt_status st = traced(c, 3, s, [&] { return launch_warm_fp64(L.dev, t, warm, s); })) return st;
-    return traced(c, 1, s, [&] { return launch_extrapolate_fp64(L.dev, t, f, pose, out, rec, s, 0, -1, false, warm); });
+    return traced(c, 1, s, [&] {
+        return split_multi(c, L.dev, s, [&](cudaStream_t sm) {
+            return launch_extrapolate_fp64(L.dev, t, f, pose, out, rec, s, 0, -1, false, warm, sm);
+        });
+    });
 }
 
 drt_status synth_into(drt_ctx *c, Link &L, const drt_time_grid *tg, const drt_freq_grid *fg, float2 *H,
@@ -512,6 +533,14 @@ drt_status drt::pack_link(const drt_scene *s, const drt_path_set *ps, PackedLink
     int n_bulk = 0;
     for (int p = 0; p < P; ++p) n_bulk += multi_d(code[p]) ? 0 : 1;
     d.n_bulk = n_bulk;
+    // start of each chain length among the first n_bulk (sorted) paths
+    {
+        int cnt[MAXI + 1] = {0, 0, 0, 0, 0};
+        for (int p = 0; p < P; ++p)
+            if (!multi_d(code[p])) ++cnt[ps->n_int[p]];
+        d.len_start[0] = 0;
+        for (int k = 0; k <= MAXI; ++k) d.len_start[k + 1] = d.len_start[k] + cnt[k];
+    }
     std::vector<uint32_t> &ptypes = H.ptypes;
     ptypes.resize(P);
     std::vector<int4> &pprims = H.pprims;
@@ -882,31 +911,22 @@ drt_status drt_probe_peak(drt_ctx *c, int32_t kind, int32_t blocks, double *flop
 // Allocation-free synthesis.  Some callers cannot allocate device memory when they ask for a
 // channel prediction: a latency-bound prediction loop cannot afford cudaMalloc / cudaFree, which
 // may synchronise the device, and a process whose device memory is already reserved by another
-// allocator has none to give.  For them the scratch of drt_synthesize_H (pose table + synthesis
-// records) lives in this file-scope device array instead of context-owned buffers.  Host code
-// never names the array directly: its device address comes from cudaGetSymbolAddress, looked up
-// once per device (with that device current) on the first call there.
+// allocator has none to give.  For them the scratch of drt_synthesize_H (pose table, warm-start
+// table of the multi-diffraction chains, synthesis records) lives in this file-scope device array
+// instead of context-owned buffers.  Host code never names the array directly: its device address
+// comes from cudaGetSymbolAddress with the context's device current, looked up on every call (the
+// lookup allocates nothing, and a cached address would go stale if the device were reset).
 namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[DRT_NOALLOC_SCRATCH_BYTES];
 
-std::mutex g_noalloc_mu;
-constexpr int NOALLOC_MAX_DEVICES = 64;
-void *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
-
-// device address of the static scratch on `device` (which must be current)
+// device address of the static scratch on the current device
 drt_status noalloc_scratch(int device, unsigned char **out) {
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (device < 0 || device >= NOALLOC_MAX_DEVICES)
-        return fail(DRT_EINVAL, "device %d out of range for the allocation-free entry point", device);
-    if (!g_noalloc_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(DRT_ECUDA, "cudaGetSymbolAddress(scratch) on device %d: %s", device, cudaGetErrorString(e));
-        g_noalloc_addr[device] = p;
-    }
-    *out = reinterpret_cast<unsigned char *>(g_noalloc_addr[device]);
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return fail(DRT_ECUDA, "cudaGetSymbolAddress(scratch) on device %d: %s", device, cudaGetErrorString(e));
+    *out = reinterpret_cast<unsigned char *>(p);
     return DRT_OK;
 }
 
@@ -921,10 +941,13 @@ extern "C" drt_status drt_synthesize_H_noalloc(drt_ctx *c, uint64_t link, const 
     std::lock_guard<std::mutex> lk(c->mu);
     Link *L = find_link(c, link);
     if (!L) return fail(DRT_ENOTFOUND, "unknown link %llu", (unsigned long long)link);
+    TimeGridD t = tgd(tg);
+    FreqGridD f = fgd(fg);
     size_t pose_bytes = round256((size_t)tg->n_steps * L->dev.n_bodies * POSE_W * sizeof(double));
+    size_t warm_sz = round256(warm_bytes(L->dev, t));
     size_t reca_bytes = round256((size_t)tg->n_steps * L->n_paths * sizeof(float4));
     size_t recb_bytes = round256((size_t)tg->n_steps * L->n_paths * sizeof(float));
-    size_t need = pose_bytes + reca_bytes + recb_bytes;
+    size_t need = pose_bytes + warm_sz + reca_bytes + recb_bytes;
     if (need > (size_t)DRT_NOALLOC_SCRATCH_BYTES)
         return fail(DRT_EINVAL,
                     "allocation-free synthesis needs %zu bytes of scratch for %d steps x %d paths x %d bodies, "
@@ -934,13 +957,16 @@ extern "C" drt_status drt_synthesize_H_noalloc(drt_ctx *c, uint64_t link, const 
     unsigned char *base = nullptr;
     if (drt_status st = noalloc_scratch(c->device, &base)) return st;
     double *pose = reinterpret_cast<double *>(base);
-    RecD rec{reinterpret_cast<float4 *>(base + pose_bytes), reinterpret_cast<float *>(base + pose_bytes + reca_bytes)};
+    double *warm = reinterpret_cast<double *>(base + pose_bytes);
+    RecD rec{reinterpret_cast<float4 *>(base + pose_bytes + warm_sz),
+             reinterpret_cast<float *>(base + pose_bytes + warm_sz + reca_bytes)};
     cudaStream_t s = (cudaStream_t)stream;
-    TimeGridD t = tgd(tg);
-    FreqGridD f = fgd(fg);
     OutD none{};
+    // the same launches as drt_synthesize_H's FP64 form: pose table, multi-diffraction warm starts,
+    // extrapolation into the records, synthesis
     CUDA_TRY(launch_pose(L->dev, t, pose, s));
-    CUDA_TRY(launch_extrapolate_fp64(L->dev, t, f, pose, none, rec, s));
+    CUDA_TRY(launch_warm_fp64(L->dev, t, warm, s));
+    CUDA_TRY(launch_extrapolate_fp64(L->dev, t, f, pose, none, rec, s, 0, -1, false, warm));
     CUDA_TRY(launch_synth(rec, L->n_paths, t, f, reinterpret_cast<float2 *>(H), s));
     return DRT_OK;
 }

@@ -9,7 +9,8 @@
 //   stage 1  FP64 chunk-base poses        (link, body, chunk)
 //   stage 2  multi-diffraction warm start (link, path with >= 2 D in a segment, chunk base 0..n)
 //   stage 3  FP64 chunk anchors           (link, path, chunk)
-//   stage 4  FP32-bulk extrapolation      (link, path, 32 consecutive steps: one warp)
+//   stage 4  FP32-bulk extrapolation      (link, path, 32 consecutive steps: one warp), one unit
+//            range and launch per chain length 0..3 and one for the chains that need generic code
 //   stage 5  H synthesis                  (link, 32 consecutive (step, bin tile) pairs: one block)
 // All stages run in waves of links whose per-path-step records (20 B each) fit one record buffer and
 // whose poses, warm starts and anchors fit one scratch region, both reused by the next wave, so a
@@ -22,6 +23,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <type_traits>
@@ -33,7 +35,7 @@
 namespace drt {
 
 // stage slots; the synthesis has one slot per tile variant (its units depend on the tile width)
-enum { ST_POSEB = 0, ST_POSE64 = 1, ST_WARM = 2, ST_BASE = 3, ST_BULK = 4, ST_SYNTH = 5, N_STAGES = 8 };
+enum { ST_POSEB = 0, ST_POSE64 = 1, ST_WARM = 2, ST_BASE = 3, ST_BULK = 4, ST_SYNTH = 8, ST_BULKM = 11, N_STAGES = 12 };
 constexpr int BULK_W = 32;                // time steps per extrapolation unit (one warp's lanes)
 constexpr int SYNTH_U = 32;               // (step, tile) pairs per synthesis unit (one block) ...
 constexpr int SYNTH_PG = 4;               // ... whose warps split the paths
@@ -42,7 +44,7 @@ constexpr size_t REC_BYTES = sizeof(float4) + sizeof(float);   // one synthesis 
 constexpr size_t REC_CAP = (size_t)4 << 30;                    // record buffer of one wave (bytes)
 constexpr size_t SCRATCH_CAP = (size_t)8 << 30;                // poses, warm starts, anchors of one wave
 
-struct BatchLink {
+struct alignas(16) BatchLink {
     LinkDev L;
     TimeGridD tg;
     FreqGridD fg;
@@ -117,29 +119,41 @@ __global__ void __launch_bounds__(128) k_stage(const BatchDev B) {
     }
 }
 
-// stage 4: a warp claims (link, path, 32 steps); the lanes share the chain signature
-// at most 128 registers: 16 warps per SM instead of 8 (4096-link batch +26 %)
-template <bool DUAL>
-__global__ void __launch_bounds__(128, 4) k_batch_bulk(const BatchDev B) {
+// stage 4: a warp claims (link, path, 32 steps) and the lanes share the chain signature.  Chains of
+// up to 3 vertices with at most one diffraction between point sources run code unrolled for their
+// length, one persistent launch per length (stage slots 4 + N, unit ranges per length: the signature
+// sort makes each length a contiguous path range of its link), each with the register budget of its
+// length; the other chains (several diffractions in a segment, 4 vertices) are stage 8, generic code.
+// At most 128 registers: 16 warps per SM instead of 8 (4096-link batch +26 %); 1-vertex chains 24.
+template <int N, bool MULTI, bool OUT, class S>
+__device__ __forceinline__ void batch_unit(const BatchDev &B, const BatchLink &BL, int li, int p, int t) {
+    Rec5 r;
+    bulk_eval<N, MULTI, OUT, S>(BL.L, BL.tg, BL.fg, BL.poseb, BL.base, BL.warm, p, t, BL.out, r, B.redo, li);
+    const size_t ri = BL.rec0 + (size_t)t * BL.L.n_paths + p;
+    B.rec_a[ri] = make_float4(r.ar, r.ai, r.ph, r.hi);
+    B.rec_b[ri] = r.lo;
+}
+
+template <int N> struct BatchBlocks { static constexpr int v = N < 0 ? 4 : N <= 1 ? 6 : N == 2 ? 4 : 3; };
+
+// N >= 0: the units of the chains of length N; N < 0: the units of the generic chains
+template <int N, bool DUAL, bool OUT>
+__global__ void __launch_bounds__(128, BatchBlocks<N>::v) k_batch_bulk(const BatchDev B) {
+    typedef std::conditional_t<DUAL, dd, de> S;
+    constexpr int slot = N >= 0 ? ST_BULK + N : ST_BULKM;
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long it = 0;
         if (lane == 0) it = atomicAdd(B.counter, 1ull);
         it = __shfl_sync(0xffffffffu, it, 0);
         if ((long long)it >= B.n_items) break;
-        const int li = find_link(B, ST_BULK, (long long)it);
+        const int li = find_link(B, slot, (long long)it);
         const BatchLink &BL = B.links[li];
-        const long long local = (long long)it - BL.it0[ST_BULK];
+        const long long local = (long long)it - BL.it0[slot];
         const int nb = (BL.tg.n_steps + BULK_W - 1) / BULK_W;
-        const int p = (int)(local / nb), t = (int)(local % nb) * BULK_W + lane;
-        if (t < BL.tg.n_steps) {
-            Rec5 r;
-            if constexpr (DUAL) bulk_eval<dd>(BL.L, BL.tg, BL.fg, BL.poseb, BL.base, BL.warm, p, t, BL.out, r, B.redo, li);
-            else bulk_eval<de>(BL.L, BL.tg, BL.fg, BL.poseb, BL.base, BL.warm, p, t, BL.out, r, B.redo, li);
-            const size_t ri = BL.rec0 + (size_t)t * BL.L.n_paths + p;
-            B.rec_a[ri] = make_float4(r.ar, r.ai, r.ph, r.hi);
-            B.rec_b[ri] = r.lo;
-        }
+        const int p0 = N >= 0 ? BL.L.len_start[N >= 0 ? N : 0] : BL.L.len_start[MAXI];
+        const int p = p0 + (int)(local / nb), t = (int)(local % nb) * BULK_W + lane;
+        if (t < BL.tg.n_steps) batch_unit<N, (N < 0), (N < 0 || OUT), S>(B, BL, li, p, t);
     }
 }
 
@@ -255,7 +269,7 @@ __global__ void __launch_bounds__(32) k_batch_redo(const BatchDev B) {   // one 
 // allocation.
 // a wave: consecutive links whose records and scratch fit their buffers; its preparation items
 // [prep0, prep0 + n_prep) per stage 0-3, its bulk units and synthesis units per tile variant
-struct Wave { int l0, l1; long long prep0[4], n_prep[4], n_bulk, n_synth[3]; };
+struct Wave { int l0, l1; long long prep0[4], n_prep[4], n_bulk[MAXI], n_bulkm, n_synth[3]; };
 
 struct BatchPlan {
     int n_links = 0;
@@ -268,6 +282,7 @@ struct BatchPlan {
     bool owns = false;
     int variant = -1;   // synthesis tile width index (autotuner or caller)
     bool dual = false;  // some link asks for Doppler outputs: carry the rates
+    bool any_out = false;   // some link asks for per-path-step records
     cudaGraphExec_t graph = nullptr;
     cudaStream_t capture = nullptr;   // private stream the graph is captured on (any caller stream,
                                       // the legacy default stream included, can then launch it)
@@ -306,8 +321,9 @@ static cudaError_t launch_synth_variant(int v, const BatchDev &B, int grid, cuda
     return cudaGetLastError();
 }
 
-// counters: 6 per wave (stages 0-3, bulk, synthesis)
-static size_t counter_of(size_t w, int slot) { return 6 * w + slot; }
+// counters: 10 per wave (stages 0-3, bulk per chain length 0..3, synthesis, generic bulk)
+constexpr int N_COUNTERS = 10;
+static size_t counter_of(size_t w, int slot) { return N_COUNTERS * w + slot; }
 
 // stages 0-3 of wave w
 static cudaError_t run_prep(BatchPlan &P, size_t w, cudaStream_t s) {
@@ -327,10 +343,40 @@ static cudaError_t run_prep(BatchPlan &P, size_t w, cudaStream_t s) {
 
 static cudaError_t run_wave_bulk(BatchPlan &P, size_t w, cudaStream_t s) {
     const Wave &W = P.waves[w];
-    if (!W.n_bulk) return cudaSuccess;
-    const BatchDev B = dev_view(P, W.l0, W.l1, W.n_bulk, counter_of(w, 4));
-    if (P.dual) k_batch_bulk<true><<<sm_count() * 4, 128, 0, s>>>(B);
-    else k_batch_bulk<false><<<sm_count() * 4, 128, 0, s>>>(B);
+    const int g4 = sm_count() * 4, g6 = sm_count() * 6;
+    for (int n = 0; n < MAXI; ++n) {
+        if (!W.n_bulk[n]) continue;
+        const BatchDev B = dev_view(P, W.l0, W.l1, W.n_bulk[n], counter_of(w, 4 + n));
+        const int g = n <= 1 ? g6 : n == 2 ? g4 : sm_count() * 3;
+        if (P.dual) {
+            switch (n) {
+            case 0: k_batch_bulk<0, true, true><<<g, 128, 0, s>>>(B); break;
+            case 1: k_batch_bulk<1, true, true><<<g, 128, 0, s>>>(B); break;
+            case 2: k_batch_bulk<2, true, true><<<g, 128, 0, s>>>(B); break;
+            default: k_batch_bulk<3, true, true><<<g, 128, 0, s>>>(B); break;
+            }
+        } else if (P.any_out) {
+            switch (n) {
+            case 0: k_batch_bulk<0, false, true><<<g, 128, 0, s>>>(B); break;
+            case 1: k_batch_bulk<1, false, true><<<g, 128, 0, s>>>(B); break;
+            case 2: k_batch_bulk<2, false, true><<<g, 128, 0, s>>>(B); break;
+            default: k_batch_bulk<3, false, true><<<g, 128, 0, s>>>(B); break;
+            }
+        } else {
+            switch (n) {
+            case 0: k_batch_bulk<0, false, false><<<g, 128, 0, s>>>(B); break;
+            case 1: k_batch_bulk<1, false, false><<<g, 128, 0, s>>>(B); break;
+            case 2: k_batch_bulk<2, false, false><<<g, 128, 0, s>>>(B); break;
+            default: k_batch_bulk<3, false, false><<<g, 128, 0, s>>>(B); break;
+            }
+        }
+        if (cudaError_t e = cudaGetLastError()) return e;
+    }
+    if (W.n_bulkm) {
+        const BatchDev B = dev_view(P, W.l0, W.l1, W.n_bulkm, counter_of(w, 8));
+        if (P.dual) k_batch_bulk<-1, true, true><<<g4, 128, 0, s>>>(B);
+        else k_batch_bulk<-1, false, true><<<g4, 128, 0, s>>>(B);
+    }
     return cudaGetLastError();
 }
 
@@ -339,7 +385,7 @@ static cudaError_t run_wave_synth(BatchPlan &P, size_t w, cudaStream_t s, long l
     const int v = P.variant < 0 ? 1 : P.variant;
     long long n = limit >= 0 ? std::min(limit, W.n_synth[v]) : W.n_synth[v];
     if (!n) return cudaSuccess;
-    return launch_synth_variant(v, dev_view(P, W.l0, W.l1, n, counter_of(w, 5)), (int)n, s);
+    return launch_synth_variant(v, dev_view(P, W.l0, W.l1, n, counter_of(w, 9)), (int)n, s);
 }
 
 // the wave's queued FP64 steps (before the next wave reuses its scratch), then an empty list
@@ -412,7 +458,7 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
     };
     long long it[4] = {};
     size_t rec_max = 0, scratch_max = 0;
-    Wave W{0, 0, {0, 0, 0, 0}, {0, 0, 0, 0}, 0, {0, 0, 0}};
+    Wave W{0, 0, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, 0, {0, 0, 0}};
     size_t wave_rec = 0;
     auto close_wave = [&](int l1) {
         W.l1 = l1;
@@ -432,6 +478,8 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
         B.H = reinterpret_cast<float2 *>(H[i]);
         if (outs) B.out = outs[i];
         P->dual = P->dual || B.out.doppler != nullptr;
+        P->any_out = P->any_out || B.out.tau || B.out.amp || B.out.doppler || B.out.angles || B.out.flags ||
+                     B.out.points;
         const long long T = tgs[i].n_steps, Pn = B.L.n_paths;
         long long nch = (T + chunk - 1) / chunk;
         int md = B.L.n_paths - B.L.n_bulk;
@@ -444,7 +492,7 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
         const size_t recs = (size_t)T * Pn;
         if (k > W.l0 && ((wave_rec + recs) * REC_BYTES > REC_CAP || off + sbytes > SCRATCH_CAP)) {
             close_wave(k);
-            W = Wave{k, k, {it[0], it[1], it[2], it[3]}, {0, 0, 0, 0}, 0, {0, 0, 0}};
+            W = Wave{k, k, {it[0], it[1], it[2], it[3]}, {0, 0, 0, 0}, {0, 0, 0, 0}, 0, {0, 0, 0}};
             wave_rec = 0;
             off = 0;
         }
@@ -460,8 +508,13 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
         }
         B.rec0 = wave_rec;
         wave_rec += recs;
-        B.it0[ST_BULK] = W.n_bulk;
-        W.n_bulk += Pn * ((T + BULK_W - 1) / BULK_W);
+        const long long nbw = (T + BULK_W - 1) / BULK_W;
+        for (int nl = 0; nl < MAXI; ++nl) {
+            B.it0[ST_BULK + nl] = W.n_bulk[nl];
+            W.n_bulk[nl] += (long long)(B.L.len_start[nl + 1] - B.L.len_start[nl]) * nbw;
+        }
+        B.it0[ST_BULKM] = W.n_bulkm;
+        W.n_bulkm += (Pn - B.L.len_start[MAXI]) * nbw;
         for (int v = 0; v < 3; ++v) {   // a link without paths gets H = 0
             const long long pairs = T * ((fgs[i].n_bins + SYNTH_KT[v] - 1) / SYNTH_KT[v]);
             B.it0[ST_SYNTH + v] = W.n_synth[v];
@@ -471,10 +524,15 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
     if (n) close_wave(n);
     for (int st = 0; st < 4; ++st) P->n_items[st] = it[st];
     P->rec_count = rec_max;
-    P->n_counters = 6 * std::max<size_t>(P->waves.size(), 1);
+    P->n_counters = N_COUNTERS * std::max<size_t>(P->waves.size(), 1);
     // the redo list of a wave is bounded: beyond 2^22 + 1/128 of the wave's steps the surplus is
     // dropped and counted (measured redo rates stay below 1e-3 of the steps)
-    P->redo_bytes = 256 + r256(std::min<size_t>(rec_max, ((size_t)1 << 22) + rec_max / 128) * sizeof(int4));
+    size_t redo_cap = std::min<size_t>(rec_max, ((size_t)1 << 22) + rec_max / 128);
+    if (const char *env = std::getenv("DRT_BATCH_REDO_CAP")) {   // a smaller list, for memory-tight callers
+        const long long v = std::atoll(env);
+        if (v >= 1) redo_cap = std::min<size_t>(redo_cap, (size_t)v);
+    }
+    P->redo_bytes = 256 + r256(redo_cap * sizeof(int4));
     P->off_links = r256(sizeof(unsigned long long) * P->n_counters);
     P->off_redo = P->off_links + r256(sizeof(BatchLink) * std::max(n, 1));
     P->off_rec = P->off_redo + P->redo_bytes;
@@ -536,7 +594,7 @@ cudaError_t batch_autotune(BatchPlan *P, cudaStream_t s, float *best_ms) {
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep)   // first pass warms up
         for (int v = 0; v < 3 && e == cudaSuccess; ++v) {
             P->variant = v;
-            e = cudaMemsetAsync(P->mem + counter_of(0, 5) * sizeof(unsigned long long), 0,
+            e = cudaMemsetAsync(P->mem + counter_of(0, 9) * sizeof(unsigned long long), 0,
                                 sizeof(unsigned long long), s);
             cudaEventRecord(a, s);
             if (e == cudaSuccess) e = run_wave_synth(*P, 0, s, sample);
@@ -577,6 +635,12 @@ int batch_variant(const BatchPlan *P) { return P->variant; }
 void batch_set_variant(BatchPlan *P, int v) { P->variant = v; }
 int batch_chunk(const BatchPlan *P, int k) { return P->host[k].tg.chunk; }
 size_t batch_bytes(const BatchPlan *P) { return P->bytes; }
+
+// device address of the last run's redo overflow word (non-zero when a wave queued more FP64 redo
+// steps than its list holds, so that run's H misses their contributions)
+const unsigned long long *batch_redo_overflow(const BatchPlan *P) {
+    return reinterpret_cast<const unsigned long long *>(P->mem + P->off_redo + 16);
+}
 
 // queued FP64 redo steps of the last completed run, all waves (a wave's count may exceed its list's
 // capacity; the total counts every queued step)

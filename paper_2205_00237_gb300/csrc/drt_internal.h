@@ -33,6 +33,10 @@ struct BodyD { double o[3], v[3], a[3], k[3], w0, wdot; };
 struct LinkDev {
     int32_t n_paths, n_bodies, n_faces, n_edges, n_tiles, n_mats;
     int32_t n_bulk;   // paths [0, n_bulk) have at most one diffraction per segment (FP32-bulk capable)
+    // among those, paths [len_start[n], len_start[n + 1]) have n vertices (the signature sort groups
+    // them by length); the unrolled kernels take lengths 0..3, paths [len_start[MAXI], n_paths) run the
+    // generic code
+    int32_t len_start[MAXI + 2];
     TermD tx, rx;
     const BodyD *bodies;
     const FaceD *faces;
@@ -113,6 +117,7 @@ void batch_set_variant(BatchPlan *P, int v);
 int batch_chunk(const BatchPlan *P, int k);
 size_t batch_bytes(const BatchPlan *P);
 cudaError_t batch_redo_count(const BatchPlan *P, long long *n, bool *overflow = nullptr);
+const unsigned long long *batch_redo_overflow(const BatchPlan *P);
 int choose_chunk(const drt_scene_view &v, const drt_time_grid &tg, const drt_freq_grid &fg);
 
 // a11 serving loop (drt_serve.cu): one request as the serving thread sees it
@@ -158,10 +163,12 @@ cudaError_t launch_pose(const LinkDev &L, const TimeGridD &tg, double *pose, cud
 // FP64 per-(path, step) kernel over paths [p0, p1); f32out selects the FP32-bulk output formats
 // warm != nullptr: a pre-pass fills warm (warm_bytes) with per-chunk Newton starts for the paths
 // [n_bulk, n_paths) first
+// multi-diffraction chains [n_bulk, n_paths) run in a launch of their own on s_multi (null: on s; the
+// caller orders s_multi after the warm starts and joins it back)
 cudaError_t launch_extrapolate_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg,
                                     const double *pose, const OutD &out, const RecD &rec,
                                     cudaStream_t s, int p0 = 0, int p1 = -1, bool f32out = false,
-                                    double *warm = nullptr);
+                                    double *warm = nullptr, cudaStream_t s_multi = nullptr);
 size_t warm_bytes(const LinkDev &L, const TimeGridD &tg);
 // the warm-start table of the multi-diffraction chains (FP64 dual-number solves at the chunk bases)
 // edge parameters and rates at t = 0 of the multi-diffraction paths (LinkDev::t0par), at load
@@ -182,7 +189,7 @@ cudaError_t launch_base_paths(const LinkDev &L, const TimeGridD &tg, const FreqG
 // the redo scratch holds an int counter (zeroed here, on the stream) followed by the (path, step) list
 cudaError_t launch_extrapolate_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const void *poseb,
                                     const void *base, const double *warm, const OutD &out, const RecD &rec,
-                                    void *redo, cudaStream_t s);
+                                    void *redo, cudaStream_t s, cudaStream_t s_multi = nullptr);
 cudaError_t launch_redo(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const OutD &out, const RecD &rec,
                         void *redo, const double *warm, cudaStream_t s);
 // the redo for an H synthesis: (Re a, Im a, tau) per queued step into out3 ([cap][3] doubles), then

@@ -1,24 +1,18 @@
-// drt_kernels.cu -- kernels of the DRT hot path on sm_103a:
+// drt_kernels.cu -- kernels of the DRT hot path on sm_103a (the per-(path, step) extrapolation
+// kernels are in drt_k_fp64.cu and drt_k_bulk.cu):
 //   k_pose           a2: per (time-step, body) pose table R(t), O(t), v_O(t), omega(t) (FP64)
-//   k_extrapolate    a3-a8: one thread per (path, time-step); a warp covers 32 consecutive time
-//                    steps of one path, so all its lanes run the same chain signature
-//   k_warm_fp64      warm starts of the multi-diffraction chains at the chunk bases (FP64)
-//   k_pose_bulk, k_base_fp64, k_extrapolate_bulk, k_redo
-//                    FP32-bulk form: FP32 base poses and FP64 path-length / phase anchors per
-//                    16-step chunk, FP32 delta-number geometry and field per (path, step), FP64
-//                    redo of the steps FP32 cannot resolve
+//   k_power_bin      power-Doppler / power-delay profiles
+//   k_step_power, k_toggle, k_select, k_window_mask
+//                    multipath-lifetime expiry and T_C windows
 //   k_synth          a9: H(t, f) = sum_p a_p exp(-j 2 pi f tau_p); one thread per (time-step,
 //                    16-bin frequency tile, path group), sincos seed per tile and a complex
 //                    rotation recurrence inside it, FP32 FMA accumulation, groups added in
 //                    shared memory
 //   k_probe          FMA issue-rate probe for the roofline denominators
 #include <algorithm>
-#include "drt_internal.h"
-#include "drt_physics.cuh"
+#include "drt_launch.cuh"
 
 namespace drt {
-
-DRT_HD int n_chunks_of(const TimeGridD &tg) { return (tg.n_steps + tg.chunk - 1) / tg.chunk; }
 
 // ------------------------------------------------------------------------------------------------
 // a2: poses.  theta(t) = w0 t + wdot t^2 / 2 about the fixed axis k (Rodrigues), O(t) by Eq. Taylor,
@@ -35,242 +29,6 @@ cudaError_t launch_pose(const LinkDev &L, const TimeGridD &tg, double *pose, cud
     int n = tg.n_steps * L.n_bodies;
     if (n == 0) return cudaSuccess;
     k_pose<<<(n + 255) / 256, 256, 0, s>>>(L.bodies, L.n_bodies, tg.t_start, tg.dt, tg.n_steps, pose);
-    return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------------------------------------
-// a3-a8 in FP64.  A block covers 128 consecutive time steps of ONE path, so every lane of a warp
-// runs the same chain signature (no type divergence); branches that remain (validity, Newton
-// iteration counts, transition-function ranges) are correlated between neighbouring instants.
-constexpr int EXT_T = 128;
-
-template <bool DUAL>
-__global__ void __launch_bounds__(EXT_T)
-k_extrapolate_fp64(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const double *__restrict__ pose,
-                   const OutD out, const RecD rec, int p0, int f32out, const double *__restrict__ warm) {
-    int p = p0 + blockIdx.x;
-    int ti = blockIdx.y * EXT_T + threadIdx.x;
-    if (p >= L.n_paths || ti >= tg.n_steps) return;
-    path_step_fp64<DUAL>(L, tg, fg, pose, p, ti, out, rec, f32out != 0, warm);
-}
-
-// warm-start pre-pass over (multi-diffraction path, chunk)
-constexpr int WARM_T = 32;
-__global__ void __launch_bounds__(WARM_T)
-k_warm_fp64(const LinkDev L, const TimeGridD tg, double *__restrict__ warm) {
-    int p = L.n_bulk + blockIdx.x;
-    int c = blockIdx.y * WARM_T + threadIdx.x;
-    if (p >= L.n_paths || c > n_chunks_of(tg)) return;   // rows 0..n_chunks
-    path_warm_fp64(L, tg, p, c, warm);
-}
-
-__global__ void __launch_bounds__(32) k_t0par(const LinkDev L, double *__restrict__ t0par) {
-    const int p = L.n_bulk + blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= L.n_paths) return;
-    path_t0par_fp64(L, p, t0par + (size_t)(p - L.n_bulk) * (2 * MAXI));
-}
-
-cudaError_t launch_t0par(const LinkDev &L, double *t0par, cudaStream_t s) {
-    const int n = L.n_paths - L.n_bulk;
-    if (n <= 0) return cudaSuccess;
-    k_t0par<<<(n + 31) / 32, 32, 0, s>>>(L, t0par);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_warm_fp64(const LinkDev &L, const TimeGridD &tg, double *warm, cudaStream_t s) {
-    if (!warm || L.n_bulk >= L.n_paths || tg.n_steps == 0) return cudaSuccess;
-    dim3 gw(L.n_paths - L.n_bulk, (n_chunks_of(tg) + 1 + WARM_T - 1) / WARM_T);
-    k_warm_fp64<<<gw, WARM_T, 0, s>>>(L, tg, warm);
-    return cudaGetLastError();
-}
-
-size_t warm_bytes(const LinkDev &L, const TimeGridD &tg) {
-    return (size_t)(L.n_paths - L.n_bulk) * (n_chunks_of(tg) + 1) * 2 * MAXI * sizeof(double);
-}
-
-cudaError_t launch_extrapolate_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg,
-                                    const double *pose, const OutD &out, const RecD &rec, cudaStream_t s, int p0,
-                                    int p1, bool f32out, double *warm) {
-    if (p1 < 0) p1 = L.n_paths;
-    if (p1 <= p0 || tg.n_steps == 0) return cudaSuccess;
-    dim3 grid(p1 - p0, (tg.n_steps + EXT_T - 1) / EXT_T);
-    // the Doppler shift needs the interaction points' velocities (dual numbers); nothing else does
-    if (out.doppler) k_extrapolate_fp64<true><<<grid, EXT_T, 0, s>>>(L, tg, fg, pose, out, rec, p0, f32out ? 1 : 0, warm);
-    else k_extrapolate_fp64<false><<<grid, EXT_T, 0, s>>>(L, tg, fg, pose, out, rec, p0, f32out ? 1 : 0, warm);
-    return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------------------------------------
-// FP32-bulk form: base poses per (body or terminal, chunk), FP64 anchors per (path, chunk), then
-// the per-(path, step) delta-number kernel with the same block mapping as the FP64 form
-size_t bulk_pose_bytes(const LinkDev &L, const TimeGridD &tg) {
-    return (size_t)(L.n_bodies + 2) * n_chunks_of(tg) * sizeof(PoseB);
-}
-size_t bulk_base_bytes(const LinkDev &L, const TimeGridD &tg) {
-    return (size_t)L.n_paths * n_chunks_of(tg) * sizeof(BaseRec);
-}
-
-__global__ void k_pose_bulk(const BodyD *__restrict__ bodies, int n_bodies, TermD tx, TermD rx, double t_start,
-                            double dt, int n_chunks, int chunk, PoseB *__restrict__ poseb) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (n_bodies + 2) * n_chunks) return;
-    int b = i / n_chunks, c = i - b * n_chunks;
-    double tb = t_start + (double)c * chunk * dt;
-    if (b < n_bodies) body_pose_base(bodies[b], tb, poseb[i]);
-    else terminal_base(b == n_bodies ? tx : rx, tb, poseb[i]);
-}
-
-cudaError_t launch_pose_bulk(const LinkDev &L, const TimeGridD &tg, void *poseb, cudaStream_t s) {
-    int n = (L.n_bodies + 2) * n_chunks_of(tg);
-    if (tg.n_steps == 0) return cudaSuccess;
-    k_pose_bulk<<<(n + 127) / 128, 128, 0, s>>>(L.bodies, L.n_bodies, L.tx, L.rx, tg.t_start, tg.dt, n_chunks_of(tg),
-                                                tg.chunk, reinterpret_cast<PoseB *>(poseb));
-    return cudaGetLastError();
-}
-
-size_t bulk_pose64_bytes(const LinkDev &L, const TimeGridD &tg) {
-    return (size_t)L.n_bodies * n_chunks_of(tg) * POSE_W * sizeof(double);
-}
-size_t bulk_redo_bytes(const LinkDev &L, const TimeGridD &tg) {
-    return 256 + (size_t)L.n_paths * tg.n_steps * sizeof(int4);
-}
-
-// one block per path, one thread per chunk: lanes share the chain signature; body poses at the
-// chunk bases come from an FP64 pose table [body][chunk] built first
-constexpr int BASE_T = 64;
-__global__ void __launch_bounds__(BASE_T)
-k_base_fp64(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const double *__restrict__ pose64,
-            BaseRec *__restrict__ base, const double *__restrict__ warm, int p0) {
-    int p = p0 + blockIdx.x;
-    int c = blockIdx.y * BASE_T + threadIdx.x;
-    if (p >= L.n_paths || c >= n_chunks_of(tg)) return;
-    path_base_fp64(L, tg, fg, pose64, p, c, base, warm);
-}
-
-cudaError_t launch_base_pose64(const LinkDev &L, const TimeGridD &tg, double *pose64, cudaStream_t s) {
-    if (L.n_paths == 0 || tg.n_steps == 0) return cudaSuccess;
-    TimeGridD tc = make_tgrid(tg.t_start, tg.dt * tg.chunk, n_chunks_of(tg), 1);   // chunk bases
-    return launch_pose(L, tc, pose64, s);
-}
-
-// anchors of paths [p0, p1); the multi-diffraction paths [n_bulk, n_paths) read the warm starts
-cudaError_t launch_base_paths(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const double *pose64,
-                              void *base, const double *warm, int p0, int p1, cudaStream_t s) {
-    if (p1 <= p0 || tg.n_steps == 0) return cudaSuccess;
-    dim3 grid(p1 - p0, (n_chunks_of(tg) + BASE_T - 1) / BASE_T);
-    k_base_fp64<<<grid, BASE_T, 0, s>>>(L, tg, fg, pose64, reinterpret_cast<BaseRec *>(base), warm, p0);
-    return cudaGetLastError();
-}
-
-static RedoList redo_list(void *redo, const LinkDev &L, const TimeGridD &tg) {
-    RedoList r;
-    r.count = reinterpret_cast<int *>(redo);
-    r.items = reinterpret_cast<int4 *>(reinterpret_cast<char *>(redo) + 256);
-    r.cap = L.n_paths * tg.n_steps;
-    return r;
-}
-
-// at most 128 registers (4 blocks of 4 warps per SM): the latency-bound FP32 step gains more from
-// the extra warps than it loses to spills (2048-path link 1.47 -> 1.12 ms, canyon within 3 %)
-template <bool DUAL>
-__global__ void __launch_bounds__(EXT_T, 4)
-k_extrapolate_bulk(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const PoseB *__restrict__ poseb,
-                   const BaseRec *__restrict__ base, const double *__restrict__ warm, const OutD out, const RecD rec,
-                   const RedoList redo) {
-    int p = blockIdx.y;   // time-major block order: an SM's resident blocks are nearby paths (signatures)
-    int ti = blockIdx.x * EXT_T + threadIdx.x;
-    if (p >= L.n_paths || ti >= tg.n_steps) return;
-    if constexpr (DUAL) path_step_bulk<dd>(L, tg, fg, poseb, base, warm, p, ti, out, rec, redo);
-    else path_step_bulk<de>(L, tg, fg, poseb, base, warm, p, ti, out, rec, redo);
-}
-
-cudaError_t launch_extrapolate_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const void *poseb,
-                                    const void *base, const double *warm, const OutD &out, const RecD &rec, void *redo,
-                                    cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(redo, 0, sizeof(int), s);
-    if (e != cudaSuccess) return e;
-    if (L.n_paths == 0 || tg.n_steps == 0) return cudaSuccess;
-    dim3 grid((tg.n_steps + EXT_T - 1) / EXT_T, L.n_paths);
-    const PoseB *pb = reinterpret_cast<const PoseB *>(poseb);
-    const BaseRec *bs = reinterpret_cast<const BaseRec *>(base);
-    // rates (dual parts) only when the Doppler shift is asked for
-    if (out.doppler) k_extrapolate_bulk<true><<<grid, EXT_T, 0, s>>>(L, tg, fg, pb, bs, warm, out, rec, redo_list(redo, L, tg));
-    else k_extrapolate_bulk<false><<<grid, EXT_T, 0, s>>>(L, tg, fg, pb, bs, warm, out, rec, redo_list(redo, L, tg));
-    return cudaGetLastError();
-}
-
-// FP64 redo of the queued path-steps: a fixed grid strides over the device-side count
-// one warp per block: the few queued steps spread over all SMs (each is a long FP64 chain)
-__global__ void __launch_bounds__(32)
-k_redo(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const OutD out, const RecD rec, const RedoList redo,
-       const double *__restrict__ warm) {
-    int n = min(*redo.count, redo.cap);
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        int4 it = redo.items[k];
-        path_step_redo(L, tg, fg, it.y, it.z, out, rec, warm);
-    }
-}
-
-cudaError_t launch_redo(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const OutD &out, const RecD &rec,
-                        void *redo, const double *warm, cudaStream_t s) {
-    if (L.n_paths == 0 || tg.n_steps == 0) return cudaSuccess;
-    k_redo<<<152 * 8, 32, 0, s>>>(L, tg, fg, out, rec, redo_list(redo, L, tg), warm);
-    return cudaGetLastError();
-}
-
-// The same redo beside the H synthesis: each queued step's (Re a, Im a, tau) goes to out3 (its record
-// keeps a = 0, so the synthesis skips it), and k_redo_add then adds a exp(-j 2 pi f tau) into H
-__global__ void __launch_bounds__(32)
-k_redo_rec(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const RedoList redo, const double *__restrict__ warm,
-           double *__restrict__ out3) {
-    const int n = min(*redo.count, redo.cap);
-    const OutD none{};
-    const RecD nor{nullptr, nullptr};
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        int4 it = redo.items[k];
-        path_step_redo(L, tg, fg, it.y, it.z, none, nor, warm, out3 + 3 * (size_t)k);
-    }
-}
-
-// one thread per (queued step, 16-bin tile): FP64-reduced seed, FP32 rotation across the tile
-__global__ void __launch_bounds__(128)
-k_redo_add(const FreqGridD fg, const RedoList redo, const double *__restrict__ in3, float2 *__restrict__ H, int ld) {
-    const int n = min(*redo.count, redo.cap);
-    const int F = fg.n_bins, ntile = (F + 15) / 16;
-    const double f0 = fg.fc - 0.5 * fg.bandwidth, df = fg.bandwidth / F;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < (long long)n * ntile;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(q / ntile), k0 = (int)(q % ntile) * 16;
-        const double ar = in3[3 * (size_t)k], ai = in3[3 * (size_t)k + 1], tau = in3[3 * (size_t)k + 2];
-        if (ar == 0.0 && ai == 0.0) continue;
-        float2 *row = H + (size_t)redo.items[k].z * ld;
-        double x = (f0 + k0 * df) * tau, xs = df * tau;
-        float sn, cs, ws, wc;
-        sincospif(2.f * (float)(x - floor(x)), &sn, &cs);
-        sincospif(2.f * (float)(xs - floor(xs)), &ws, &wc);
-        float zr = fmaf((float)ar, cs, (float)ai * sn), zi = fmaf((float)ai, cs, -(float)ar * sn);
-        for (int j = 0; j < 16 && k0 + j < F; ++j) {
-            atomicAdd(&row[k0 + j].x, zr);
-            atomicAdd(&row[k0 + j].y, zi);
-            const float nr = fmaf(zr, wc, zi * ws);
-            zi = fmaf(zi, wc, -zr * ws);
-            zr = nr;
-        }
-    }
-}
-
-cudaError_t launch_redo_rec(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, void *redo, const double *warm,
-                            double *out3, cudaStream_t s) {
-    if (L.n_paths == 0 || tg.n_steps == 0) return cudaSuccess;
-    k_redo_rec<<<152 * 8, 32, 0, s>>>(L, tg, fg, redo_list(redo, L, tg), warm, out3);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_redo_add(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, void *redo, const double *in3,
-                            float2 *H, cudaStream_t s, int ld) {
-    if (L.n_paths == 0 || tg.n_steps == 0) return cudaSuccess;
-    if (ld < 0) ld = fg.n_bins;
-    k_redo_add<<<152 * 4, 128, 0, s>>>(fg, redo_list(redo, L, tg), in3, H, ld);
     return cudaGetLastError();
 }
 

@@ -366,9 +366,10 @@ DRT_OUTLINE void multi_diffraction(const Prim<S> *pr, v3<S> *V, int a, int b, co
         }
 }
 
-// geometry of one path-step: vertices V[0..n+1] (TX, interaction points, RX) with velocities
+// geometry of one path-step, any chain: vertices V[0..n+1] (TX, interaction points, RX) with velocities;
+// segments between point sources are found at run time, so the arrays are indexed dynamically
 template <class S>
-DRT_HD void solve_geometry(const Prim<S> *pr, int n, v3<S> *V, const double *s0, uint32_t &fl,
+DRT_HD void solve_geometry_generic(const Prim<S> *pr, int n, v3<S> *V, const double *s0, uint32_t &fl,
                            const double *ds0 = nullptr, const double *rate0 = nullptr) {
     for (int i = 1; i <= n; ++i)
         if (pr[i - 1].type == T_S) V[i] = pr[i - 1].p;   // Sec. III-C: tile centroid moves rigidly
@@ -398,6 +399,73 @@ DRT_HD void solve_geometry(const Prim<S> *pr, int n, v3<S> *V, const double *s0,
     }
 }
 
+// The same geometry for a chain of N vertices (N known at compile time) with at most one diffraction
+// between point sources, the class of nearly every chain: every vertex loop unrolls with constant
+// indices, so positions and images stay in registers, and nothing is called out of line.
+template <int N, class S>
+DRT_HD void solve_geometry_fast(const Prim<S> *pr, v3<S> *V, uint32_t &fl) {
+    static_assert(N >= 0 && N <= MAXI, "chain length");
+    bool has_d = false;
+#pragma unroll
+    for (int i = 1; i <= N; ++i) {
+        if (pr[i - 1].type == T_S) V[i] = pr[i - 1].p;   // Sec. III-C: tile centroid moves rigidly
+        has_d = has_d || pr[i - 1].type == T_D;
+    }
+    v3<S> img[N > 0 ? N : 1];
+    if (has_d) {
+        // a diffraction point lies on the Keller cone between its virtual source (the segment's left
+        // point source imaged through the reflections in between) and its virtual receiver (the right
+        // point source imaged backwards through the reflections after it)
+        v3<S> cur = V[0];
+#pragma unroll
+        for (int i = 1; i <= N; ++i) {
+            const Prim<S> &q = pr[i - 1];
+            if (q.type == T_D) img[i - 1] = cur;
+            else if (q.type == T_R) cur = mirror(cur, q.p, q.a);
+            else cur = V[i];
+        }
+        cur = V[N + 1];
+#pragma unroll
+        for (int i = N; i >= 1; --i) {
+            const Prim<S> &q = pr[i - 1];
+            if (q.type == T_D) V[i] = q.p + q.a * keller_s(img[i - 1], cur, q, fl);
+            else if (q.type == T_R) cur = mirror(cur, q.p, q.a);
+            else cur = V[i];
+        }
+    }
+    // reflection points by back-tracking (Sec. III-A.2) between the known points (point sources and
+    // diffraction points): a wall's source image is the last known point imaged through the walls
+    // before it; the points are placed from the right, each by Eq. ref_point towards the point placed
+    // before it
+    v3<S> cur = V[0];
+#pragma unroll
+    for (int i = 1; i <= N; ++i) {
+        const Prim<S> &q = pr[i - 1];
+        if (q.type == T_R) {
+            img[i - 1] = cur;
+            cur = mirror(cur, q.p, q.a);
+        } else {
+            cur = V[i];
+        }
+    }
+    v3<S> next = V[N + 1];
+#pragma unroll
+    for (int i = N; i >= 1; --i) {
+        const Prim<S> &q = pr[i - 1];
+        if (q.type == T_R) V[i] = refl_point(img[i - 1], next, q.p, q.a);
+        next = V[i];
+    }
+}
+
+// N >= 0 and !MULTI: the unrolled solver; otherwise (N < 0: length known at run time, or chains with
+// several diffractions in a segment) the generic one
+template <int N, bool MULTI, class S>
+DRT_HD void solve_geometry(const Prim<S> *pr, int n, v3<S> *V, const double *s0, uint32_t &fl,
+                           const double *ds0 = nullptr, const double *rate0 = nullptr) {
+    if constexpr (N >= 0 && !MULTI) solve_geometry_fast<N>(pr, V, fl);
+    else solve_geometry_generic(pr, n, V, s0, fl, ds0, rate0);
+}
+
 template <class T> DRT_HD T wrap2pi(T x) {
     x = fmod(x, T(2 * PI));
     return x < T(0) ? x + T(2 * PI) : x;
@@ -405,27 +473,60 @@ template <class T> DRT_HD T wrap2pi(T x) {
 
 // validity (Sec. II: the t0 multipath structure still holds): reflection points inside their
 // faces with both neighbours in front, diffraction points on their edge segments with both
-// neighbours in the wedge exterior, tiles lit from and seen from the front
-template <class S>
+// neighbours in the wedge exterior, tiles lit from and seen from the front.
+// In FP32 (the FP32-bulk form) the positions carry rounding errors of a few ulp of the coordinates,
+// amplified a little by the image construction, so a decision whose margin (the distance of the tested
+// point from the face rim, the edge end, the face plane or the wedge face) is within a bound on that
+// error is not taken here: the step gets F_REDO64 and the FP64 redo decides it, which makes the flags
+// of the form exact outside the 1e-9 m band of the FP64 form.
+template <class T> DRT_HD T amax3(v3<T> a) { return fmax(fmax(fabs(a.x), fabs(a.y)), fabs(a.z)); }
+// bound on the FP32 error of a margin computed from positions of magnitude `scale` (m): 2e-6 of the
+// scale is ~17 ulp of the largest coordinate; the FP32 flags of the canyon, link and highway workloads
+// were found exact outside 1e-4 m of every boundary without this test (coordinates up to ~600 m)
+DRT_HD float fp32_margin_tol(float scale) { return 2e-6f * (scale + 1.f); }
+
+// Vertex loops run over a fixed bound (MAXI) and stop at the chain length, so their array indices
+// are constants after unrolling and the arrays stay in registers; N >= 0 fixes the length at compile
+// time (shorter code), N < 0 takes the run-time n.
+template <int N = -1, class S>
 DRT_HD uint32_t validity(const Prim<S> *pr, int n, const v3<typename ST<S>::R> *P) {
     typedef typename ST<S>::R T;
+    constexpr bool F32 = sizeof(T) == 4;
+    const int nv = N >= 0 ? N : n;
     uint32_t fl = 0;
-    for (int i = 1; i <= n + 1; ++i) {
+    bool near = false;   // FP32 only: some margin within the error bound
+#pragma unroll
+    for (int i = 1; i <= MAXI + 1; ++i) {
+        if (i > nv + 1) break;
         v3<T> d = P[i] - P[i - 1];
         if (!(dot(d, d) >= T(1e-18))) fl |= F_DEGEN;
     }
-    for (int i = 1; i <= n; ++i) {
+#pragma unroll
+    for (int i = 1; i <= MAXI; ++i) {
+        if (i > nv) break;
         const Prim<S> &q = pr[i - 1];
         if (q.type == T_R) {
             v3<T> c = val(q.p), nn = val(q.a);
             v3<T> r = P[i] - c;
             T al = dot(r, q.b), be = dot(r, cross(q.b, nn));
             if (fabs(al) > q.h1 || fabs(be) > q.h2) fl |= F_FACE;
-            if (!(dot(P[i - 1] - c, nn) > T(0)) || !(dot(P[i + 1] - c, nn) > T(0))) fl |= F_SIDE;
+            const T dp = dot(P[i - 1] - c, nn), dn = dot(P[i + 1] - c, nn);
+            if (!(dp > T(0)) || !(dn > T(0))) fl |= F_SIDE;
+            if constexpr (F32) {
+                const T tol = fp32_margin_tol(fmax(fmax(amax3(P[i - 1]), amax3(P[i + 1])), fmax(amax3(P[i]), amax3(c))));
+                near = near || fabs(fabs(al) - q.h1) < tol || fabs(fabs(be) - q.h2) < tol || fabs(dp) < tol ||
+                       fabs(dn) < tol;
+            }
         } else if (q.type == T_D) {
             v3<T> A = val(q.p), e = val(q.a);
             T s = dot(P[i] - A, e);
             if (s < T(0) || s > q.h1) fl |= F_EDGE;
+            T tol = T(0);
+            if constexpr (F32) {
+                tol = fp32_margin_tol(fmax(fmax(amax3(P[i - 1]), amax3(P[i + 1])), fmax(amax3(P[i]), amax3(A))));
+                near = near || fabs(s) < tol || fabs(q.h1 - s) < tol;
+            }
+#pragma unroll
             for (int side = -1; side <= 1; side += 2) {
                 // the neighbour's direction about the edge, at angle phi from the 0-face tangent
                 // towards the 0-face normal, must lie in the exterior (0, n pi), 1 <= n <= 2: phi in
@@ -435,17 +536,25 @@ DRT_HD uint32_t validity(const Prim<S> *pr, int n, const v3<typename ST<S>::R> *
                 v3<T> rp = r - e * dot(r, e);
                 const T y = dot(rp, q.c), x = dot(rp, q.b);
                 bool in = y > T(0);
+                const T sn = q.h3 * x - q.h4 * y;   // r sin(n pi - phi): distance from the n-face plane
                 if (!in && !(y == T(0) && x >= T(0))) {
-                    const T sn = q.h3 * x - q.h4 * y, cs = q.h4 * x + q.h3 * y;   // r sin, r cos of (n pi - phi)
+                    const T cs = q.h4 * x + q.h3 * y;   // r cos(n pi - phi)
                     in = sn > T(0) || (sn == T(0) && cs < T(0));
                 }
                 if (!in) fl |= F_SIDE;
+                if constexpr (F32) near = near || fabs(y) < tol || fabs(sn) < tol;
             }
         } else {
             v3<T> nn = val(q.a);
-            if (!(dot(P[i - 1] - P[i], nn) > T(0)) || !(dot(P[i + 1] - P[i], nn) > T(0))) fl |= F_SIDE;
+            const T dp = dot(P[i - 1] - P[i], nn), dn = dot(P[i + 1] - P[i], nn);
+            if (!(dp > T(0)) || !(dn > T(0))) fl |= F_SIDE;
+            if constexpr (F32) {
+                const T tol = fp32_margin_tol(fmax(fmax(amax3(P[i - 1]), amax3(P[i + 1])), amax3(P[i])));
+                near = near || fabs(dp) < tol || fabs(dn) < tol;
+            }
         }
     }
+    if (near) fl |= F_REDO64;
     return fl;
 }
 
@@ -682,53 +791,105 @@ template <class T> DRT_HD v3<T> vertical_pol(v3<T> k) {
     return unit(p);
 }
 
-// complex amplitude a_p excluding exp(-j k d): (lambda / 4 pi) x ray spreading (1/length per
-// segment between point sources; UTD sqrt(s'/(s(s'+s))) per diffraction) x polarimetric chain of
-// Fresnel / UTD / ER factors; TX and RX vertically polarised.
-template <class S, class T = typename ST<S>::R>
+// complex amplitude a_p excluding exp(-j k d): (lambda / 4 pi) x ray spreading x polarimetric chain of
+// Fresnel / UTD / ER factors; TX and RX vertically polarised.  seg[1..n+1] are the segment vectors.
+// Spreading and UTD distance parameters per stretch between point sources (TX, tiles, RX), after
+// Kouyoumjian-Pathak: spherical from a point source; an edge-diffracted ray spreads as
+// sqrt(rho_e / (s (rho_e + s))) to the next diffraction or point source at s, rho_e being the
+// incident wavefront's radius of curvature in the plane of the incident ray and the edge (the distance
+// from the source for a spherical wave; after a diffraction the principal radii are the distance from
+// the edge along e x k_out and rho_e + distance, carried through planar reflections with mirrored
+// directions, so Euler's formula gives rho_e at a second diffraction); the distance parameter is
+// L = s (rho_e + s) rho1 rho2 sin^2 b0 / (rho_e (rho1 + s)(rho2 + s)), s s' sin^2 b0 / (s + s') for a
+// spherical incident wave.  Loops run over the fixed bound MAXI (see validity).
+template <int N = -1, class S, class T = typename ST<S>::R>
 DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *seg, T fc) {
+    const int nv = N >= 0 ? N : n;
     v3<T> kd[MAXI + 2];
     T len[MAXI + 2];
-    for (int i = 1; i <= n + 1; ++i) {
+#pragma unroll
+    for (int i = 1; i <= MAXI + 1; ++i) {
+        if (i > nv + 1) break;
         const T q = dot(seg[i], seg[i]), rs = rsqrt(q);   // one reciprocal square root per segment
         len[i] = q * rs;
         kd[i] = seg[i] * rs;
     }
-    T spread = T(1), sprime[MAXI + 1], sdist[MAXI + 1];
-    int a = 0;
-    for (int b = 1; b <= n + 1; ++b) {
-        if (b <= n && pr[b - 1].type != T_S) continue;
-        int prev = a;
-        T acc = T(0), sp = T(0);
-        for (int i = a + 1; i <= b; ++i) {
-            acc += len[i];
-            if (i == b || pr[i - 1].type == T_D) {
-                if (prev == a) {
-                    spread /= acc;
-                    sp = acc;
-                } else {
-                    sdist[prev] = acc;
-                    sprime[prev] = sp;
-                    spread *= sqrt(sp / (acc * (sp + acc)));
-                    sp = acc;
-                }
-                prev = i;
+    // distance from each diffraction to the next diffraction or point source
+    T snx[MAXI + 1];
+    {
+        T acc = T(0);
+#pragma unroll
+        for (int i = MAXI; i >= 1; --i) {
+            if (i > nv) continue;
+            acc += len[i + 1];
+            const int ty = pr[i - 1].type;
+            if (ty == T_D) {
+                snx[i] = acc;
+                acc = T(0);
+            } else if (ty == T_S) {
                 acc = T(0);
             }
         }
-        a = b;
+    }
+    // spreading and, per diffraction, L / sin^2 b0
+    T spread = T(1), Lfac[MAXI + 1];
+    {
+        T d = T(0), re = T(0);          // distance since the point source or latest diffraction; its rho_e
+        bool after_d = false;
+        v3<T> X1 = V3<T>(T(0), T(0), T(0));   // after a diffraction: direction of its caustic on the edge
+#pragma unroll
+        for (int i = 1; i <= MAXI + 1; ++i) {
+            if (i > nv + 1) break;
+            d += len[i];
+            const int ty = i <= nv ? pr[i - 1].type : T_S;   // the RX ends the last stretch like a source
+            if (ty == T_R) {
+                if (after_d) X1 = mirror_dir(X1, val(pr[i - 1].a));
+                continue;
+            }
+            if (!after_d) spread /= d;
+            else spread *= sqrt(re / (d * (re + d)));
+            if (ty == T_S) {
+                after_d = false;
+                d = T(0);
+                continue;
+            }
+            const v3<T> e = val(pr[i - 1].a);
+            const T s = snx[i];
+            if (!after_d) {   // spherical incident wave: rho1 = rho2 = rho_e = d
+                Lfac[i] = s * d / (s + d);
+                re = d;
+            } else {
+                const v3<T> u = e - kd[i] * dot(e, kd[i]);
+                const T uu = dot(u, u), ux = dot(u, X1);
+                const T cg2 = uu > T(1e-24) ? ux * ux / uu : T(0);
+                const T r1 = d, r2 = re + d;
+                const T rhe = T(1) / (cg2 / r1 + (T(1) - cg2) / r2);
+                Lfac[i] = s * (rhe + s) * r1 * r2 / (rhe * (r1 + s) * (r2 + s));
+                re = rhe;
+            }
+            // the caustic direction is only needed by a later diffraction of the same stretch
+            bool more_d = false;
+#pragma unroll
+            for (int j = i + 1; j <= MAXI; ++j) {
+                if (j > nv || pr[j - 1].type == T_S) break;
+                more_d = more_d || pr[j - 1].type == T_D;
+            }
+            if (more_d) X1 = unit(cross(e, kd[i + 1]));
+            after_d = true;
+            d = T(0);
+        }
     }
     const T k = T(2 * PI) * fc / T(C0);
     const T ieps = T(1) / (T(2 * PI) * fc * T(EPS0));   // eps_c = eps_r - j sigma ieps
-    c3<T> E = {C<T>(T(0), T(0)), C<T>(T(0), T(0)), C<T>(T(0), T(0))};
-    {
-        v3<T> e0 = vertical_pol(kd[1]);
-        E = cscale(e0, C<T>(T(1), T(0)));
-    }
-    for (int i = 1; i <= n; ++i) {
+    c3<T> E = cscale(vertical_pol(kd[1]), C<T>(T(1), T(0)));
+    v3<T> klast = kd[1];
+#pragma unroll
+    for (int i = 1; i <= MAXI; ++i) {
+        if (i > nv) break;
         const Prim<S> &q = pr[i - 1];
         const MatV<T> m = matv<T>(L.mats[q.mat]);
-        v3<T> kin = kd[i], kout = kd[i + 1];
+        const v3<T> kin = kd[i], kout = kd[i + 1];
+        klast = kout;
         if (q.type == T_R) {
             v3<T> nf = val(q.a);
             if (dot(nf, kin) > T(0)) nf = -nf;
@@ -751,7 +912,7 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
             T phip = wrap2pi(atan2(yi, xi));
             T phi = wrap2pi(atan2(yo, xo));
             T sinb0 = norm(cross(kin, e));
-            T Lp = sdist[i] * sprime[i] * sinb0 * sinb0 / (sdist[i] + sprime[i]);
+            const T Lp = Lfac[i] * sinb0 * sinb0;
             T sphip = T(0), snphi = T(0);
             if (!m.pec) {   // Luebbers' face coefficients: sin phi' and sin(n pi - phi) from components
                 const T ri = sqrt(xi * xi + yi * yi), ro = sqrt(xo * xo + yo * yo);
@@ -787,15 +948,19 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
         }
     }
     T lam = T(C0) / fc;
-    return cdot(E, vertical_pol(kd[n + 1])) * (lam / T(4 * PI) * spread);
+    return cdot(E, vertical_pol(klast)) * (lam / T(4 * PI) * spread);
 }
 
 // App. A Eq. doppler_freq: f' = f0 prod_i (c - v_i.k_i) / (c - v_{i-1}.k_i), evaluated without
 // cancellation as f_D = f0 expm1( sum_i log1p(-v_i.k_i / c) - log1p(-v_{i-1}.k_i / c) )
-template <class S, class T = typename ST<S>::R> DRT_HD T doppler(int n, const v3<S> *V, const v3<T> *seg, T fc) {
+template <int N = -1, class S, class T = typename ST<S>::R>
+DRT_HD T doppler(int n, const v3<S> *V, const v3<T> *seg, T fc) {
+    const int nv = N >= 0 ? N : n;
     T acc = T(0);
     const T ic = T(1) / T(C0);
-    for (int i = 1; i <= n + 1; ++i) {
+#pragma unroll
+    for (int i = 1; i <= MAXI + 1; ++i) {
+        if (i > nv + 1) break;
         v3<T> k = unit(seg[i]);
         acc += log1p(-dot(der(V[i]), k) * ic) - log1p(-dot(der(V[i - 1]), k) * ic);
     }
@@ -805,8 +970,8 @@ template <class S, class T = typename ST<S>::R> DRT_HD T doppler(int n, const v3
 // ------------------------------------------------------------------------------------------------
 // one (path, time-step) of the FP64 form: geometry, validity, delay, Doppler, angles, amplitude;
 // user outputs at [ti][perm[p]], synthesis record at [ti][p]
-DRT_HD void write_outputs_fp64(const OutD &o, size_t oi, int n, const v3<double> *P, const v3<double> *seg,
-                               double tau, cx<double> a, double fd, uint32_t fl) {
+DRT_HD void write_outputs_fp64(const OutD &o, size_t oi, int n, const v3<double> *P, v3<double> seg_first,
+                               v3<double> seg_last, double tau, cx<double> a, double fd, uint32_t fl) {
     if (o.tau) o.tau[oi] = tau;
     if (o.amp) {
         double *q = reinterpret_cast<double *>(o.amp) + 2 * oi;
@@ -815,7 +980,7 @@ DRT_HD void write_outputs_fp64(const OutD &o, size_t oi, int n, const v3<double>
     }
     if (o.doppler) reinterpret_cast<double *>(o.doppler)[oi] = fd;
     if (o.angles) {
-        v3<double> kd = unit(seg[1]), ka = -unit(seg[n + 1]);
+        v3<double> kd = unit(seg_first), ka = -unit(seg_last);
         float *q = o.angles + 4 * oi;
         q[0] = (float)atan2(kd.y, kd.x);
         q[1] = (float)atan2(kd.z, hypot(kd.x, kd.y));
@@ -826,6 +991,7 @@ DRT_HD void write_outputs_fp64(const OutD &o, size_t oi, int n, const v3<double>
     if (o.points) {
         double *q = o.points + oi * (MAXI * 3);
         const double qn = nan("");
+#pragma unroll
         for (int j = 0; j < MAXI; ++j) {
             bool in = j < n;
             q[3 * j + 0] = in ? P[j + 1].x : qn;
@@ -889,64 +1055,81 @@ template <> DRT_HD v3<double> terminal_as<double>(const TermD &m, double t) { re
 
 // S = dl<double> carries every position with its time derivative (the interaction points' sliding
 // velocities, which only the Doppler shift needs); S = double runs the same geometry on values
-// alone, for calls that ask for no Doppler output (H synthesis), at about half the FP64 work
-template <class S = dl<double>, class Loader>
+// alone, for calls that ask for no Doppler output (H synthesis), at about half the FP64 work.
+// N >= 0: chains of exactly N vertices with at most one diffraction between point sources (the
+// unrolled solver; every per-vertex array in registers); N < 0: any chain, length read at run time.
+// MULTI: the chain may have several diffractions in a segment (Newton, warm starts).  OUT = false
+// drops the user-output code (calls that only fill synthesis records).
+template <int N = -1, bool MULTI = true, bool OUT = true, class S = dl<double>, class Loader>
 DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, int p, int ti,
                                 const OutD &out, const RecD &rec, bool f32out, Loader load,
                                 const double *warm = nullptr, double *rec64 = nullptr) {
     typedef double T;
     const T t = tg.t_start + ti * tg.dt;
-    uint32_t code = L.ptypes[p];
-    int4 pi = L.pprims[p];
-    int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
+    const uint32_t code = L.ptypes[p];
+    const int4 pi = L.pprims[p];
+    const int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
     int n = 0;
     Prim<S> pr[MAXI];
-    for (int j = 0; j < MAXI; ++j) {
-        int ty = (code >> (8 * j)) & 0xff;
-        if (ty != T_NONE) {
+#pragma unroll
+    for (int j = 0; j < (N >= 0 ? N : MAXI); ++j) {
+        const int ty = (code >> (8 * j)) & 0xff;
+        if (N >= 0 || ty != T_NONE) {
             pr[j] = load(ty, prim[j]);
             n = j + 1;
         }
     }
+    if constexpr (N >= 0) n = N;
     v3<S> V[MAXI + 2];
     V[0] = terminal_as<S>(L.tx, t);
-    V[n + 1] = terminal_as<S>(L.rx, t);
+    if constexpr (N >= 0) V[N + 1] = terminal_as<S>(L.rx, t);
+    else V[n + 1] = terminal_as<S>(L.rx, t);
     uint32_t fl = 0;
-    if (warm && p >= L.n_bulk) {
+    if (MULTI && warm && p >= L.n_bulk) {
         WarmStart ws;
         warm_start_at(L, tg, warm, p, ti, ws);
-        solve_geometry(pr, n, V, ws.s, fl, ws.ds, ws.rate);
+        solve_geometry<N, MULTI>(pr, n, V, ws.s, fl, ws.ds, ws.rate);
     } else {
-        solve_geometry(pr, n, V, L.ps0 + (size_t)p * MAXI, fl);
+        solve_geometry<N, MULTI>(pr, n, V, L.ps0 + (size_t)p * MAXI, fl);
     }
     v3<T> P[MAXI + 2];
-    for (int i = 0; i <= n + 1; ++i) P[i] = val(V[i]);
-    fl |= validity(pr, n, P);
     v3<T> seg[MAXI + 2];
     T d = T(0);
-    for (int i = 1; i <= n + 1; ++i) {
-        seg[i] = P[i] - P[i - 1];
-        d += norm(seg[i]);
+#pragma unroll
+    for (int i = 0; i <= MAXI + 1; ++i) {
+        if (i > n + 1) break;
+        P[i] = val(V[i]);
+        if (i > 0) {
+            seg[i] = P[i] - P[i - 1];
+            d += norm(seg[i]);
+        }
     }
+    fl |= validity<N>(pr, n, P);
     T tau = d / T(C0);
-    cx<T> a = (fl & F_DEGEN) ? C<T>(T(0), T(0)) : amplitude(L, pr, n, seg, T(fg.fc));
-    if (out.tau || out.amp || out.doppler || out.angles || out.flags || out.points) {
-        T fd = 0;
-        if constexpr (!std::is_same<S, double>::value) fd = doppler(n, V, seg, T(fg.fc));
-        size_t oi = (size_t)ti * L.n_paths + L.perm[p];
-        if (f32out) {
-            OutD o2 = out;
-            o2.amp = nullptr;
-            o2.doppler = nullptr;
-            write_outputs_fp64(o2, oi, n, P, seg, tau, a, fd, fl);
-            if (out.amp) {
-                float *q = reinterpret_cast<float *>(out.amp) + 2 * oi;
-                q[0] = (float)a.re;
-                q[1] = (float)a.im;
+    cx<T> a = (fl & F_DEGEN) ? C<T>(T(0), T(0)) : amplitude<N>(L, pr, n, seg, T(fg.fc));
+    if constexpr (OUT) {
+        if (out.tau || out.amp || out.doppler || out.angles || out.flags || out.points) {
+            T fd = 0;
+            if constexpr (!std::is_same<S, double>::value) fd = doppler<N>(n, V, seg, T(fg.fc));
+            const size_t oi = (size_t)ti * L.n_paths + L.perm[p];
+            v3<T> s_last = seg[1];
+#pragma unroll
+            for (int i = 2; i <= MAXI + 1; ++i)
+                if (i == n + 1) s_last = seg[i];
+            if (f32out) {
+                OutD o2 = out;
+                o2.amp = nullptr;
+                o2.doppler = nullptr;
+                write_outputs_fp64(o2, oi, n, P, seg[1], s_last, tau, a, fd, fl);
+                if (out.amp) {
+                    float *q = reinterpret_cast<float *>(out.amp) + 2 * oi;
+                    q[0] = (float)a.re;
+                    q[1] = (float)a.im;
+                }
+                if (out.doppler) reinterpret_cast<float *>(out.doppler)[oi] = (float)fd;
+            } else {
+                write_outputs_fp64(out, oi, n, P, seg[1], s_last, tau, a, fd, fl);
             }
-            if (out.doppler) reinterpret_cast<float *>(out.doppler)[oi] = (float)fd;
-        } else {
-            write_outputs_fp64(out, oi, n, P, seg, tau, a, fd, fl);
         }
     }
     if (rec.rec_a) {
@@ -982,7 +1165,7 @@ DRT_HD void solve_edge_params(const LinkDev &L, int p, double t, const double *s
     V[0] = terminal<T>(L.tx, t);
     V[n + 1] = terminal<T>(L.rx, t);
     uint32_t fl = 0;
-    solve_geometry(pr, n, V, sin, fl);
+    solve_geometry_generic(pr, n, V, sin, fl);
     for (int j = 0; j < MAXI; ++j) {
         sv[j] = sin[j];
         sd[j] = 0.0;
@@ -1204,7 +1387,7 @@ DRT_HD void path_base_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGrid
     uint32_t fl = 0;
     const double *s0 = L.ps0 + (size_t)p * MAXI;
     if (warm && p >= L.n_bulk) s0 = warm_row(L, warm, chunk, p);
-    solve_geometry(pr, n, V, s0, fl);
+    solve_geometry_generic(pr, n, V, s0, fl);
     BaseRec r;
     double d = 0.0;
     for (int i = 0; i <= MAXI; ++i) r.seg[i][0] = r.seg[i][1] = r.seg[i][2] = 0.f;
@@ -1271,8 +1454,8 @@ template <class S> DRT_HD v3<S> terminal_as(const PoseB &q, float tau) {
 }
 
 template <class S>
-DRT_OUTLINE void write_outputs_bulk(const OutD &o, size_t oi, int n, const v3<S> *V, const v3<float> *seg, double tau,
-                               cx<float> a, float fd, uint32_t fl) {
+DRT_HD void write_outputs_bulk(const OutD &o, size_t oi, int n, const v3<S> *V, v3<float> seg_first,
+                               v3<float> seg_last, double tau, cx<float> a, float fd, uint32_t fl) {
     if (o.tau) o.tau[oi] = tau;
     if (o.amp) {
         float *q = reinterpret_cast<float *>(o.amp) + 2 * oi;
@@ -1281,7 +1464,7 @@ DRT_OUTLINE void write_outputs_bulk(const OutD &o, size_t oi, int n, const v3<S>
     }
     if (o.doppler) reinterpret_cast<float *>(o.doppler)[oi] = fd;
     if (o.angles) {
-        v3<float> kd = unit(seg[1]), ka = -unit(seg[n + 1]);
+        v3<float> kd = unit(seg_first), ka = -unit(seg_last);
         float *q = o.angles + 4 * oi;
         q[0] = atan2f(kd.y, kd.x);
         q[1] = atan2f(kd.z, hypotf(kd.x, kd.y));
@@ -1292,6 +1475,7 @@ DRT_OUTLINE void write_outputs_bulk(const OutD &o, size_t oi, int n, const v3<S>
     if (o.points) {
         double *q = o.points + oi * (MAXI * 3);
         const double qn = nan("");
+#pragma unroll
         for (int j = 0; j < MAXI; ++j) {
             bool in = j < n;
             q[3 * j + 0] = in ? (double)V[j + 1].x.b + (double)V[j + 1].x.d : qn;
@@ -1312,8 +1496,8 @@ struct Rec5 { float ar, ai, ph, hi, lo; };
 // Chains with >= 2 diffractions in a segment start their Newton solve from the FP64 chunk-base
 // parameters (warm, may be null for the others).  Returns false when the step was queued for the
 // FP64 redo (its record is then zero).  S = dd carries the rates the Doppler shift needs, S = de
-// (calls without Doppler output) leaves them out.
-template <class S = dd>
+// (calls without Doppler output) leaves them out.  N, MULTI and OUT as for path_step_fp64_core.
+template <int N = -1, bool MULTI = true, bool OUT = true, class S = dd>
 DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const PoseB *poseb,
                       const BaseRec *base, const double *warm, int p, int ti, const OutD &out, Rec5 &rec,
                       const RedoList &redo, int link) {
@@ -1322,32 +1506,40 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
     const int n_chunks = (tg.n_steps + tg.chunk - 1) / tg.chunk;
     const int chunk = ti / tg.chunk;
     const float tau_t = (float)(ti - chunk * tg.chunk) * tg.dtf;
-    uint32_t code = L.ptypes[p];
-    int4 pi = L.pprims[p];
-    int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
+    const uint32_t code = L.ptypes[p];
+    const int4 pi = L.pprims[p];
+    const int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
     int n = 0;
     Prim<S> pr[MAXI];
-    for (int j = 0; j < MAXI; ++j) {
-        int ty = (code >> (8 * j)) & 0xff;
-        if (ty != T_NONE) {
+#pragma unroll
+    for (int j = 0; j < (N >= 0 ? N : MAXI); ++j) {
+        const int ty = (code >> (8 * j)) & 0xff;
+        if (N >= 0 || ty != T_NONE) {
             pr[j] = load_prim_as<S>(L, poseb, n_chunks, chunk, tau_t, ty, prim[j]);
             n = j + 1;
         }
     }
+    if constexpr (N >= 0) n = N;
     v3<S> V[MAXI + 2];
     V[0] = terminal_as<S>(poseb[(size_t)L.n_bodies * n_chunks + chunk], tau_t);
-    V[n + 1] = terminal_as<S>(poseb[(size_t)(L.n_bodies + 1) * n_chunks + chunk], tau_t);
+    const v3<S> rx = terminal_as<S>(poseb[(size_t)(L.n_bodies + 1) * n_chunks + chunk], tau_t);
+    if constexpr (N >= 0) V[N + 1] = rx;
+    else V[n + 1] = rx;
     uint32_t fl = 0;
-    if (warm && p >= L.n_bulk) {
+    if (MULTI && warm && p >= L.n_bulk) {
         WarmStart ws;
         warm_start_at(L, tg, warm, p, ti, ws);
-        solve_geometry(pr, n, V, ws.s, fl, ws.ds, ws.rate);
+        solve_geometry<N, MULTI>(pr, n, V, ws.s, fl, ws.ds, ws.rate);
     } else {
-        solve_geometry(pr, n, V, L.ps0 + (size_t)p * MAXI, fl);
+        solve_geometry<N, MULTI>(pr, n, V, L.ps0 + (size_t)p * MAXI, fl);
     }
     v3<T> P[MAXI + 2];
-    for (int i = 0; i <= n + 1; ++i) P[i] = val(V[i]);
-    fl |= validity(pr, n, P);
+#pragma unroll
+    for (int i = 0; i <= MAXI + 1; ++i) {
+        if (i > n + 1) break;
+        P[i] = val(V[i]);
+    }
+    fl |= validity<N>(pr, n, P);
     {
         // The FP32 bases carry rounding errors of ~1 ulp of the coordinates (~1e-5 m at 100 m),
         // and the delta rules multiply them by the deltas: the phase error grows with how far an
@@ -1355,12 +1547,14 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
         // diffraction point slides fast near grazing).  Steps past 0.8 m at 60 GHz (scaled by
         // 1/fc) are left to the FP64 redo.
         float disp2 = 0.f;
-        for (int i = 1; i <= n; ++i) disp2 = fmaxf(disp2, V[i].x.d * V[i].x.d + V[i].y.d * V[i].y.d + V[i].z.d * V[i].z.d);
-        if (disp2 > fg.disp_lim * fg.disp_lim) fl |= F_REDO64;
-    }
-    {
         bool finite = true;
-        for (int i = 1; i <= n; ++i) finite = finite && isfinite(P[i].x) && isfinite(P[i].y) && isfinite(P[i].z);
+#pragma unroll
+        for (int i = 1; i <= MAXI; ++i) {
+            if (i > n) break;
+            disp2 = fmaxf(disp2, V[i].x.d * V[i].x.d + V[i].y.d * V[i].y.d + V[i].z.d * V[i].z.d);
+            finite = finite && isfinite(P[i].x) && isfinite(P[i].y) && isfinite(P[i].z);
+        }
+        if (disp2 > fg.disp_lim * fg.disp_lim) fl |= F_REDO64;
         if (!finite || (fl & (F_REDO64 | F_NOCONV | F_DEGEN))) {
             // geometry FP32 cannot resolve: queue this path-step for the FP64 redo kernel (rare,
             // see F_REDO64); the list holds every path-step in the worst case
@@ -1384,18 +1578,26 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
     const BaseRec &B = base[(size_t)chunk * L.n_paths + p];
     float dd_len = 0.f;   // change of the path length since the chunk base
     v3<float> seg[MAXI + 2];
-    for (int i = 1; i <= n + 1; ++i) {
+#pragma unroll
+    for (int i = 1; i <= MAXI + 1; ++i) {
+        if (i > n + 1) break;
         v3<S> sv = V[i] - V[i - 1];
         dd_len += norm(sv).d;
         // segment vector: FP64-accurate base + FP32 delta
         seg[i] = V3<float>(B.seg[i - 1][0] + sv.x.d, B.seg[i - 1][1] + sv.y.d, B.seg[i - 1][2] + sv.z.d);
     }
-    cx<T> a = (fl & F_DEGEN) ? C<T>(T(0), T(0)) : amplitude(L, pr, n, seg, fg.fcf);
-    if (out.tau || out.amp || out.doppler || out.angles || out.flags || out.points) {
-        T fd = 0.f;
-        if constexpr (std::is_same<S, dd>::value) fd = doppler(n, V, seg, fg.fcf);
-        size_t oi = (size_t)ti * L.n_paths + L.perm[p];
-        write_outputs_bulk(out, oi, n, V, seg, (B.d + (double)dd_len) / C0, a, fd, fl);
+    cx<T> a = (fl & F_DEGEN) ? C<T>(T(0), T(0)) : amplitude<N>(L, pr, n, seg, fg.fcf);
+    if constexpr (OUT) {
+        if (out.tau || out.amp || out.doppler || out.angles || out.flags || out.points) {
+            T fd = 0.f;
+            if constexpr (std::is_same<S, dd>::value) fd = doppler<N>(n, V, seg, fg.fcf);
+            const size_t oi = (size_t)ti * L.n_paths + L.perm[p];
+            v3<float> s_last = seg[1];
+#pragma unroll
+            for (int i = 2; i <= MAXI + 1; ++i)
+                if (i == n + 1) s_last = seg[i];
+            write_outputs_bulk(out, oi, n, V, seg[1], s_last, (B.d + (double)dd_len) / C0, a, fd, fl);
+        }
     }
     const float f0c = fg.f0c, dfc = fg.dfc;
     float x = f0c * dd_len;
@@ -1410,12 +1612,12 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
     return true;
 }
 
-template <class S = dd>
+template <int N = -1, bool MULTI = true, bool OUT = true, class S = dd>
 DRT_HD void path_step_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const PoseB *poseb,
                            const BaseRec *base, const double *warm, int p, int ti, const OutD &out, const RecD &rec,
                            const RedoList &redo) {
     Rec5 r;
-    bulk_eval<S>(L, tg, fg, poseb, base, warm, p, ti, out, r, redo, 0);
+    bulk_eval<N, MULTI, OUT, S>(L, tg, fg, poseb, base, warm, p, ti, out, r, redo, 0);
     if (rec.rec_a) {
         size_t ri = (size_t)ti * L.n_paths + p;
         rec.rec_a[ri] = make_float4(r.ar, r.ai, r.ph, r.hi);
@@ -1428,34 +1630,40 @@ DRT_HD void path_step_redo(const LinkDev &L, const TimeGridD &tg, const FreqGrid
                            const RecD &rec, const double *warm, double *rec64 = nullptr) {
     const double t = tg.t_start + ti * tg.dt;
     if (out.doppler) {
-        path_step_fp64_core<dl<double>>(
+        path_step_fp64_core<-1, true, true, dl<double>>(
             L, tg, fg, p, ti, out, rec, true, [&](int ty, int idx) { return load_prim_direct<double>(L, t, ty, idx); },
             warm, rec64);
     } else {   // no Doppler output: values only
-        path_step_fp64_core<double>(
+        path_step_fp64_core<-1, true, true, double>(
             L, tg, fg, p, ti, out, rec, true,
             [&](int ty, int idx) { return val_prim(load_prim_direct<double>(L, t, ty, idx)); }, warm, rec64);
     }
 }
 
 // one (path, step) of the FP64 form from the per-step pose table; DUAL = false when no Doppler
-// output is asked for (values only)
-template <bool DUAL>
+// output is asked for (values only); N, MULTI and OUT as for path_step_fp64_core
+template <bool DUAL, int N = -1, bool MULTI = true, bool OUT = true>
 DRT_HD void path_step_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const double *pose, int p,
                            int ti, const OutD &out, const RecD &rec, bool f32out = false,
                            const double *warm = nullptr) {
     if constexpr (DUAL) {
-        path_step_fp64_core<dl<double>>(
+        path_step_fp64_core<N, MULTI, OUT, dl<double>>(
             L, tg, fg, p, ti, out, rec, f32out,
             [&](int ty, int idx) { return load_prim<double>(L, pose, tg.n_steps, ti, ty, idx); }, warm);
     } else {
-        path_step_fp64_core<double>(
+        path_step_fp64_core<N, MULTI, OUT, double>(
             L, tg, fg, p, ti, out, rec, f32out,
             [&](int ty, int idx) {
                 return load_prim_value(L, pose_at(pose, tg.n_steps, prim_body(L, ty, idx), ti), ty, idx);
             },
             warm);
     }
+}
+
+// chain length of path p (vertices before the first empty type byte)
+DRT_HD int chain_length(const LinkDev &L, int p) {
+    const uint32_t c = L.ptypes[p];
+    return (c & 0xffu) == 0 ? 0 : (c & 0xff00u) == 0 ? 1 : (c & 0xff0000u) == 0 ? 2 : (c & 0xff000000u) == 0 ? 3 : 4;
 }
 
 }  // namespace drt

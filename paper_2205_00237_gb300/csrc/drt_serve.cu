@@ -38,6 +38,7 @@ struct Slot {
     BatchPlan *plan = nullptr;
     size_t off = 0, size = 0;
     std::vector<uint64_t> tickets;
+    unsigned long long *overflow = nullptr;   // pinned: the batch's FP64 redo-overflow word, copied behind it
 };
 
 struct Request {
@@ -103,11 +104,14 @@ static void CUDART_CB on_batch_done(void *arg) {
     Slot *sl = static_cast<Slot *>(arg);
     Server *S = sl->srv;
     const double t = now_s();
+    // a wave that queued more FP64 redo steps than its list holds left those steps out of H
+    const drt_status st = (sl->overflow && *sl->overflow) ? DRT_ENOMEM : DRT_OK;
     {
         std::lock_guard<std::mutex> lk(S->m);
         for (uint64_t tk : sl->tickets) {
             auto it = S->reqs.find(tk);
             if (it == S->reqs.end()) continue;
+            if (st != DRT_OK) it->second.res.status = st;
             it->second.res.t_done = t;
             it->second.done = true;
             it->second.item.inflight->fetch_sub(1);
@@ -184,7 +188,7 @@ static void serve_loop(Server *S) {
         BatchPlan *P = nullptr;
         size_t bytes = 0, off = 0;
         size_t n = batch.size();
-        bool placed = false;
+        bool placed = false, build_failed = false;
         while (n > 0) {
             std::vector<const LinkDev *> devs(n);
             std::vector<drt_scene_view> views(n);
@@ -200,7 +204,12 @@ static void serve_loop(Server *S) {
                 Hs[i] = items[i].H;
                 outs[i] = items[i].out;
             }
-            batch_build(devs, views, tgs.data(), fgs.data(), Hs.data(), outs.data(), &P, &bytes);
+            if (batch_build(devs, views, tgs.data(), fgs.data(), Hs.data(), outs.data(), &P, &bytes) != cudaSuccess) {
+                batch_free(P);
+                P = nullptr;
+                build_failed = true;
+                break;
+            }
             {
                 std::lock_guard<std::mutex> lk(S->m);
                 placed = S->arena_take(bytes, &off);
@@ -209,6 +218,11 @@ static void serve_loop(Server *S) {
             batch_free(P);
             P = nullptr;
             n = n > 1 ? n / 2 : 0;
+        }
+        if (build_failed) {   // the planner could not describe this batch: its requests fail
+            fail_requests(S, batch, DRT_EINVAL);
+            S->cv_done.notify_all();
+            continue;
         }
         if (!placed) {
             // with batches in flight: back to the queue until memory frees up; with none, the
@@ -251,8 +265,10 @@ static void serve_loop(Server *S) {
             float ms = 0.f;
             e = batch_autotune(P, slot->stream, &ms);
             variant = batch_variant(P);
-            std::lock_guard<std::mutex> lk(S->m);
-            S->variant_of_bins[F] = variant;
+            if (e == cudaSuccess) {   // a failed tuning run is not remembered
+                std::lock_guard<std::mutex> lk(S->m);
+                S->variant_of_bins[F] = variant;
+            }
         }
         batch_set_variant(P, variant);
         const double t_launch = now_s();
@@ -271,6 +287,9 @@ static void serve_loop(Server *S) {
             S->stats.launches++;
         }
         if (e == cudaSuccess) e = batch_run(P, slot->stream, false);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(slot->overflow, batch_redo_overflow(P), sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, slot->stream);
         if (e == cudaSuccess) e = cudaLaunchHostFunc(slot->stream, on_batch_done, slot);
         if (e != cudaSuccess) {
             cudaStreamSynchronize(slot->stream);
@@ -296,11 +315,17 @@ Server *server_start(int device, void *arena, size_t arena_bytes, int n_slots, i
     for (size_t i = 0; i < S->slots.size(); ++i) {
         S->slots[i].srv = S;
         S->slots[i].index = (int)i;
-        if (cudaStreamCreateWithFlags(&S->slots[i].stream, cudaStreamNonBlocking) != cudaSuccess) {
-            for (size_t j = 0; j < i; ++j) cudaStreamDestroy(S->slots[j].stream);
+        if (cudaStreamCreateWithFlags(&S->slots[i].stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaHostAlloc(reinterpret_cast<void **>(&S->slots[i].overflow), sizeof(unsigned long long),
+                          cudaHostAllocDefault) != cudaSuccess) {
+            for (size_t j = 0; j <= i; ++j) {
+                if (S->slots[j].stream) cudaStreamDestroy(S->slots[j].stream);
+                if (S->slots[j].overflow) cudaFreeHost(S->slots[j].overflow);
+            }
             delete S;
             return nullptr;
         }
+        *S->slots[i].overflow = 0;
     }
     S->stats.arena_bytes = S->arena_bytes;
     S->th = std::thread(serve_loop, S);
@@ -316,7 +341,10 @@ void server_stop(Server *S) {
     }
     S->cv.notify_all();
     S->th.join();
-    for (auto &sl : S->slots) cudaStreamDestroy(sl.stream);
+    for (auto &sl : S->slots) {
+        cudaStreamDestroy(sl.stream);
+        cudaFreeHost(sl.overflow);
+    }
     delete S;
 }
 

@@ -189,6 +189,28 @@ def _dptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _check_buf(X, shape, dtype, device=None, name="H"):
+    """A caller-provided buffer the library writes through a raw pointer: right dtype, contiguous, at
+    least `shape` elements, and on the context's device (device=None: host memory)."""
+    import torch
+    if not isinstance(X, torch.Tensor):
+        raise ValueError(f"{name} must be a torch tensor")
+    if X.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {X.dtype}")
+    if not X.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    need = 1
+    for d in shape:
+        need *= int(d)
+    if X.numel() < need:
+        raise ValueError(f"{name} holds {X.numel()} elements, {need} ({'x'.join(map(str, shape))}) required")
+    if device is None:
+        if X.is_cuda:
+            raise ValueError(f"{name} must be in host memory")
+    elif not X.is_cuda or X.device.index != int(device):
+        raise ValueError(f"{name} must be a CUDA tensor on device {device}")
+
+
 class Context:
     """A device context: owns loaded links, scratch and the HBM budget (drt_create)."""
 
@@ -253,7 +275,10 @@ class Context:
     def batch(self, links, tgrids, fgrids, Hs, precision: int = FP32_BULK) -> "Batch":
         """drt_batch_create: one batched synthesis plan over loaded links; Hs are complex64 CUDA
         tensors [T_i][F_i] (kept referenced by the plan).  Autotunes on the device (synchronous)."""
+        import torch
         n = len(links)
+        for i, (t, f, h) in enumerate(zip(tgrids, fgrids, Hs)):
+            _check_buf(h, (t.n_steps, f.n_bins), torch.complex64, self.device, name=f"Hs[{i}]")
         ids = (C.c_uint64 * n)(*[lk.handle for lk in links])
         tgs = (_TimeGrid * n)(*[_tg(t) for t in tgrids])
         fgs = (_FreqGrid * n)(*[_fg(f) for f in fgrids])
@@ -274,6 +299,8 @@ class Context:
                precision: int = FP32_BULK) -> int:
         """drt_submit: queue one prediction request; H (complex64 CUDA tensor [T][F]) and the optional
         record tensors must stay alive until the request is done.  Returns the ticket."""
+        import torch
+        _check_buf(H, (tg.n_steps, fg.n_bins), torch.complex64, self.device)
         rec = records or {}
         req = _Request(link.handle, _tg(tg), _fg(fg), H.data_ptr(),
                        _Outputs(*(_dptr(rec.get(k)) for k in ("tau", "amp", "doppler", "angles", "flags", "points"))),
@@ -347,6 +374,7 @@ class Link:
         if H is None:
             H = torch.empty((int(tg.n_steps), int(fg.n_bins)), dtype=torch.complex64,
                             device=torch.device("cuda", self.ctx.device))
+        _check_buf(H, (tg.n_steps, fg.n_bins), torch.complex64, self.ctx.device)
         tgs, fgs = _tg(tg), _fg(fg)
         _check(load_library().drt_synthesize_H(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs), _dptr(H),
                                                int(precision), _stream_ptr(stream)))
@@ -357,6 +385,7 @@ class Link:
         import torch
         if H is None:
             H = torch.empty((int(tg.n_steps), int(fg.n_bins)), dtype=torch.complex64, pin_memory=True)
+        _check_buf(H, (tg.n_steps, fg.n_bins), torch.complex64, None)
         tgs, fgs = _tg(tg), _fg(fg)
         _check(load_library().drt_synthesize_H_host(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs),
                                                     _dptr(H), int(precision), _stream_ptr(stream)))
@@ -370,6 +399,7 @@ class Link:
         n_t = -(-int(tg.n_steps) // int(steps_per_bin)) if int(steps_per_bin) > 0 else 0   # the call rejects < 1
         if P is None:
             P = torch.empty((n_t, int(n_bins)), dtype=torch.float64, device=torch.device("cuda", self.ctx.device))
+        _check_buf(P, (n_t, max(int(n_bins), 0)), torch.float64, self.ctx.device, name="P")
         g = _PowerGrid(int(steps_per_bin), int(n_bins), float(x0), float(dx), int(kind), 0)
         tgs, fgs = _tg(tg), _fg(fg)
         _check(load_library().drt_power_profile(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs), C.byref(g),
@@ -399,6 +429,7 @@ class Link:
         if H is None:
             H = torch.empty((int(tg.n_steps), int(fg.n_bins)), dtype=torch.complex64,
                             device=torch.device("cuda", self.ctx.device))
+        _check_buf(H, (tg.n_steps, fg.n_bins), torch.complex64, self.ctx.device)
         st_ = np.ascontiguousarray(np.asarray(starts, dtype=np.int32))
         tgs, fgs = _tg(tg), _fg(fg)
         _check(load_library().drt_synthesize_H_windows(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs),
@@ -413,6 +444,7 @@ class Link:
         if H is None:
             H = torch.empty((int(tg.n_steps), int(fg.n_bins)), dtype=torch.complex64,
                             device=torch.device("cuda", self.ctx.device))
+        _check_buf(H, (tg.n_steps, fg.n_bins), torch.complex64, self.ctx.device)
         tgs, fgs = _tg(tg), _fg(fg)
         _check(load_library().drt_synthesize_H_wideband(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs),
                                                         int(n_sub), _dptr(H), int(precision), _stream_ptr(stream)))
@@ -421,6 +453,8 @@ class Link:
     def synthesize_H_noalloc(self, tg: I.TimeGrid, fg: I.FreqGrid, H, precision: int = FP64, stream=None):
         """drt_synthesize_H_noalloc: the same H as synthesize_H without any device allocation, for
         callers that cannot allocate at call time; H is a caller-provided complex64 CUDA tensor."""
+        import torch
+        _check_buf(H, (tg.n_steps, fg.n_bins), torch.complex64, self.ctx.device)
         tgs, fgs = _tg(tg), _fg(fg)
         _check(load_library().drt_synthesize_H_noalloc(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs),
                                                        _dptr(H), int(precision), _stream_ptr(stream)))

@@ -21,7 +21,7 @@ from test_oracle_pins import wall_scene
 
 pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-BAND = {"fp64": 1e-9, "fp32": 1e-4}
+BAND = {"fp64": 1e-9, "fp32": 1e-9}
 A_TOL = {"fp64": 1e-9, "fp32": 5e-3}
 
 

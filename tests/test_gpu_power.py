@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 # per form: flags band (m), Doppler tolerance (Hz), delay tolerance (relative), amplitude bar
-BARS = {"fp64": (1e-9, 1e-3, 1e-12, 1e-9), "fp32": (1e-4, 0.1, 1e-8, 5e-3)}
+BARS = {"fp64": (1e-9, 1e-3, 1e-12, 1e-9), "fp32": (1e-9, 0.1, 1e-8, 5e-3)}
 
 
 @pytest.fixture(scope="module")

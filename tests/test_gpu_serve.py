@@ -145,3 +145,35 @@ def test_request_larger_than_the_arena_fails_cleanly():
         compare_H_band(Hs.cpu().numpy(), r, fg)
         ctx.serve_stop()
         link.unload()
+
+
+def test_redo_list_overflow_is_reported(monkeypatch):
+    """A batch whose FP64 redo list is too small for the steps FP32 could not resolve leaves their
+    contributions out of H: drt_batch_info says so (DRT_ENOMEM) and the serving loop marks every
+    request of such a batch DRT_ENOMEM instead of DRT_OK.  The list is shrunk to one entry through
+    DRT_BATCH_REDO_CAP (a host-side setting read when a plan is built); with the default list the
+    same request is served with DRT_OK."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_00237_gb300 import drt
+    sc, ps = canyon()
+    tg, fg = I.TimeGrid(0.0, 1e-3, 400), I.FreqGrid(60e9, 1e9, 128)
+    with drt.Context(0) as ctx:
+        link = ctx.load(sc, ps)
+        H = torch.empty((tg.n_steps, fg.n_bins), dtype=torch.complex64, device="cuda")
+        ctx.serve_start(pool_bytes=1 << 30, n_slots=2, max_batch=4)
+        res = ctx.wait(ctx.submit(link, tg, fg, H))
+        assert res["status"] == 0
+        ctx.serve_stop()
+        monkeypatch.setenv("DRT_BATCH_REDO_CAP", "1")
+        with ctx.batch([link], [tg], [fg], [H]) as b:
+            b.run(use_graph=False)
+            with pytest.raises(drt.DrtError) as ei:
+                b.info(redo=True)
+            assert ei.value.code == drt.DRT_ENOMEM
+        ctx.serve_start(pool_bytes=1 << 30, n_slots=2, max_batch=4)
+        res = ctx.wait(ctx.submit(link, tg, fg, H))
+        assert res["status"] == drt.DRT_ENOMEM
+        ctx.serve_stop()
+        link.unload()

@@ -18,7 +18,7 @@ from test_gpu_parity import band_amplitude
 
 pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-BAND = {"fp64": 1e-9, "fp32": 1e-4}
+BAND = {"fp64": 1e-9, "fp32": 1e-9}
 
 
 @pytest.fixture(scope="module")
