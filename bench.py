@@ -6,11 +6,21 @@ vehicles, 512 ray chains of <= 3 interactions (R:D:S = 6:2:2, committed t0 path 
 2000 steps x 0.5 ms, 512 frequency bins over 1 GHz, FP64 form.
 
 One step = one drt_synthesize_H call on the resident link: pose table (a2), extrapolation of every
-(path, time-step) with field coefficients and Doppler (a3-a8), H(t, f) synthesis (a9).
-value = path-timesteps/s over all ranks (each rank runs its own link: weak scaling, no data-path
-collective).  L2 (129 MB) is flushed by a 256 MB write between timed steps, outside the events.
+(path, time-step) with field coefficients (a3-a8), H(t, f) synthesis (a9).  value = path-timesteps/s
+over all ranks (each rank runs its own link: weak scaling, no data-path collective).  L2 (129 MB) is
+flushed by a 256 MB write between timed steps, outside the events.  `error` compares 16 sampled rows
+of the timed run's H with the FP64 oracle.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Beside the headline the JSON line carries: the FP32-bulk form of the same link; the records form
+(drt_extrapolate writing delay, amplitude, Doppler, angles and flags, both forms, with its HBM-write
+roofline and record errors); the tiny 28 GHz case; power profiles, multipath-lifetime windows and
+wideband coefficients; the 4096-link batched form; the large highway batch (64 links x 20300 paths
+x 20000 steps x 1024 bins, 28 and 60 GHz); serving (Poisson arrivals on the canyon link and on 32
+mixed links, at 2000 and 10000 requests/s); the oracle timed on the host cores.  With N ranks the
+batched and highway links are split over the ranks (greedy by path-steps).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-highway]
+                  [--serve-seconds S] [--batch-links L]
 
 --impl reference times the FP64 CPU oracle (the reference implementation of this method here) on
 the host cores on a bounded sample of the same workload.
@@ -39,24 +49,39 @@ UNIT = "path-timesteps/s"
 WORKLOAD = "canyon"
 PATHSET = os.path.join(ROOT, "tests", "golden", "pathset_canyon_seed0.npz")
 
-# Roofline of the dominant kernel (k_extrapolate_fp64, FP64-pipe bound; the H synthesis asks for no
-# Doppler output, so its geometry runs on values).  FP64 FLOPs executed per path-step on this
-# workload (DADD + DMUL + 2 DFMA thread-instructions counted by ncu, see
-# profiles/k_extrapolate_fp64_canyon.md) and the FP64 peak of the GB300 derived from its unit counts:
-# 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz = 1.26 TFLOP/s (no FP64 tensor path is used).  DRAM bytes
-# per launch from the same capture (set to None whenever the kernel changes after the capture).
-FP64_FLOP_PER_PATH_STEP = 1747.0
-FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
-K1_DRAM_BYTES_PER_LAUNCH = 28.32e6
-# the same capture: the FP64 pipe was busy this fraction of the launch (conversions, compares and the
-# division / square-root sequences occupy it without counting as DADD / DMUL / DFMA FLOPs)
+# Roofline constants of the extrapolation kernels, from one ncu capture of one call on this workload
+# (profiles/k_extrapolate_fp64_canyon.md, profiles/k_extrapolate_bulk_canyon.md): FP64 / FP32 FLOPs
+# executed per path-step (DADD + DMUL + 2 DFMA, or FADD + FMUL + 2 FFMA, thread-instructions summed over
+# the call's extrapolation launches), their DRAM bytes and FP64-pipe activity.  They hold for the kernel
+# sources whose hash is KERNEL_HASH; after any change to the sources the bench reports them as null
+# until they are measured again.  FP64 peak of the GB300 derived from its unit counts: 152 SMs x 2
+# DFMA/clk x 2 FLOP x 2.07 GHz = 1.26 TFLOP/s (no FP64 tensor path is used); FP32 peak 152 SMs x 128
+# lanes x 2 FLOP x 2.07 GHz = 80.5 TFLOP/s; 8 FP32 FLOP per synthesis term.
+KERNEL_HASH = "fc9808c975648018"
+FP64_FLOP_PER_PATH_STEP = 1742.0
+K1_DRAM_BYTES_PER_CALL = 10.6e6
 K1_FP64_PIPE_ACTIVE = 0.869
-# FP32-bulk form (profiles/k_extrapolate_bulk_canyon.md, profiles/k_synth_canyon.md): FP32 FLOPs per
-# path-step of k_extrapolate_bulk (FADD + FMUL + 2 FFMA, ncu) and 8 FLOP per synthesis term; FP32
-# peak 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz = 80.5 TFLOP/s
-FP32_FLOP_PER_PATH_STEP = 1733.0
+FP32_FLOP_PER_PATH_STEP = 1783.0
+FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9
 SYNTH_FLOP_PER_TERM = 8.0
+# bytes a call writes per path-step with every record asked for: tau 8 + amp 16 (FP64) / 8 (FP32) +
+# Doppler 8 / 4 + 4 angles 16 + flags 1
+RECORD_BYTES = {"fp64": 49, "fp32_bulk": 37}
+
+
+def kernel_source_hash():
+    """Hash of the library's CUDA sources (the roofline constants above belong to one of them)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2205_00237_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
+                    glob.glob(os.path.join(csrc, "*.h"))):
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -69,11 +94,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-links", type=int, default=4096, help="links of the batched workload (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3)
-    ap.add_argument("--serve-seconds", type=float, default=10.0, help="measured serving window (0: skip)")
-    ap.add_argument("--highway", action="store_true", help="also time the large highway batch (~1 min)")
-    ap.add_argument("--highway-steps", type=int, default=1, help="timed runs of the highway batch")
-    ap.add_argument("--serve-warmup", type=float, default=2.0)
+    ap.add_argument("--serve-seconds", type=float, default=30.0,
+                    help="measured window of the main serving run (canyon links, 2000 req/s; 0: skip serving)")
+    ap.add_argument("--serve-warmup", type=float, default=5.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--serve-high-rate", type=float, default=10000.0,
+                    help="second offered rate, where requests queue behind each other")
+    ap.add_argument("--serve-short-seconds", type=float, default=10.0,
+                    help="window of the other three serving runs (the mixed links, the high rate)")
+    ap.add_argument("--no-highway", action="store_true", help="skip the large highway batch (~1 min)")
+    ap.add_argument("--highway-steps", type=int, default=1, help="timed runs of the highway batch")
     return ap.parse_args()
 
 
@@ -103,6 +133,60 @@ def max_over_ranks(seconds: float, world: int, device=None) -> float:
 def whole_job_rate(units_per_rank: float, world: int, max_seconds: float) -> float:
     """Units all ranks processed divided by the slowest rank's time (weak scaling)."""
     return world * units_per_rank / max_seconds
+
+
+def measured_peaks():
+    """HBM copy bandwidth (GB/s) measured on the GB300s (MEASURED_PEAKS.json beside this file),
+    else the recipe's fallback of one earlier measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except Exception:
+        return 6800.0, "fallback (6.8 TB/s, one earlier GB300 measurement)"
+
+
+def sample_rows(n_steps, n_rows):
+    """n_rows time steps spread evenly over the grid (an arithmetic progression, so the oracle takes
+    them as one time grid)."""
+    stride = max(1, n_steps // n_rows)
+    return np.arange(0, n_steps, stride)[:n_rows], stride
+
+
+def oracle_rows(scene, paths, tg, fc, n_rows, n_threads):
+    import oracle as O
+    rows, stride = sample_rows(tg.n_steps, n_rows)
+    sub = I.TimeGrid(tg.t_start + rows[0] * tg.dt, tg.dt * stride, len(rows))
+    return rows, O.extrapolate(scene, paths, sub, fc, n_threads=n_threads)
+
+
+def h_errors(Hg_rows, r, fg, n_threads):
+    """Errors of sampled H rows against the oracle's H of the same instants: max over rows and bins of
+    |H - H_ref| and of ||H| - |H_ref|| over the row's RMS_f |H_ref| (the |H| bar of 1e-4)."""
+    import oracle as O
+    Href = O.synthesize_H(r, fg, n_threads=n_threads)
+    Hg = np.asarray(Hg_rows, np.complex128)
+    rms = np.sqrt(np.mean(np.abs(Href) ** 2, axis=1, keepdims=True))
+    nz = rms[:, 0] > 0
+    return {"H_rel_max": float((np.abs(Hg - Href)[nz] / rms[nz]).max()) if nz.any() else 0.0,
+            "absH_rel_max": float((np.abs(np.abs(Hg) - np.abs(Href))[nz] / rms[nz]).max()) if nz.any() else 0.0,
+            "rows": int(len(Hg))}
+
+
+def record_errors(g, r, fc):
+    """Per-path-step record errors on sampled rows against the oracle: delay (relative), carrier phase
+    2 pi fc |d tau| (rad) and amplitude (relative) over the valid path-steps, flag mismatches outside
+    the 1e-9 m boundary band."""
+    import oracle as O
+    far = r["margin"] > 1e-9
+    ok = (r["flags"] & (O.F_DEGEN | O.F_SIDE | O.F_NOCONV)) == 0
+    valid = ok & (r["flags"] == 0)
+    a = g["amp"][..., 0].astype(np.float64) + 1j * g["amp"][..., 1].astype(np.float64)
+    dtau = np.abs(g["tau"] - r["tau"])
+    return {"delay_rel_max": float((dtau / r["tau"])[valid].max()),
+            "phase_rad_max": float((2 * np.pi * fc * dtau)[valid].max()),
+            "amp_rel_max": float((np.abs(a - r["a"]) / np.abs(r["a"]))[valid].max()),
+            "flag_mismatches": int((g["flags"][far] != r["flags"][far]).sum()),
+            "path_steps": int(valid.size)}
 
 
 class ClockSampler:
@@ -202,13 +286,87 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def time_calls(fn, steps, flush, stream):
+    """Mean device time (ms) of `steps` calls, CUDA events on the launch stream, L2 flushed between."""
+    import torch
+    evs = []
+    for _ in range(max(1, steps)):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in evs)
+
+
+def run_records(args, ctx, link, scene, paths, tg, fg, drt, flush):
+    """drt_extrapolate with every record written (delay, amplitude, Doppler, angles, flags), both
+    forms, on the canyon link: its HBM-write roofline (bytes written per path-step over the extrapolation
+    kernels' device time) and its errors against the oracle on sampled rows."""
+    import torch
+    stream = torch.cuda.current_stream()
+    P, T = paths.n_paths, tg.n_steps
+    hbm, src = measured_peaks()
+    out = {"l2": "flushed between timed calls", "peak_source": src}
+    rows, r = oracle_rows(scene, paths, tg, fg.fc, 16, os.cpu_count() or 1)
+    for prec, name in ((drt.FP64, "fp64"), (drt.FP32_BULK, "fp32_bulk")):
+        rec = link.extrapolate(tg, fg, prec)
+        for _ in range(2):
+            link.extrapolate(tg, fg, prec, out=rec)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.profile_read()
+        ms = time_calls(lambda: link.extrapolate(tg, fg, prec, out=rec), args.steps, flush, stream)
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        k_ms = prof["extrapolate"][1] / max(1, args.steps)
+        gbs = RECORD_BYTES[name] * P * T / (k_ms * 1e-3) / 1e9
+        g = {k: rec[k][torch.as_tensor(rows, device=rec[k].device)].cpu().numpy() for k in ("tau", "amp", "flags")}
+        out[name] = {"ms_per_call": ms, "extrapolation_kernels_ms": k_ms,
+                     "path_steps_per_s": P * T / (ms * 1e-3),
+                     "roofline_hbm_write": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                            "frac": gbs / hbm,
+                                            "algorithmic": f"{RECORD_BYTES[name]} B written per path-step x {P * T}"},
+                     "error": record_errors(g, r, fg.fc)}
+        del rec
+    return out
+
+
+def run_tiny(args, ctx, drt, flush):
+    """The tiny 28 GHz FP64 case (3 paths x 1000 steps x 256 bins): one drt_synthesize_H per call, and
+    its H against the oracle over the whole horizon."""
+    import torch
+    sc = I.scene_tiny(0)
+    ps = I.PathSet.from_npz(os.path.join(ROOT, "tests", "golden", "pathset_tiny_seed0.npz"))
+    tg, fg = I.grids("tiny")
+    link = ctx.load(sc, ps)
+    H = torch.empty((tg.n_steps, fg.n_bins), dtype=torch.complex64, device="cuda")
+    for _ in range(5):
+        link.synthesize_H(tg, fg, drt.FP64, H)
+    ms = time_calls(lambda: link.synthesize_H(tg, fg, drt.FP64, H), max(50, args.steps), flush,
+                    torch.cuda.current_stream())
+    rows, r = oracle_rows(sc, ps, tg, fg.fc, tg.n_steps, os.cpu_count() or 1)
+    err = h_errors(H.cpu().numpy()[rows], r, fg, os.cpu_count() or 1)
+    link.unload()
+    return {"workload": "tiny-3paths-1000x1ms-256bins-28GHz-fp64", "ms_per_call": ms,
+            "value": ps.n_paths * tg.n_steps / (ms * 1e-3), "unit": UNIT,
+            "h_samples_per_s": tg.n_steps * fg.n_bins / (ms * 1e-3), "error": err,
+            "note": "3 paths: a launch-latency-bound call"}
+
+
 def run_batched(args, ctx, drt, flush):
     """The batched FP32-bulk form over `--batch-links` uneven links (log-uniform 8..2048 paths,
     horizons uniform 100..5000 x 1 ms, 256 bins at 28 GHz): one drt_batch_run per step, replayed
     from its CUDA graph."""
     import torch
+    from paper_2205_00237_gb300.partition import rank_links
     w = I.BATCH
-    spec = I.batch_links(args.batch_links, seed=0)
+    rank, local_rank, world = dist_env()
+    full = I.batch_links(args.batch_links, seed=0)
+    # links are independent: each rank takes its share (greedy by path-steps), no data-path collective
+    spec = [full[i] for i in rank_links([P * T for _, P, T in full], rank, world)] if world > 1 else full
     sets = [(I.scene_link(k), I.PathSet.from_npz(os.path.join(ROOT, "tests", "golden", f"pathset_link_seed{k}.npz")))
             for k in range(I.LINK_SCENES)]
     t0 = time.perf_counter()
@@ -238,9 +396,17 @@ def run_batched(args, ctx, drt, flush):
         evs.append((e0, e1))
     torch.cuda.synchronize()
     total_s = sum(a.elapsed_time(c) for a, c in evs) * 1e-3
+    total_s = max_over_ranks(total_s, world, torch.device("cuda", local_rank))
     info = b.info(redo=True)
-    ps_steps = sum(P * T for _, P, T in spec)
-    h_samples = sum(T for _, _, T in spec) * w["n_bins"]
+    # errors of the timed run's H on sampled rows of four links against the oracle
+    errs = []
+    cores = os.cpu_count() or 1
+    for j in np.linspace(0, len(spec) - 1, 4).astype(int):
+        k, P, T = spec[j]
+        rows, r = oracle_rows(sets[k][0], sets[k][1].subset(np.arange(P)), tgs[j], fgs[j].fc, 8, cores)
+        errs.append(h_errors(Hs[j].cpu().numpy()[rows], r, fgs[j], cores))
+    ps_steps = sum(P * T for _, P, T in full)      # all ranks' links over the slowest rank's time
+    h_samples = sum(T for _, _, T in full) * w["n_bins"]
     out = {"value": ps_steps * args.batch_steps / total_s, "unit": UNIT,
            "h_samples_per_s": h_samples * args.batch_steps / total_s,
            "terms_per_s": ps_steps * w["n_bins"] * args.batch_steps / total_s,
@@ -250,7 +416,13 @@ def run_batched(args, ctx, drt, flush):
                        f"{w['n_bins']} bins over 400 MHz at 28 GHz",
            "path_steps_per_step": ps_steps, "precision": "DRT_FP32_BULK", "graph": True,
            "synth_tile_variant": info["variant"], "scratch_gb": info["scratch_bytes"] / 1e9,
-           "redo_steps_per_step": info["redo_steps"], "load_s": load_s, "plan_and_autotune_s": plan_s,
+           "links_this_rank": len(spec),
+           "redo_steps_per_step": info["redo_steps"],
+           "redo_fraction": info["redo_steps"] / sum(P * T for _, P, T in spec),
+           "load_s": load_s, "plan_and_autotune_s": plan_s,
+           "error": {"H_rel_max": max(e["H_rel_max"] for e in errs),
+                     "absH_rel_max": max(e["absH_rel_max"] for e in errs),
+                     "sample": "8 rows of each of 4 links spread over the batch"},
            "l2": "flushed by a 256 MB write between timed steps (outside the events)"}
     b.close()
     del Hs
@@ -355,14 +527,17 @@ def run_highway(args, ctx, drt, flush):
     """The large vehicular highway (64 links x 20300 paths, 28 and 60 GHz, 20000 x 0.1 ms, 1024
     bins, FP32-bulk) through one drt_batch_run per step, graph-replayed."""
     import torch
+    from paper_2205_00237_gb300.partition import rank_links
     hw = I.HIGHWAY
+    rank, local_rank, world = dist_env()
     rd = I.PathSet.from_npz(os.path.join(ROOT, "tests", "golden", "pathset_highway_rd_seed0.npz"))
     tg = I.TimeGrid(0.0, hw["dt"], hw["n_steps"])
     fgs = [I.FreqGrid(fc, hw["bandwidth"], hw["n_bins"]) for fc in hw["carriers"]]
+    mine = rank_links([1.0] * hw["n_links"], rank, world) if world > 1 else list(range(hw["n_links"]))
     t0 = time.perf_counter()
-    links = [ctx.load(I.scene_highway(0, l), I.highway_pathset(rd, l)) for l in range(hw["n_links"])]
+    links = {l: ctx.load(I.scene_highway(0, l), I.highway_pathset(rd, l)) for l in mine}
     load_s = time.perf_counter() - t0
-    entries = [(l, fg) for fg in fgs for l in range(hw["n_links"])]
+    entries = [(l, fg) for fg in fgs for l in mine]
     Hs = [torch.empty((tg.n_steps, fg.n_bins), dtype=torch.complex64, device="cuda") for _, fg in entries]
     t0 = time.perf_counter()
     b = ctx.batch([links[l] for l, _ in entries], [tg] * len(entries), [fg for _, fg in entries], Hs)
@@ -380,49 +555,73 @@ def run_highway(args, ctx, drt, flush):
         evs.append((e0, e1))
     torch.cuda.synchronize()
     sec = statistics.mean(a.elapsed_time(c) for a, c in evs) * 1e-3
+    sec = max_over_ranks(sec, world, torch.device("cuda", local_rank))
     info = b.info(redo=True)
+    # errors of the timed run's H on sampled rows of one link per carrier against the oracle
+    errs = []
+    cores = os.cpu_count() or 1
+    for j in (0, len(entries) - 1):
+        l, fg = entries[j]
+        rows, r = oracle_rows(I.scene_highway(0, l), I.highway_pathset(rd, l), tg, fg.fc, 4, cores)
+        errs.append(h_errors(Hs[j].cpu().numpy()[rows], r, fg, cores))
     P = rd.n_paths // hw["n_links"] + hw["n_tiles"]
-    ps = len(entries) * P * tg.n_steps
+    ps = len(fgs) * hw["n_links"] * P * tg.n_steps    # all ranks' entries over the slowest rank's time
     out = {"value": ps / sec, "unit": UNIT, "s_per_step": sec, "steps": len(evs),
-           "h_samples_per_s": len(entries) * tg.n_steps * hw["n_bins"] / sec,
+           "h_samples_per_s": len(fgs) * hw["n_links"] * tg.n_steps * hw["n_bins"] / sec,
            "terms_per_s": ps * hw["n_bins"] / sec, "path_steps_per_step": ps,
            "workload": f"{hw['n_links']} links x {P} paths ({hw['n_tiles']} ER tiles + {hw['n_rd']} R/D), "
                        f"carriers {[f / 1e9 for f in hw['carriers']]} GHz, {tg.n_steps} x {tg.dt * 1e3} ms, "
                        f"{hw['n_bins']} bins over {hw['bandwidth'] / 1e6:.0f} MHz, FP32-bulk",
            "synth_tile_variant": info["variant"], "scratch_gb": info["scratch_bytes"] / 1e9,
-           "redo_steps_per_step": info["redo_steps"], "load_s": load_s, "plan_and_autotune_s": plan_s}
+           "redo_steps_per_step": info["redo_steps"], "redo_fraction": info["redo_steps"] / ps,
+           "load_s": load_s, "plan_and_autotune_s": plan_s,
+           "error": {"H_rel_max": max(e["H_rel_max"] for e in errs),
+                     "absH_rel_max": max(e["absH_rel_max"] for e in errs),
+                     "sample": "4 rows of the first 28 GHz and the last 60 GHz entry"}}
     b.close()
     del Hs
-    for lk in links:
+    for lk in links.values():
         lk.unload()
     return out
 
 
-def run_serving(args, drt):
-    """Poisson-arriving prediction requests on resident canyon links (512, 128 and 32 paths),
-    horizons U{50..500} x 1 ms from random start times, 512 bins at 60 GHz, HBM budget 64 GB."""
+def run_serving(args, drt, mix, rate, seconds, warmup):
+    """Poisson-arriving anticipative-prediction requests (horizons U{50..500} x 1 ms from start times
+    U[0, 1) s) on resident links, HBM budget 64 GB with the serving arena taking what the links leave.
+    mix "canyon512": the full-3D canyon link (512 paths, 512 bins over 1 GHz at 60 GHz);
+    mix "mixed": 32 resident links of the four 28 GHz link scenes with P ~ log-U[8, 2048] paths
+    (256 bins over 400 MHz).  Latency is submit -> completion from the library's own stamps."""
     import torch
-    ctx = drt.Context(torch.cuda.current_device(), hbm_budget=64 << 30)
-    scene = I.scene_canyon(0)
-    paths = I.PathSet.from_npz(PATHSET)
-    links = [ctx.load(scene, paths), ctx.load(scene, paths.subset(np.arange(128))),
-             ctx.load(scene, paths.subset(np.arange(32)))]
-    weights = np.array([0.6, 0.25, 0.15])
-    ctx.serve_start(0, 4, 256)
-    F, ring = 512, 2048
-    bufs = [torch.empty((500, F), dtype=torch.complex64, device="cuda") for _ in range(ring)]
+    budget = 64 << 30
+    ctx = drt.Context(torch.cuda.current_device(), hbm_budget=budget)
     rng = np.random.default_rng(11)
-    duration = args.serve_warmup + args.serve_seconds
-    n_req = int(args.serve_rate * duration * 1.2) + 16
-    gaps = rng.exponential(1.0 / args.serve_rate, n_req)
-    arrivals = np.cumsum(gaps)
+    if mix == "canyon512":
+        links = [ctx.load(I.scene_canyon(0), I.PathSet.from_npz(PATHSET))]
+        fg = I.FreqGrid(60e9, 1e9, 512)
+        weights = np.array([1.0])
+        workload = ("canyon link, 512 paths, 512 bins over 1 GHz at 60 GHz")
+    else:
+        sets = [(I.scene_link(k), I.PathSet.from_npz(os.path.join(ROOT, "tests", "golden", f"pathset_link_seed{k}.npz")))
+                for k in range(I.LINK_SCENES)]
+        sizes = np.exp(rng.uniform(np.log(8), np.log(2048), 32)).astype(int)
+        links = [ctx.load(sets[i % 4][0], sets[i % 4][1].subset(np.arange(int(P)))) for i, P in enumerate(sizes)]
+        fg = I.FreqGrid(I.BATCH["fc"], I.BATCH["bandwidth"], I.BATCH["n_bins"])
+        weights = np.full(len(links), 1.0 / len(links))
+        workload = (f"32 links of the 28 GHz link scenes, P ~ log-U[8, 2048] (mean {sizes.mean():.0f}), "
+                    f"{fg.n_bins} bins over 400 MHz")
+    arena = int(budget * 0.9)
+    ctx.serve_start(arena, 4, 256)
+    F, ring = fg.n_bins, 2048
+    bufs = [torch.empty((500, F), dtype=torch.complex64, device="cuda") for _ in range(ring)]
+    duration = warmup + seconds
+    n_req = int(rate * duration * 1.2) + 16
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
     arrivals = arrivals[arrivals < duration]
     li = rng.choice(len(links), len(arrivals), p=weights)
     hor = rng.integers(50, 501, len(arrivals))
     t_starts = rng.integers(0, 1000, len(arrivals)) * 1e-3
     tickets = [None] * len(arrivals)
     results = [None] * len(arrivals)
-    fg = I.FreqGrid(60e9, 1e9, F)
     done_upto = [0]
 
     def collector():
@@ -435,11 +634,13 @@ def run_serving(args, drt):
     th = threading.Thread(target=collector, daemon=True)
     th.start()
     t0 = time.perf_counter()
+    lag = []
     for i, ta in enumerate(arrivals):
         while time.perf_counter() - t0 < ta:
             pass
         while i - done_upto[0] >= ring - 1:      # the ring buffer slot is still in use
             time.sleep(1e-4)
+        lag.append(time.perf_counter() - t0 - ta)
         H = bufs[i % ring][:hor[i]]
         tickets[i] = ctx.submit(links[li[i]], I.TimeGrid(float(t_starts[i]), 1e-3, int(hor[i])), fg, H)
     th.join()
@@ -448,8 +649,7 @@ def run_serving(args, drt):
     ctx.serve_stop()
     n_paths = np.array([lk.n_paths for lk in links])
     sub = np.array([r["t_submit"] for r in results])
-    t_first = sub.min()
-    meas = (sub - t_first) >= args.serve_warmup
+    meas = (sub - sub.min()) >= warmup
     lat = np.array([r["latency"] for r in results])[meas] * 1e3
     done_t = np.array([r["t_done"] for r in results])
     ps = (n_paths[li] * hor)[meas]
@@ -458,17 +658,18 @@ def run_serving(args, drt):
     for lk in links:
         lk.unload()
     ctx.close()
-    return {"requests": int(meas.sum()), "offered_req_per_s": args.serve_rate,
+    del bufs
+    return {"mix": mix, "requests": int(meas.sum()), "offered_req_per_s": rate,
             "achieved_req_per_s": meas.sum() / span, "value": ps.sum() / span, "unit": UNIT,
             "h_samples_per_s": (hor[meas] * F).sum() / span,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
                            "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
-            "mean_batch_requests": float(np.mean([r["batch_requests"] for r in results])),
-            "launches": stats["launches"], "arena_peak_gb": stats["arena_peak"] / 1e9, "all_ok": ok,
-            "window_s": args.serve_seconds, "warmup_s": args.serve_warmup, "wall_s": t_end,
-            "workload": "Poisson arrivals; canyon links of 512/128/32 paths (p = 0.6/0.25/0.15); horizons "
-                        "U{50..500} x 1 ms from t_start U[0,1) s; 512 bins over 1 GHz at 60 GHz; FP32-bulk; "
-                        "HBM budget 64 GB"}
+            "mean_batch_requests": float(np.mean([r["batch_requests"] for r in np.array(results)[meas]])),
+            "submit_lag_ms_p99": float(np.percentile(np.array(lag)[meas], 99) * 1e3),
+            "launches": stats["launches"], "arena_gb": arena / 1e9, "arena_peak_gb": stats["arena_peak"] / 1e9,
+            "all_ok": ok, "window_s": seconds, "warmup_s": warmup, "wall_s": t_end,
+            "workload": f"Poisson arrivals at {rate:.0f} req/s; {workload}; horizons U{{50..500}} x 1 ms from "
+                        "t_start U[0,1) s; FP32-bulk; HBM budget 64 GB"}
 
 
 def run_ours(args):
@@ -528,6 +729,10 @@ def run_ours(args):
     n_launch, k1_ms = prof["extrapolate"]
     k1_avg_s = k1_ms * 1e-3 / max(1, args.steps)
     kernel_launches = sum(v[0] for v in prof.values())
+    # errors of the timed run's H (the last timed call) on 16 sampled rows against the FP64 oracle
+    cores = os.cpu_count() or 1
+    rows, r_rows = oracle_rows(scene, paths, tg, fg.fc, 16, cores)
+    head_err = h_errors(H.cpu().numpy()[rows], r_rows, fg, cores)
 
     # the FP32-bulk form on the same link (reported beside the FP64 headline)
     for _ in range(3):
@@ -548,17 +753,22 @@ def run_ours(args):
     ctx.profile(False)
     bulk_s = sum(a.elapsed_time(b) for a, b in evb) * 1e-3
     bulk_s = max_over_ranks(bulk_s, world, dev)
+    bulk_err = h_errors(H.cpu().numpy()[rows], r_rows, fg, cores)
     fp32_bulk = {"value": whole_job_rate(P * T * args.steps, world, bulk_s), "unit": UNIT, "ms_per_step": 1e3 * bulk_s / args.steps,
                  "h_samples_per_s": world * T * F * args.steps / bulk_s, "precision": "DRT_FP32_BULK",
                  "kernel_ms": {k: (v[1] / args.steps) for k, v in profb.items() if v[0]},
-                 "kernel_ms_note": "device time per step of each kernel kind (all its launches)"}
+                 "kernel_ms_note": "device time per step of each kernel kind (all its launches)",
+                 "error": bulk_err}
     ke, ks = fp32_bulk["kernel_ms"].get("extrapolate"), fp32_bulk["kernel_ms"].get("synth")
+    fresh = KERNEL_HASH is not None and KERNEL_HASH == kernel_source_hash()
     if ke and ks:
-        a1 = FP32_FLOP_PER_PATH_STEP * P * T / (ke * 1e-3)
         a3 = SYNTH_FLOP_PER_TERM * P * T * F / (ks * 1e-3)
+        a1 = FP32_FLOP_PER_PATH_STEP * P * T / (ke * 1e-3) if fresh and FP32_FLOP_PER_PATH_STEP else None
         fp32_bulk["rooflines"] = {
-            "k_extrapolate_bulk": {"bound": "alu", "achieved": a1 / 1e12, "peak": FP32_PEAK_FLOPS / 1e12,
-                                   "unit": "TFLOP/s", "frac": a1 / FP32_PEAK_FLOPS},
+            "k_extrapolate_bulk": {"bound": "alu", "achieved": a1 / 1e12 if a1 else None,
+                                   "peak": FP32_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                                   "frac": a1 / FP32_PEAK_FLOPS if a1 else None,
+                                   "note": None if a1 else "FLOP count not measured on this kernel build"},
             "k_synth": {"bound": "alu", "achieved": a3 / 1e12, "peak": FP32_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
                         "frac": a3 / FP32_PEAK_FLOPS, "terms_per_s": P * T * F / (ks * 1e-3)}}
 
@@ -590,20 +800,24 @@ def run_ours(args):
             "gpu_launches": int(kernel_launches),
             "kernel_ms": {k: (v[1] / args.steps) for k, v in prof.items() if v[0]},
             "kernel_ms_note": "device time per step of each kernel kind (all its launches)",
-            "wall_s": wall, "clocks": clocks, "fp32_bulk": fp32_bulk}
-    if FP64_FLOP_PER_PATH_STEP:
+            "wall_s": wall, "clocks": clocks, "error": head_err, "fp32_bulk": fp32_bulk,
+            "kernel_source_hash": kernel_source_hash()}
+    if fresh and FP64_FLOP_PER_PATH_STEP:
         achieved = FP64_FLOP_PER_PATH_STEP * P * T / k1_avg_s
-        line["roofline"] = {"bound": "alu", "kernel": "k_extrapolate_fp64", "achieved": achieved / 1e12,
+        line["roofline"] = {"bound": "alu", "kernel": "k_extrapolate_fp64 (all launches of one call)",
+                            "achieved": achieved / 1e12,
                             "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS,
                             "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (no FP64 figure in "
                                            "MEASURED_PEAKS.json)",
                             "algorithmic": f"{FP64_FLOP_PER_PATH_STEP:.0f} FP64 FLOP per path-step x {P * T} path-steps",
-                            "traffic": K1_DRAM_BYTES_PER_LAUNCH,
+                            "traffic": K1_DRAM_BYTES_PER_CALL,
                             "ncu_fp64_pipe_active": K1_FP64_PIPE_ACTIVE}
     else:
-        line["roofline"] = {"bound": "alu", "kernel": "k_extrapolate_fp64", "achieved": None,
-                            "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s", "frac": None,
-                            "traffic": None, "note": "per-path-step FLOP count not yet measured"}
+        line["roofline"] = {"bound": "alu", "kernel": "k_extrapolate_fp64 (all launches of one call)",
+                            "achieved": None, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s", "frac": None,
+                            "traffic": None, "note": "per-path-step FLOP count not measured on this kernel build"}
+    line["extrapolate_records"] = run_records(args, ctx, link, scene, paths, tg, fg, drt, flush)
+    line["tiny"] = run_tiny(args, ctx, drt, flush)
     probe = ctx.probe_peak(0)
     line["roofline"]["probe_fp64_tflops"] = probe / 1e12
     line["power_profiles"] = run_power(args, link, tg, fg, drt, flush)
@@ -611,10 +825,14 @@ def run_ours(args):
     line["wideband"] = run_wideband(args, link, tg, fg, drt, flush)
     if args.batch_links > 0:
         line["batched"] = run_batched(args, ctx, drt, flush)
-    if args.highway:
+    if not args.no_highway:
         line["highway"] = run_highway(args, ctx, drt, flush)
     if args.serve_seconds > 0:
-        line["serving"] = run_serving(args, drt)
+        short, sw = args.serve_short_seconds, min(2.0, args.serve_warmup)
+        line["serving"] = [run_serving(args, drt, "canyon512", args.serve_rate, args.serve_seconds, args.serve_warmup),
+                           run_serving(args, drt, "canyon512", args.serve_high_rate, short, sw),
+                           run_serving(args, drt, "mixed", args.serve_rate, short, sw),
+                           run_serving(args, drt, "mixed", args.serve_high_rate, short, sw)]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, paths, tg, fg, n_steps=tg.n_steps)
     link.unload()

@@ -74,6 +74,11 @@ def lib():
             L.or_frame_roundtrip.argtypes = [C.c_void_p, C.c_int32, C.c_double, dp, dp, dp]
             L.or_ref_point_local.argtypes = [dp, dp, dp]
             L.or_diff_point_local.argtypes = [dp, dp, dp]
+            L.or_trace_candidates.restype = C.c_int64
+            L.or_trace_candidates.argtypes = [C.c_void_p, C.c_int32, C.c_int32]
+            L.or_trace.restype = C.c_int32
+            L.or_trace.argtypes = [C.c_void_p, C.c_double, C.c_int32, C.c_int32, C.c_double, C.c_int32, C.c_int32] + \
+                [C.c_void_p] * 7
             L.or_doppler_chain.restype = C.c_double
             L.or_doppler_chain.argtypes = [C.c_int32, dp, dp, C.c_double]
             _lib = L
@@ -318,3 +323,34 @@ def doppler_chain(pos, vel, fc):
     pos = np.ascontiguousarray(pos, float)
     vel = np.ascontiguousarray(vel, float)
     return lib().or_doppler_chain(pos.shape[0] - 2, _dp(pos), _dp(vel), fc)
+
+
+def trace(scene, t, max_order=2, with_tiles=True, report=1e-9, n_threads=8):
+    """Conventional ray tracing at instant t (drt_oracle.c or_trace): the chains that are rays, as a
+    PathSet in enumeration order (edge parameters at t in s0), plus the candidates a run at t could
+    decide either way (decision margin below `report` m): dict(paths, index, margin, ambiguous)."""
+    from paper_2205_00237_gb300 import inputs as I
+    L = lib()
+    h = _SceneHandle(scene)
+    cap = 1 << 16
+    while True:
+        index = np.empty(cap, np.int64)
+        found = np.empty(cap, np.uint8)
+        margin = np.empty(cap)
+        n_int = np.empty(cap, np.uint8)
+        types = np.empty((cap, MAX_INT), np.uint8)
+        prims = np.empty((cap, MAX_INT), np.int32)
+        s0 = np.empty((cap, MAX_INT))
+        n = L.or_trace(h.ref, float(t), int(max_order), int(bool(with_tiles)), float(report), int(n_threads), cap,
+                       *[_ptr(a) for a in (index, found, margin, n_int, types, prims, s0)])
+        if n <= cap:
+            break
+        cap = n
+    o = np.argsort(index[:n], kind="stable")
+    index, found, margin = index[:n][o], found[:n][o].astype(bool), margin[:n][o]
+    ps = I.PathSet(n_int[:n][o].copy(), types[:n][o].copy(), prims[:n][o].copy(), s0[:n][o].copy())
+    rays = ps.subset(np.nonzero(found)[0])
+    return dict(paths=rays, index=index[found], margin=margin[found],
+                ambiguous=index[(~found) | (margin < report)], candidates=int(L.or_trace_candidates(h.ref, int(max_order),
+                                                                                                    int(bool(with_tiles)))))
+

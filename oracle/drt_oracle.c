@@ -1095,6 +1095,169 @@ int or_synthesize_H(int32_t n_steps, int32_t n_paths, const double *tau, const d
     return 0;
 }
 
+/* ---------------------------------------------------------------- conventional ray tracing at t (Sec. II)
+ * DRT starts from the ray chains of one conventional ray-tracing run at t0 and re-runs it at every
+ * multipath-lifetime boundary (Sec. II, Sec. IV-B).  This is that run by brute-force image-tree
+ * enumeration: every chain of at most max_order reflections / diffractions (no primitive twice in a
+ * row) and, if with_tiles, every single-tile scattering chain, posed at t, solved with the O-DRT
+ * geometry (Newton for two diffractions in one segment, from the edge midpoints), kept when the chain
+ * is valid (path_flags, as for the extrapolation) and no face blocks any of its segments. */
+
+/* Does face f block the segment A -> B?  It does when the segment crosses the face's plane strictly
+ * between its ends at a point inside the rectangle; a face whose plane holds A or B (the face a
+ * reflection point or a tile lies on, the faces of a diffracting edge, faces coplanar with those)
+ * does not.  *mg is lowered to the distance of this decision from its boundary (m). */
+static int face_blocks(const or_scene *S, int f, double t, v3 A, v3 B, double *mg) {
+    or_frame F;
+    face_frame(S, f, t, &F);
+    const or_face *fc = &S->faces[f];
+    double ha = dot(sub(A, F.O.p), F.ey), hb = dot(sub(B, F.O.p), F.ey);
+    if (fabs(ha) < 1e-9 || fabs(hb) < 1e-9) return 0;
+    if ((ha > 0) == (hb > 0)) return 0;
+    v3 X = add(A, scl(sub(B, A), ha / (ha - hb)));
+    v3 r = sub(X, F.O.p);
+    double al = dot(r, F.ex), be = dot(r, F.ez);
+    double m = fmin(fabs(ha), fabs(hb));
+    if (isfinite(fc->hu)) m = fmin(m, fabs(fc->hu - fabs(al)));
+    if (isfinite(fc->hw)) m = fmin(m, fabs(fc->hw - fabs(be)));
+    *mg = fmin(*mg, m);
+    return fabs(al) <= fc->hu && fabs(be) <= fc->hw;
+}
+
+/* candidate k of the enumeration: 0 = line of sight; then the single interactions (faces as
+ * reflections, edges as diffractions, tiles as scatterers); then the ordered pairs (a, b), a != b, of
+ * faces and edges.  Returns 0 for a skipped index (a == b). */
+static int trace_candidate(const or_scene *S, int64_t k, int with_tiles, or_path *pa) {
+    const int NP = S->n_faces + S->n_edges, NT = with_tiles ? S->n_tiles : 0;
+    memset(pa, 0, sizeof(*pa));
+    if (k == 0) return 1;
+    k -= 1;
+    int code[2], n = 0;
+    if (k < NP + NT) {
+        code[n++] = (int)k;
+    } else {
+        k -= NP + NT;
+        code[0] = (int)(k / NP);
+        code[1] = (int)(k % NP);
+        if (code[0] == code[1]) return 0;
+        n = 2;
+    }
+    pa->n = n;
+    for (int j = 0; j < n; ++j) {
+        int c = code[j];
+        if (c < S->n_faces) { pa->type[j] = OR_T_R; pa->prim[j] = c; }
+        else if (c < NP) {
+            const or_edge *e = &S->edges[c - S->n_faces];
+            pa->type[j] = OR_T_D;
+            pa->prim[j] = c - S->n_faces;
+            pa->s0[j] = 0.5 * nrm(sub(V(e->b), V(e->a)));
+        } else { pa->type[j] = OR_T_S; pa->prim[j] = c - NP; }
+    }
+    return 1;
+}
+
+int64_t or_trace_candidates(const or_scene *S, int32_t max_order, int32_t with_tiles) {
+    const int64_t NP = S->n_faces + S->n_edges, NT = with_tiles ? S->n_tiles : 0;
+    return 1 + (max_order >= 1 ? NP + NT : 0) + (max_order >= 2 ? NP * NP : 0);
+}
+
+/* Decision of candidate k at t: 1 when it is a ray; *margin is the smallest distance (m) of any of the
+ * decisions (validity, occlusion) from its boundary; the chain and its diffraction parameters at t go
+ * to *pa. */
+static int trace_one(const or_scene *S, double t, int64_t k, int with_tiles, or_path *pa, double *margin) {
+    *margin = INFINITY;
+    if (!trace_candidate(S, k, with_tiles, pa)) return 0;
+    or_geom G;
+    odrt_solve(S, pa, t, &G);
+    v3 P[OR_MAXI + 2];
+    for (int i = 0; i <= pa->n + 1; ++i) P[i] = G.V[i].p;
+    double mg;
+    int fl = G.flags | path_flags(S, pa, t, P, &mg);
+    *margin = mg;
+    for (int i = 1; i <= pa->n; ++i)
+        if (pa->type[i - 1] == OR_T_D) {
+            or_frame F;
+            double len, wn;
+            edge_frame(S, pa->prim[i - 1], t, &F, &len, &wn);
+            pa->s0[i - 1] = dot(sub(P[i], F.O.p), F.ez);
+        }
+    for (int i = 0; i <= pa->n + 1; ++i)
+        if (!(isfinite(P[i].x) && isfinite(P[i].y) && isfinite(P[i].z))) fl |= OR_F_DEGEN;
+    if (fl) return 0;
+    int blocked = 0;
+    for (int i = 1; i <= pa->n + 1; ++i)
+        for (int f = 0; f < S->n_faces; ++f) blocked |= face_blocks(S, f, t, P[i - 1], P[i], margin);
+    return !blocked;
+}
+
+typedef struct {
+    const or_scene *S;
+    double t;
+    int32_t with_tiles, cap;
+    int64_t total, next;
+    double report;
+    int32_t count;
+    uint8_t *n_int, *types, *found;
+    int32_t *prims;
+    double *s0, *margin;
+    int64_t *index;
+    pthread_mutex_t mu;
+} or_trjob;
+
+static void *trace_worker(void *arg) {
+    or_trjob *J = (or_trjob *)arg;
+    for (;;) {
+        pthread_mutex_lock(&J->mu);
+        int64_t lo = J->next;
+        J->next += 256;
+        pthread_mutex_unlock(&J->mu);
+        if (lo >= J->total) break;
+        int64_t hi = lo + 256 < J->total ? lo + 256 : J->total;
+        for (int64_t k = lo; k < hi; ++k) {
+            or_path pa;
+            double mg;
+            int ray = trace_one(J->S, J->t, k, J->with_tiles, &pa, &mg);
+            if (!ray && !(mg < J->report)) continue;
+            pthread_mutex_lock(&J->mu);
+            int slot = J->count++;
+            pthread_mutex_unlock(&J->mu);
+            if (slot >= J->cap) continue;
+            J->index[slot] = k;
+            J->found[slot] = (uint8_t)ray;
+            J->margin[slot] = mg;
+            J->n_int[slot] = (uint8_t)pa.n;
+            for (int j = 0; j < OR_MAXI; ++j) {
+                J->types[slot * OR_MAXI + j] = (uint8_t)(j < pa.n ? pa.type[j] : 0);
+                J->prims[slot * OR_MAXI + j] = j < pa.n ? pa.prim[j] : -1;
+                J->s0[slot * OR_MAXI + j] = j < pa.n ? pa.s0[j] : 0.0;
+            }
+        }
+    }
+    return NULL;
+}
+
+/* Ray tracing at t: writes (in no particular order) every candidate that is a ray (found = 1) and every
+ * other candidate whose decision margin is below `report` m (found = 0: a run at this instant could
+ * decide it either way), with its enumeration index, margin, chain and diffraction parameters at t.
+ * Returns the number of such candidates (only the first cap are written). */
+int32_t or_trace(const or_scene *S, double t, int32_t max_order, int32_t with_tiles, double report, int32_t n_threads,
+                 int32_t cap, int64_t *index, uint8_t *found, double *margin, uint8_t *n_int, uint8_t *types,
+                 int32_t *prims, double *s0) {
+    pthread_once(&gl_once, gl_init);
+    or_trjob J;
+    memset(&J, 0, sizeof(J));
+    J.S = S; J.t = t; J.with_tiles = with_tiles; J.cap = cap; J.report = report;
+    J.total = or_trace_candidates(S, max_order, with_tiles);
+    J.n_int = n_int; J.types = types; J.found = found; J.prims = prims; J.s0 = s0; J.margin = margin; J.index = index;
+    pthread_mutex_init(&J.mu, NULL);
+    int nt = n_threads < 1 ? 1 : n_threads > 256 ? 256 : n_threads;
+    pthread_t th[256];
+    for (int i = 0; i < nt; ++i) pthread_create(&th[i], NULL, trace_worker, &J);
+    for (int i = 0; i < nt; ++i) pthread_join(th[i], NULL);
+    pthread_mutex_destroy(&J.mu);
+    return J.count;
+}
+
 /* ---------------------------------------------------------------- unit-level entry points for pins */
 void or_fresnel_coeffs(double eps_r, double sigma, double pec, double fc, double ct, double *out4) {
     or_mat m = {eps_r, sigma, 0.0, pec};
