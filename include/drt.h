@@ -261,6 +261,47 @@ drt_status drt_synthesize_H_windows(drt_ctx *ctx, uint64_t link, const drt_time_
                                     int32_t n_windows, void *H, int32_t precision, void *stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Conventional ray tracing at one instant (Sec. II: the ray-tracing run DRT starts from at t0; Sec.
+ * IV-B: it is run again at the start of every multipath-lifetime window) over the scene of a loaded
+ * link, whose own chains are not used.  Brute-force image-tree enumeration on the device: every chain
+ * of at most max_order (0, 1 or 2) reflections / diffractions with no primitive twice in a row and,
+ * when with_tiles != 0, every single-tile scattering chain, posed at t (seconds after t0), is solved
+ * with the extrapolation's FP64 geometry (image method and back-tracking, Keller cone, Newton from the
+ * edge midpoints for two diffractions in one segment) and kept when its FP64 validity flags are 0 and
+ * no face of the scene blocks any of its segments (a face blocks a segment that crosses its plane
+ * strictly between the segment's ends inside its rectangle; a face whose plane holds an end of the
+ * segment -- the face a reflection point or a tile lies on, the faces of a diffracting edge -- does
+ * not).  Candidates are enumerated as the line of sight, then faces (reflections), edges
+ * (diffractions) and tiles (scattering), then ordered pairs of faces and edges; the rays found are
+ * written to the caller's HOST arrays in that order, at most cap of them, with the edge parameter
+ * (m from edge point a) of each diffraction point at t in s0, so that the result loads as a link's
+ * path set (drt_load_paths).  n_found receives the number found (above cap, only the first cap were
+ * written).  Runs on `stream` and waits for it.  Errors: DRT_EINVAL, DRT_ENOTFOUND, DRT_ENOMEM (more
+ * than 2^22 rays), DRT_ECUDA. */
+typedef struct {
+    int32_t cap, n_found;
+    uint8_t *n_int;      /* [cap]    */
+    uint8_t *types;      /* [cap][4] */
+    int32_t *prims;      /* [cap][4] */
+    double *s0;          /* [cap][4] */
+} drt_traced_paths;
+drt_status drt_trace_paths(drt_ctx *ctx, uint64_t link, double t, int32_t max_order, int32_t with_tiles,
+                           drt_traced_paths *out, void *stream);
+
+/* DRT with a ray-tracing run at every window start, the paper's procedure over a span (Sec. II,
+ * Sec. IV-B): the span divides into T_C windows starting at the HOST steps starts[0..n_windows)
+ * (starts[0] = 0, strictly increasing, < n_steps); window w takes the chains of drt_trace_paths at its
+ * first instant t_start + starts[w] dt (max_order, with_tiles as there), extrapolates them over its
+ * instants and synthesises its rows of H (caller-owned DEVICE buffer [n_steps][n_bins] complex64, as
+ * drt_synthesize_H; `precision` selects the form).  A ray that appears inside a window is found at the
+ * next window start.  Each window's chains go to the host to be packed into a temporary link, so the
+ * call is synchronous.  Errors: DRT_EINVAL, DRT_ENOTFOUND, DRT_ENOMEM, DRT_ECUDA. */
+drt_status drt_synthesize_H_retraced(drt_ctx *ctx, uint64_t link, const drt_time_grid *tgrid,
+                                     const drt_freq_grid *fgrid, const int32_t *starts, int32_t n_windows,
+                                     int32_t max_order, int32_t with_tiles, void *H, int32_t precision,
+                                     void *stream);
+
+/* ---------------------------------------------------------------------------------------------
  * a10: batched synthesis over many resident links (FP32-bulk form).  drt_batch_create plans one
  * batch: link i is synthesised over tgrids[i] x fgrids[i] into the caller's DEVICE buffer H[i]
  * ([n_steps][n_bins] complex64).  Each stage (base poses, FP64 chunk poses, multi-diffraction warm

@@ -354,3 +354,40 @@ def trace(scene, t, max_order=2, with_tiles=True, report=1e-9, n_threads=8):
                 ambiguous=index[(~found) | (margin < report)], candidates=int(L.or_trace_candidates(h.ref, int(max_order),
                                                                                                     int(bool(with_tiles)))))
 
+
+
+def trace_chain(scene, index, with_tiles=True):
+    """The chain of enumeration index `index` of or_trace (line of sight; faces, edges, tiles; ordered
+    pairs of faces / edges): (n, types, prims), or None for an excluded pair."""
+    from paper_2205_00237_gb300 import inputs as I
+    nf, ne = len(scene.faces), len(scene.edges)
+    NP, NT = nf + ne, (len(scene.tiles) if with_tiles else 0)
+
+    def one(c):
+        return (I.T_R, c) if c < nf else (I.T_D, c - nf) if c < NP else (I.T_S, c - NP)
+    if index == 0:
+        return []
+    j = index - 1
+    if j < NP + NT:
+        return [one(j)]
+    q = j - NP - NT
+    a, b = q // NP, q % NP
+    return None if a == b else [one(a), one(b)]
+
+
+def synthesize_H_retraced(scene, tgrid, fgrid, starts, chains_at, n_threads=1):
+    """DRT over T_C windows with a ray-tracing run at every window start: window w extrapolates the
+    PathSet chains_at(w) (the rays at its first instant) over its instants.  H [T][F]."""
+    from paper_2205_00237_gb300 import inputs as I
+    T = int(tgrid.n_steps)
+    H = np.zeros((T, int(fgrid.n_bins)), np.complex128)
+    bounds = list(starts) + [T]
+    for w in range(len(starts)):
+        k0, k1 = bounds[w], bounds[w + 1]
+        sub = I.TimeGrid(tgrid.t_start + k0 * tgrid.dt, tgrid.dt, k1 - k0)
+        ps = chains_at(w)
+        if ps.n_paths == 0:
+            continue
+        rec = extrapolate(scene, ps, sub, fgrid.fc, n_threads=n_threads)
+        H[k0:k1] = synthesize_H(rec, fgrid, n_threads=n_threads)
+    return H

@@ -41,10 +41,38 @@ drt_status fail(drt_status code, const char *fmt, ...) {
         if (e_ != cudaSuccess) return fail(DRT_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
     } while (0)
 
+// host copy of a link's scene (the environment database), kept for ray-tracing runs whose chains
+// are packed into new links
+struct HostScene {
+    drt_terminal tx, rx;
+    std::vector<drt_body> bodies;
+    std::vector<drt_material> mats;
+    std::vector<drt_face> faces;
+    std::vector<drt_edge> edges;
+    std::vector<drt_tile> tiles;
+    drt_scene view() const {
+        drt_scene s{};
+        s.tx = tx;
+        s.rx = rx;
+        s.n_bodies = (int32_t)bodies.size();
+        s.n_materials = (int32_t)mats.size();
+        s.n_faces = (int32_t)faces.size();
+        s.n_edges = (int32_t)edges.size();
+        s.n_tiles = (int32_t)tiles.size();
+        s.bodies = bodies.data();
+        s.materials = mats.data();
+        s.faces = faces.data();
+        s.edges = edges.data();
+        s.tiles = tiles.data();
+        return s;
+    }
+};
+
 struct Link {
     LinkDev dev;
     drt_scene_view view{};
     std::shared_ptr<std::atomic<int>> inflight = std::make_shared<std::atomic<int>>(0);   // serving
+    std::shared_ptr<HostScene> scene;
     std::vector<void *> allocs;
     size_t bytes = 0;
     int32_t n_paths = 0;
@@ -65,7 +93,7 @@ struct drt_ctx {
     std::map<uint64_t, Link> links;
     uint64_t next_link = 1;
     Scratch pose, rec_a, rec_b, h, poseb, base, pose64, redo, warm, redo3, pp_tau, pp_amp, pp_fd, pp_fl, lt_tot,
-        lt_major, win_sel, win_starts;
+        lt_major, win_sel, win_starts, tr_faces, tr_rays, tr_count;
     double *probe_sink = nullptr;
     // side streams for work that overlaps within one call (FP32-bulk: anchors and the FP64
     // multi-diffraction paths run beside the FP32 kernel), joined back with events
@@ -607,7 +635,8 @@ void drt_destroy(drt_ctx *c) {
     for (auto &kv : c->links)
         for (void *p : kv.second.allocs) cudaFree(p);
     for (Scratch *s : {&c->pose, &c->rec_a, &c->rec_b, &c->h, &c->poseb, &c->base, &c->pose64, &c->redo, &c->warm, &c->redo3, &c->pp_tau,
-                       &c->pp_amp, &c->pp_fd, &c->pp_fl, &c->lt_tot, &c->lt_major, &c->win_sel, &c->win_starts})
+                       &c->pp_amp, &c->pp_fd, &c->pp_fl, &c->lt_tot, &c->lt_major, &c->win_sel, &c->win_starts,
+                       &c->tr_faces, &c->tr_rays, &c->tr_count})
         if (s->ptr) cudaFree(s->ptr);
     cudaFree(c->probe_sink);
     for (int i = 0; i < 2; ++i) {
@@ -622,13 +651,23 @@ void drt_destroy(drt_ctx *c) {
     delete c;
 }
 
-drt_status drt_load_paths(drt_ctx *c, const drt_scene *s, const drt_path_set *ps, uint64_t *out_link) {
-    if (!c || !out_link) return fail(DRT_EINVAL, "ctx and out_link must be non-NULL");
+}  // extern "C"
+
+namespace {
+
+// validate, pack and upload one link (the caller holds the context lock and set the device)
+drt_status load_link(drt_ctx *c, const drt_scene *s, const drt_path_set *ps, Link &L) {
     PackedLink H;
     if (drt_status st = pack_link(s, ps, H)) return st;
-    std::lock_guard<std::mutex> lk(c->mu);
-    CUDA_TRY(cudaSetDevice(c->device));
-    Link L;
+    auto hs = std::make_shared<HostScene>();
+    hs->tx = s->tx;
+    hs->rx = s->rx;
+    hs->bodies.assign(s->bodies, s->bodies + s->n_bodies);
+    hs->mats.assign(s->materials, s->materials + s->n_materials);
+    hs->faces.assign(s->faces, s->faces + s->n_faces);
+    hs->edges.assign(s->edges, s->edges + s->n_edges);
+    hs->tiles.assign(s->tiles, s->tiles + s->n_tiles);
+    L.scene = hs;
     L.dev = H.dev;
     L.view = H.view;
     L.n_paths = ps->n_paths;
@@ -659,8 +698,31 @@ drt_status drt_load_paths(drt_ctx *c, const drt_scene *s, const drt_path_set *ps
     if (st) {
         for (void *p : L.allocs) cudaFree(p);
         c->used -= L.bytes;
+        L.allocs.clear();
+        L.bytes = 0;
         return st;
     }
+    return DRT_OK;
+}
+
+void free_link(drt_ctx *c, Link &L) {
+    for (void *p : L.allocs) cudaFree(p);
+    c->used -= L.bytes;
+    L.allocs.clear();
+    L.bytes = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+drt_status drt_load_paths(drt_ctx *c, const drt_scene *s, const drt_path_set *ps, uint64_t *out_link) {
+    if (!c || !out_link) return fail(DRT_EINVAL, "ctx and out_link must be non-NULL");
+    if (!s || !ps) return fail(DRT_EINVAL, "scene and paths must be non-NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    CUDA_TRY(cudaSetDevice(c->device));
+    Link L;
+    if (drt_status st = load_link(c, s, ps, L)) return st;
     uint64_t id = c->next_link++;
     c->links.emplace(id, std::move(L));
     *out_link = id;
@@ -861,6 +923,101 @@ drt_status drt_synthesize_H_wideband(drt_ctx *c, uint64_t link, const drt_time_g
         const int n = k1 - k0;
         drt_freq_grid fs{fg->fc - 0.5 * fg->bandwidth + (k0 + 0.5 * n) * df, n * df, n, 0};
         if (drt_status st = synth_into(c, *L, tg, &fs, h + k0, precision, (cudaStream_t)stream, nullptr, N)) return st;
+    }
+    return DRT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// conventional ray tracing at t over a link's scene into host arrays (the context lock is held)
+drt_status trace_into(drt_ctx *c, Link &L, double t, int max_order, int with_tiles, drt_traced_paths *out,
+                      cudaStream_t s) {
+    const long long n_cand = trace_candidates(L.dev, max_order, with_tiles);
+    const int cap_dev = (int)std::min<long long>(n_cand, 1 << 22);
+    if (drt_status st = ensure(c, c->tr_faces, (size_t)std::max(L.dev.n_faces, 1) * trace_face_bytes())) return st;
+    if (drt_status st = ensure(c, c->tr_rays, (size_t)cap_dev * trace_ray_bytes())) return st;
+    if (drt_status st = ensure(c, c->tr_count, 256)) return st;
+    int *cnt = reinterpret_cast<int *>(c->tr_count.ptr);
+    CUDA_TRY(launch_trace(L.dev, t, max_order, with_tiles, c->tr_faces.ptr, c->tr_rays.ptr, cap_dev, cnt, s));
+    int count = 0;
+    CUDA_TRY(cudaMemcpyAsync(&count, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (count > cap_dev) return fail(DRT_ENOMEM, "ray tracing found %d rays, more than %d", count, cap_dev);
+    std::vector<char> rays((size_t)count * trace_ray_bytes());
+    if (count) CUDA_TRY(cudaMemcpy(rays.data(), c->tr_rays.ptr, rays.size(), cudaMemcpyDeviceToHost));
+    out->n_found = count;
+    trace_unpack(rays.data(), count, out->n_int, out->types, out->prims, out->s0, out->cap);
+    return DRT_OK;
+}
+
+drt_status check_trace_args(int32_t max_order, const drt_traced_paths *out) {
+    if (max_order < 0 || max_order > 2) return fail(DRT_EINVAL, "max_order must be 0, 1 or 2");
+    if (out && (out->cap < 0 || (out->cap > 0 && (!out->n_int || !out->types || !out->prims || !out->s0))))
+        return fail(DRT_EINVAL, "traced paths: cap >= 0 and non-NULL arrays required");
+    return DRT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+drt_status drt_trace_paths(drt_ctx *c, uint64_t link, double t, int32_t max_order, int32_t with_tiles,
+                           drt_traced_paths *out, void *stream) {
+    if (!c || !out) return fail(DRT_EINVAL, "ctx and out must be non-NULL");
+    if (!std::isfinite(t)) return fail(DRT_EINVAL, "t must be finite");
+    if (drt_status st = check_trace_args(max_order, out)) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    Link *L = find_link(c, link);
+    if (!L) return fail(DRT_ENOTFOUND, "unknown link %llu", (unsigned long long)link);
+    CUDA_TRY(cudaSetDevice(c->device));
+    return trace_into(c, *L, t, max_order, with_tiles != 0, out, (cudaStream_t)stream);
+}
+
+drt_status drt_synthesize_H_retraced(drt_ctx *c, uint64_t link, const drt_time_grid *tg, const drt_freq_grid *fg,
+                                     const int32_t *starts, int32_t n_windows, int32_t max_order, int32_t with_tiles,
+                                     void *H, int32_t precision, void *stream) {
+    if (!c) return fail(DRT_EINVAL, "ctx must be non-NULL");
+    if (drt_status st = check_grids(tg, fg, precision)) return st;
+    if (drt_status st = check_trace_args(max_order, nullptr)) return st;
+    const int T = tg->n_steps;
+    if (T > 0) {
+        if (!H || !starts || n_windows < 1 || starts[0] != 0)
+            return fail(DRT_EINVAL, "H, starts and n_windows >= 1 with starts[0] = 0 required");
+        for (int k = 1; k < n_windows; ++k)
+            if (starts[k] <= starts[k - 1] || starts[k] >= T)
+                return fail(DRT_EINVAL, "window starts must increase strictly and stay below n_steps");
+    }
+    std::lock_guard<std::mutex> lk(c->mu);
+    Link *L = find_link(c, link);
+    if (!L) return fail(DRT_ENOTFOUND, "unknown link %llu", (unsigned long long)link);
+    CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int F = fg->n_bins;
+    const drt_scene scene = L->scene->view();
+    for (int w = 0; w < n_windows && T > 0; ++w) {
+        const int k0 = starts[w], k1 = w + 1 < n_windows ? starts[w + 1] : T;
+        const double tw = tg->t_start + k0 * tg->dt;
+        // the window's chains: a ray-tracing run at its first instant
+        const long long n_cand = trace_candidates(L->dev, max_order, with_tiles != 0);
+        const int cap = (int)std::min<long long>(n_cand, 1 << 22);
+        std::vector<uint8_t> n_int(cap), types((size_t)cap * MAXI);
+        std::vector<int32_t> prims((size_t)cap * MAXI);
+        std::vector<double> s0((size_t)cap * MAXI);
+        drt_traced_paths tp{cap, 0, n_int.data(), types.data(), prims.data(), s0.data()};
+        if (drt_status st = trace_into(c, *L, tw, max_order, with_tiles != 0, &tp, s)) return st;
+        // extrapolated over the window's instants into its rows of H
+        const drt_path_set ps{tp.n_found, 0, n_int.data(), types.data(), prims.data(), s0.data()};
+        Link W;
+        if (drt_status st = load_link(c, &scene, &ps, W)) return st;
+        const drt_time_grid tw_grid{tw, tg->dt, k1 - k0, 0};
+        drt_status st = synth_into(c, W, &tw_grid, fg, reinterpret_cast<float2 *>(H) + (size_t)k0 * F, precision, s,
+                                   nullptr, F);
+        cudaError_t e = cudaStreamSynchronize(s);
+        free_link(c, W);
+        if (st) return st;
+        if (e != cudaSuccess) return fail(DRT_ECUDA, "window %d: %s", w, cudaGetErrorString(e));
     }
     return DRT_OK;
 }

@@ -224,5 +224,15 @@ cudaError_t launch_power_bin(bool fp64, const OutD &rec, int n_steps, int n_path
 cudaError_t launch_synth(const RecD &rec, int32_t n_paths, const TimeGridD &tg, const FreqGridD &fg,
                          float2 *H, cudaStream_t s, int ld = -1);
 cudaError_t launch_probe(int kind, int blocks, double *sink, cudaStream_t s, float *ms);
+// conventional ray tracing at an instant (drt_trace.cu): candidates of the enumeration, sizes of the
+// scratch records (faces posed at the instant, rays found), the launch, and the host-side unpacking of
+// `count` rays into path-set arrays in enumeration order
+long long trace_candidates(const LinkDev &L, int max_order, int with_tiles);
+size_t trace_ray_bytes();
+size_t trace_face_bytes();
+cudaError_t launch_trace(const LinkDev &L, double t, int max_order, int with_tiles, void *faces, void *rays, int cap,
+                         int *count, cudaStream_t s);
+void trace_unpack(const void *rays_host, int count, uint8_t *n_int, uint8_t *types, int32_t *prims, double *s0,
+                  int cap);
 
 }  // namespace drt

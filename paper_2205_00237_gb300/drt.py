@@ -28,7 +28,7 @@ EXPORTS = ["drt_create", "drt_destroy", "drt_last_error", "drt_load_paths", "drt
            "drt_profile_read", "drt_synthesize_H_noalloc", "drt_batch_create", "drt_batch_run", "drt_batch_info",
            "drt_batch_destroy", "drt_serve_start", "drt_serve_stop", "drt_submit", "drt_poll", "drt_wait",
            "drt_serve_stats_read", "drt_power_profile", "drt_lifetime_windows", "drt_synthesize_H_windows",
-           "drt_synthesize_H_wideband"]
+           "drt_synthesize_H_wideband", "drt_trace_paths", "drt_synthesize_H_retraced"]
 PP_DOPPLER, PP_DELAY = 0, 1
 
 
@@ -74,6 +74,11 @@ class _PowerGrid(C.Structure):
 
 class _LifetimeParams(C.Structure):
     _fields_ = [("share", C.c_double), ("min_steps", C.c_int32), ("max_steps", C.c_int32)]
+
+
+class _Traced(C.Structure):
+    _fields_ = [("cap", C.c_int32), ("n_found", C.c_int32), ("n_int", C.c_void_p), ("types", C.c_void_p),
+                ("prims", C.c_void_p), ("s0", C.c_void_p)]
 
 
 class _Request(C.Structure):
@@ -162,6 +167,11 @@ def load_library(path: str = LIB_PATH):
         L.drt_synthesize_H_windows.restype = st
         L.drt_synthesize_H_wideband.argtypes = [vp, C.c_uint64, vp, vp, C.c_int32, vp, C.c_int32, vp]
         L.drt_synthesize_H_wideband.restype = st
+        L.drt_trace_paths.argtypes = [vp, C.c_uint64, C.c_double, C.c_int32, C.c_int32, C.POINTER(_Traced), vp]
+        L.drt_trace_paths.restype = st
+        L.drt_synthesize_H_retraced.argtypes = [vp, C.c_uint64, vp, vp, vp, C.c_int32, C.c_int32, C.c_int32, vp,
+                                                C.c_int32, vp]
+        L.drt_synthesize_H_retraced.restype = st
         _lib = L
         return L
 
@@ -448,6 +458,39 @@ class Link:
         tgs, fgs = _tg(tg), _fg(fg)
         _check(load_library().drt_synthesize_H_wideband(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs),
                                                         int(n_sub), _dptr(H), int(precision), _stream_ptr(stream)))
+        return H
+
+    def trace_paths(self, t: float, max_order: int = 2, with_tiles: bool = True, cap: int = 1 << 16,
+                    stream=None) -> I.PathSet:
+        """drt_trace_paths: conventional ray tracing at instant t over this link's scene; the rays found,
+        in enumeration order, as a PathSet (edge parameters at t in s0)."""
+        while True:
+            n_int = np.zeros(cap, np.uint8)
+            types = np.zeros((cap, 4), np.uint8)
+            prims = np.zeros((cap, 4), np.int32)
+            s0 = np.zeros((cap, 4), np.float64)
+            tr = _Traced(int(cap), 0, n_int.ctypes.data, types.ctypes.data, prims.ctypes.data, s0.ctypes.data)
+            _check(load_library().drt_trace_paths(self.ctx._h, self.handle, float(t), int(max_order),
+                                                  1 if with_tiles else 0, C.byref(tr), _stream_ptr(stream)))
+            if tr.n_found <= cap:
+                n = tr.n_found
+                return I.PathSet(n_int[:n].copy(), types[:n].copy(), prims[:n].copy(), s0[:n].copy())
+            cap = tr.n_found
+
+    def synthesize_H_retraced(self, tg: I.TimeGrid, fg: I.FreqGrid, starts, max_order: int = 2,
+                              with_tiles: bool = True, precision: int = FP64, H=None, stream=None):
+        """drt_synthesize_H_retraced: H over T_C windows with a ray-tracing run at every window start."""
+        import torch
+        if H is None:
+            H = torch.empty((int(tg.n_steps), int(fg.n_bins)), dtype=torch.complex64,
+                            device=torch.device("cuda", self.ctx.device))
+        _check_buf(H, (tg.n_steps, fg.n_bins), torch.complex64, self.ctx.device)
+        st_ = np.ascontiguousarray(np.asarray(starts, dtype=np.int32))
+        tgs, fgs = _tg(tg), _fg(fg)
+        _check(load_library().drt_synthesize_H_retraced(self.ctx._h, self.handle, C.byref(tgs), C.byref(fgs),
+                                                        st_.ctypes.data if st_.size else None, int(st_.size),
+                                                        int(max_order), 1 if with_tiles else 0, _dptr(H),
+                                                        int(precision), _stream_ptr(stream)))
         return H
 
     def synthesize_H_noalloc(self, tg: I.TimeGrid, fg: I.FreqGrid, H, precision: int = FP64, stream=None):
