@@ -415,7 +415,9 @@ def run_batched(args, ctx, drt, flush):
                        f"steps U[100,5000] x 1 ms (mean {np.mean([t for _, _, t in spec]):.0f}), "
                        f"{w['n_bins']} bins over 400 MHz at 28 GHz",
            "path_steps_per_step": ps_steps, "precision": "DRT_FP32_BULK", "graph": True,
-           "synth_tile_variant": info["variant"], "scratch_gb": info["scratch_bytes"] / 1e9,
+           "synth_tile_variant": info["variant"], "chunk_div": info["chunk_div"],
+           "chunk_ns_per_step": [round(x, 4) for x in info["chunk_ns_per_step"]],
+           "scratch_gb": info["scratch_bytes"] / 1e9,
            "links_this_rank": len(spec),
            "redo_steps_per_step": info["redo_steps"],
            "redo_fraction": info["redo_steps"] / sum(P * T for _, P, T in spec),
@@ -572,7 +574,9 @@ def run_highway(args, ctx, drt, flush):
            "workload": f"{hw['n_links']} links x {P} paths ({hw['n_tiles']} ER tiles + {hw['n_rd']} R/D), "
                        f"carriers {[f / 1e9 for f in hw['carriers']]} GHz, {tg.n_steps} x {tg.dt * 1e3} ms, "
                        f"{hw['n_bins']} bins over {hw['bandwidth'] / 1e6:.0f} MHz, FP32-bulk",
-           "synth_tile_variant": info["variant"], "scratch_gb": info["scratch_bytes"] / 1e9,
+           "synth_tile_variant": info["variant"], "chunk_div": info["chunk_div"],
+           "chunk_ns_per_step": [round(x, 4) for x in info["chunk_ns_per_step"]],
+           "scratch_gb": info["scratch_bytes"] / 1e9,
            "redo_steps_per_step": info["redo_steps"], "redo_fraction": info["redo_steps"] / ps,
            "load_s": load_s, "plan_and_autotune_s": plan_s,
            "error": {"H_rel_max": max(e["H_rel_max"] for e in errs),

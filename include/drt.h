@@ -309,9 +309,10 @@ drt_status drt_synthesize_H_retraced(drt_ctx *ctx, uint64_t link, const drt_time
  * launch over the (link, work unit) pairs of all links, claimed with atomic counters, largest links
  * first, so uneven links (8 to thousands of paths, 100 to thousands of steps) share one launch per
  * stage.  Extrapolation and synthesis stream through a record buffer of at most 4 GiB in waves of
- * links.  The chunk length per link comes from a phase-error model and the synthesis frequency
- * tile (bins per thread) from timing its variants on the batch (autotuning, done synchronously
- * inside drt_batch_create).  Scratch is allocated once per batch within the HBM budget.  The links
+ * links.  The chunk length per link comes from a phase-error model, shortened by a factor 1, 2 or 4
+ * chosen by timing the first wave's preparation and extrapolation (drt_batch_tuning), and the
+ * synthesis frequency tile (bins per thread) from timing its variants on the batch (autotuning,
+ * done synchronously inside drt_batch_create).  Scratch is allocated once per batch within the HBM budget.  The links
  * must stay loaded and the H buffers valid while the batch exists.
  * drt_batch_run launches the batch on `stream`; with use_graph != 0 the first run is captured into
  * a CUDA graph (captured on a stream of the batch, so any stream can replay it) and later runs
@@ -331,6 +332,12 @@ drt_status drt_batch_run(drt_ctx *ctx, drt_batch *batch, int32_t use_graph, void
  * that run's H is then incomplete. */
 drt_status drt_batch_info(drt_ctx *ctx, const drt_batch *batch, int32_t *variant,
                           uint64_t *scratch_bytes, float *tune_ms, int64_t *redo_steps);
+/* the chunk length drt_batch_create chose: every link's chunk is the phase-error model's choice
+ * divided by *chunk_div (1, 2 or 4; at least 4 steps), the fastest of the three in ns_per_step
+ * (device time of the first wave's preparation and extrapolation over its path-steps, with the
+ * model's chunk, half and a quarter of it; 0 for a batch without path-steps); either output may be
+ * NULL.  Errors: DRT_EINVAL. */
+drt_status drt_batch_tuning(drt_ctx *ctx, const drt_batch *batch, int32_t *chunk_div, float ns_per_step[3]);
 void drt_batch_destroy(drt_ctx *ctx, drt_batch *batch);
 
 /* ---------------------------------------------------------------------------------------------

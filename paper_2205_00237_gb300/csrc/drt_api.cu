@@ -1135,6 +1135,9 @@ struct drt_batch {
     size_t bytes = 0;
     int32_t n_links = 0;
     float tune_ms = 0.f;
+    int32_t chunk_div = 1;                  // chosen divisor of the phase-error model's chunk
+    float chunk_ns[3] = {0.f, 0.f, 0.f};    // first wave's preparation + extrapolation, ns per path-step,
+                                            // at the model's chunk, 1/2 and 1/4 of it
 };
 
 extern "C" drt_status drt_batch_create(drt_ctx *c, int32_t n_links, const uint64_t *links, const drt_time_grid *tgrids,
@@ -1158,25 +1161,59 @@ extern "C" drt_status drt_batch_create(drt_ctx *c, int32_t n_links, const uint64
         views[i] = L->view;
     }
     CUDA_TRY(cudaSetDevice(c->device));
-    BatchPlan *P = nullptr;
-    size_t bytes = 0;
-    CUDA_TRY(batch_build(devs, views, tgrids, fgrids, H, nullptr, &P, &bytes));
+    // Chunk autotuning: the phase-error model gives each link the longest chunk whose FP32 deltas stay
+    // within the phase bar; shorter chunks meet it too (more FP64 anchors, shorter deltas).  Plans with
+    // the model's chunk, half and a quarter of it share one allocation (the largest), the first wave's
+    // preparation and extrapolation are timed in each (per path-step: the waves may differ), and the
+    // fastest plan is kept.
+    constexpr int N_DIV = 3;
+    const int divs[N_DIV] = {1, 2, 4};
+    BatchPlan *cand[N_DIV] = {nullptr, nullptr, nullptr};
+    size_t sizes[N_DIV] = {0, 0, 0}, bytes = 0;
+    auto drop = [&](int keep) {
+        for (int k = 0; k < N_DIV; ++k)
+            if (k != keep && cand[k]) batch_free(cand[k]);
+    };
+    for (int k = 0; k < N_DIV; ++k) {
+        cudaError_t e = batch_build(devs, views, tgrids, fgrids, H, nullptr, &cand[k], &sizes[k], divs[k]);
+        if (e != cudaSuccess) {
+            drop(-1);
+            return fail(DRT_ECUDA, "batch planning: %s", cudaGetErrorString(e));
+        }
+        bytes = std::max(bytes, sizes[k]);
+    }
     if (c->budget && c->used + bytes > c->budget) {
-        batch_free(P);
+        drop(-1);
         return fail(DRT_ENOMEM, "batch needs %zu bytes of scratch; HBM budget %llu, in use %llu", bytes,
                     (unsigned long long)c->budget, (unsigned long long)c->used);
     }
-    cudaError_t e = batch_alloc(P);
+    void *mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, std::max<size_t>(bytes, 256));
     if (e != cudaSuccess) {
-        batch_free(P);
+        drop(-1);
         return fail(DRT_ENOMEM, "batch allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
     }
+    float ns[N_DIV] = {0.f, 0.f, 0.f};
+    int best = 0;
+    cudaStream_t s0 = c->side[0];
+    for (int k = 0; k < N_DIV && e == cudaSuccess; ++k) {
+        e = batch_bind(cand[k], mem, s0);
+        if (e == cudaSuccess) e = batch_time_extrapolation(cand[k], s0, &ns[k]);
+        if (e == cudaSuccess && ns[k] < ns[best]) best = k;
+    }
+    drop(best);
+    BatchPlan *P = cand[best];
+    batch_adopt(P, mem);
+    if (e == cudaSuccess) e = batch_bind(P, mem, s0);   // the chosen plan's link table back in place
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s0);
     c->used += bytes;
     drt_batch *b = new drt_batch();
     b->plan = P;
     b->bytes = bytes;
     b->n_links = n_links;
-    e = batch_autotune(P, c->side[0], &b->tune_ms);
+    b->chunk_div = divs[best];
+    for (int k = 0; k < N_DIV; ++k) b->chunk_ns[k] = ns[k];
+    if (e == cudaSuccess) e = batch_autotune(P, s0, &b->tune_ms);
     if (e != cudaSuccess) {
         c->used -= bytes;
         batch_free(P);
@@ -1184,6 +1221,14 @@ extern "C" drt_status drt_batch_create(drt_ctx *c, int32_t n_links, const uint64
         return fail(DRT_ECUDA, "batch autotune: %s", cudaGetErrorString(e));
     }
     *out = b;
+    return DRT_OK;
+}
+
+extern "C" drt_status drt_batch_tuning(drt_ctx *c, const drt_batch *b, int32_t *chunk_div, float ns_per_step[3]) {
+    if (!c || !b) return fail(DRT_EINVAL, "ctx and batch must be non-NULL");
+    if (chunk_div) *chunk_div = b->chunk_div;
+    if (ns_per_step)
+        for (int k = 0; k < 3; ++k) ns_per_step[k] = b->chunk_ns[k];
     return DRT_OK;
 }
 

@@ -25,62 +25,15 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <numeric>
+#include <tuple>
 #include <type_traits>
 #include <vector>
 
-#include "drt_internal.h"
-#include "drt_physics.cuh"
+#include "drt_batch.cuh"
 
 namespace drt {
-
-// stage slots; the synthesis has one slot per tile variant (its units depend on the tile width)
-enum { ST_POSEB = 0, ST_POSE64 = 1, ST_WARM = 2, ST_BASE = 3, ST_BULK = 4, ST_SYNTH = 8, ST_BULKM = 11, N_STAGES = 12 };
-constexpr int BULK_W = 32;                // time steps per extrapolation unit (one warp's lanes)
-constexpr int SYNTH_U = 32;               // (step, tile) pairs per synthesis unit (one block) ...
-constexpr int SYNTH_PG = 4;               // ... whose warps split the paths
-constexpr int SYNTH_KT[3] = {8, 16, 32};
-constexpr size_t REC_BYTES = sizeof(float4) + sizeof(float);   // one synthesis record
-constexpr size_t REC_CAP = (size_t)4 << 30;                    // record buffer of one wave (bytes)
-constexpr size_t SCRATCH_CAP = (size_t)8 << 30;                // poses, warm starts, anchors of one wave
-
-struct alignas(16) BatchLink {
-    LinkDev L;
-    TimeGridD tg;
-    FreqGridD fg;
-    PoseB *poseb;      // [bodies + 2][chunks]
-    double *pose64;    // [bodies][chunks]
-    double *warm;      // [chunks + 1][n_paths - n_bulk][2 * MAXI]
-    BaseRec *base;     // [chunks][paths]
-    float2 *H;         // caller's [T][F]
-    OutD out;          // caller's optional per-path-step records (FP32 formats), [T][P]
-    size_t rec0;       // first record of this link in its wave's record buffer ([T][P])
-    long long it0[N_STAGES];   // first item per stage slot (4 on: counted within the link's wave)
-};
-
-// one launch: the links [l0, l1) of its stage or wave, its item count and claim counter
-struct BatchDev {
-    int l0, l1;
-    const BatchLink *links;
-    long long n_items;
-    long long it_base;   // stages 0-3: item of the wave's first link
-    unsigned long long *counter;
-    float4 *rec_a;
-    float *rec_b;
-    RedoList redo;   // items (link, path, step)
-};
-
-__device__ __forceinline__ int find_link(const BatchDev &B, int stage, long long it) {
-    int lo = B.l0, hi = B.l1 - 1;
-    while (lo < hi) {   // last link whose first item is <= it
-        int mid = (lo + hi + 1) >> 1;
-        if (B.links[mid].it0[stage] <= it) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ int chunks_of(const TimeGridD &tg) { return (tg.n_steps + tg.chunk - 1) / tg.chunk; }
 
 // stages 0-3: block-wide claims of blockDim.x consecutive items
 template <int STAGE>
@@ -116,44 +69,6 @@ __global__ void __launch_bounds__(128) k_stage(const BatchDev B) {
             int p = (int)(local / nch), c = (int)(local % nch);
             path_base_fp64(BL.L, BL.tg, BL.fg, BL.pose64, p, c, BL.base, BL.warm);
         }
-    }
-}
-
-// stage 4: a warp claims (link, path, 32 steps) and the lanes share the chain signature.  Chains of
-// up to 3 vertices with at most one diffraction between point sources run code unrolled for their
-// length, one persistent launch per length (stage slots 4 + N, unit ranges per length: the signature
-// sort makes each length a contiguous path range of its link), each with the register budget of its
-// length; the other chains (several diffractions in a segment, 4 vertices) are stage 8, generic code.
-// At most 128 registers: 16 warps per SM instead of 8 (4096-link batch +26 %); 1-vertex chains 24.
-template <int N, bool MULTI, bool OUT, class S>
-__device__ __forceinline__ void batch_unit(const BatchDev &B, const BatchLink &BL, int li, int p, int t) {
-    Rec5 r;
-    bulk_eval<N, MULTI, OUT, S>(BL.L, BL.tg, BL.fg, BL.poseb, BL.base, BL.warm, p, t, BL.out, r, B.redo, li);
-    const size_t ri = BL.rec0 + (size_t)t * BL.L.n_paths + p;
-    B.rec_a[ri] = make_float4(r.ar, r.ai, r.ph, r.hi);
-    B.rec_b[ri] = r.lo;
-}
-
-template <int N> struct BatchBlocks { static constexpr int v = N < 0 ? 4 : N <= 1 ? 6 : N == 2 ? 4 : 3; };
-
-// N >= 0: the units of the chains of length N; N < 0: the units of the generic chains
-template <int N, bool DUAL, bool OUT>
-__global__ void __launch_bounds__(128, BatchBlocks<N>::v) k_batch_bulk(const BatchDev B) {
-    typedef std::conditional_t<DUAL, dd, de> S;
-    constexpr int slot = N >= 0 ? ST_BULK + N : ST_BULKM;
-    const int lane = threadIdx.x & 31;
-    for (;;) {
-        unsigned long long it = 0;
-        if (lane == 0) it = atomicAdd(B.counter, 1ull);
-        it = __shfl_sync(0xffffffffu, it, 0);
-        if ((long long)it >= B.n_items) break;
-        const int li = find_link(B, slot, (long long)it);
-        const BatchLink &BL = B.links[li];
-        const long long local = (long long)it - BL.it0[slot];
-        const int nb = (BL.tg.n_steps + BULK_W - 1) / BULK_W;
-        const int p0 = N >= 0 ? BL.L.len_start[N >= 0 ? N : 0] : BL.L.len_start[MAXI];
-        const int p = p0 + (int)(local / nb), t = (int)(local % nb) * BULK_W + lane;
-        if (t < BL.tg.n_steps) batch_unit<N, (N < 0), (N < 0 || OUT), S>(B, BL, li, p, t);
     }
 }
 
@@ -222,7 +137,36 @@ __global__ void __launch_bounds__(SYNTH_U * SYNTH_PG) k_batch_synth(const BatchD
     }
 }
 
-// FP64 redo of queued steps; their contribution is added to H (all bins) with atomics
+// FP64 redo of queued steps; their contribution is added to H (all bins) with atomics, for the entry
+// and, for a carrier pair, its partner
+__device__ void redo_add_entry(const BatchLink &BL, int p, int ti) {
+    double r[3];
+    const RecD nor{nullptr, nullptr};
+    path_step_redo(BL.L, BL.tg, BL.fg, p, ti, BL.out, nor, BL.warm, r);
+    if (r[0] == 0.0 && r[1] == 0.0) return;
+    // a exp(-j 2 pi f_k tau): FP64-reduced seed per 16-bin tile, FP32 rotation across the tile
+    const double f0 = BL.fg.fc - 0.5 * BL.fg.bandwidth, df = BL.fg.bandwidth / BL.fg.n_bins;
+    const int F = BL.fg.n_bins;
+    float2 *row = BL.H + (size_t)ti * F;
+    double xs = df * r[2];
+    float ws, wc;
+    sincospif(2.f * (float)(xs - floor(xs)), &ws, &wc);
+    for (int k0 = 0; k0 < F; k0 += 16) {
+        double x = (f0 + k0 * df) * r[2];
+        float sn, cs;
+        sincospif(2.f * (float)(x - floor(x)), &sn, &cs);
+        const float ar = (float)r[0], ai = (float)r[1];
+        float zr = fmaf(ar, cs, ai * sn), zi = fmaf(ai, cs, -ar * sn);
+        for (int j = 0; j < 16 && k0 + j < F; ++j) {
+            atomicAdd(&row[k0 + j].x, zr);
+            atomicAdd(&row[k0 + j].y, zi);
+            const float nr = fmaf(zr, wc, zi * ws);
+            zi = fmaf(zi, wc, -zr * ws);
+            zr = nr;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(32) k_batch_redo(const BatchDev B) {   // one warp per block, spread over SMs
     if (blockIdx.x == 0 && threadIdx.x == 0) {   // the run's total; a wave whose count exceeds the list
         unsigned long long *hdr = reinterpret_cast<unsigned long long *>(B.redo.count);   // marks the run
@@ -233,31 +177,8 @@ __global__ void __launch_bounds__(32) k_batch_redo(const BatchDev B) {   // one 
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int4 itm = B.redo.items[k];
         const BatchLink &BL = B.links[itm.x];
-        double r[3];
-        const RecD nor{nullptr, nullptr};
-        path_step_redo(BL.L, BL.tg, BL.fg, itm.y, itm.z, BL.out, nor, BL.warm, r);
-        if (r[0] == 0.0 && r[1] == 0.0) continue;
-        // a exp(-j 2 pi f_k tau): FP64-reduced seed per 16-bin tile, FP32 rotation across the tile
-        const double f0 = BL.fg.fc - 0.5 * BL.fg.bandwidth, df = BL.fg.bandwidth / BL.fg.n_bins;
-        const int F = BL.fg.n_bins;
-        float2 *row = BL.H + (size_t)itm.z * F;
-        double xs = df * r[2];
-        float ws, wc;
-        sincospif(2.f * (float)(xs - floor(xs)), &ws, &wc);
-        for (int k0 = 0; k0 < F; k0 += 16) {
-            double x = (f0 + k0 * df) * r[2];
-            float sn, cs;
-            sincospif(2.f * (float)(x - floor(x)), &sn, &cs);
-            const float ar = (float)r[0], ai = (float)r[1];
-            float zr = fmaf(ar, cs, ai * sn), zi = fmaf(ai, cs, -ar * sn);
-            for (int j = 0; j < 16 && k0 + j < F; ++j) {
-                atomicAdd(&row[k0 + j].x, zr);
-                atomicAdd(&row[k0 + j].y, zi);
-                const float nr = fmaf(zr, wc, zi * ws);
-                zi = fmaf(zi, wc, -zr * ws);
-                zr = nr;
-            }
-        }
+        redo_add_entry(BL, itm.y, itm.z);
+        if (BL.partner >= 0 && itm.y >= BL.pair_p0) redo_add_entry(B.links[BL.partner], itm.y, itm.z);
     }
 }
 
@@ -269,7 +190,7 @@ __global__ void __launch_bounds__(32) k_batch_redo(const BatchDev B) {   // one 
 // allocation.
 // a wave: consecutive links whose records and scratch fit their buffers; its preparation items
 // [prep0, prep0 + n_prep) per stage 0-3, its bulk units and synthesis units per tile variant
-struct Wave { int l0, l1; long long prep0[4], n_prep[4], n_bulk[MAXI], n_bulkm, n_synth[3]; };
+struct Wave { int l0, l1; long long prep0[4], n_prep[4], n_bulk[MAXI], n_bulkm, n_synth[3], n_rec; };
 
 struct BatchPlan {
     int n_links = 0;
@@ -282,7 +203,8 @@ struct BatchPlan {
     bool owns = false;
     int variant = -1;   // synthesis tile width index (autotuner or caller)
     bool dual = false;  // some link asks for Doppler outputs: carry the rates
-    bool any_out = false;   // some link asks for per-path-step records
+    bool any_out = false;   // some link asks for per-path-step records (all units then run generic code)
+    bool any_pair = false;  // some entries form carrier pairs
     cudaGraphExec_t graph = nullptr;
     cudaStream_t capture = nullptr;   // private stream the graph is captured on (any caller stream,
                                       // the legacy default stream included, can then launch it)
@@ -343,41 +265,16 @@ static cudaError_t run_prep(BatchPlan &P, size_t w, cudaStream_t s) {
 
 static cudaError_t run_wave_bulk(BatchPlan &P, size_t w, cudaStream_t s) {
     const Wave &W = P.waves[w];
-    const int g4 = sm_count() * 4, g6 = sm_count() * 6;
     for (int n = 0; n < MAXI; ++n) {
         if (!W.n_bulk[n]) continue;
         const BatchDev B = dev_view(P, W.l0, W.l1, W.n_bulk[n], counter_of(w, 4 + n));
-        const int g = n <= 1 ? g6 : n == 2 ? g4 : sm_count() * 3;
-        if (P.dual) {
-            switch (n) {
-            case 0: k_batch_bulk<0, true, true><<<g, 128, 0, s>>>(B); break;
-            case 1: k_batch_bulk<1, true, true><<<g, 128, 0, s>>>(B); break;
-            case 2: k_batch_bulk<2, true, true><<<g, 128, 0, s>>>(B); break;
-            default: k_batch_bulk<3, true, true><<<g, 128, 0, s>>>(B); break;
-            }
-        } else if (P.any_out) {
-            switch (n) {
-            case 0: k_batch_bulk<0, false, true><<<g, 128, 0, s>>>(B); break;
-            case 1: k_batch_bulk<1, false, true><<<g, 128, 0, s>>>(B); break;
-            case 2: k_batch_bulk<2, false, true><<<g, 128, 0, s>>>(B); break;
-            default: k_batch_bulk<3, false, true><<<g, 128, 0, s>>>(B); break;
-            }
-        } else {
-            switch (n) {
-            case 0: k_batch_bulk<0, false, false><<<g, 128, 0, s>>>(B); break;
-            case 1: k_batch_bulk<1, false, false><<<g, 128, 0, s>>>(B); break;
-            case 2: k_batch_bulk<2, false, false><<<g, 128, 0, s>>>(B); break;
-            default: k_batch_bulk<3, false, false><<<g, 128, 0, s>>>(B); break;
-            }
-        }
-        if (cudaError_t e = cudaGetLastError()) return e;
+        if (cudaError_t e = launch_batch_bulk(n, false, P.any_pair, B, sm_count() * batch_bulk_blocks(n), s)) return e;
     }
     if (W.n_bulkm) {
         const BatchDev B = dev_view(P, W.l0, W.l1, W.n_bulkm, counter_of(w, 8));
-        if (P.dual) k_batch_bulk<-1, true, true><<<g4, 128, 0, s>>>(B);
-        else k_batch_bulk<-1, false, true><<<g4, 128, 0, s>>>(B);
+        return launch_batch_bulk(-1, P.dual, true, B, sm_count() * batch_bulk_blocks(-1), s);
     }
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 static cudaError_t run_wave_synth(BatchPlan &P, size_t w, cudaStream_t s, long long limit = -1) {
@@ -439,7 +336,7 @@ static size_t r256(size_t b) { return (b + 255) & ~(size_t)255; }
 // plan the batch on the host; *bytes is the size of the device block it needs
 cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::vector<drt_scene_view> &views,
                         const drt_time_grid *tgs, const drt_freq_grid *fgs, void *const *H, const OutD *outs,
-                        BatchPlan **out, size_t *bytes) {
+                        BatchPlan **out, size_t *bytes, int chunk_div) {
     const int n = (int)links.size();
     BatchPlan *P = new BatchPlan();
     P->n_links = n;
@@ -449,6 +346,48 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         return (long long)links[a]->n_paths * tgs[a].n_steps > (long long)links[b]->n_paths * tgs[b].n_steps;
     });
+    // carrier pairs: entries of the same link over the same time grid without per-path-step records
+    // (different carriers of one prediction) share the geometry; each second entry goes right after its
+    // first, in the same wave
+    auto no_out = [&](int i) {
+        if (!outs) return true;
+        const OutD &o = outs[i];
+        return !(o.tau || o.amp || o.doppler || o.angles || o.flags || o.points);
+    };
+    for (int i = 0; i < n; ++i)
+        if (!no_out(i)) P->any_out = true;
+    std::vector<int> mate(n, -1);
+    {
+        std::map<std::tuple<const LinkDev *, double, double, int>, int> open;
+        for (int k = 0; k < n; ++k) {
+            const int i = order[k];
+            if (!no_out(i)) continue;
+            auto key = std::make_tuple(links[i], tgs[i].t_start, tgs[i].dt, tgs[i].n_steps);
+            auto it = open.find(key);
+            if (it == open.end()) {
+                open.emplace(key, i);
+            } else {
+                mate[it->second] = i;
+                mate[i] = it->second;
+                open.erase(it);
+            }
+        }
+        std::vector<int> grouped;
+        std::vector<char> placed(n, 0);
+        for (int k = 0; k < n; ++k) {
+            const int i = order[k];
+            if (placed[i]) continue;
+            grouped.push_back(i);
+            placed[i] = 1;
+            if (mate[i] >= 0 && !placed[mate[i]]) {
+                grouped.push_back(mate[i]);
+                placed[mate[i]] = 1;
+            }
+        }
+        order.swap(grouped);
+    }
+    std::vector<int> pos(n);
+    for (int k = 0; k < n; ++k) pos[order[k]] = k;
     P->host.resize(n);
     size_t off = 0;   // scratch offsets; made absolute in batch_bind
     auto take = [&](size_t b) {
@@ -458,10 +397,11 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
     };
     long long it[4] = {};
     size_t rec_max = 0, scratch_max = 0;
-    Wave W{0, 0, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, 0, {0, 0, 0}};
+    Wave W{0, 0, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, 0, {0, 0, 0}, 0};
     size_t wave_rec = 0;
     auto close_wave = [&](int l1) {
         W.l1 = l1;
+        W.n_rec = (long long)wave_rec;
         for (int st = 0; st < 4; ++st) W.n_prep[st] = it[st] - W.prep0[st];
         P->waves.push_back(W);
         rec_max = std::max(rec_max, wave_rec);
@@ -472,14 +412,21 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
         BatchLink &B = P->host[k];
         std::memset(&B, 0, sizeof(B));
         B.L = *links[i];
+        const bool first = mate[i] >= 0 && pos[mate[i]] > k, second = mate[i] >= 0 && !first;
+        B.partner = first ? pos[mate[i]] : -1;
+        B.shared = second ? 1 : 0;
+        // a pair shares the chunks of its geometry: the shorter of the two carriers' choices
         int chunk = choose_chunk(views[i], tgs[i], fgs[i]);
+        if (mate[i] >= 0) chunk = std::min(chunk, choose_chunk(views[i], tgs[i], fgs[mate[i]]));
+        chunk = std::max(4, chunk / std::max(1, chunk_div));
         B.tg = make_tgrid(tgs[i].t_start, tgs[i].dt, tgs[i].n_steps, chunk);
         B.fg = make_fgrid(fgs[i].fc, fgs[i].bandwidth, fgs[i].n_bins);
         B.H = reinterpret_cast<float2 *>(H[i]);
         if (outs) B.out = outs[i];
         P->dual = P->dual || B.out.doppler != nullptr;
-        P->any_out = P->any_out || B.out.tau || B.out.amp || B.out.doppler || B.out.angles || B.out.flags ||
-                     B.out.points;
+        P->any_pair = P->any_pair || mate[i] >= 0;
+        B.gen_p0 = P->any_out ? 0 : B.L.len_start[MAXI];
+        B.pair_p0 = P->any_out ? 0 : B.L.len_start[2];
         const long long T = tgs[i].n_steps, Pn = B.L.n_paths;
         long long nch = (T + chunk - 1) / chunk;
         int md = B.L.n_paths - B.L.n_bulk;
@@ -490,9 +437,9 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
         // waves: consecutive links whose records fit the record buffer and whose scratch fits its cap
         // (the scratch of a wave is reused by the next one)
         const size_t recs = (size_t)T * Pn;
-        if (k > W.l0 && ((wave_rec + recs) * REC_BYTES > REC_CAP || off + sbytes > SCRATCH_CAP)) {
+        if (k > W.l0 && !second && ((wave_rec + recs) * REC_BYTES > REC_CAP || off + sbytes > SCRATCH_CAP)) {
             close_wave(k);
-            W = Wave{k, k, {it[0], it[1], it[2], it[3]}, {0, 0, 0, 0}, {0, 0, 0, 0}, 0, {0, 0, 0}};
+            W = Wave{k, k, {it[0], it[1], it[2], it[3]}, {0, 0, 0, 0}, {0, 0, 0, 0}, 0, {0, 0, 0}, 0};
             wave_rec = 0;
             off = 0;
         }
@@ -508,13 +455,16 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
         }
         B.rec0 = wave_rec;
         wave_rec += recs;
+        // units of 32 steps per path: a pair's second entry has those of its lengths 0 and 1 only (the
+        // others are evaluated by its first entry together with the first's own)
         const long long nbw = (T + BULK_W - 1) / BULK_W;
         for (int nl = 0; nl < MAXI; ++nl) {
             B.it0[ST_BULK + nl] = W.n_bulk[nl];
-            W.n_bulk[nl] += (long long)(B.L.len_start[nl + 1] - B.L.len_start[nl]) * nbw;
+            if (!P->any_out && !(second && nl >= 2))
+                W.n_bulk[nl] += (long long)(B.L.len_start[nl + 1] - B.L.len_start[nl]) * nbw;
         }
         B.it0[ST_BULKM] = W.n_bulkm;
-        W.n_bulkm += (Pn - B.L.len_start[MAXI]) * nbw;
+        if (!second) W.n_bulkm += (Pn - B.gen_p0) * nbw;
         for (int v = 0; v < 3; ++v) {   // a link without paths gets H = 0
             const long long pairs = T * ((fgs[i].n_bins + SYNTH_KT[v] - 1) / SYNTH_KT[v]);
             B.it0[ST_SYNTH + v] = W.n_synth[v];
@@ -612,6 +562,37 @@ cudaError_t batch_autotune(BatchPlan *P, cudaStream_t s, float *best_ms) {
     P->variant = pick;
     *best_ms = best;
     return e;
+}
+
+cudaError_t batch_time_extrapolation(BatchPlan *P, cudaStream_t s, float *ns) {
+    *ns = 0.f;
+    if (P->waves.empty() || P->waves[0].n_rec == 0) return cudaSuccess;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    cudaError_t e = cudaSuccess;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first pass warms up
+        e = cudaMemsetAsync(P->mem, 0, sizeof(unsigned long long) * P->n_counters, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(P->mem + P->off_redo, 0, 24, s);
+        cudaEventRecord(a, s);
+        if (e == cudaSuccess) e = run_prep(*P, 0, s);
+        if (e == cudaSuccess) e = run_wave_bulk(*P, 0, s);
+        cudaEventRecord(b, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, a, b);
+        if (rep == 1) best = t;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *ns = (float)(best * 1e6 / (double)P->waves[0].n_rec);   // the waves of the plans may differ
+    return e;
+}
+
+void batch_adopt(BatchPlan *P, void *mem) {
+    P->mem = reinterpret_cast<char *>(mem);
+    P->owns = true;
 }
 
 cudaError_t batch_run(BatchPlan *P, cudaStream_t s, bool use_graph) {

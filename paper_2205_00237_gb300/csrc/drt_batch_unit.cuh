@@ -1,0 +1,59 @@
+// drt_batch_unit.cuh -- the extrapolation unit of a batch plan (stage 4: one warp, one (link, path,
+// 32 steps) unit), shared by the unrolled per-length kernels (drt_k_batch.cu) and the generic-code
+// kernel (drt_k_batch_gen.cu), which compile in separate translation units.
+#pragma once
+#include <type_traits>
+
+#include "drt_batch.cuh"
+
+namespace drt {
+
+template <int N, bool MULTI, bool OUT, bool PAIR, class S>
+__device__ __forceinline__ void batch_unit(const BatchDev &B, const BatchLink &BL, int li, int p, int t) {
+    Rec5 r, r2;
+    const BatchLink *Q = (PAIR && BL.partner >= 0) ? &B.links[BL.partner] : nullptr;
+    if (PAIR && Q)
+        bulk_eval<N, MULTI, OUT, S>(BL.L, BL.tg, BL.fg, BL.poseb, BL.base, BL.warm, p, t, BL.out, r, B.redo, li,
+                                    &Q->fg, Q->base, &r2);
+    else
+        bulk_eval<N, MULTI, OUT, S>(BL.L, BL.tg, BL.fg, BL.poseb, BL.base, BL.warm, p, t, BL.out, r, B.redo, li);
+    const size_t ri = BL.rec0 + (size_t)t * BL.L.n_paths + p;
+    B.rec_a[ri] = make_float4(r.ar, r.ai, r.ph, r.hi);
+    B.rec_b[ri] = r.lo;
+    if (PAIR && Q) {
+        const size_t r2i = Q->rec0 + (size_t)t * BL.L.n_paths + p;
+        B.rec_a[r2i] = make_float4(r2.ar, r2.ai, r2.ph, r2.hi);
+        B.rec_b[r2i] = r2.lo;
+    }
+}
+
+template <int N> struct BatchBlocks { static constexpr int v = N < 0 ? 4 : N <= 1 ? 6 : N == 2 ? 4 : 3; };
+
+// N >= 0: the units of the chains of length N (no records); N < 0: the units of the generic range
+template <int N, bool DUAL, bool PAIR>
+__global__ void __launch_bounds__(128, BatchBlocks<N>::v) k_batch_bulk(const BatchDev B) {
+    typedef std::conditional_t<DUAL, dd, de> S;
+    constexpr int slot = N >= 0 ? ST_BULK + N : ST_BULKM;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(B.counter, 1ull);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if ((long long)it >= B.n_items) break;
+        const int li = find_link(B, slot, (long long)it);
+        const BatchLink &BL = B.links[li];
+        const long long local = (long long)it - BL.it0[slot];
+        const int nb = (BL.tg.n_steps + BULK_W - 1) / BULK_W;
+        const int p0 = N >= 0 ? BL.L.len_start[N >= 0 ? N : 0] : BL.gen_p0;
+        const int p = p0 + (int)(local / nb), t = (int)(local % nb) * BULK_W + lane;
+        if (t < BL.tg.n_steps) {
+            if constexpr (N >= 0) batch_unit<N, false, false, PAIR, S>(B, BL, li, p, t);
+            else if (BL.partner >= 0) batch_unit<-1, true, true, true, S>(B, BL, li, p, t);
+            else batch_unit<-1, true, true, false, S>(B, BL, li, p, t);
+        }
+    }
+}
+
+cudaError_t launch_batch_bulk_gen(bool dual, const BatchDev &B, int grid, cudaStream_t s);
+
+}  // namespace drt

@@ -104,9 +104,14 @@ struct drt_scene_view { double vmax, amax, wmax; };
 
 // a10 batch plans (drt_batch.cu)
 struct BatchPlan;
+// chunk_div: every link's chunk is the phase-error model's choice divided by chunk_div (at least 4 steps)
 cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::vector<drt_scene_view> &views,
                         const drt_time_grid *tgs, const drt_freq_grid *fgs, void *const *H, const OutD *outs,
-                        BatchPlan **out, size_t *bytes);
+                        BatchPlan **out, size_t *bytes, int chunk_div = 1);
+// device time of the first wave's preparation and extrapolation stages of a bound plan, in ns per
+// path-step of that wave
+cudaError_t batch_time_extrapolation(BatchPlan *P, cudaStream_t s, float *ns);
+void batch_adopt(BatchPlan *P, void *mem);   // the plan, bound to mem, takes ownership of it
 cudaError_t batch_bind(BatchPlan *P, void *mem, cudaStream_t s);
 cudaError_t batch_alloc(BatchPlan *P);
 cudaError_t batch_autotune(BatchPlan *P, cudaStream_t s, float *best_ms);

@@ -1,0 +1,13 @@
+// drt_k_batch_gen.cu -- stage 4 of a batch plan for the chains that run the generic code (several
+// diffractions in a segment, 4 vertices, or any chain of a batch that writes per-path-step records).
+#include "drt_batch_unit.cuh"
+
+namespace drt {
+
+cudaError_t launch_batch_bulk_gen(bool dual, const BatchDev &B, int grid, cudaStream_t s) {
+    if (dual) k_batch_bulk<-1, true, false><<<grid, 128, 0, s>>>(B);
+    else k_batch_bulk<-1, false, false><<<grid, 128, 0, s>>>(B);
+    return cudaGetLastError();
+}
+
+}  // namespace drt

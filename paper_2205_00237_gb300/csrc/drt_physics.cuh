@@ -406,7 +406,7 @@ template <int N, class S>
 DRT_HD void solve_geometry_fast(const Prim<S> *pr, v3<S> *V, uint32_t &fl) {
     static_assert(N >= 0 && N <= MAXI, "chain length");
     bool has_d = false;
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
     for (int i = 1; i <= N; ++i) {
         if (pr[i - 1].type == T_S) V[i] = pr[i - 1].p;   // Sec. III-C: tile centroid moves rigidly
         has_d = has_d || pr[i - 1].type == T_D;
@@ -417,7 +417,7 @@ DRT_HD void solve_geometry_fast(const Prim<S> *pr, v3<S> *V, uint32_t &fl) {
         // point source imaged through the reflections in between) and its virtual receiver (the right
         // point source imaged backwards through the reflections after it)
         v3<S> cur = V[0];
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
         for (int i = 1; i <= N; ++i) {
             const Prim<S> &q = pr[i - 1];
             if (q.type == T_D) img[i - 1] = cur;
@@ -425,7 +425,7 @@ DRT_HD void solve_geometry_fast(const Prim<S> *pr, v3<S> *V, uint32_t &fl) {
             else cur = V[i];
         }
         cur = V[N + 1];
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
         for (int i = N; i >= 1; --i) {
             const Prim<S> &q = pr[i - 1];
             if (q.type == T_D) V[i] = q.p + q.a * keller_s(img[i - 1], cur, q, fl);
@@ -438,7 +438,7 @@ DRT_HD void solve_geometry_fast(const Prim<S> *pr, v3<S> *V, uint32_t &fl) {
     // before it; the points are placed from the right, each by Eq. ref_point towards the point placed
     // before it
     v3<S> cur = V[0];
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
     for (int i = 1; i <= N; ++i) {
         const Prim<S> &q = pr[i - 1];
         if (q.type == T_R) {
@@ -449,7 +449,7 @@ DRT_HD void solve_geometry_fast(const Prim<S> *pr, v3<S> *V, uint32_t &fl) {
         }
     }
     v3<S> next = V[N + 1];
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
     for (int i = N; i >= 1; --i) {
         const Prim<S> &q = pr[i - 1];
         if (q.type == T_R) V[i] = refl_point(img[i - 1], next, q.p, q.a);
@@ -466,10 +466,6 @@ DRT_HD void solve_geometry(const Prim<S> *pr, int n, v3<S> *V, const double *s0,
     else solve_geometry_generic(pr, n, V, s0, fl, ds0, rate0);
 }
 
-template <class T> DRT_HD T wrap2pi(T x) {
-    x = fmod(x, T(2 * PI));
-    return x < T(0) ? x + T(2 * PI) : x;
-}
 
 // validity (Sec. II: the t0 multipath structure still holds): reflection points inside their
 // faces with both neighbours in front, diffraction points on their edge segments with both
@@ -495,13 +491,13 @@ DRT_HD uint32_t validity(const Prim<S> *pr, int n, const v3<typename ST<S>::R> *
     const int nv = N >= 0 ? N : n;
     uint32_t fl = 0;
     bool near = false;   // FP32 only: some margin within the error bound
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
     for (int i = 1; i <= MAXI + 1; ++i) {
         if (i > nv + 1) break;
         v3<T> d = P[i] - P[i - 1];
         if (!(dot(d, d) >= T(1e-18))) fl |= F_DEGEN;
     }
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
     for (int i = 1; i <= MAXI; ++i) {
         if (i > nv) break;
         const Prim<S> &q = pr[i - 1];
@@ -526,7 +522,7 @@ DRT_HD uint32_t validity(const Prim<S> *pr, int n, const v3<typename ST<S>::R> *
                 tol = fp32_margin_tol(fmax(fmax(amax3(P[i - 1]), amax3(P[i + 1])), fmax(amax3(P[i]), amax3(A))));
                 near = near || fabs(s) < tol || fabs(q.h1 - s) < tol;
             }
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
             for (int side = -1; side <= 1; side += 2) {
                 // the neighbour's direction about the edge, at angle phi from the 0-face tangent
                 // towards the 0-face normal, must lie in the exterior (0, n pi), 1 <= n <= 2: phi in
@@ -807,7 +803,7 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
     const int nv = N >= 0 ? N : n;
     v3<T> kd[MAXI + 2];
     T len[MAXI + 2];
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
     for (int i = 1; i <= MAXI + 1; ++i) {
         if (i > nv + 1) break;
         const T q = dot(seg[i], seg[i]), rs = rsqrt(q);   // one reciprocal square root per segment
@@ -818,7 +814,7 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
     T snx[MAXI + 1];
     {
         T acc = T(0);
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
         for (int i = MAXI; i >= 1; --i) {
             if (i > nv) continue;
             acc += len[i + 1];
@@ -837,7 +833,7 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
         T d = T(0), re = T(0);          // distance since the point source or latest diffraction; its rho_e
         bool after_d = false;
         v3<T> X1 = V3<T>(T(0), T(0), T(0));   // after a diffraction: direction of its caustic on the edge
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
         for (int i = 1; i <= MAXI + 1; ++i) {
             if (i > nv + 1) break;
             d += len[i];
@@ -869,7 +865,7 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
             }
             // the caustic direction is only needed by a later diffraction of the same stretch
             bool more_d = false;
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
             for (int j = i + 1; j <= MAXI; ++j) {
                 if (j > nv || pr[j - 1].type == T_S) break;
                 more_d = more_d || pr[j - 1].type == T_D;
@@ -883,7 +879,7 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
     const T ieps = T(1) / (T(2 * PI) * fc * T(EPS0));   // eps_c = eps_r - j sigma ieps
     c3<T> E = cscale(vertical_pol(kd[1]), C<T>(T(1), T(0)));
     v3<T> klast = kd[1];
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
     for (int i = 1; i <= MAXI; ++i) {
         if (i > nv) break;
         const Prim<S> &q = pr[i - 1];
@@ -909,8 +905,10 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
             v3<T> wi = -kin + e * dot(kin, e);
             v3<T> wo = kout - e * dot(kout, e);
             const T yi = dot(wi, q.c), xi = dot(wi, q.b), yo = dot(wo, q.c), xo = dot(wo, q.b);
-            T phip = wrap2pi(atan2(yi, xi));
-            T phi = wrap2pi(atan2(yo, xo));
+            // atan2 lies in [-pi, pi]: one conditional turn maps it to [0, 2 pi) (no fmod)
+            T phip = atan2(yi, xi), phi = atan2(yo, xo);
+            if (phip < T(0)) phip += T(2 * PI);
+            if (phi < T(0)) phi += T(2 * PI);
             T sinb0 = norm(cross(kin, e));
             const T Lp = Lfac[i] * sinb0 * sinb0;
             T sphip = T(0), snphi = T(0);
@@ -933,10 +931,11 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
             T cpsi = dot(kspec, kout);
             int alpha = tl.alpha;
             T Fa = er_norm<T>(alpha, cti);
-            T lobe = T(1);
-            T hb = T(0.5) * (T(1) + cpsi);
-            for (int j = 0; j < alpha; ++j) lobe *= hb;   // ((1 + cos psi)/2)^alpha
-            T amp = tl.s * sqrt(tl.area * cti / Fa) * sqrt(lobe);
+            const T hb = T(0.5) * (T(1) + cpsi);
+            T lobe_h = T(1);   // ((1 + cos psi)/2)^(alpha/2): the field of the power lobe
+            for (int j = 0; j < alpha / 2; ++j) lobe_h *= hb;
+            if (alpha & 1) lobe_h *= sqrt(hb);
+            T amp = tl.s * sqrt(tl.area * cti / Fa) * lobe_h;
             cx<T> ph = C<T>(tl.cph, tl.sph);
             T nE = cnorm(E);
             cx<T> ek = cdot(E, kout);
@@ -958,7 +957,7 @@ DRT_HD T doppler(int n, const v3<S> *V, const v3<T> *seg, T fc) {
     const int nv = N >= 0 ? N : n;
     T acc = T(0);
     const T ic = T(1) / T(C0);
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
     for (int i = 1; i <= MAXI + 1; ++i) {
         if (i > nv + 1) break;
         v3<T> k = unit(seg[i]);
@@ -1071,7 +1070,7 @@ DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const Fre
     const int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
     int n = 0;
     Prim<S> pr[MAXI];
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
     for (int j = 0; j < (N >= 0 ? N : MAXI); ++j) {
         const int ty = (code >> (8 * j)) & 0xff;
         if (N >= 0 || ty != T_NONE) {
@@ -1095,7 +1094,7 @@ DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const Fre
     v3<T> P[MAXI + 2];
     v3<T> seg[MAXI + 2];
     T d = T(0);
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
     for (int i = 0; i <= MAXI + 1; ++i) {
         if (i > n + 1) break;
         P[i] = val(V[i]);
@@ -1113,7 +1112,7 @@ DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const Fre
             if constexpr (!std::is_same<S, double>::value) fd = doppler<N>(n, V, seg, T(fg.fc));
             const size_t oi = (size_t)ti * L.n_paths + L.perm[p];
             v3<T> s_last = seg[1];
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
             for (int i = 2; i <= MAXI + 1; ++i)
                 if (i == n + 1) s_last = seg[i];
             if (f32out) {
@@ -1497,12 +1496,16 @@ struct Rec5 { float ar, ai, ph, hi, lo; };
 // parameters (warm, may be null for the others).  Returns false when the step was queued for the
 // FP64 redo (its record is then zero).  S = dd carries the rates the Doppler shift needs, S = de
 // (calls without Doppler output) leaves them out.  N, MULTI and OUT as for path_step_fp64_core.
+// A second carrier (fg2 with its anchors base2; the same time grid and chunks) shares the geometry:
+// its field coefficients and phase record go to *rec2.
 template <int N = -1, bool MULTI = true, bool OUT = true, class S = dd>
 DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const PoseB *poseb,
                       const BaseRec *base, const double *warm, int p, int ti, const OutD &out, Rec5 &rec,
-                      const RedoList &redo, int link) {
+                      const RedoList &redo, int link, const FreqGridD *fg2 = nullptr, const BaseRec *base2 = nullptr,
+                      Rec5 *rec2 = nullptr) {
     typedef float T;
     rec = Rec5{0.f, 0.f, 0.f, 0.f, 0.f};
+    if (rec2) *rec2 = Rec5{0.f, 0.f, 0.f, 0.f, 0.f};
     const int n_chunks = (tg.n_steps + tg.chunk - 1) / tg.chunk;
     const int chunk = ti / tg.chunk;
     const float tau_t = (float)(ti - chunk * tg.chunk) * tg.dtf;
@@ -1511,7 +1514,7 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
     const int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
     int n = 0;
     Prim<S> pr[MAXI];
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
     for (int j = 0; j < (N >= 0 ? N : MAXI); ++j) {
         const int ty = (code >> (8 * j)) & 0xff;
         if (N >= 0 || ty != T_NONE) {
@@ -1534,7 +1537,7 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
         solve_geometry<N, MULTI>(pr, n, V, L.ps0 + (size_t)p * MAXI, fl);
     }
     v3<T> P[MAXI + 2];
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
     for (int i = 0; i <= MAXI + 1; ++i) {
         if (i > n + 1) break;
         P[i] = val(V[i]);
@@ -1548,13 +1551,14 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
         // 1/fc) are left to the FP64 redo.
         float disp2 = 0.f;
         bool finite = true;
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
         for (int i = 1; i <= MAXI; ++i) {
             if (i > n) break;
             disp2 = fmaxf(disp2, V[i].x.d * V[i].x.d + V[i].y.d * V[i].y.d + V[i].z.d * V[i].z.d);
             finite = finite && isfinite(P[i].x) && isfinite(P[i].y) && isfinite(P[i].z);
         }
-        if (disp2 > fg.disp_lim * fg.disp_lim) fl |= F_REDO64;
+        const float dlim = fg2 ? fminf(fg.disp_lim, fg2->disp_lim) : fg.disp_lim;
+        if (disp2 > dlim * dlim) fl |= F_REDO64;
         if (!finite || (fl & (F_REDO64 | F_NOCONV | F_DEGEN))) {
             // geometry FP32 cannot resolve: queue this path-step for the FP64 redo kernel (rare,
             // see F_REDO64); the list holds every path-step in the worst case
@@ -1578,7 +1582,7 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
     const BaseRec &B = base[(size_t)chunk * L.n_paths + p];
     float dd_len = 0.f;   // change of the path length since the chunk base
     v3<float> seg[MAXI + 2];
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
     for (int i = 1; i <= MAXI + 1; ++i) {
         if (i > n + 1) break;
         v3<S> sv = V[i] - V[i - 1];
@@ -1593,22 +1597,28 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
             if constexpr (std::is_same<S, dd>::value) fd = doppler<N>(n, V, seg, fg.fcf);
             const size_t oi = (size_t)ti * L.n_paths + L.perm[p];
             v3<float> s_last = seg[1];
-#pragma unroll
+#pragma unroll (N >= 0 ? 8 : 1)
             for (int i = 2; i <= MAXI + 1; ++i)
                 if (i == n + 1) s_last = seg[i];
             write_outputs_bulk(out, oi, n, V, seg[1], s_last, (B.d + (double)dd_len) / C0, a, fd, fl);
         }
     }
-    const float f0c = fg.f0c, dfc = fg.dfc;
-    float x = f0c * dd_len;
-    x -= floorf(x);
-    float ph = B.ph0 + x;
-    ph -= floorf(ph);
-    rec.ar = fl ? 0.f : a.re;
-    rec.ai = fl ? 0.f : a.im;
-    rec.ph = ph;
-    rec.hi = B.st_hi;
-    rec.lo = fmaf(dfc, dd_len, B.st_lo);
+    auto phase_record = [&](const FreqGridD &g, const BaseRec &Bk, cx<T> ak, Rec5 &r) {
+        float x = g.f0c * dd_len;
+        x -= floorf(x);
+        float ph = Bk.ph0 + x;
+        ph -= floorf(ph);
+        r.ar = fl ? 0.f : ak.re;
+        r.ai = fl ? 0.f : ak.im;
+        r.ph = ph;
+        r.hi = Bk.st_hi;
+        r.lo = fmaf(g.dfc, dd_len, Bk.st_lo);
+    };
+    phase_record(fg, B, a, rec);
+    if (fg2) {
+        const cx<T> a2 = (fl & F_DEGEN) ? C<T>(T(0), T(0)) : amplitude<N>(L, pr, n, seg, fg2->fcf);
+        phase_record(*fg2, base2[(size_t)chunk * L.n_paths + p], a2, *rec2);
+    }
     return true;
 }
 

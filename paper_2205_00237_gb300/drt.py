@@ -28,7 +28,7 @@ EXPORTS = ["drt_create", "drt_destroy", "drt_last_error", "drt_load_paths", "drt
            "drt_profile_read", "drt_synthesize_H_noalloc", "drt_batch_create", "drt_batch_run", "drt_batch_info",
            "drt_batch_destroy", "drt_serve_start", "drt_serve_stop", "drt_submit", "drt_poll", "drt_wait",
            "drt_serve_stats_read", "drt_power_profile", "drt_lifetime_windows", "drt_synthesize_H_windows",
-           "drt_synthesize_H_wideband", "drt_trace_paths", "drt_synthesize_H_retraced"]
+           "drt_synthesize_H_wideband", "drt_trace_paths", "drt_synthesize_H_retraced", "drt_batch_tuning"]
 PP_DOPPLER, PP_DELAY = 0, 1
 
 
@@ -144,6 +144,8 @@ def load_library(path: str = LIB_PATH):
         L.drt_batch_info.argtypes = [vp, vp, C.POINTER(C.c_int32), C.POINTER(C.c_uint64), C.POINTER(C.c_float),
                                      C.POINTER(C.c_int64)]
         L.drt_batch_info.restype = st
+        L.drt_batch_tuning.argtypes = [vp, vp, C.POINTER(C.c_int32), C.POINTER(C.c_float)]
+        L.drt_batch_tuning.restype = st
         L.drt_batch_destroy.argtypes = [vp, vp]
         L.drt_batch_destroy.restype = None
         L.drt_serve_start.argtypes = [vp, C.c_uint64, C.c_int32, C.c_int32]
@@ -521,6 +523,10 @@ class Batch:
         out = dict(variant=v.value, scratch_bytes=b.value, tune_ms=ms.value)
         if redo:
             out["redo_steps"] = r.value
+        div, cms = C.c_int32(), (C.c_float * 3)()
+        _check(load_library().drt_batch_tuning(self.ctx._h, self._h, C.byref(div), cms))
+        out["chunk_div"] = div.value
+        out["chunk_ns_per_step"] = [float(x) for x in cms]
         return out
 
     def close(self):

@@ -60,6 +60,10 @@ def test_uneven_batch_matches_oracle_and_single_link(ctx):
         torch.cuda.synchronize()
         info = b.info(redo=True)
         assert 0 <= info["variant"] < 3 and info["scratch_bytes"] > 0
+        # the chunk autotuner timed the model's chunk, half and a quarter of it and kept the fastest
+        ns = info["chunk_ns_per_step"]
+        assert info["chunk_div"] in (1, 2, 4) and min(ns) > 0
+        assert ns[(1, 2, 4).index(info["chunk_div"])] == min(ns)
         got = [h.cpu().numpy() for h in Hs]
         for (sc, ps, tg, fg), link, H in zip(cases, links, got):
             assert np.isfinite(H).all()
@@ -161,3 +165,28 @@ def test_batched_workload_sample_at_scale(ctx):
             compare_H_band(Hg[j:j + 1], r, fgs[i])
     for lk in loaded.values():
         lk.unload()
+
+
+def test_carrier_pairs_share_the_geometry(ctx):
+    """Entries of one link over one time grid at different carriers (28 and 60 GHz, different bin
+    counts) form carrier pairs that evaluate the geometry once; each carrier's H must still match the
+    oracle at its own carrier, with and without graph replay, and a third, unpaired entry of the same
+    link over another grid must be unaffected.  The canyon link has chains of every length and
+    multi-diffraction chains, so every kind of unit (per-carrier, paired, generic) is exercised."""
+    import torch
+    sc, ps = I.scene_canyon(0), I.PathSet.from_npz(os.path.join(GOLD, "pathset_canyon_seed0.npz"))
+    link = ctx.load(sc, ps)
+    tg = I.TimeGrid(0.05, 0.5e-3, 160)
+    entries = [(tg, I.FreqGrid(28e9, 400e6, 256)), (tg, I.FreqGrid(60e9, 1e9, 512)),
+               (I.TimeGrid(0.3, 0.5e-3, 90), I.FreqGrid(60e9, 1e9, 128))]
+    Hs = [torch.full((t.n_steps, f.n_bins), float("nan"), dtype=torch.complex64, device="cuda") for t, f in entries]
+    with ctx.batch([link] * 3, [e[0] for e in entries], [e[1] for e in entries], Hs) as b:
+        for use_graph in (False, True, True):
+            for H in Hs:
+                H.fill_(float("nan"))
+            b.run(use_graph=use_graph)
+            torch.cuda.synchronize()
+            for (t, f), H in zip(entries, Hs):
+                r = O.extrapolate(sc, ps, t, f.fc, n_threads=8)
+                compare_H_band(H.cpu().numpy(), r, f)
+    link.unload()
