@@ -71,13 +71,16 @@ RECORD_BYTES = {"fp64": 49, "fp32_bulk": 37}
 
 
 def kernel_source_hash():
-    """Hash of the library's CUDA sources (the roofline constants above belong to one of them)."""
+    """Hash of the sources the device code compiles from: the kernel translation units (drt_k_*.cu,
+    drt_kernels.cu) and every header (the roofline constants above belong to one version of them; the
+    host-only files drt_api.cu, drt_batch.cu, drt_serve.cu and drt_trace.cu's host part do not change them)."""
     import glob
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2205_00237_gb300", "csrc")
-    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
-                    glob.glob(os.path.join(csrc, "*.h"))):
+    for f in sorted(glob.glob(os.path.join(csrc, "drt_k_*.cu")) + [os.path.join(csrc, "drt_kernels.cu")] +
+                    glob.glob(os.path.join(csrc, "*.cuh")) + glob.glob(os.path.join(csrc, "*.h")) +
+                    [os.path.join(ROOT, "include", "drt.h")]):
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())
             h.update(fh.read())

@@ -352,11 +352,29 @@ drt_status run_extrapolation(drt_ctx *c, Link &L, const drt_time_grid *tg, const
     double *pose = reinterpret_cast<double *>(c->pose.ptr);
     double *warm = reinterpret_cast<double *>(c->warm.ptr);
     if (drt_status st = traced(c, 0, s, [&] { return launch_pose(L.dev, t, pose, s); })) return st;
-    if (drt_status st = traced(c, 3, s, [&] { return launch_warm_fp64(L.dev, t, warm, s); })) return st;
+    // The FP64 kernels all wait on the FP64 pipe, so the launches of one call run side by side on three
+    // streams: every launch's last wave of blocks then shares the SMs with the others instead of
+    // leaving them idle, and the latency-bound multi-diffraction warm starts overlap the chains that
+    // do not need them.  side[1]: warm starts, the generic chains (several diffractions in a segment,
+    // 4 vertices), length 1; side[0]: length 2, length 0; s: length 3.
     return traced(c, 1, s, [&] {
-        return split_multi(c, L.dev, s, [&](cudaStream_t sm) {
-            return launch_extrapolate_fp64(L.dev, t, f, pose, out, rec, s, 0, -1, false, warm, sm);
-        });
+        const LinkDev &D = L.dev;
+        const int *ls = D.len_start;
+        cudaStream_t s0 = c->side[0], s1 = c->side[1];
+        cudaError_t e = cudaEventRecord(c->ev_fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, c->ev_fork, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s1, c->ev_fork, 0);
+        if (e == cudaSuccess) e = launch_warm_fp64(D, t, warm, s1);
+        if (e == cudaSuccess) e = launch_extrapolate_fp64(D, t, f, pose, out, rec, s1, ls[MAXI], -1, false, warm);
+        if (e == cudaSuccess) e = launch_extrapolate_fp64(D, t, f, pose, out, rec, s1, ls[1], ls[2], false, warm);
+        if (e == cudaSuccess) e = launch_extrapolate_fp64(D, t, f, pose, out, rec, s0, ls[2], ls[3], false, warm);
+        if (e == cudaSuccess) e = launch_extrapolate_fp64(D, t, f, pose, out, rec, s0, ls[0], ls[1], false, warm);
+        if (e == cudaSuccess) e = launch_extrapolate_fp64(D, t, f, pose, out, rec, s, ls[3], ls[MAXI], false, warm);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_join[0], s0);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_join[1], s1);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join[0], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join[1], 0);
+        return e;
     });
 }
 
@@ -561,6 +579,13 @@ drt_status drt::pack_link(const drt_scene *s, const drt_path_set *ps, PackedLink
     int n_bulk = 0;
     for (int p = 0; p < P; ++p) n_bulk += multi_d(code[p]) ? 0 : 1;
     d.n_bulk = n_bulk;
+    {   // the multi-diffraction chains by length (2..4 vertices; sorted by signature, so by length)
+        int cnt[MAXI + 1] = {0, 0, 0, 0, 0};
+        for (int p = 0; p < P; ++p)
+            if (multi_d(code[p])) ++cnt[ps->n_int[p]];
+        d.multi_start[0] = n_bulk;
+        for (int k = 0; k + 1 < MAXI; ++k) d.multi_start[k + 1] = d.multi_start[k] + cnt[k + 2];
+    }
     // start of each chain length among the first n_bulk (sorted) paths
     {
         int cnt[MAXI + 1] = {0, 0, 0, 0, 0};

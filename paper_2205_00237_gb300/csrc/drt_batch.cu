@@ -35,43 +35,6 @@
 
 namespace drt {
 
-// stages 0-3: block-wide claims of blockDim.x consecutive items
-template <int STAGE>
-__global__ void __launch_bounds__(128) k_stage(const BatchDev B) {
-    __shared__ long long s_start;
-    const long long total = B.n_items;
-    for (;;) {
-        if (threadIdx.x == 0) s_start = (long long)atomicAdd(B.counter, (unsigned long long)blockDim.x);
-        __syncthreads();
-        long long q = s_start + threadIdx.x;
-        bool done = s_start >= total;
-        __syncthreads();
-        if (done) break;
-        if (q >= total) continue;
-        const long long it = B.it_base + q;
-        int li = find_link(B, STAGE, it);
-        const BatchLink &BL = B.links[li];
-        long long local = it - BL.it0[STAGE];
-        int nch = chunks_of(BL.tg);
-        if (STAGE == ST_POSEB) {
-            int b = (int)(local / nch), c = (int)(local - (long long)b * nch);
-            double tb = BL.tg.t_start + (double)c * BL.tg.chunk * BL.tg.dt;
-            if (b < BL.L.n_bodies) body_pose_base(BL.L.bodies[b], tb, BL.poseb[local]);
-            else terminal_base(b == BL.L.n_bodies ? BL.L.tx : BL.L.rx, tb, BL.poseb[local]);
-        } else if (STAGE == ST_POSE64) {
-            int b = (int)(local / nch), c = (int)(local - (long long)b * nch);
-            body_pose_row(BL.L.bodies[b], BL.tg.t_start + (double)c * BL.tg.chunk * BL.tg.dt,
-                          BL.pose64 + local * POSE_W);
-        } else if (STAGE == ST_WARM) {   // rows 0..nch
-            int p = BL.L.n_bulk + (int)(local / (nch + 1)), c = (int)(local % (nch + 1));
-            path_warm_fp64(BL.L, BL.tg, p, c, BL.warm);
-        } else {
-            int p = (int)(local / nch), c = (int)(local % nch);
-            path_base_fp64(BL.L, BL.tg, BL.fg, BL.pose64, p, c, BL.base, BL.warm);
-        }
-    }
-}
-
 // stage 5: a block takes (link, SYNTH_U consecutive (step, tile of KT bins) pairs), as in the
 // single-link synthesis: lane l owns pair l, the SYNTH_PG warps split the paths and add their
 // partial sums in shared memory; exact FP32 seed per (pair, path), complex rotation across the tile
@@ -137,51 +100,6 @@ __global__ void __launch_bounds__(SYNTH_U * SYNTH_PG) k_batch_synth(const BatchD
     }
 }
 
-// FP64 redo of queued steps; their contribution is added to H (all bins) with atomics, for the entry
-// and, for a carrier pair, its partner
-__device__ void redo_add_entry(const BatchLink &BL, int p, int ti) {
-    double r[3];
-    const RecD nor{nullptr, nullptr};
-    path_step_redo(BL.L, BL.tg, BL.fg, p, ti, BL.out, nor, BL.warm, r);
-    if (r[0] == 0.0 && r[1] == 0.0) return;
-    // a exp(-j 2 pi f_k tau): FP64-reduced seed per 16-bin tile, FP32 rotation across the tile
-    const double f0 = BL.fg.fc - 0.5 * BL.fg.bandwidth, df = BL.fg.bandwidth / BL.fg.n_bins;
-    const int F = BL.fg.n_bins;
-    float2 *row = BL.H + (size_t)ti * F;
-    double xs = df * r[2];
-    float ws, wc;
-    sincospif(2.f * (float)(xs - floor(xs)), &ws, &wc);
-    for (int k0 = 0; k0 < F; k0 += 16) {
-        double x = (f0 + k0 * df) * r[2];
-        float sn, cs;
-        sincospif(2.f * (float)(x - floor(x)), &sn, &cs);
-        const float ar = (float)r[0], ai = (float)r[1];
-        float zr = fmaf(ar, cs, ai * sn), zi = fmaf(ai, cs, -ar * sn);
-        for (int j = 0; j < 16 && k0 + j < F; ++j) {
-            atomicAdd(&row[k0 + j].x, zr);
-            atomicAdd(&row[k0 + j].y, zi);
-            const float nr = fmaf(zr, wc, zi * ws);
-            zi = fmaf(zi, wc, -zr * ws);
-            zr = nr;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(32) k_batch_redo(const BatchDev B) {   // one warp per block, spread over SMs
-    if (blockIdx.x == 0 && threadIdx.x == 0) {   // the run's total; a wave whose count exceeds the list
-        unsigned long long *hdr = reinterpret_cast<unsigned long long *>(B.redo.count);   // marks the run
-        atomicAdd(hdr + 1, (unsigned long long)*B.redo.count);
-        if (*B.redo.count > B.redo.cap) atomicOr(hdr + 2, 1ull);
-    }
-    const int n = min(*B.redo.count, B.redo.cap);
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const int4 itm = B.redo.items[k];
-        const BatchLink &BL = B.links[itm.x];
-        redo_add_entry(BL, itm.y, itm.z);
-        if (BL.partner >= 0 && itm.y >= BL.pair_p0) redo_add_entry(B.links[BL.partner], itm.y, itm.z);
-    }
-}
-
 // ------------------------------------------------------------------------------------------------
 // host side
 //
@@ -190,7 +108,7 @@ __global__ void __launch_bounds__(32) k_batch_redo(const BatchDev B) {   // one 
 // allocation.
 // a wave: consecutive links whose records and scratch fit their buffers; its preparation items
 // [prep0, prep0 + n_prep) per stage 0-3, its bulk units and synthesis units per tile variant
-struct Wave { int l0, l1; long long prep0[4], n_prep[4], n_bulk[MAXI], n_bulkm, n_synth[3], n_rec; };
+struct Wave { int l0, l1; long long prep0[4], n_prep[4], n_bulk[MAXI], n_bulkm, n_synth[3], n_rec, n_bulkd[2]; };
 
 struct BatchPlan {
     int n_links = 0;
@@ -243,8 +161,9 @@ static cudaError_t launch_synth_variant(int v, const BatchDev &B, int grid, cuda
     return cudaGetLastError();
 }
 
-// counters: 10 per wave (stages 0-3, bulk per chain length 0..3, synthesis, generic bulk)
-constexpr int N_COUNTERS = 10;
+// counters: 12 per wave (stages 0-3, bulk per chain length 0..3, generic bulk, synthesis, bulk of the
+// multi-diffraction chains of 2 and 3 vertices)
+constexpr int N_COUNTERS = 12;
 static size_t counter_of(size_t w, int slot) { return N_COUNTERS * w + slot; }
 
 // stages 0-3 of wave w
@@ -256,11 +175,10 @@ static cudaError_t run_prep(BatchPlan &P, size_t w, cudaStream_t s) {
         B.it_base = W.prep0[st];
         return B;
     };
-    if (W.n_prep[ST_POSEB]) k_stage<ST_POSEB><<<grid, 128, 0, s>>>(view(ST_POSEB));
-    if (W.n_prep[ST_POSE64]) k_stage<ST_POSE64><<<grid, 128, 0, s>>>(view(ST_POSE64));
-    if (W.n_prep[ST_WARM]) k_stage<ST_WARM><<<grid, 128, 0, s>>>(view(ST_WARM));
-    if (W.n_prep[ST_BASE]) k_stage<ST_BASE><<<grid, 128, 0, s>>>(view(ST_BASE));
-    return cudaGetLastError();
+    for (int st = ST_POSEB; st <= ST_BASE; ++st)
+        if (W.n_prep[st])
+            if (cudaError_t e = launch_batch_stage(st, view(st), grid, s)) return e;
+    return cudaSuccess;
 }
 
 static cudaError_t run_wave_bulk(BatchPlan &P, size_t w, cudaStream_t s) {
@@ -269,6 +187,12 @@ static cudaError_t run_wave_bulk(BatchPlan &P, size_t w, cudaStream_t s) {
         if (!W.n_bulk[n]) continue;
         const BatchDev B = dev_view(P, W.l0, W.l1, W.n_bulk[n], counter_of(w, 4 + n));
         if (cudaError_t e = launch_batch_bulk(n, false, P.any_pair, B, sm_count() * batch_bulk_blocks(n), s)) return e;
+    }
+    for (int k = 0; k < 2; ++k) {   // multi-diffraction chains of 2 and 3 vertices
+        if (!W.n_bulkd[k]) continue;
+        const BatchDev B = dev_view(P, W.l0, W.l1, W.n_bulkd[k], counter_of(w, 10 + k));
+        if (cudaError_t e = launch_batch_bulk_multi(k + 2, P.any_pair, B, sm_count() * batch_bulk_blocks(k + 2, true), s))
+            return e;
     }
     if (W.n_bulkm) {
         const BatchDev B = dev_view(P, W.l0, W.l1, W.n_bulkm, counter_of(w, 8));
@@ -288,8 +212,7 @@ static cudaError_t run_wave_synth(BatchPlan &P, size_t w, cudaStream_t s, long l
 // the wave's queued FP64 steps (before the next wave reuses its scratch), then an empty list
 static cudaError_t run_redo(BatchPlan &P, size_t w, cudaStream_t s) {
     const Wave &W = P.waves[w];
-    k_batch_redo<<<sm_count() * 8, 32, 0, s>>>(dev_view(P, W.l0, W.l1, 0, 0));
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_batch_redo(P.dual, dev_view(P, W.l0, W.l1, 0, 0), sm_count() * 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(P.mem + P.off_redo, 0, sizeof(int), s);
     return e;
 }
@@ -397,7 +320,7 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
     };
     long long it[4] = {};
     size_t rec_max = 0, scratch_max = 0;
-    Wave W{0, 0, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, 0, {0, 0, 0}, 0};
+    Wave W{0, 0, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, 0, {0, 0, 0}, 0, {0, 0}};
     size_t wave_rec = 0;
     auto close_wave = [&](int l1) {
         W.l1 = l1;
@@ -426,6 +349,8 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
         P->dual = P->dual || B.out.doppler != nullptr;
         P->any_pair = P->any_pair || mate[i] >= 0;
         B.gen_p0 = P->any_out ? 0 : B.L.len_start[MAXI];
+        B.skip_p0 = P->any_out ? 0 : B.L.multi_start[0];   // multi-diffraction chains of 2 and 3 vertices
+        B.skip_p1 = P->any_out ? 0 : B.L.multi_start[2];   // have unit ranges of their own
         B.pair_p0 = P->any_out ? 0 : B.L.len_start[2];
         const long long T = tgs[i].n_steps, Pn = B.L.n_paths;
         long long nch = (T + chunk - 1) / chunk;
@@ -439,7 +364,7 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
         const size_t recs = (size_t)T * Pn;
         if (k > W.l0 && !second && ((wave_rec + recs) * REC_BYTES > REC_CAP || off + sbytes > SCRATCH_CAP)) {
             close_wave(k);
-            W = Wave{k, k, {it[0], it[1], it[2], it[3]}, {0, 0, 0, 0}, {0, 0, 0, 0}, 0, {0, 0, 0}, 0};
+            W = Wave{k, k, {it[0], it[1], it[2], it[3]}, {0, 0, 0, 0}, {0, 0, 0, 0}, 0, {0, 0, 0}, 0, {0, 0}};
             wave_rec = 0;
             off = 0;
         }
@@ -465,6 +390,10 @@ cudaError_t batch_build(const std::vector<const LinkDev *> &links, const std::ve
         }
         B.it0[ST_BULKM] = W.n_bulkm;
         if (!second) W.n_bulkm += (Pn - B.gen_p0) * nbw;
+        for (int k = 0; k < 2; ++k) {
+            B.it0[ST_BULKD + k] = W.n_bulkd[k];
+            if (!second && !P->any_out) W.n_bulkd[k] += (long long)(B.L.multi_start[k + 1] - B.L.multi_start[k]) * nbw;
+        }
         for (int v = 0; v < 3; ++v) {   // a link without paths gets H = 0
             const long long pairs = T * ((fgs[i].n_bins + SYNTH_KT[v] - 1) / SYNTH_KT[v]);
             B.it0[ST_SYNTH + v] = W.n_synth[v];

@@ -7,7 +7,10 @@
 namespace drt {
 
 // stage slots; the synthesis has one slot per tile variant (its units depend on the tile width)
-enum { ST_POSEB = 0, ST_POSE64 = 1, ST_WARM = 2, ST_BASE = 3, ST_BULK = 4, ST_SYNTH = 8, ST_BULKM = 11, N_STAGES = 12 };
+// (ST_BULK + n: chains of n vertices; ST_BULKD + k: multi-diffraction chains of k + 2 vertices; ST_BULKM:
+// the generic code)
+enum { ST_POSEB = 0, ST_POSE64 = 1, ST_WARM = 2, ST_BASE = 3, ST_BULK = 4, ST_SYNTH = 8, ST_BULKM = 11, ST_BULKD = 12,
+       N_STAGES = 14 };
 constexpr int BULK_W = 32;                // time steps per extrapolation unit (one warp's lanes)
 constexpr int SYNTH_U = 32;               // (step, tile) pairs per synthesis unit (one block) ...
 constexpr int SYNTH_PG = 4;               // ... whose warps split the paths
@@ -34,6 +37,8 @@ struct alignas(16) BatchLink {
     int32_t partner, shared;
     int32_t gen_p0;    // first path of the generic-code unit range (len_start[MAXI]; 0 when the batch
                        // writes per-path-step records, which only the generic code does)
+    int32_t skip_p0, skip_p1;   // paths of that range with units of their own (the multi-diffraction
+                                // chains of 2 and 3 vertices; empty when the batch writes records)
     int32_t pair_p0;   // a pair's first entry also evaluates its partner's paths [pair_p0, n_paths)
 };
 
@@ -64,6 +69,12 @@ __device__ __forceinline__ int chunks_of(const TimeGridD &tg) { return (tg.n_ste
 // the per-chain-length extrapolation launch of one wave (drt_k_batch.cu): N = 0..3 with pair = the
 // batch has carrier pairs, N < 0 the generic code (dual: Doppler rates; records allowed)
 cudaError_t launch_batch_bulk(int N, bool dual, bool pair, const BatchDev &B, int grid, cudaStream_t s);
-int batch_bulk_blocks(int N);
+// the multi-diffraction chains of N = 2 or 3 vertices (values only)
+cudaError_t launch_batch_bulk_multi(int N, bool pair, const BatchDev &B, int grid, cudaStream_t s);
+int batch_bulk_blocks(int N, bool multi = false);
+
+// the stage kernels in their own translation units
+cudaError_t launch_batch_stage(int stage, const BatchDev &B, int grid, cudaStream_t s);   // stages 0-3
+cudaError_t launch_batch_redo(bool dual, const BatchDev &B, int grid, cudaStream_t s);
 
 }  // namespace drt

@@ -27,13 +27,16 @@ __device__ __forceinline__ void batch_unit(const BatchDev &B, const BatchLink &B
     }
 }
 
-template <int N> struct BatchBlocks { static constexpr int v = N < 0 ? 4 : N <= 1 ? 6 : N == 2 ? 4 : 3; };
+template <int N, bool MULTI = false> struct BatchBlocks {
+    static constexpr int v = N < 0 ? 4 : MULTI ? 3 : N <= 1 ? 6 : N == 2 ? 4 : 3;
+};
 
-// N >= 0: the units of the chains of length N (no records); N < 0: the units of the generic range
-template <int N, bool DUAL, bool PAIR>
-__global__ void __launch_bounds__(128, BatchBlocks<N>::v) k_batch_bulk(const BatchDev B) {
+// N >= 0: the units of the chains of length N (no records), MULTI: of the multi-diffraction chains of
+// length N (2 or 3); N < 0: the units of the generic range
+template <int N, bool DUAL, bool PAIR, bool MULTI = false>
+__global__ void __launch_bounds__(128, BatchBlocks<N, MULTI>::v) k_batch_bulk(const BatchDev B) {
     typedef std::conditional_t<DUAL, dd, de> S;
-    constexpr int slot = N >= 0 ? ST_BULK + N : ST_BULKM;
+    constexpr int slot = N < 0 ? ST_BULKM : MULTI ? ST_BULKD + N - 2 : ST_BULK + N;
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long it = 0;
@@ -44,12 +47,12 @@ __global__ void __launch_bounds__(128, BatchBlocks<N>::v) k_batch_bulk(const Bat
         const BatchLink &BL = B.links[li];
         const long long local = (long long)it - BL.it0[slot];
         const int nb = (BL.tg.n_steps + BULK_W - 1) / BULK_W;
-        const int p0 = N >= 0 ? BL.L.len_start[N >= 0 ? N : 0] : BL.gen_p0;
+        const int p0 = N < 0 ? BL.gen_p0 : MULTI ? BL.L.multi_start[N - 2] : BL.L.len_start[N];
         const int p = p0 + (int)(local / nb), t = (int)(local % nb) * BULK_W + lane;
         if (t < BL.tg.n_steps) {
-            if constexpr (N >= 0) batch_unit<N, false, false, PAIR, S>(B, BL, li, p, t);
-            else if (BL.partner >= 0) batch_unit<-1, true, true, true, S>(B, BL, li, p, t);
-            else batch_unit<-1, true, true, false, S>(B, BL, li, p, t);
+            // the generic range: one instance per chain length, each taking a carrier pair or one carrier
+            if constexpr (N >= 0) batch_unit<N, MULTI, false, PAIR, S>(B, BL, li, p, t);
+            else if (p < BL.skip_p0 || p >= BL.skip_p1) batch_unit<LEN_ANY, true, true, true, S>(B, BL, li, p, t);
         }
     }
 }

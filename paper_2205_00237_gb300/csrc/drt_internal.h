@@ -34,9 +34,12 @@ struct LinkDev {
     int32_t n_paths, n_bodies, n_faces, n_edges, n_tiles, n_mats;
     int32_t n_bulk;   // paths [0, n_bulk) have at most one diffraction per segment (FP32-bulk capable)
     // among those, paths [len_start[n], len_start[n + 1]) have n vertices (the signature sort groups
-    // them by length); the unrolled kernels take lengths 0..3, paths [len_start[MAXI], n_paths) run the
-    // generic code
+    // them by length); the unrolled kernels take lengths 0..3, paths [len_start[MAXI], n_paths) form
+    // the generic range (4-vertex chains, then the multi-diffraction chains)
     int32_t len_start[MAXI + 2];
+    // the multi-diffraction chains of k + 2 vertices are [multi_start[k], multi_start[k + 1]), k = 0..2
+    // (multi_start[0] = n_bulk, multi_start[3] = n_paths)
+    int32_t multi_start[MAXI];
     TermD tx, rx;
     const BodyD *bodies;
     const FaceD *faces;

@@ -14,7 +14,8 @@
 
 namespace drt {
 
-int batch_bulk_blocks(int N) {
+int batch_bulk_blocks(int N, bool multi) {
+    if (multi) return N == 2 ? BatchBlocks<2, true>::v : BatchBlocks<3, true>::v;
     return N < 0 ? BatchBlocks<-1>::v : N <= 1 ? BatchBlocks<1>::v : N == 2 ? BatchBlocks<2>::v : BatchBlocks<3>::v;
 }
 

@@ -172,7 +172,7 @@ k_select(const LinkDev L, const TimeGridD tg, const FreqGridD fg, WinMask wm, co
     OutD o{};
     o.flags = wm.sel;   // written at [starts[w]][caller index]
     const RecD none{nullptr, nullptr};
-    path_step_redo(L, tg, fg, p, wm.starts[w], o, none, warm);
+    path_step_redo_as<false>(L, tg, fg, p, wm.starts[w], o, none, warm);   // flags only: values suffice
 }
 
 cudaError_t launch_select(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const WinMask &wm,

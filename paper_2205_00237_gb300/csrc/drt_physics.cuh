@@ -169,28 +169,6 @@ DRT_HD Prim<dl<T>> load_prim_direct(const LinkDev &L, double t, int type, int id
     return load_prim_row<T>(L, P, type, idx);
 }
 
-// back-tracking over the reflections strictly between vertices a and b (Sec. III-A.2): images of
-// V[a] through the walls in order, then from V[b] back towards V[a] each point by Eq. ref_point
-// between the image through the preceding walls and the point found at the previous step.
-template <class S>
-DRT_HD void backtrack(const Prim<S> *pr, v3<S> *V, int a, int b) {
-    int m = b - a - 1;
-    if (m <= 0) return;
-    v3<S> img[MAXI];
-    img[0] = V[a];
-#pragma unroll
-    for (int j = 1; j < MAXI; ++j)
-        if (j < m) img[j] = mirror(img[j - 1], pr[a + j - 1].p, pr[a + j - 1].a);
-    v3<S> next = V[b];
-#pragma unroll
-    for (int j = MAXI; j >= 1; --j) {
-        if (j > m) continue;
-        const Prim<S> &w = pr[a + j - 1];
-        next = refl_point(img[j - 1], next, w.p, w.a);
-        V[a + j] = next;
-    }
-}
-
 // Keller-cone point on the edge line (A, e) between a virtual source and a virtual receiver:
 // s = s_A + (s_B - s_A) rho_A / (rho_A + rho_B), the 3D form of Eq. diff_point.
 template <class S>
@@ -208,52 +186,6 @@ DRT_HD S keller_s(v3<S> Sv, v3<S> Rv, const Prim<S> &e, uint32_t &fl) {
     if (sizeof(T) == 4 && (ra2 < T(1e-6) || rb2 < T(1e-6))) fl |= F_REDO64;
     S ra = norm(pa), rb = norm(pb);
     return sa + (sb - sa) * ra / (ra + rb);
-}
-
-// Edge parameters of a segment with m >= 2 diffractions: Newton on the unfolded length (the
-// stationary, here minimal, path; reflections between diffraction points unfolded by imaging)
-// with the analytic tridiagonal Hessian, started from the t0 parameters.  The length is convex in
-// the edge parameters, so a step that lengthens the path is halved until it does not (backtracking
-// line search).  Carried on dual numbers, the converged iterate's derivative is the implicit-function
-// derivative, so the diffraction points' sliding velocities come out of the same solve.
-template <class S>
-DRT_HD S unfolded_length(const Prim<S> *pr, const v3<S> *V, int a, int b, const int *didx, int m, const S *s, S *g,
-                         S *hd, S *ho) {
-    typedef typename ST<S>::R T;
-    const S one = scst<S>(T(1));
-    S Ltot = scst<S>(T(0));
-    for (int j = 0; j < m; ++j) g[j] = hd[j] = ho[j] = scst<S>(T(0));
-    for (int j = 0; j <= m; ++j) {
-        int i0 = (j == 0) ? a : didx[j - 1];
-        int i1 = (j == m) ? b : didx[j];
-        v3<S> X = (j == 0) ? V[a] : pr[i0 - 1].p + pr[i0 - 1].a * s[j - 1];
-        v3<S> ex = (j == 0) ? V[a] : pr[i0 - 1].a;
-        for (int i = i0 + 1; i < i1; ++i) {
-            X = mirror(X, pr[i - 1].p, pr[i - 1].a);
-            if (j > 0) ex = mirror_dir(ex, pr[i - 1].a);
-        }
-        v3<S> Y = (j == m) ? V[b] : pr[i1 - 1].p + pr[i1 - 1].a * s[j];
-        v3<S> r = X - Y;
-        S l = norm(r);
-        Ltot = Ltot + l;
-        S il = one / l;
-        v3<S> rh = r * il;
-        if (j > 0) {
-            S q = dot(rh, ex);
-            g[j - 1] = g[j - 1] + q;
-            hd[j - 1] = hd[j - 1] + (one - q * q) * il;
-        }
-        if (j < m) {
-            S q = dot(rh, pr[i1 - 1].a);
-            g[j] = g[j] - q;
-            hd[j] = hd[j] + (one - q * q) * il;
-            if (j > 0) {
-                S qx = dot(rh, ex);
-                ho[j - 1] = ho[j - 1] + (qx * q - dot(ex, pr[i1 - 1].a)) * il;
-            }
-        }
-    }
-    return Ltot;
 }
 
 template <class S> DRT_HD void clamp_positive(S &x, typename ST<S>::R eps);
@@ -288,36 +220,184 @@ template <> DRT_HD dd newton_start<dd>(double base, double delta, double rate) {
     return {(float)base, (float)delta, (float)rate};
 }
 
-template <class S>
-DRT_OUTLINE void multi_diffraction(const Prim<S> *pr, v3<S> *V, int a, int b, const double *s0, const double *ds0,
-                              const double *rate0, uint32_t &fl) {
+// chain length of path p (vertices before the first empty type byte)
+DRT_HD int chain_length(const LinkDev &L, int p) {
+    const uint32_t c = L.ptypes[p];
+    return (c & 0xffu) == 0 ? 0 : (c & 0xff00u) == 0 ? 1 : (c & 0xff0000u) == 0 ? 2 : (c & 0xff000000u) == 0 ? 3 : 4;
+}
+
+// The solvers below run on chains of N vertices, N known at compile time: every vertex loop has a
+// fixed bound and unrolls, so the per-vertex arrays (positions, images, Newton state) are indexed by
+// constants and stay in registers; the chain's interaction types are read at run time.
+
+// tile centroids move rigidly with their bodies (Sec. III-C)
+template <int N, class S> DRT_HD void place_tiles(const Prim<S> *pr, v3<S> *V) {
+#pragma unroll
+    for (int i = 1; i <= N; ++i)
+        if (pr[i - 1].type == T_S) V[i] = pr[i - 1].p;
+}
+
+// Keller-cone points of the diffractions that are alone between their point sources: each lies on
+// the cone between its virtual source (the segment's left point source imaged through the
+// reflections in between) and its virtual receiver (the right point source imaged backwards through
+// the reflections after it).  Vertices with nv[i] set were placed by the Newton solve.
+template <int N, class S>
+DRT_HD void place_keller(const Prim<S> *pr, v3<S> *V, uint32_t &fl, const bool *nv) {
+    v3<S> img[N > 0 ? N : 1];
+    v3<S> cur = V[0];
+#pragma unroll
+    for (int i = 1; i <= N; ++i) {
+        const Prim<S> &q = pr[i - 1];
+        if (q.type == T_D) img[i - 1] = cur;
+        else if (q.type == T_R) cur = mirror(cur, q.p, q.a);
+        else cur = V[i];
+    }
+    cur = V[N + 1];
+#pragma unroll
+    for (int i = N; i >= 1; --i) {
+        const Prim<S> &q = pr[i - 1];
+        if (q.type == T_D && !(nv && nv[i])) V[i] = q.p + q.a * keller_s(img[i - 1], cur, q, fl);
+        else if (q.type == T_R) cur = mirror(cur, q.p, q.a);
+        else cur = V[i];
+    }
+}
+
+// reflection points by back-tracking (Sec. III-A.2) between the known points (point sources and
+// diffraction points): a wall's source image is the last known point imaged through the walls
+// before it; the points are placed from the right, each by Eq. ref_point towards the point placed
+// before it
+template <int N, class S> DRT_HD void place_reflections(const Prim<S> *pr, v3<S> *V) {
+    v3<S> img[N > 0 ? N : 1];
+    v3<S> cur = V[0];
+#pragma unroll
+    for (int i = 1; i <= N; ++i) {
+        const Prim<S> &q = pr[i - 1];
+        if (q.type == T_R) {
+            img[i - 1] = cur;
+            cur = mirror(cur, q.p, q.a);
+        } else {
+            cur = V[i];
+        }
+    }
+    v3<S> next = V[N + 1];
+#pragma unroll
+    for (int i = N; i >= 1; --i) {
+        const Prim<S> &q = pr[i - 1];
+        if (q.type == T_R) V[i] = refl_point(img[i - 1], next, q.p, q.a);
+        next = V[i];
+    }
+}
+
+// Edge parameters of the diffractions of a segment with two or more of them (the reading of Sec.
+// III-B for multiple diffraction): Newton on the unfolded length of the segment -- the stationary,
+// here minimal, path, with the reflections between diffraction points unfolded by imaging -- using
+// its analytic tridiagonal Hessian, started from s0 (+ ds0, at rate rate0).  The length is convex in
+// the edge parameters, so a step that lengthens the path is halved until it does not (backtracking
+// line search).  Carried on dual numbers, the converged iterate's derivative is the implicit-function
+// derivative, so the diffraction points' sliding velocities come out of the same solve.
+// The unknowns are indexed by their vertex (nv[i]).  One sweep over the vertices meets the legs of
+// the unfolded path in order (a leg runs from an anchor -- point source or unknown diffraction point
+// -- to the next, through the reflections in between) and eliminates each unknown of the
+// tridiagonal system at the anchor that closes its outgoing leg; the back substitution runs the
+// other way.  Nothing is indexed at run time.
+template <int N, class S>
+DRT_HD void newton_diffractions(const Prim<S> *pr, v3<S> *V, const bool *nv, const double *s0, const double *ds0,
+                                const double *rate0, uint32_t &fl) {
     typedef typename ST<S>::R T;
     // convergence threshold on the Newton step (m): near round-off of the working precision
     const T tol = sizeof(T) == 8 ? T(1e-10) : T(1e-4);
     // below this step (m) the length change of a Newton step is at round-off of the ~100 m path
     // length, so the backtracking test is only applied to larger steps
     const T ls_min = sizeof(T) == 8 ? T(1e-4) : T(1e-2);
-    int didx[MAXI], m = 0;
-    S s[MAXI], step[MAXI];
-    for (int i = a + 1; i < b; ++i)
-        if (pr[i - 1].type == T_D) {
-            didx[m] = i;
-            s[m] = newton_start<S>(s0[i - 1], ds0 ? ds0[i - 1] : 0.0, rate0 ? rate0[i - 1] : 0.0);
-            step[m] = scst<S>(T(0));
-            ++m;
+    const S zero = scst<S>(T(0)), one = scst<S>(T(1));
+    S s[N + 1], step[N + 1];
+#pragma unroll
+    for (int i = 1; i <= N; ++i)
+        if (nv[i]) {
+            s[i] = newton_start<S>(s0[i - 1], ds0 ? ds0[i - 1] : 0.0, rate0 ? rate0[i - 1] : 0.0);
+            step[i] = zero;
         }
     bool conv = false;
     int halvings = 0;
     T Lprev = T(0), smax_prev = T(0);
     bool have_prev = false;
     for (int it = 0; it < 64; ++it) {
-        S g[MAXI], hd[MAXI], ho[MAXI];
-        S Lc = unfolded_length(pr, V, a, b, didx, m, s, g, hd, ho);
-        if (have_prev && smax_prev > ls_min && !(sval(Lc) <= Lprev) && halvings < 40) {
-            for (int j = 0; j < m; ++j) {     // backtrack: s_prev + step / 2
-                step[j] = step[j] * T(0.5);
-                s[j] = s[j] - step[j];
+        // cpS[i], dpS[i]: elimination of the unknown whose outgoing leg ends at anchor i (cl[i])
+        S cpS[N + 2], dpS[N + 2];
+        bool cl[N + 2];
+        v3<S> X = V[0], ex = V[0];   // the leg's start imaged through its walls so far; its edge alike
+        bool startN = false, first = true;
+        // gk, hk: gradient and Hessian diagonal of the unknown starting the current leg; hop: its
+        // coupling to the unknown before it; cpP, dpP: elimination of that previous unknown
+        S Lc = zero, gk = zero, hk = zero, hop = zero, cpP = zero, dpP = zero;
+#pragma unroll
+        for (int i = 1; i <= N + 1; ++i) {
+            cl[i] = false;
+            const int ty = i <= N ? pr[i - 1].type : T_S;   // vertex N + 1 is RX, a point source
+            const bool var = i <= N && nv[i];
+            if (ty == T_R) {
+                X = mirror(X, pr[i - 1].p, pr[i - 1].a);
+                if (startN) ex = mirror_dir(ex, pr[i - 1].a);
+                continue;
             }
+            if (ty == T_D && !var) {   // a Keller diffraction: its segment has no unknowns
+                startN = false;
+                continue;
+            }
+            const v3<S> Y = var ? pr[i - 1].p + pr[i - 1].a * s[i] : V[i];
+            if (startN || var) {
+                const v3<S> r = X - Y;
+                const S l = norm(r);
+                Lc = Lc + l;
+                const S il = one / l;
+                const v3<S> rh = r * il;
+                S qs = zero, gi = zero, hi = zero, hoi = zero;
+                if (startN) {
+                    qs = dot(rh, ex);
+                    gk = gk + qs;
+                    hk = hk + (one - qs * qs) * il;
+                }
+                if (var) {
+                    const S q = dot(rh, pr[i - 1].a);
+                    gi = zero - q;
+                    hi = (one - q * q) * il;
+                    if (startN) hoi = (qs * q - dot(ex, pr[i - 1].a)) * il;
+                }
+                if (startN) {   // the unknown starting this leg has all its terms: eliminate it
+                    clamp_positive(hk, T(1e-12));
+                    S cp, dp;
+                    if (first) {
+                        cp = hoi / hk;
+                        dp = -gk / hk;
+                    } else {
+                        const S den = hk - hop * cpP;
+                        cp = hoi / den;
+                        dp = (-gk - hop * dpP) / den;
+                    }
+                    first = false;
+                    cpS[i] = cp;
+                    dpS[i] = dp;
+                    cl[i] = true;
+                    cpP = cp;
+                    dpP = dp;
+                }
+                if (var) {
+                    gk = gi;
+                    hk = hi;
+                    hop = hoi;
+                }
+            }
+            X = Y;
+            if (var) ex = pr[i - 1].a;
+            startN = var;
+        }
+        if (have_prev && smax_prev > ls_min && !(sval(Lc) <= Lprev) && halvings < 40) {
+#pragma unroll
+            for (int i = 1; i <= N; ++i)
+                if (nv[i]) {   // backtrack: s_prev + step / 2
+                    step[i] = step[i] * T(0.5);
+                    s[i] = s[i] - step[i];
+                }
             smax_prev *= T(0.5);
             ++halvings;
             continue;
@@ -325,26 +405,28 @@ DRT_OUTLINE void multi_diffraction(const Prim<S> *pr, v3<S> *V, int a, int b, co
         halvings = 0;
         Lprev = sval(Lc);
         have_prev = true;
-        for (int j = 0; j < m; ++j) clamp_positive(hd[j], T(1e-12));
-        // Thomas algorithm for H step = -g (H symmetric tridiagonal: diag hd, off-diagonal ho)
-        S cp[MAXI], dp[MAXI];
-        cp[0] = ho[0] / hd[0];
-        dp[0] = -g[0] / hd[0];
-        for (int j = 1; j < m; ++j) {
-            S den = hd[j] - ho[j - 1] * cp[j - 1];
-            cp[j] = ho[j] / den;
-            dp[j] = (-g[j] - ho[j - 1] * dp[j - 1]) / den;
-        }
+        // back substitution from the right: the step computed at the anchor closing an unknown's
+        // outgoing leg is applied when the sweep reaches that unknown
+        S x[N + 1];
+        S xp = zero, xn = zero;
         T smax = T(0);
-        for (int j = m - 1; j >= 0; --j) {
-            if (j < m - 1) dp[j] = dp[j] - cp[j] * dp[j + 1];
-            smax = fmax(smax, fabs(sval(dp[j])));
+#pragma unroll
+        for (int i = N + 1; i >= 1; --i) {
+            const bool var = i <= N && nv[i];
+            if (var) {
+                x[i] = xp;
+                xn = xp;
+                smax = fmax(smax, fabs(sval(xp)));
+            }
+            if (cl[i]) xp = var ? dpS[i] - cpS[i] * xn : dpS[i];
         }
         if (!(smax == smax)) break;   // NaN
-        for (int j = 0; j < m; ++j) {
-            s[j] = s[j] + dp[j];
-            step[j] = dp[j];
-        }
+#pragma unroll
+        for (int i = 1; i <= N; ++i)
+            if (nv[i]) {
+                s[i] = s[i] + x[i];
+                step[i] = x[i];
+            }
         smax_prev = smax;
         // On dual numbers one Newton step from a value within smax of the root leaves the
         // derivative part O(smax) from the implicit-function derivative whatever the start's
@@ -357,116 +439,84 @@ DRT_OUTLINE void multi_diffraction(const Prim<S> *pr, v3<S> *V, int a, int b, co
         }
     }
     if (!conv) fl |= F_NOCONV;
-    for (int j = 0; j < m; ++j) V[didx[j]] = pr[didx[j] - 1].p + pr[didx[j] - 1].a * s[j];
-    int prev = a;
-    for (int i = a + 1; i <= b; ++i)
-        if (i == b || pr[i - 1].type == T_D) {
-            backtrack(pr, V, prev, i);
-            prev = i;
-        }
+#pragma unroll
+    for (int i = 1; i <= N; ++i)
+        if (nv[i]) V[i] = pr[i - 1].p + pr[i - 1].a * s[i];
 }
 
-// geometry of one path-step, any chain: vertices V[0..n+1] (TX, interaction points, RX) with velocities;
-// segments between point sources are found at run time, so the arrays are indexed dynamically
-template <class S>
-DRT_HD void solve_geometry_generic(const Prim<S> *pr, int n, v3<S> *V, const double *s0, uint32_t &fl,
-                           const double *ds0 = nullptr, const double *rate0 = nullptr) {
-    for (int i = 1; i <= n; ++i)
-        if (pr[i - 1].type == T_S) V[i] = pr[i - 1].p;   // Sec. III-C: tile centroid moves rigidly
-    int a = 0;
-    for (int b = 1; b <= n + 1; ++b) {
-        if (b <= n && pr[b - 1].type != T_S) continue;
-        int nd = 0, dpos = -1;
-        for (int i = a + 1; i < b; ++i)
-            if (pr[i - 1].type == T_D) {
-                ++nd;
-                dpos = i;
-            }
-        if (nd == 0) {
-            backtrack(pr, V, a, b);
-        } else if (nd == 1) {
-            v3<S> src = V[a], rcv = V[b];
-            for (int i = a + 1; i < dpos; ++i) src = mirror(src, pr[i - 1].p, pr[i - 1].a);
-            for (int i = b - 1; i > dpos; --i) rcv = mirror(rcv, pr[i - 1].p, pr[i - 1].a);
-            const Prim<S> &e = pr[dpos - 1];
-            V[dpos] = e.p + e.a * keller_s(src, rcv, e, fl);
-            backtrack(pr, V, a, dpos);
-            backtrack(pr, V, dpos, b);
-        } else {
-            multi_diffraction(pr, V, a, b, s0, ds0, rate0, fl);
-        }
-        a = b;
-    }
-}
-
-// The same geometry for a chain of N vertices (N known at compile time) with at most one diffraction
-// between point sources, the class of nearly every chain: every vertex loop unrolls with constant
-// indices, so positions and images stay in registers, and nothing is called out of line.
+// chains with at most one diffraction between point sources (nearly every chain)
 template <int N, class S>
 DRT_HD void solve_geometry_fast(const Prim<S> *pr, v3<S> *V, uint32_t &fl) {
     static_assert(N >= 0 && N <= MAXI, "chain length");
+    place_tiles<N>(pr, V);
     bool has_d = false;
-#pragma unroll (N >= 0 ? 8 : 1)
+#pragma unroll
+    for (int i = 1; i <= N; ++i) has_d = has_d || pr[i - 1].type == T_D;
+    if (has_d) place_keller<N>(pr, V, fl, nullptr);
+    place_reflections<N>(pr, V);
+}
+
+// any chain of N vertices: the diffractions of a segment with two or more of them by Newton (their
+// start values s0 [+ ds0, rate0] indexed by vertex - 1), the others on their Keller cones
+template <int N, class S>
+DRT_HD void solve_geometry_any(const Prim<S> *pr, v3<S> *V, const double *s0, uint32_t &fl,
+                               const double *ds0 = nullptr, const double *rate0 = nullptr) {
+    static_assert(N >= 0 && N <= MAXI, "chain length");
+    place_tiles<N>(pr, V);
+    // diffractions per segment: running count from the left, then each segment's total from the right
+    int cf[N + 1];
+    int c = 0;
+#pragma unroll
     for (int i = 1; i <= N; ++i) {
-        if (pr[i - 1].type == T_S) V[i] = pr[i - 1].p;   // Sec. III-C: tile centroid moves rigidly
-        has_d = has_d || pr[i - 1].type == T_D;
+        const int ty = pr[i - 1].type;
+        c = ty == T_S ? 0 : c + (ty == T_D ? 1 : 0);
+        cf[i] = c;
     }
-    v3<S> img[N > 0 ? N : 1];
-    if (has_d) {
-        // a diffraction point lies on the Keller cone between its virtual source (the segment's left
-        // point source imaged through the reflections in between) and its virtual receiver (the right
-        // point source imaged backwards through the reflections after it)
-        v3<S> cur = V[0];
-#pragma unroll (N >= 0 ? 8 : 1)
-        for (int i = 1; i <= N; ++i) {
-            const Prim<S> &q = pr[i - 1];
-            if (q.type == T_D) img[i - 1] = cur;
-            else if (q.type == T_R) cur = mirror(cur, q.p, q.a);
-            else cur = V[i];
-        }
-        cur = V[N + 1];
-#pragma unroll (N >= 0 ? 8 : 1)
-        for (int i = N; i >= 1; --i) {
-            const Prim<S> &q = pr[i - 1];
-            if (q.type == T_D) V[i] = q.p + q.a * keller_s(img[i - 1], cur, q, fl);
-            else if (q.type == T_R) cur = mirror(cur, q.p, q.a);
-            else cur = V[i];
-        }
-    }
-    // reflection points by back-tracking (Sec. III-A.2) between the known points (point sources and
-    // diffraction points): a wall's source image is the last known point imaged through the walls
-    // before it; the points are placed from the right, each by Eq. ref_point towards the point placed
-    // before it
-    v3<S> cur = V[0];
-#pragma unroll (N >= 0 ? 8 : 1)
-    for (int i = 1; i <= N; ++i) {
-        const Prim<S> &q = pr[i - 1];
-        if (q.type == T_R) {
-            img[i - 1] = cur;
-            cur = mirror(cur, q.p, q.a);
-        } else {
-            cur = V[i];
-        }
-    }
-    v3<S> next = V[N + 1];
-#pragma unroll (N >= 0 ? 8 : 1)
+    bool nv[N + 1];
+    bool any_nv = false, any_single = false;
+    int run = -1;
+#pragma unroll
     for (int i = N; i >= 1; --i) {
-        const Prim<S> &q = pr[i - 1];
-        if (q.type == T_R) V[i] = refl_point(img[i - 1], next, q.p, q.a);
-        next = V[i];
+        const int ty = pr[i - 1].type;
+        if (ty == T_S) run = -1;
+        else if (run < 0) run = cf[i];
+        nv[i] = ty == T_D && run >= 2;
+        any_nv = any_nv || nv[i];
+        any_single = any_single || (ty == T_D && run == 1);
+    }
+    if constexpr (N >= 2)   // two diffractions need two vertices
+        if (any_nv) newton_diffractions<N>(pr, V, nv, s0, ds0, rate0, fl);
+    if (any_single) place_keller<N>(pr, V, fl, nv);
+    place_reflections<N>(pr, V);
+}
+
+// MULTI: the chain may have several diffractions between point sources
+template <int N, bool MULTI, class S>
+DRT_HD void solve_geometry(const Prim<S> *pr, v3<S> *V, const double *s0, uint32_t &fl,
+                           const double *ds0 = nullptr, const double *rate0 = nullptr) {
+    static_assert(N >= 0 && N <= MAXI, "chain length");
+    if constexpr (MULTI) solve_geometry_any<N>(pr, V, s0, fl, ds0, rate0);
+    else solve_geometry_fast<N>(pr, V, fl);
+}
+
+// Chain length as a template argument: N >= 0 a fixed length; LEN_ANY the length read at run time
+// (one instance per length); LEN_GEN the same for the chains of the generic range (several
+// diffractions in a segment, or 4 vertices), which have at least 2 vertices.
+constexpr int LEN_ANY = -1, LEN_GEN = -2;
+
+// one instance of f per chain length: f(std::integral_constant<int, N>) for N = n; lengths below
+// NMIN have no instance (nothing runs for them)
+static_assert(MAXI == 4, "with_length covers the lengths 0..4");
+template <int NMIN = 0, class F> DRT_HD void with_length(int n, F &&f) {
+    switch (n) {
+    case 0: if constexpr (NMIN <= 0) f(std::integral_constant<int, 0>()); break;
+    case 1: if constexpr (NMIN <= 1) f(std::integral_constant<int, 1>()); break;
+    case 2: if constexpr (NMIN <= 2) f(std::integral_constant<int, 2>()); break;
+    case 3: if constexpr (NMIN <= 3) f(std::integral_constant<int, 3>()); break;
+    default: f(std::integral_constant<int, MAXI>()); break;
     }
 }
-
-// N >= 0 and !MULTI: the unrolled solver; otherwise (N < 0: length known at run time, or chains with
-// several diffractions in a segment) the generic one
-template <int N, bool MULTI, class S>
-DRT_HD void solve_geometry(const Prim<S> *pr, int n, v3<S> *V, const double *s0, uint32_t &fl,
-                           const double *ds0 = nullptr, const double *rate0 = nullptr) {
-    if constexpr (N >= 0 && !MULTI) solve_geometry_fast<N>(pr, V, fl);
-    else solve_geometry_generic(pr, n, V, s0, fl, ds0, rate0);
-}
-
-
+template <int N> constexpr int len_min() { return N == LEN_GEN ? 2 : 0; }
 // validity (Sec. II: the t0 multipath structure still holds): reflection points inside their
 // faces with both neighbours in front, diffraction points on their edge segments with both
 // neighbours in the wedge exterior, tiles lit from and seen from the front.
@@ -1063,33 +1113,32 @@ template <int N = -1, bool MULTI = true, bool OUT = true, class S = dl<double>, 
 DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, int p, int ti,
                                 const OutD &out, const RecD &rec, bool f32out, Loader load,
                                 const double *warm = nullptr, double *rec64 = nullptr) {
+    if constexpr (N < 0) {
+        with_length<len_min<N>()>(chain_length(L, p), [&](auto NC) {
+            path_step_fp64_core<decltype(NC)::value, MULTI, OUT, S>(L, tg, fg, p, ti, out, rec, f32out, load, warm,
+                                                                    rec64);
+        });
+        return;
+    } else {
     typedef double T;
     const T t = tg.t_start + ti * tg.dt;
     const uint32_t code = L.ptypes[p];
     const int4 pi = L.pprims[p];
     const int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
-    int n = 0;
+    constexpr int n = N;
     Prim<S> pr[MAXI];
-#pragma unroll (N >= 0 ? 8 : 1)
-    for (int j = 0; j < (N >= 0 ? N : MAXI); ++j) {
-        const int ty = (code >> (8 * j)) & 0xff;
-        if (N >= 0 || ty != T_NONE) {
-            pr[j] = load(ty, prim[j]);
-            n = j + 1;
-        }
-    }
-    if constexpr (N >= 0) n = N;
+#pragma unroll
+    for (int j = 0; j < N; ++j) pr[j] = load((code >> (8 * j)) & 0xff, prim[j]);
     v3<S> V[MAXI + 2];
     V[0] = terminal_as<S>(L.tx, t);
-    if constexpr (N >= 0) V[N + 1] = terminal_as<S>(L.rx, t);
-    else V[n + 1] = terminal_as<S>(L.rx, t);
+    V[N + 1] = terminal_as<S>(L.rx, t);
     uint32_t fl = 0;
     if (MULTI && warm && p >= L.n_bulk) {
         WarmStart ws;
         warm_start_at(L, tg, warm, p, ti, ws);
-        solve_geometry<N, MULTI>(pr, n, V, ws.s, fl, ws.ds, ws.rate);
+        solve_geometry<N, MULTI>(pr, V, ws.s, fl, ws.ds, ws.rate);
     } else {
-        solve_geometry<N, MULTI>(pr, n, V, L.ps0 + (size_t)p * MAXI, fl);
+        solve_geometry<N, MULTI>(pr, V, L.ps0 + (size_t)p * MAXI, fl);
     }
     v3<T> P[MAXI + 2];
     v3<T> seg[MAXI + 2];
@@ -1140,39 +1189,42 @@ DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const Fre
         rec64[1] = fl ? 0.0 : a.im;
         rec64[2] = tau;
     }
+    }
 }
 
 // One dual-number FP64 solve of a chain at time t from the edge-parameter start `sin`; writes each
-// diffraction vertex's parameter and rate to sv/sd (sin and 0 where the solve failed)
-template <class Loader>
+// diffraction vertex's parameter and rate to sv/sd (sin and 0 where the solve failed).  N < 0: the
+// chain length is read at run time and the solve runs in the instance for that length.
+template <int N = -1, class Loader>
 DRT_HD void solve_edge_params(const LinkDev &L, int p, double t, const double *sin, double *sv, double *sd,
                               Loader load) {
-    typedef double T;
-    uint32_t code = L.ptypes[p];
-    int4 pi = L.pprims[p];
-    int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
-    int n = 0;
-    Prim<dl<T>> pr[MAXI];
-    for (int j = 0; j < MAXI; ++j) {
-        int ty = (code >> (8 * j)) & 0xff;
-        if (ty != T_NONE) {
-            pr[j] = load(ty, prim[j]);
-            n = j + 1;
-        }
-    }
-    v3<dl<T>> V[MAXI + 2];
-    V[0] = terminal<T>(L.tx, t);
-    V[n + 1] = terminal<T>(L.rx, t);
-    uint32_t fl = 0;
-    solve_geometry_generic(pr, n, V, sin, fl);
-    for (int j = 0; j < MAXI; ++j) {
-        sv[j] = sin[j];
-        sd[j] = 0.0;
-        if (j < n && pr[j].type == T_D && !(fl & F_NOCONV)) {
-            dl<T> sj = dot(V[j + 1] - pr[j].p, pr[j].a);
-            if (isfinite(sj.v) && isfinite(sj.d)) {
-                sv[j] = sj.v;
-                sd[j] = sj.d;
+    if constexpr (N < 0) {
+        with_length<len_min<N>()>(chain_length(L, p), [&](auto NC) {
+            solve_edge_params<decltype(NC)::value>(L, p, t, sin, sv, sd, load);
+        });
+    } else {
+        typedef double T;
+        const uint32_t code = L.ptypes[p];
+        const int4 pi = L.pprims[p];
+        const int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
+        Prim<dl<T>> pr[N > 0 ? N : 1];
+#pragma unroll
+        for (int j = 0; j < N; ++j) pr[j] = load((code >> (8 * j)) & 0xff, prim[j]);
+        v3<dl<T>> V[N + 2];
+        V[0] = terminal<T>(L.tx, t);
+        V[N + 1] = terminal<T>(L.rx, t);
+        uint32_t fl = 0;
+        solve_geometry_any<N>(pr, V, sin, fl);
+#pragma unroll
+        for (int j = 0; j < MAXI; ++j) {
+            sv[j] = sin[j];
+            sd[j] = 0.0;
+            if (j < N && pr[j].type == T_D && !(fl & F_NOCONV)) {
+                dl<T> sj = dot(V[j + 1] - pr[j].p, pr[j].a);
+                if (isfinite(sj.v) && isfinite(sj.d)) {
+                    sv[j] = sj.v;
+                    sd[j] = sj.d;
+                }
             }
         }
     }
@@ -1182,7 +1234,7 @@ DRT_HD void solve_edge_params(const LinkDev &L, int p, double t, const double *s
 // edge parameters and their rates at t = 0, where the ray-tracing parameters s0 are already the
 // solution (one iteration); written to out[2 * MAXI]
 DRT_HD void path_t0par_fp64(const LinkDev &L, int p, double *out) {
-    solve_edge_params(L, p, 0.0, L.ps0 + (size_t)p * MAXI, out, out + MAXI,
+    solve_edge_params<LEN_GEN>(L, p, 0.0, L.ps0 + (size_t)p * MAXI, out, out + MAXI,
                       [&](int ty, int idx) { return load_prim_direct<double>(L, 0.0, ty, idx); });
 }
 
@@ -1193,7 +1245,7 @@ DRT_HD void path_warm_fp64(const LinkDev &L, const TimeGridD &tg, int p, int row
     double start[MAXI];
     for (int j = 0; j < MAXI; ++j) start[j] = q[j] + q[MAXI + j] * t;
     double *w = warm + ((size_t)row * (L.n_paths - L.n_bulk) + (p - L.n_bulk)) * (2 * MAXI);
-    solve_edge_params(L, p, t, start, w, w + MAXI,
+    solve_edge_params<LEN_GEN>(L, p, t, start, w, w + MAXI,
                       [&](int ty, int idx) { return load_prim_direct<double>(L, t, ty, idx); });
 }
 
@@ -1363,50 +1415,56 @@ DRT_HD Prim<double> load_prim_value(const LinkDev &L, const double *Pr, int type
 }
 
 // (path, chunk) FP64 anchors: path length and segment vectors at the chunk's first instant, phase
-// seed and per-bin step
+// seed and per-bin step.  N < 0: the chain length is read at run time (one instance per length).
+template <int N = -1>
 DRT_HD void path_base_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const double *pose64, int p,
                            int chunk, BaseRec *out, const double *warm = nullptr) {
-    const double tb = tg.t_start + (double)chunk * tg.chunk * tg.dt;
-    const int n_chunks = (tg.n_steps + tg.chunk - 1) / tg.chunk;
-    uint32_t code = L.ptypes[p];
-    int4 pi = L.pprims[p];
-    int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
-    int n = 0;
-    Prim<double> pr[MAXI];
-    for (int j = 0; j < MAXI; ++j) {
-        int ty = (code >> (8 * j)) & 0xff;
-        if (ty != T_NONE) {
+    if constexpr (N < 0) {
+        with_length(chain_length(L, p), [&](auto NC) {
+            path_base_fp64<decltype(NC)::value>(L, tg, fg, pose64, p, chunk, out, warm);
+        });
+    } else {
+        const double tb = tg.t_start + (double)chunk * tg.chunk * tg.dt;
+        const int n_chunks = (tg.n_steps + tg.chunk - 1) / tg.chunk;
+        const uint32_t code = L.ptypes[p];
+        const int4 pi = L.pprims[p];
+        const int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
+        Prim<double> pr[N > 0 ? N : 1];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const int ty = (code >> (8 * j)) & 0xff;
             pr[j] = load_prim_value(L, pose_at(pose64, n_chunks, prim_body(L, ty, prim[j]), chunk), ty, prim[j]);
-            n = j + 1;
         }
+        v3<double> V[N + 2];
+        V[0] = val(terminal<double>(L.tx, tb));
+        V[N + 1] = val(terminal<double>(L.rx, tb));
+        uint32_t fl = 0;
+        const double *s0 = L.ps0 + (size_t)p * MAXI;
+        if (warm && p >= L.n_bulk) s0 = warm_row(L, warm, chunk, p);
+        solve_geometry_any<N>(pr, V, s0, fl);
+        BaseRec r;
+        double d = 0.0;
+#pragma unroll
+        for (int i = 0; i <= MAXI; ++i) r.seg[i][0] = r.seg[i][1] = r.seg[i][2] = 0.f;
+#pragma unroll
+        for (int i = 1; i <= N + 1; ++i) {
+            v3<double> sg = V[i] - V[i - 1];
+            d += norm(sg);
+            r.seg[i - 1][0] = (float)sg.x;
+            r.seg[i - 1][1] = (float)sg.y;
+            r.seg[i - 1][2] = (float)sg.z;
+        }
+        double f0 = fg.fc - 0.5 * fg.bandwidth, df = fg.bandwidth / fg.n_bins;
+        double x = f0 * d / C0, y = df * d / C0;
+        double st = y - floor(y);
+        double hi = ldexp(rint(ldexp(st, 12)), -12);   // 12 leading bits: k * hi exact in FP32
+        r.d = d;
+        r.ph0 = (float)(x - floor(x));
+        r.st_hi = (float)hi;
+        r.st_lo = (float)(st - hi);
+        r.pad = 0.f;
+        out[(size_t)chunk * L.n_paths + p] = r;
     }
-    v3<double> V[MAXI + 2];
-    V[0] = val(terminal<double>(L.tx, tb));
-    V[n + 1] = val(terminal<double>(L.rx, tb));
-    uint32_t fl = 0;
-    const double *s0 = L.ps0 + (size_t)p * MAXI;
-    if (warm && p >= L.n_bulk) s0 = warm_row(L, warm, chunk, p);
-    solve_geometry_generic(pr, n, V, s0, fl);
-    BaseRec r;
-    double d = 0.0;
-    for (int i = 0; i <= MAXI; ++i) r.seg[i][0] = r.seg[i][1] = r.seg[i][2] = 0.f;
-    for (int i = 1; i <= n + 1; ++i) {
-        v3<double> sg = V[i] - V[i - 1];
-        d += norm(sg);
-        r.seg[i - 1][0] = (float)sg.x;
-        r.seg[i - 1][1] = (float)sg.y;
-        r.seg[i - 1][2] = (float)sg.z;
-    }
-    double f0 = fg.fc - 0.5 * fg.bandwidth, df = fg.bandwidth / fg.n_bins;
-    double x = f0 * d / C0, y = df * d / C0;
-    double st = y - floor(y);
-    double hi = ldexp(rint(ldexp(st, 12)), -12);   // 12 leading bits: k * hi exact in FP32
-    r.d = d;
-    r.ph0 = (float)(x - floor(x));
-    r.st_hi = (float)hi;
-    r.st_lo = (float)(st - hi);
-    r.pad = 0.f;
-    out[(size_t)chunk * L.n_paths + p] = r;
 }
 
 // an FP64 dual-number primitive without its rates
@@ -1503,6 +1561,14 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
                       const BaseRec *base, const double *warm, int p, int ti, const OutD &out, Rec5 &rec,
                       const RedoList &redo, int link, const FreqGridD *fg2 = nullptr, const BaseRec *base2 = nullptr,
                       Rec5 *rec2 = nullptr) {
+    if constexpr (N < 0) {
+        bool ok = false;
+        with_length<len_min<N>()>(chain_length(L, p), [&](auto NC) {
+            ok = bulk_eval<decltype(NC)::value, MULTI, OUT, S>(L, tg, fg, poseb, base, warm, p, ti, out, rec, redo,
+                                                               link, fg2, base2, rec2);
+        });
+        return ok;
+    } else {
     typedef float T;
     rec = Rec5{0.f, 0.f, 0.f, 0.f, 0.f};
     if (rec2) *rec2 = Rec5{0.f, 0.f, 0.f, 0.f, 0.f};
@@ -1512,29 +1578,21 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
     const uint32_t code = L.ptypes[p];
     const int4 pi = L.pprims[p];
     const int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
-    int n = 0;
+    constexpr int n = N;
     Prim<S> pr[MAXI];
-#pragma unroll (N >= 0 ? 8 : 1)
-    for (int j = 0; j < (N >= 0 ? N : MAXI); ++j) {
-        const int ty = (code >> (8 * j)) & 0xff;
-        if (N >= 0 || ty != T_NONE) {
-            pr[j] = load_prim_as<S>(L, poseb, n_chunks, chunk, tau_t, ty, prim[j]);
-            n = j + 1;
-        }
-    }
-    if constexpr (N >= 0) n = N;
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+        pr[j] = load_prim_as<S>(L, poseb, n_chunks, chunk, tau_t, (code >> (8 * j)) & 0xff, prim[j]);
     v3<S> V[MAXI + 2];
     V[0] = terminal_as<S>(poseb[(size_t)L.n_bodies * n_chunks + chunk], tau_t);
-    const v3<S> rx = terminal_as<S>(poseb[(size_t)(L.n_bodies + 1) * n_chunks + chunk], tau_t);
-    if constexpr (N >= 0) V[N + 1] = rx;
-    else V[n + 1] = rx;
+    V[N + 1] = terminal_as<S>(poseb[(size_t)(L.n_bodies + 1) * n_chunks + chunk], tau_t);
     uint32_t fl = 0;
     if (MULTI && warm && p >= L.n_bulk) {
         WarmStart ws;
         warm_start_at(L, tg, warm, p, ti, ws);
-        solve_geometry<N, MULTI>(pr, n, V, ws.s, fl, ws.ds, ws.rate);
+        solve_geometry<N, MULTI>(pr, V, ws.s, fl, ws.ds, ws.rate);
     } else {
-        solve_geometry<N, MULTI>(pr, n, V, L.ps0 + (size_t)p * MAXI, fl);
+        solve_geometry<N, MULTI>(pr, V, L.ps0 + (size_t)p * MAXI, fl);
     }
     v3<T> P[MAXI + 2];
 #pragma unroll (N >= 0 ? 8 : 1)
@@ -1620,6 +1678,7 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
         phase_record(*fg2, base2[(size_t)chunk * L.n_paths + p], a2, *rec2);
     }
     return true;
+    }
 }
 
 template <int N = -1, bool MULTI = true, bool OUT = true, class S = dd>
@@ -1635,16 +1694,18 @@ DRT_HD void path_step_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGrid
     }
 }
 
-// FP64 redo of one queued FP32-bulk path-step (FP32 output formats)
-DRT_HD void path_step_redo(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, int p, int ti, const OutD &out,
-                           const RecD &rec, const double *warm, double *rec64 = nullptr) {
+// FP64 redo of one queued FP32-bulk path-step (FP32 output formats); DUAL: with the rates the Doppler
+// output needs (dual numbers), else values only
+template <bool DUAL>
+DRT_HD void path_step_redo_as(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, int p, int ti,
+                              const OutD &out, const RecD &rec, const double *warm, double *rec64 = nullptr) {
     const double t = tg.t_start + ti * tg.dt;
-    if (out.doppler) {
-        path_step_fp64_core<-1, true, true, dl<double>>(
+    if constexpr (DUAL) {
+        path_step_fp64_core<LEN_ANY, true, true, dl<double>>(
             L, tg, fg, p, ti, out, rec, true, [&](int ty, int idx) { return load_prim_direct<double>(L, t, ty, idx); },
             warm, rec64);
-    } else {   // no Doppler output: values only
-        path_step_fp64_core<-1, true, true, double>(
+    } else {
+        path_step_fp64_core<LEN_ANY, true, true, double>(
             L, tg, fg, p, ti, out, rec, true,
             [&](int ty, int idx) { return val_prim(load_prim_direct<double>(L, t, ty, idx)); }, warm, rec64);
     }
@@ -1668,12 +1729,6 @@ DRT_HD void path_step_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGrid
             },
             warm);
     }
-}
-
-// chain length of path p (vertices before the first empty type byte)
-DRT_HD int chain_length(const LinkDev &L, int p) {
-    const uint32_t c = L.ptypes[p];
-    return (c & 0xffu) == 0 ? 0 : (c & 0xff00u) == 0 ? 1 : (c & 0xff0000u) == 0 ? 2 : (c & 0xff000000u) == 0 ? 3 : 4;
 }
 
 }  // namespace drt

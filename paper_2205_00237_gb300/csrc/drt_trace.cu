@@ -58,6 +58,53 @@ constexpr int TRACE_T = 128;
 // candidate k of the enumeration (0 = line of sight; single faces (R), edges (D), tiles (S); ordered
 // pairs of faces / edges, the same primitive twice excluded) solved at t: true when it is a ray, which
 // then fills *r
+// the candidate's chain of N interactions (codes c[0..N-1]): solved, checked and, if it is a ray, stored
+template <int N>
+DRT_HD bool trace_chain(const LinkDev &L, double t, long long k, const int *code, const PosedFace *faces,
+                        TracedRay *r) {
+    const int NP = L.n_faces + L.n_edges;
+    Prim<double> pr[N > 0 ? N : 1];
+    double s0[MAXI] = {0.0, 0.0, 0.0, 0.0};
+    uint32_t types = 0;
+    int prims[MAXI] = {0, 0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const int c = code[j];
+        int ty, idx;
+        if (c < L.n_faces) { ty = T_R; idx = c; }
+        else if (c < NP) { ty = T_D; idx = c - L.n_faces; s0[j] = 0.5 * L.edges[idx].len; }
+        else { ty = T_S; idx = c - NP; }
+        pr[j] = val_prim(load_prim_direct<double>(L, t, ty, idx));
+        types |= (uint32_t)ty << (8 * j);
+        prims[j] = idx;
+    }
+    v3<double> V[N + 2];
+    V[0] = val(terminal<double>(L.tx, t));
+    V[N + 1] = val(terminal<double>(L.rx, t));
+    uint32_t fl = 0;
+    solve_geometry_any<N>(pr, V, s0, fl);
+    fl |= validity<N>(pr, N, V);
+#pragma unroll
+    for (int i = 1; i <= N; ++i)
+        if (!(isfinite(V[i].x) && isfinite(V[i].y) && isfinite(V[i].z))) fl |= F_DEGEN;
+    if (fl) return false;
+#pragma unroll
+    for (int i = 1; i <= N + 1; ++i)
+        for (int f = 0; f < L.n_faces; ++f)
+            if (face_blocks(faces[f], V[i - 1], V[i])) return false;
+    r->index = k;
+    r->n = N;
+    r->types = types;
+#pragma unroll
+    for (int j = 0; j < MAXI; ++j) {
+        r->prims[j] = prims[j];
+        r->s[j] = 0.0;
+        if (j < N)
+            if (pr[j].type == T_D) r->s[j] = dot(V[j + 1] - pr[j].p, pr[j].a);
+    }
+    return true;
+}
+
 DRT_HD bool trace_eval(const LinkDev &L, double t, long long k, int with_tiles, const PosedFace *faces, TracedRay *r) {
     const int NP = L.n_faces + L.n_edges, NT = with_tiles ? L.n_tiles : 0;
     int n = 0, code[2] = {0, 0};
@@ -74,40 +121,9 @@ DRT_HD bool trace_eval(const LinkDev &L, double t, long long k, int with_tiles, 
             n = 2;
         }
     }
-    Prim<double> pr[MAXI];
-    double s0[MAXI] = {0.0, 0.0, 0.0, 0.0};
-    uint32_t types = 0;
-    int prims[MAXI] = {0, 0, 0, 0};
-    for (int j = 0; j < n; ++j) {
-        const int c = code[j];
-        int ty, idx;
-        if (c < L.n_faces) { ty = T_R; idx = c; }
-        else if (c < NP) { ty = T_D; idx = c - L.n_faces; s0[j] = 0.5 * L.edges[idx].len; }
-        else { ty = T_S; idx = c - NP; }
-        pr[j] = val_prim(load_prim_direct<double>(L, t, ty, idx));
-        types |= (uint32_t)ty << (8 * j);
-        prims[j] = idx;
-    }
-    v3<double> V[MAXI + 2];
-    V[0] = val(terminal<double>(L.tx, t));
-    V[n + 1] = val(terminal<double>(L.rx, t));
-    uint32_t fl = 0;
-    solve_geometry_generic(pr, n, V, s0, fl);
-    fl |= validity<-1>(pr, n, V);
-    for (int i = 1; i <= n; ++i)
-        if (!(isfinite(V[i].x) && isfinite(V[i].y) && isfinite(V[i].z))) fl |= F_DEGEN;
-    if (fl) return false;
-    for (int i = 1; i <= n + 1; ++i)
-        for (int f = 0; f < L.n_faces; ++f)
-            if (face_blocks(faces[f], V[i - 1], V[i])) return false;
-    r->index = k;
-    r->n = n;
-    r->types = types;
-    for (int j = 0; j < MAXI; ++j) {
-        r->prims[j] = prims[j];
-        r->s[j] = (j < n && ((types >> (8 * j)) & 0xff) == T_D) ? dot(V[j + 1] - pr[j].p, pr[j].a) : 0.0;
-    }
-    return true;
+    if (n == 0) return trace_chain<0>(L, t, k, code, faces, r);
+    if (n == 1) return trace_chain<1>(L, t, k, code, faces, r);
+    return trace_chain<2>(L, t, k, code, faces, r);
 }
 
 __global__ void __launch_bounds__(TRACE_T)
