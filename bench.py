@@ -71,9 +71,9 @@ RECORD_BYTES = {"fp64": 49, "fp32_bulk": 37}
 
 
 def kernel_source_hash():
-    """Hash of the sources the device code compiles from: the kernel translation units (drt_k_*.cu,
-    drt_kernels.cu) and every header (the roofline constants above belong to one version of them; the
-    host-only files drt_api.cu, drt_batch.cu, drt_serve.cu and drt_trace.cu's host part do not change them)."""
+    """Hash of the sources the extrapolation kernels compile from: the kernel translation units
+    (drt_k_*.cu, drt_kernels.cu) and every header; the roofline constants above belong to one version
+    of them (the host-side files drt_api.cu, drt_batch.cu, drt_serve.cu and the tracer do not change them)."""
     import glob
     import hashlib
     h = hashlib.sha256()

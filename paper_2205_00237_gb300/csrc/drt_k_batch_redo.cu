@@ -44,10 +44,17 @@ __global__ void __launch_bounds__(32) k_batch_redo(const BatchDev B) {   // one 
         if (*B.redo.count > B.redo.cap) atomicOr(hdr + 2, 1ull);
     }
     const int n = min(*B.redo.count, B.redo.cap);
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    // few queued steps: one per warp, on one lane (a step is one long dependent FP64 chain; lanes of
+    // different chains would wait for each other's branches); otherwise grid row y takes the chains of
+    // length y, whose code is one instance
+    const bool one = n <= (int)(gridDim.x * gridDim.y);
+    const int k0 = one ? blockIdx.y * gridDim.x + blockIdx.x : blockIdx.x * blockDim.x + threadIdx.x;
+    const int kstep = one ? n + 1 : gridDim.x * blockDim.x;
+    if (one && threadIdx.x != 0) return;
+    for (int k = k0; k < n; k += kstep) {
         const int4 itm = B.redo.items[k];
         const BatchLink &BL = B.links[itm.x];
-        if (chain_length(BL.L, itm.y) != (int)blockIdx.y) continue;   // grid row y: chains of length y
+        if (!one && chain_length(BL.L, itm.y) != (int)blockIdx.y) continue;
         redo_add_entry<DUAL>(BL, itm.y, itm.z);
         if (BL.partner >= 0 && itm.y >= BL.pair_p0) redo_add_entry<DUAL>(B.links[BL.partner], itm.y, itm.z);
     }

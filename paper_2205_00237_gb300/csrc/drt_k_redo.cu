@@ -6,14 +6,24 @@ namespace drt {
 
 // The same redo beside the H synthesis: each queued step's (Re a, Im a, tau) goes to out3 (its record
 // keeps a = 0, so the synthesis skips it), and k_redo_add then adds a exp(-j 2 pi f tau) into H.
-// Grid row y takes the queued steps of chains of length y only: the code for each length is its own
-// instance, so a warp whose lanes held chains of several lengths would run them one after the other.
+// A queued step is one long dependent FP64 chain, so the kernel's time is the latency of its slowest
+// warp.  With no more queued steps than warps, each warp takes one step on one lane: no two chains
+// share a warp, so none waits for another's branches.  Otherwise grid row y takes the steps of chains
+// of length y (each length is its own code instance, which lanes of one warp would run in turn).
 __global__ void __launch_bounds__(32)
 k_redo_rec(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const RedoList redo, const double *__restrict__ warm,
            double *__restrict__ out3) {
     const int n = min(*redo.count, redo.cap);
     const OutD none{};
     const RecD nor{nullptr, nullptr};
+    const int warp = blockIdx.y * gridDim.x + blockIdx.x;
+    if (n <= (int)(gridDim.x * gridDim.y)) {
+        if (threadIdx.x == 0 && warp < n) {
+            const int4 it = redo.items[warp];
+            path_step_redo_as<false>(L, tg, fg, it.y, it.z, none, nor, warm, out3 + 3 * (size_t)warp);
+        }
+        return;
+    }
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int4 it = redo.items[k];
         if (chain_length(L, it.y) != (int)blockIdx.y) continue;

@@ -12,6 +12,15 @@ __global__ void __launch_bounds__(32)
 k_redo(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const OutD out, const RecD rec, const RedoList redo,
        const double *__restrict__ warm) {
     int n = min(*redo.count, redo.cap);
+    const int warp = blockIdx.y * gridDim.x + blockIdx.x;
+    if (n <= (int)(gridDim.x * gridDim.y)) {   // few queued steps: one per warp (see k_redo_rec)
+        if (threadIdx.x == 0 && warp < n) {
+            const int4 it = redo.items[warp];
+            if constexpr (DUAL) path_step_redo_as<true>(L, tg, fg, it.y, it.z, out, rec, warm);
+            else path_step_redo_as<false>(L, tg, fg, it.y, it.z, out, rec, warm);
+        }
+        return;
+    }
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int4 it = redo.items[k];
         if (chain_length(L, it.y) != (int)blockIdx.y) continue;

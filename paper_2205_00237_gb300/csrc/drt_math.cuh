@@ -105,6 +105,12 @@ template <> struct ST<double> {   // plain values (FP64 chunk-base solve: no der
     static DRT_HD double rate(double) { return 0.0; }
     static DRT_HD double cst(double x) { return x; }
 };
+template <> struct ST<float> {   // plain FP32 values (the first Newton iterations of a warm-start solve)
+    typedef float R;
+    static DRT_HD float val(float x) { return x; }
+    static DRT_HD float rate(float) { return 0.f; }
+    static DRT_HD float cst(float x) { return x; }
+};
 DRT_HD double dsqrt(double x) { return sqrt(x); }
 template <class S> DRT_HD typename ST<S>::R sval(S x) { return ST<S>::val(x); }
 template <class S> DRT_HD typename ST<S>::R srate(S x) { return ST<S>::rate(x); }

@@ -23,6 +23,8 @@ enum : uint32_t { F_FACE = 1, F_EDGE = 2, F_SIDE = 4, F_NOCONV = 8, F_DEGEN = 16
 // internal: the FP32-bulk solve met a geometry it cannot resolve in FP32 (near-grazing Keller cone,
 // unconverged Newton, non-finite value); the path-step is redone in FP64.  Never written out.
 constexpr uint32_t F_REDO64 = 128;
+// internal: some FP32 validity margin lies within 100x the FP32 error bound (fp32_margin_tol)
+constexpr uint32_t F_NEAR100 = 64;
 
 enum : int { T_NONE = 0, T_R = 1, T_D = 2, T_S = 3 };
 
@@ -195,6 +197,9 @@ template <> DRT_HD void clamp_positive<dl<double>>(dl<double> &x, double eps) {
 template <> DRT_HD void clamp_positive<double>(double &x, double eps) {
     if (!(x > eps)) x = eps;
 }
+template <> DRT_HD void clamp_positive<float>(float &x, float eps) {
+    if (!(x > eps)) x = eps;
+}
 template <> DRT_HD void clamp_positive<de>(de &x, float eps) {
     if (!(x.b + x.d > eps)) {
         x.b = eps;
@@ -212,6 +217,7 @@ template <> DRT_HD void clamp_positive<dd>(dd &x, float eps) {
 // the base part is `base` (the chunk-base solution) and the delta `delta`
 template <class S> DRT_HD S newton_start(double base, double delta, double rate);
 template <> DRT_HD double newton_start<double>(double base, double delta, double) { return base + delta; }
+template <> DRT_HD float newton_start<float>(double base, double delta, double) { return (float)(base + delta); }
 template <> DRT_HD dl<double> newton_start<dl<double>>(double base, double delta, double rate) {
     return {base + delta, rate};
 }
@@ -524,7 +530,8 @@ template <int N> constexpr int len_min() { return N == LEN_GEN ? 2 : 0; }
 // amplified a little by the image construction, so a decision whose margin (the distance of the tested
 // point from the face rim, the edge end, the face plane or the wedge face) is within a bound on that
 // error is not taken here: the step gets F_REDO64 and the FP64 redo decides it, which makes the flags
-// of the form exact outside the 1e-9 m band of the FP64 form.
+// of the form exact outside the 1e-9 m band of the FP64 form.  F_NEAR100 marks margins within 100x
+// that bound (the FP32-bulk step uses it to keep the FP32 flags of invalid steps that moved far).
 template <class T> DRT_HD T amax3(v3<T> a) { return fmax(fmax(fabs(a.x), fabs(a.y)), fabs(a.z)); }
 // bound on the FP32 error of a margin computed from positions of magnitude `scale` (m): 2e-6 of the
 // scale is ~17 ulp of the largest coordinate; the FP32 flags of the canyon, link and highway workloads
@@ -540,7 +547,7 @@ DRT_HD uint32_t validity(const Prim<S> *pr, int n, const v3<typename ST<S>::R> *
     constexpr bool F32 = sizeof(T) == 4;
     const int nv = N >= 0 ? N : n;
     uint32_t fl = 0;
-    bool near = false;   // FP32 only: some margin within the error bound
+    T mmin = T(1e30);    // FP32 only: the smallest margin over its bound
 #pragma unroll (N >= 0 ? 8 : 1)
     for (int i = 1; i <= MAXI + 1; ++i) {
         if (i > nv + 1) break;
@@ -560,8 +567,7 @@ DRT_HD uint32_t validity(const Prim<S> *pr, int n, const v3<typename ST<S>::R> *
             if (!(dp > T(0)) || !(dn > T(0))) fl |= F_SIDE;
             if constexpr (F32) {
                 const T tol = fp32_margin_tol(fmax(fmax(amax3(P[i - 1]), amax3(P[i + 1])), fmax(amax3(P[i]), amax3(c))));
-                near = near || fabs(fabs(al) - q.h1) < tol || fabs(fabs(be) - q.h2) < tol || fabs(dp) < tol ||
-                       fabs(dn) < tol;
+                mmin = fmin(mmin, fmin(fmin(fabs(fabs(al) - q.h1), fabs(fabs(be) - q.h2)), fmin(fabs(dp), fabs(dn))) / tol);
             }
         } else if (q.type == T_D) {
             v3<T> A = val(q.p), e = val(q.a);
@@ -570,7 +576,7 @@ DRT_HD uint32_t validity(const Prim<S> *pr, int n, const v3<typename ST<S>::R> *
             T tol = T(0);
             if constexpr (F32) {
                 tol = fp32_margin_tol(fmax(fmax(amax3(P[i - 1]), amax3(P[i + 1])), fmax(amax3(P[i]), amax3(A))));
-                near = near || fabs(s) < tol || fabs(q.h1 - s) < tol;
+                mmin = fmin(mmin, fmin(fabs(s), fabs(q.h1 - s)) / tol);
             }
 #pragma unroll (N >= 0 ? 8 : 1)
             for (int side = -1; side <= 1; side += 2) {
@@ -588,7 +594,7 @@ DRT_HD uint32_t validity(const Prim<S> *pr, int n, const v3<typename ST<S>::R> *
                     in = sn > T(0) || (sn == T(0) && cs < T(0));
                 }
                 if (!in) fl |= F_SIDE;
-                if constexpr (F32) near = near || fabs(y) < tol || fabs(sn) < tol;
+                if constexpr (F32) mmin = fmin(mmin, fmin(fabs(y), fabs(sn)) / tol);
             }
         } else {
             v3<T> nn = val(q.a);
@@ -596,11 +602,14 @@ DRT_HD uint32_t validity(const Prim<S> *pr, int n, const v3<typename ST<S>::R> *
             if (!(dp > T(0)) || !(dn > T(0))) fl |= F_SIDE;
             if constexpr (F32) {
                 const T tol = fp32_margin_tol(fmax(fmax(amax3(P[i - 1]), amax3(P[i + 1])), amax3(P[i])));
-                near = near || fabs(dp) < tol || fabs(dn) < tol;
+                mmin = fmin(mmin, fmin(fabs(dp), fabs(dn)) / tol);
             }
         }
     }
-    if (near) fl |= F_REDO64;
+    if constexpr (F32) {
+        if (mmin < T(1)) fl |= F_REDO64;
+        if (mmin < T(100)) fl |= F_NEAR100;
+    }
     return fl;
 }
 
@@ -848,6 +857,91 @@ template <class T> DRT_HD v3<T> vertical_pol(v3<T> k) {
 // directions, so Euler's formula gives rho_e at a second diffraction); the distance parameter is
 // L = s (rho_e + s) rho1 rho2 sin^2 b0 / (rho_e (rho1 + s)(rho2 + s)), s s' sin^2 b0 / (s + s') for a
 // spherical incident wave.  Loops run over the fixed bound MAXI (see validity).
+// The field update at one vertex, per interaction type: E (the incident field, polarisation and
+// amplitude so far) across a reflection (Fresnel, Sec. III-A), a diffraction (UTD, Sec. III-B) or a
+// tile (ER, Sec. III-C), with kin / kout the unit directions of the incoming and outgoing segments.
+// The FP32 kernels call them out of line (one copy each, instead of one per vertex of every unrolled
+// chain length: the unrolled code otherwise outgrows the instruction cache, and the warps of an SM,
+// which run different chain signatures, wait on instruction fetch); FP64 keeps them inline.
+template <class T>
+DRT_HD c3<T> refl_field_inl(c3<T> E, v3<T> kin, v3<T> kout, v3<T> nf, MatV<T> m, T ieps) {
+    if (dot(nf, kin) > T(0)) nf = -nf;
+    T ct = -dot(nf, kin);
+    v3<T> ep = cross(kin, nf);
+    if (dot(ep, ep) < T(1e-24)) {
+        ep = cross(nf, V3<T>(T(1), T(0), T(0)));
+        if (dot(ep, ep) < T(1e-12)) ep = cross(nf, V3<T>(T(0), T(1), T(0)));
+    }
+    ep = unit(ep);
+    v3<T> epin = cross(ep, kin), epout = cross(ep, kout);
+    cx<T> rte, rtm;
+    fresnel(m, ieps, ct, rte, rtm);
+    return cscale(ep, rte * cdot(E, ep) * m.spec) + cscale(epout, rtm * cdot(E, epin) * m.spec);
+}
+
+// e: edge direction; t0, n0: the 0-face tangent and normal; wn: wedge n; snp, cnp: sin(n pi), cos(n pi);
+// Lf: the distance parameter over sin^2 b0
+template <class T>
+DRT_HD c3<T> diff_field_inl(c3<T> E, v3<T> kin, v3<T> kout, v3<T> e, v3<T> t0, v3<T> n0, T wn, T snp, T cnp, T Lf,
+                            T k, MatV<T> m, T ieps) {
+    v3<T> wi = -kin + e * dot(kin, e);
+    v3<T> wo = kout - e * dot(kout, e);
+    const T yi = dot(wi, n0), xi = dot(wi, t0), yo = dot(wo, n0), xo = dot(wo, t0);
+    // atan2 lies in [-pi, pi]: one conditional turn maps it to [0, 2 pi) (no fmod)
+    T phip = atan2(yi, xi), phi = atan2(yo, xo);
+    if (phip < T(0)) phip += T(2 * PI);
+    if (phi < T(0)) phi += T(2 * PI);
+    T sinb0 = norm(cross(kin, e));
+    const T Lp = Lf * sinb0 * sinb0;
+    T sphip = T(0), snphi = T(0);
+    if (!m.pec) {   // Luebbers' face coefficients: sin phi' and sin(n pi - phi) from components
+        const T ri = sqrt(xi * xi + yi * yi), ro = sqrt(xo * xo + yo * yo);
+        sphip = ri > T(0) ? fabs(yi) / ri : T(0);
+        snphi = ro > T(0) ? fabs(snp * xo - cnp * yo) / ro : T(0);
+    }
+    cx<T> Ds, Dh;
+    utd(wn, phi, phip, sphip, snphi, sinb0, Lp, k, m, ieps, Ds, Dh);
+    v3<T> php = -unit(cross(e, kin)), bpv = cross(php, kin);
+    v3<T> ph = unit(cross(e, kout)), bv = cross(ph, kout);
+    return cscale(bv, -(Ds * cdot(E, bpv))) + cscale(ph, -(Dh * cdot(E, php)));
+}
+
+template <class T>
+DRT_HD c3<T> tile_field_inl(c3<T> E, v3<T> kin, v3<T> kout, v3<T> nt, TileV<T> tl) {
+    if (dot(nt, kin) > T(0)) nt = -nt;
+    T cti = -dot(nt, kin);
+    v3<T> kspec = kin + nt * (T(2) * cti);
+    T cpsi = dot(kspec, kout);
+    int alpha = tl.alpha;
+    T Fa = er_norm<T>(alpha, cti);
+    const T hb = T(0.5) * (T(1) + cpsi);
+    T lobe_h = T(1);   // ((1 + cos psi)/2)^(alpha/2): the field of the power lobe
+    for (int j = 0; j < alpha / 2; ++j) lobe_h *= hb;
+    if (alpha & 1) lobe_h *= sqrt(hb);
+    T amp = tl.s * sqrt(tl.area * cti / Fa) * lobe_h;
+    cx<T> ph = C<T>(tl.cph, tl.sph);
+    T nE = cnorm(E);
+    cx<T> ek = cdot(E, kout);
+    c3<T> Ep = E + cscale(kout, -ek);
+    T nEp = cnorm(Ep);
+    if (nEp < T(1e-12) * nE || nE == T(0)) Ep = cscale(vertical_pol(kout), C<T>(nE, T(0)));
+    else Ep = cscale(Ep, C<T>(nE / nEp, T(0)));
+    return cscale(Ep, ph * amp);
+}
+
+#define DRT_NOINL __host__ __device__ __noinline__
+template <class T> DRT_NOINL c3<T> refl_field_out(c3<T> E, v3<T> kin, v3<T> kout, v3<T> nf, MatV<T> m, T ieps) {
+    return refl_field_inl(E, kin, kout, nf, m, ieps);
+}
+template <class T>
+DRT_NOINL c3<T> diff_field_out(c3<T> E, v3<T> kin, v3<T> kout, v3<T> e, v3<T> t0, v3<T> n0, T wn, T snp, T cnp, T Lf,
+                               T k, MatV<T> m, T ieps) {
+    return diff_field_inl(E, kin, kout, e, t0, n0, wn, snp, cnp, Lf, k, m, ieps);
+}
+template <class T> DRT_NOINL c3<T> tile_field_out(c3<T> E, v3<T> kin, v3<T> kout, v3<T> nt, TileV<T> tl) {
+    return tile_field_inl(E, kin, kout, nt, tl);
+}
+
 template <int N = -1, class S, class T = typename ST<S>::R>
 DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *seg, T fc) {
     const int nv = N >= 0 ? N : n;
@@ -933,67 +1027,22 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
     for (int i = 1; i <= MAXI; ++i) {
         if (i > nv) break;
         const Prim<S> &q = pr[i - 1];
-        const MatV<T> m = matv<T>(L.mats[q.mat]);
         const v3<T> kin = kd[i], kout = kd[i + 1];
         klast = kout;
+        constexpr bool OUTL = sizeof(T) == 4;
         if (q.type == T_R) {
-            v3<T> nf = val(q.a);
-            if (dot(nf, kin) > T(0)) nf = -nf;
-            T ct = -dot(nf, kin);
-            v3<T> ep = cross(kin, nf);
-            if (dot(ep, ep) < T(1e-24)) {
-                ep = cross(nf, V3<T>(T(1), T(0), T(0)));
-                if (dot(ep, ep) < T(1e-12)) ep = cross(nf, V3<T>(T(0), T(1), T(0)));
-            }
-            ep = unit(ep);
-            v3<T> epin = cross(ep, kin), epout = cross(ep, kout);
-            cx<T> rte, rtm;
-            fresnel(m, ieps, ct, rte, rtm);
-            E = cscale(ep, rte * cdot(E, ep) * m.spec) + cscale(epout, rtm * cdot(E, epin) * m.spec);
+            const MatV<T> m = matv<T>(L.mats[q.mat]);
+            if constexpr (OUTL) E = refl_field_out(E, kin, kout, val(q.a), m, ieps);
+            else E = refl_field_inl(E, kin, kout, val(q.a), m, ieps);
         } else if (q.type == T_D) {
-            v3<T> e = val(q.a);
-            v3<T> wi = -kin + e * dot(kin, e);
-            v3<T> wo = kout - e * dot(kout, e);
-            const T yi = dot(wi, q.c), xi = dot(wi, q.b), yo = dot(wo, q.c), xo = dot(wo, q.b);
-            // atan2 lies in [-pi, pi]: one conditional turn maps it to [0, 2 pi) (no fmod)
-            T phip = atan2(yi, xi), phi = atan2(yo, xo);
-            if (phip < T(0)) phip += T(2 * PI);
-            if (phi < T(0)) phi += T(2 * PI);
-            T sinb0 = norm(cross(kin, e));
-            const T Lp = Lfac[i] * sinb0 * sinb0;
-            T sphip = T(0), snphi = T(0);
-            if (!m.pec) {   // Luebbers' face coefficients: sin phi' and sin(n pi - phi) from components
-                const T ri = sqrt(xi * xi + yi * yi), ro = sqrt(xo * xo + yo * yo);
-                sphip = ri > T(0) ? fabs(yi) / ri : T(0);
-                snphi = ro > T(0) ? fabs(q.h3 * xo - q.h4 * yo) / ro : T(0);
-            }
-            cx<T> Ds, Dh;
-            utd(q.h2, phi, phip, sphip, snphi, sinb0, Lp, k, m, ieps, Ds, Dh);
-            v3<T> php = -unit(cross(e, kin)), bpv = cross(php, kin);
-            v3<T> ph = unit(cross(e, kout)), bv = cross(ph, kout);
-            E = cscale(bv, -(Ds * cdot(E, bpv))) + cscale(ph, -(Dh * cdot(E, php)));
+            const MatV<T> m = matv<T>(L.mats[q.mat]);
+            if constexpr (OUTL)
+                E = diff_field_out(E, kin, kout, val(q.a), q.b, q.c, q.h2, q.h3, q.h4, Lfac[i], k, m, ieps);
+            else E = diff_field_inl(E, kin, kout, val(q.a), q.b, q.c, q.h2, q.h3, q.h4, Lfac[i], k, m, ieps);
         } else {
             const TileV<T> tl = tilev<T>(L, q.idx);
-            v3<T> nt = val(q.a);
-            if (dot(nt, kin) > T(0)) nt = -nt;
-            T cti = -dot(nt, kin);
-            v3<T> kspec = kin + nt * (T(2) * cti);
-            T cpsi = dot(kspec, kout);
-            int alpha = tl.alpha;
-            T Fa = er_norm<T>(alpha, cti);
-            const T hb = T(0.5) * (T(1) + cpsi);
-            T lobe_h = T(1);   // ((1 + cos psi)/2)^(alpha/2): the field of the power lobe
-            for (int j = 0; j < alpha / 2; ++j) lobe_h *= hb;
-            if (alpha & 1) lobe_h *= sqrt(hb);
-            T amp = tl.s * sqrt(tl.area * cti / Fa) * lobe_h;
-            cx<T> ph = C<T>(tl.cph, tl.sph);
-            T nE = cnorm(E);
-            cx<T> ek = cdot(E, kout);
-            c3<T> Ep = E + cscale(kout, -ek);
-            T nEp = cnorm(Ep);
-            if (nEp < T(1e-12) * nE || nE == T(0)) Ep = cscale(vertical_pol(kout), C<T>(nE, T(0)));
-            else Ep = cscale(Ep, C<T>(nE / nEp, T(0)));
-            E = cscale(Ep, ph * amp);
+            if constexpr (OUTL) E = tile_field_out(E, kin, kout, val(q.a), tl);
+            else E = tile_field_inl(E, kin, kout, val(q.a), tl);
         }
     }
     T lam = T(C0) / fc;
@@ -1192,6 +1241,41 @@ DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const Fre
     }
 }
 
+// an FP64 dual-number primitive without its rates
+DRT_HD Prim<double> val_prim(const Prim<dl<double>> &q) {
+    Prim<double> r;
+    r.type = q.type;
+    r.mat = q.mat;
+    r.idx = q.idx;
+    r.p = val(q.p);
+    r.a = val(q.a);
+    r.b = q.b;
+    r.c = q.c;
+    r.h1 = q.h1;
+    r.h2 = q.h2;
+    r.h3 = q.h3;
+    r.h4 = q.h4;
+    return r;
+}
+
+// FP32 copies (the FP32 stage of a warm-start solve)
+DRT_HD v3<float> f32v(v3<double> a) { return V3<float>(a.x, a.y, a.z); }
+DRT_HD Prim<float> f32_prim(const Prim<dl<double>> &q) {
+    Prim<float> r;
+    r.type = q.type;
+    r.mat = q.mat;
+    r.idx = q.idx;
+    r.p = f32v(val(q.p));
+    r.a = f32v(val(q.a));
+    r.b = f32v(q.b);
+    r.c = f32v(q.c);
+    r.h1 = (float)q.h1;
+    r.h2 = (float)q.h2;
+    r.h3 = (float)q.h3;
+    r.h4 = (float)q.h4;
+    return r;
+}
+
 // One dual-number FP64 solve of a chain at time t from the edge-parameter start `sin`; writes each
 // diffraction vertex's parameter and rate to sv/sd (sin and 0 where the solve failed).  N < 0: the
 // chain length is read at run time and the solve runs in the instance for that length.
@@ -1213,8 +1297,41 @@ DRT_HD void solve_edge_params(const LinkDev &L, int p, double t, const double *s
         v3<dl<T>> V[N + 2];
         V[0] = terminal<T>(L.tx, t);
         V[N + 1] = terminal<T>(L.rx, t);
+        // Staged Newton: FP32 from the start `sin` to ~1e-4 m (FP32 runs at 64x the FP64 rate), then FP64
+        // values to the FP64 tolerance (quadratic convergence: two or three steps), then one dual-number
+        // step, which gives the rates (the implicit-function derivative) at the root.  A stage that does
+        // not converge leaves the next one its own start.
+        double s1[MAXI];
+#pragma unroll
+        for (int j = 0; j < MAXI; ++j) s1[j] = sin[j];
+        if constexpr (N >= 2) {
+            Prim<float> pf[N];
+            v3<float> Vf[N + 2];
+#pragma unroll
+            for (int j = 0; j < N; ++j) pf[j] = f32_prim(pr[j]);
+            Vf[0] = f32v(val(V[0]));
+            Vf[N + 1] = f32v(val(V[N + 1]));
+            uint32_t ff = 0;
+            solve_geometry_any<N>(pf, Vf, s1, ff);
+            if (!(ff & F_NOCONV))
+#pragma unroll
+                for (int j = 0; j < N; ++j)
+                    if (pf[j].type == T_D) s1[j] = (double)dot(Vf[j + 1] - pf[j].p, pf[j].a);
+            Prim<double> pd[N];
+            v3<double> Vd[N + 2];
+#pragma unroll
+            for (int j = 0; j < N; ++j) pd[j] = val_prim(pr[j]);
+            Vd[0] = val(V[0]);
+            Vd[N + 1] = val(V[N + 1]);
+            uint32_t fd = 0;
+            solve_geometry_any<N>(pd, Vd, s1, fd);
+            if (!(fd & F_NOCONV))
+#pragma unroll
+                for (int j = 0; j < N; ++j)
+                    if (pd[j].type == T_D) s1[j] = dot(Vd[j + 1] - pd[j].p, pd[j].a);
+        }
         uint32_t fl = 0;
-        solve_geometry_any<N>(pr, V, sin, fl);
+        solve_geometry_any<N>(pr, V, s1, fl);
 #pragma unroll
         for (int j = 0; j < MAXI; ++j) {
             sv[j] = sin[j];
@@ -1467,22 +1584,6 @@ DRT_HD void path_base_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGrid
     }
 }
 
-// an FP64 dual-number primitive without its rates
-DRT_HD Prim<double> val_prim(const Prim<dl<double>> &q) {
-    Prim<double> r;
-    r.type = q.type;
-    r.mat = q.mat;
-    r.idx = q.idx;
-    r.p = val(q.p);
-    r.a = val(q.a);
-    r.b = q.b;
-    r.c = q.c;
-    r.h1 = q.h1;
-    r.h2 = q.h2;
-    r.h3 = q.h3;
-    r.h4 = q.h4;
-    return r;
-}
 
 // a delta-number primitive without its rates
 DRT_HD Prim<de> strip(const Prim<dd> &q) {
@@ -1616,7 +1717,13 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
             finite = finite && isfinite(P[i].x) && isfinite(P[i].y) && isfinite(P[i].z);
         }
         const float dlim = fg2 ? fminf(fg.disp_lim, fg2->disp_lim) : fg.disp_lim;
-        if (disp2 > dlim * dlim) fl |= F_REDO64;
+        // A step past the displacement limit needs FP64 for its phase; an invalid step has none, and its
+        // flags stand when every validity margin clears 100x the FP32 error bound (most such steps are
+        // invalid: interaction points of a chain that left its faces run far and fast, and the FP32
+        // decisions there have margins of metres).
+        const bool invalid_clear = (fl & (F_FACE | F_EDGE | F_SIDE)) && !(fl & F_NEAR100);
+        if (disp2 > dlim * dlim && !invalid_clear) fl |= F_REDO64;
+        fl &= ~F_NEAR100;
         if (!finite || (fl & (F_REDO64 | F_NOCONV | F_DEGEN))) {
             // geometry FP32 cannot resolve: queue this path-step for the FP64 redo kernel (rare,
             // see F_REDO64); the list holds every path-step in the worst case
