@@ -9,14 +9,13 @@
 namespace drt {
 
 template <int N, bool MULTI, bool OUT, bool PAIR, class S>
-__device__ __forceinline__ void batch_unit(const BatchDev &B, const BatchLink &BL, int li, int p, int t) {
+__device__ __forceinline__ void batch_unit(const BatchDev &B, const BatchLink &BL, const BatchLink *Q, int li, int p,
+                                           int t, const BulkRows &R) {
     Rec5 r, r2;
-    const BatchLink *Q = (PAIR && BL.partner >= 0) ? &B.links[BL.partner] : nullptr;
     if (PAIR && Q)
-        bulk_eval<N, MULTI, OUT, S>(BL.L, BL.tg, BL.fg, BL.poseb, BL.base, BL.warm, p, t, BL.out, r, B.redo, li,
-                                    &Q->fg, Q->base, &r2);
+        bulk_eval<N, MULTI, OUT, S>(BL.L, BL.tg, BL.fg, R, BL.warm, p, t, BL.out, r, B.redo, li, &Q->fg, &r2);
     else
-        bulk_eval<N, MULTI, OUT, S>(BL.L, BL.tg, BL.fg, BL.poseb, BL.base, BL.warm, p, t, BL.out, r, B.redo, li);
+        bulk_eval<N, MULTI, OUT, S>(BL.L, BL.tg, BL.fg, R, BL.warm, p, t, BL.out, r, B.redo, li);
     const size_t ri = BL.rec0 + (size_t)t * BL.L.n_paths + p;
     B.rec_a[ri] = make_float4(r.ar, r.ai, r.ph, r.hi);
     B.rec_b[ri] = r.lo;
@@ -49,10 +48,15 @@ __global__ void __launch_bounds__(128, BatchBlocks<N, MULTI>::v) k_batch_bulk(co
         const int nb = (BL.tg.n_steps + BULK_W - 1) / BULK_W;
         const int p0 = N < 0 ? BL.gen_p0 : MULTI ? BL.L.multi_start[N - 2] : BL.L.len_start[N];
         const int p = p0 + (int)(local / nb), t = (int)(local % nb) * BULK_W + lane;
+        if (N < 0 && p >= BL.skip_p0 && p < BL.skip_p1) continue;   // units of their own (warp-uniform)
         if (t < BL.tg.n_steps) {
+            // the unit's chunk-base rows, and those of a pair's second carrier
+            const BatchLink *Q = ((PAIR || N < 0) && BL.partner >= 0) ? &B.links[BL.partner] : nullptr;
+            const BulkRows R = bulk_rows_global(BL.L, BL.poseb, BL.base, Q ? Q->base : nullptr,
+                                                (BL.tg.n_steps + BL.tg.chunk - 1) / BL.tg.chunk, p);
             // the generic range: one instance per chain length, each taking a carrier pair or one carrier
-            if constexpr (N >= 0) batch_unit<N, MULTI, false, PAIR, S>(B, BL, li, p, t);
-            else if (p < BL.skip_p0 || p >= BL.skip_p1) batch_unit<LEN_ANY, true, true, true, S>(B, BL, li, p, t);
+            if constexpr (N >= 0) batch_unit<N, MULTI, false, PAIR, S>(B, BL, Q, li, p, t, R);
+            else batch_unit<LEN_ANY, true, true, true, S>(B, BL, Q, li, p, t, R);
         }
     }
 }

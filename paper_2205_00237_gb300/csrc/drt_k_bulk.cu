@@ -53,12 +53,14 @@ k_extrapolate_bulk_out(const LinkDev L, const TimeGridD tg, const FreqGridD fg, 
     const int p = p0 + blockIdx.y;
     const int ti = blockIdx.x * EXT_T + threadIdx.x;
     if (p >= p1 || ti >= tg.n_steps) return;
+    const int n = chain_length(L, p);
+    const BulkRows R = bulk_rows_global(L, poseb, base, nullptr, (tg.n_steps + tg.chunk - 1) / tg.chunk, p);
     typedef std::conditional_t<DUAL, dd, de> S;
-    switch (chain_length(L, p)) {
-    case 0: path_step_bulk<0, false, true, S>(L, tg, fg, poseb, base, warm, p, ti, out, rec, redo); break;
-    case 1: path_step_bulk<1, false, true, S>(L, tg, fg, poseb, base, warm, p, ti, out, rec, redo); break;
-    case 2: path_step_bulk<2, false, true, S>(L, tg, fg, poseb, base, warm, p, ti, out, rec, redo); break;
-    default: path_step_bulk<3, false, true, S>(L, tg, fg, poseb, base, warm, p, ti, out, rec, redo); break;
+    switch (n) {
+    case 0: path_step_bulk<0, false, true, S>(L, tg, fg, R, warm, p, ti, out, rec, redo); break;
+    case 1: path_step_bulk<1, false, true, S>(L, tg, fg, R, warm, p, ti, out, rec, redo); break;
+    case 2: path_step_bulk<2, false, true, S>(L, tg, fg, R, warm, p, ti, out, rec, redo); break;
+    default: path_step_bulk<3, false, true, S>(L, tg, fg, R, warm, p, ti, out, rec, redo); break;
     }
 }
 

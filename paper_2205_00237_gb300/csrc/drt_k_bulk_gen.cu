@@ -15,8 +15,9 @@ k_extrapolate_bulk_gen(const LinkDev L, const TimeGridD tg, const FreqGridD fg, 
     const int p = p0 + blockIdx.y;
     const int ti = blockIdx.x * EXT_T + threadIdx.x;
     if (p >= p1 || ti >= tg.n_steps) return;
+    const BulkRows R = bulk_rows_global(L, poseb, base, nullptr, (tg.n_steps + tg.chunk - 1) / tg.chunk, p);
     typedef std::conditional_t<DUAL, dd, de> S;
-    path_step_bulk<LEN_GEN, true, true, S>(L, tg, fg, poseb, base, warm, p, ti, out, rec, redo);
+    path_step_bulk<LEN_GEN, true, true, S>(L, tg, fg, R, warm, p, ti, out, rec, redo);
 }
 
 cudaError_t launch_extrapolate_bulk_generic(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const PoseB *pb,

@@ -53,7 +53,8 @@ k_extrapolate_bulk_n(const LinkDev L, const TimeGridD tg, const FreqGridD fg, co
     const int p = p0 + blockIdx.y;
     const int ti = blockIdx.x * EXT_T + threadIdx.x;
     if (p >= p1 || ti >= tg.n_steps) return;
-    path_step_bulk<N, MULTI, false, de>(L, tg, fg, poseb, base, warm, p, ti, out, rec, redo);
+    const BulkRows R = bulk_rows_global(L, poseb, base, nullptr, (tg.n_steps + tg.chunk - 1) / tg.chunk, p);
+    path_step_bulk<N, MULTI, false, de>(L, tg, fg, R, warm, p, ti, out, rec, redo);
 }
 
 // The generic range [len_start[MAXI], n_paths) in launch classes: the multi-diffraction chains of 2

@@ -1375,15 +1375,27 @@ DRT_HD void path_warm_fp64(const LinkDev &L, const TimeGridD &tg, int p, int row
 // deltas, not on the ~100 m path length.
 
 // per (path, chunk) FP64 anchors
-struct BaseRec {
+struct alignas(16) BaseRec {
     double d;                  // path length at the chunk base (m)
     float ph0, st_hi, st_lo;   // frac(f_0 d / c); frac(df d / c) = st_hi + st_lo
     float pad;
     float seg[MAXI + 1][3];    // segment vectors V_i - V_{i-1} at the chunk base, from FP64 positions
+    float pad2[2];             // 96 B: read as six 16-byte words
 };
 
 // per (body, chunk) FP32 base pose: rows of R(t_b), O(t_b), v_O(t_b), a, axis k, w(t_b), wdot
-struct PoseB { float R[9], O[3], vO[3], a[3], k[3], w, wdot, pad; };
+struct alignas(16) PoseB { float R[9], O[3], vO[3], a[3], k[3], w, wdot, pad; };   // 96 B
+
+// a row of 16-byte words (PoseB, BaseRec) read with 16-byte loads
+template <class T> DRT_HD T ld_row(const T &src) {
+    static_assert(sizeof(T) % 16 == 0 && alignof(T) >= 16, "16-byte rows");
+    T r;
+    const float4 *s = reinterpret_cast<const float4 *>(&src);
+    float4 *d = reinterpret_cast<float4 *>(&r);
+#pragma unroll
+    for (int k = 0; k < (int)(sizeof(T) / 16); ++k) d[k] = s[k];
+    return r;
+}
 
 DRT_HD void body_pose_base(const BodyD &B, double tb, PoseB &q) {
     double P[POSE_W];
@@ -1418,7 +1430,8 @@ struct PoseDD {
     v3<float> R0, R1, R2, O, dO, vO, w, k;
     float sn, vs;   // sin(dth), 1 - cos(dth)
 };
-DRT_HD PoseDD pose_dd(const PoseB &q, float tau) {
+DRT_HD PoseDD pose_dd(const PoseB &row, float tau) {
+    const PoseB q = ld_row(row);
     PoseDD P;
     P.R0 = V3<float>(q.R[0], q.R[1], q.R[2]);
     P.R1 = V3<float>(q.R[3], q.R[4], q.R[5]);
@@ -1454,19 +1467,24 @@ DRT_HD v3<dd> pose_dir_dd(const PoseDD &P, const float *d0) {
 }
 // terminal tau seconds after its chunk base, from its base record (stored like a body pose: O = r,
 // vO = v, a = a at the chunk's first instant)
-DRT_HD v3<dd> terminal_dd(const PoseB &q, float tau) {
+DRT_HD v3<dd> terminal_dd(const PoseB &row, float tau) {
+    const PoseB q = ld_row(row);
     v3<float> b = V3<float>(q.O[0], q.O[1], q.O[2]), v = V3<float>(q.vO[0], q.vO[1], q.vO[2]);
     v3<float> a = V3<float>(q.a[0], q.a[1], q.a[2]);
     return ddv(b, v * tau + a * (0.5f * tau * tau), v + a * tau);
 }
 
-DRT_HD Prim<dd> load_prim_dd(const LinkDev &L, const PoseB *poseb, int n_chunks, int chunk, float tau, int type,
-                             int idx) {
+// the FP32 body of primitive (type, idx)
+DRT_HD int prim_body_f(const LinkDev &L, int type, int idx) {
+    return type == T_R ? L.facesF[idx].body : type == T_D ? L.edgesF[idx].body : L.tilesF[idx].body;
+}
+
+// primitive posed from its body's chunk-base row
+DRT_HD Prim<dd> load_prim_dd(const LinkDev &L, const PoseB &row, float tau, int type, int idx) {
     Prim<dd> q;
     q.type = type;
     q.idx = idx;
-    int body = type == T_R ? L.facesF[idx].body : type == T_D ? L.edgesF[idx].body : L.tilesF[idx].body;
-    PoseDD P = pose_dd(poseb[(size_t)body * n_chunks + chunk], tau);
+    PoseDD P = pose_dd(row, tau);
     if (type == T_R) {
         const FaceF &f = L.facesF[idx];
         q.p = pose_point_dd(P, f.c);
@@ -1601,11 +1619,44 @@ DRT_HD Prim<de> strip(const Prim<dd> &q) {
     r.h4 = q.h4;
     return r;
 }
-template <class S> DRT_HD Prim<S> load_prim_as(const LinkDev &L, const PoseB *poseb, int n_chunks, int chunk,
-                                               float tau, int type, int idx) {
-    if constexpr (std::is_same<S, dd>::value) return load_prim_dd(L, poseb, n_chunks, chunk, tau, type, idx);
-    else return strip(load_prim_dd(L, poseb, n_chunks, chunk, tau, type, idx));
+template <class S> DRT_HD Prim<S> load_prim_as(const LinkDev &L, const PoseB &row, float tau, int type, int idx) {
+    if constexpr (std::is_same<S, dd>::value) return load_prim_dd(L, row, tau, type, idx);
+    else return strip(load_prim_dd(L, row, tau, type, idx));
 }
+
+// Where an FP32-bulk step reads its chunk-base rows: the pose rows of its vertices' bodies and of the
+// terminals (slot j < MAXI: vertex j + 1's body; MAXI: TX; MAXI + 1: RX) and its path's anchors (base;
+// base2 those of a pair's second carrier, or null), chunk c at pose[slot][c - c0] and
+// base[(c - c0) * bstride].  The kernels read them in global memory (c0 = 0, bstride = n_paths): the
+// rows of a block's chunks are few and shared by its warps, so they stay in L1 (a copy staged in
+// shared memory per block or per warp measured 16-24 % slower).
+struct BulkRows {
+    const PoseB *pose[MAXI + 2];
+    const BaseRec *base, *base2;
+    int c0, bstride;
+};
+
+// the global-memory rows of path p (base tables [chunk][path], pose table [body + 2][chunk])
+DRT_HD BulkRows bulk_rows_global(const LinkDev &L, const PoseB *poseb, const BaseRec *base, const BaseRec *base2,
+                                 int n_chunks, int p) {
+    BulkRows R;
+    const uint32_t code = L.ptypes[p];
+    const int4 pi = L.pprims[p];
+    const int prim[MAXI] = {pi.x, pi.y, pi.z, pi.w};
+#pragma unroll
+    for (int j = 0; j < MAXI; ++j) {
+        const int ty = (code >> (8 * j)) & 0xff;
+        R.pose[j] = poseb + (size_t)(ty == T_NONE ? 0 : prim_body_f(L, ty, prim[j])) * n_chunks;
+    }
+    R.pose[MAXI] = poseb + (size_t)L.n_bodies * n_chunks;
+    R.pose[MAXI + 1] = poseb + (size_t)(L.n_bodies + 1) * n_chunks;
+    R.base = base + p;
+    R.base2 = base2 ? base2 + p : nullptr;
+    R.c0 = 0;
+    R.bstride = L.n_paths;
+    return R;
+}
+
 template <class S> DRT_HD v3<S> terminal_as(const PoseB &q, float tau) {
     if constexpr (std::is_same<S, dd>::value) return terminal_dd(q, tau);
     else return strip(terminal_dd(q, tau));
@@ -1658,22 +1709,20 @@ struct Rec5 { float ar, ai, ph, hi, lo; };
 // A second carrier (fg2 with its anchors base2; the same time grid and chunks) shares the geometry:
 // its field coefficients and phase record go to *rec2.
 template <int N = -1, bool MULTI = true, bool OUT = true, class S = dd>
-DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const PoseB *poseb,
-                      const BaseRec *base, const double *warm, int p, int ti, const OutD &out, Rec5 &rec,
-                      const RedoList &redo, int link, const FreqGridD *fg2 = nullptr, const BaseRec *base2 = nullptr,
-                      Rec5 *rec2 = nullptr) {
+DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const BulkRows &R,
+                      const double *warm, int p, int ti, const OutD &out, Rec5 &rec, const RedoList &redo, int link,
+                      const FreqGridD *fg2 = nullptr, Rec5 *rec2 = nullptr) {
     if constexpr (N < 0) {
         bool ok = false;
         with_length<len_min<N>()>(chain_length(L, p), [&](auto NC) {
-            ok = bulk_eval<decltype(NC)::value, MULTI, OUT, S>(L, tg, fg, poseb, base, warm, p, ti, out, rec, redo,
-                                                               link, fg2, base2, rec2);
+            ok = bulk_eval<decltype(NC)::value, MULTI, OUT, S>(L, tg, fg, R, warm, p, ti, out, rec, redo, link, fg2,
+                                                               rec2);
         });
         return ok;
     } else {
     typedef float T;
     rec = Rec5{0.f, 0.f, 0.f, 0.f, 0.f};
     if (rec2) *rec2 = Rec5{0.f, 0.f, 0.f, 0.f, 0.f};
-    const int n_chunks = (tg.n_steps + tg.chunk - 1) / tg.chunk;
     const int chunk = ti / tg.chunk;
     const float tau_t = (float)(ti - chunk * tg.chunk) * tg.dtf;
     const uint32_t code = L.ptypes[p];
@@ -1683,10 +1732,10 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
     Prim<S> pr[MAXI];
 #pragma unroll
     for (int j = 0; j < N; ++j)
-        pr[j] = load_prim_as<S>(L, poseb, n_chunks, chunk, tau_t, (code >> (8 * j)) & 0xff, prim[j]);
+        pr[j] = load_prim_as<S>(L, R.pose[j][chunk - R.c0], tau_t, (code >> (8 * j)) & 0xff, prim[j]);
     v3<S> V[MAXI + 2];
-    V[0] = terminal_as<S>(poseb[(size_t)L.n_bodies * n_chunks + chunk], tau_t);
-    V[N + 1] = terminal_as<S>(poseb[(size_t)(L.n_bodies + 1) * n_chunks + chunk], tau_t);
+    V[0] = terminal_as<S>(R.pose[MAXI][chunk - R.c0], tau_t);
+    V[N + 1] = terminal_as<S>(R.pose[MAXI + 1][chunk - R.c0], tau_t);
     uint32_t fl = 0;
     if (MULTI && warm && p >= L.n_bulk) {
         WarmStart ws;
@@ -1744,7 +1793,7 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
             return false;
         }
     }
-    const BaseRec &B = base[(size_t)chunk * L.n_paths + p];
+    const BaseRec B = ld_row(R.base[(size_t)(chunk - R.c0) * R.bstride]);
     float dd_len = 0.f;   // change of the path length since the chunk base
     v3<float> seg[MAXI + 2];
 #pragma unroll (N >= 0 ? 8 : 1)
@@ -1782,18 +1831,18 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
     phase_record(fg, B, a, rec);
     if (fg2) {
         const cx<T> a2 = (fl & F_DEGEN) ? C<T>(T(0), T(0)) : amplitude<N>(L, pr, n, seg, fg2->fcf);
-        phase_record(*fg2, base2[(size_t)chunk * L.n_paths + p], a2, *rec2);
+        phase_record(*fg2, ld_row(R.base2[(size_t)(chunk - R.c0) * R.bstride]), a2, *rec2);
     }
     return true;
     }
 }
 
 template <int N = -1, bool MULTI = true, bool OUT = true, class S = dd>
-DRT_HD void path_step_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const PoseB *poseb,
-                           const BaseRec *base, const double *warm, int p, int ti, const OutD &out, const RecD &rec,
+DRT_HD void path_step_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const BulkRows &R,
+                           const double *warm, int p, int ti, const OutD &out, const RecD &rec,
                            const RedoList &redo) {
     Rec5 r;
-    bulk_eval<N, MULTI, OUT, S>(L, tg, fg, poseb, base, warm, p, ti, out, r, redo, 0);
+    bulk_eval<N, MULTI, OUT, S>(L, tg, fg, R, warm, p, ti, out, r, redo, 0);
     if (rec.rec_a) {
         size_t ri = (size_t)ti * L.n_paths + p;
         rec.rec_a[ri] = make_float4(r.ar, r.ai, r.ph, r.hi);
