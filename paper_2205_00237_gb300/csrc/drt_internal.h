@@ -74,6 +74,7 @@ struct FreqGridD {
     float fcf;        // fc
     float f0c, dfc;   // (fc - B/2) / c and B / (n_bins c): first bin and bin step over c (1/m)
     float disp_lim;   // interaction-point displacement since the chunk base past which a step is redone in FP64 (m)
+    double f0, df;    // first bin fc - B/2 and bin step B / n_bins (Hz), so that no kernel divides per step
 };
 inline TimeGridD make_tgrid(double t_start, double dt, int32_t n_steps, int32_t chunk) {
     return TimeGridD{t_start, dt, n_steps, chunk, (float)dt};
@@ -81,7 +82,8 @@ inline TimeGridD make_tgrid(double t_start, double dt, int32_t n_steps, int32_t 
 inline FreqGridD make_fgrid(double fc, double bandwidth, int32_t n_bins) {
     const double c0 = 299792458.0;
     return FreqGridD{fc, bandwidth, n_bins, (float)fc, (float)((fc - 0.5 * bandwidth) / c0),
-                     (float)(bandwidth / n_bins / c0), (float)(0.8 * 60e9 / fc)};
+                     (float)(bandwidth / n_bins / c0), (float)(0.8 * 60e9 / fc), fc - 0.5 * bandwidth,
+                     n_bins > 0 ? bandwidth / n_bins : 0.0};
 }
 
 // user-visible outputs (caller order), any may be null

@@ -14,7 +14,7 @@ __device__ void redo_add_entry(const BatchLink &BL, int p, int ti) {
     path_step_redo_as<DUAL>(BL.L, BL.tg, BL.fg, p, ti, BL.out, nor, BL.warm, r);
     if (r[0] == 0.0 && r[1] == 0.0) return;
     // a exp(-j 2 pi f_k tau): FP64-reduced seed per 16-bin tile, FP32 rotation across the tile
-    const double f0 = BL.fg.fc - 0.5 * BL.fg.bandwidth, df = BL.fg.bandwidth / BL.fg.n_bins;
+    const double f0 = BL.fg.f0, df = BL.fg.df;
     const int F = BL.fg.n_bins;
     float2 *row = BL.H + (size_t)ti * F;
     double xs = df * r[2];

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(128)
 k_redo_add(const FreqGridD fg, const RedoList redo, const double *__restrict__ in3, float2 *__restrict__ H, int ld) {
     const int n = min(*redo.count, redo.cap);
     const int F = fg.n_bins, ntile = (F + 15) / 16;
-    const double f0 = fg.fc - 0.5 * fg.bandwidth, df = fg.bandwidth / F;
+    const double f0 = fg.f0, df = fg.df;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < (long long)n * ntile;
          q += (long long)gridDim.x * blockDim.x) {
         const int k = (int)(q / ntile), k0 = (int)(q % ntile) * 16;

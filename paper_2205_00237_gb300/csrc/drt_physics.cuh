@@ -541,6 +541,65 @@ DRT_HD float fp32_margin_tol(float scale) { return 2e-6f * (scale + 1.f); }
 // Vertex loops run over a fixed bound (MAXI) and stop at the chain length, so their array indices
 // are constants after unrolling and the arrays stay in registers; N >= 0 fixes the length at compile
 // time (shorter code), N < 0 takes the run-time n.
+// The tests at one vertex of type ty (c, nn: its point and normal or edge direction; b, cc, h1..h4 as
+// in Prim) between its neighbours Pm, Pp: its flag bits, and (FP32) its smallest margin over the FP32
+// error bound.  (Called out of line in the FP32 kernels it measured no faster, unlike the field
+// updates, so it stays inline.)
+template <class T> struct VertexCheck { uint32_t fl; T m; };
+template <class T>
+DRT_HD VertexCheck<T> vertex_validity_inl(int ty, v3<T> c, v3<T> nn, v3<T> b, v3<T> cc, T h1, T h2, T h3, T h4,
+                                          v3<T> Pm, v3<T> Pi, v3<T> Pp) {
+    constexpr bool F32 = sizeof(T) == 4;
+    uint32_t fl = 0;
+    T mmin = T(1e30);
+    if (ty == T_R) {
+        v3<T> r = Pi - c;
+        T al = dot(r, b), be = dot(r, cross(b, nn));
+        if (fabs(al) > h1 || fabs(be) > h2) fl |= F_FACE;
+        const T dp = dot(Pm - c, nn), dn = dot(Pp - c, nn);
+        if (!(dp > T(0)) || !(dn > T(0))) fl |= F_SIDE;
+        if constexpr (F32) {
+            const T tol = fp32_margin_tol(fmax(fmax(amax3(Pm), amax3(Pp)), fmax(amax3(Pi), amax3(c))));
+            mmin = fmin(fmin(fabs(fabs(al) - h1), fabs(fabs(be) - h2)), fmin(fabs(dp), fabs(dn))) / tol;
+        }
+    } else if (ty == T_D) {
+        const v3<T> A = c, e = nn;
+        T s = dot(Pi - A, e);
+        if (s < T(0) || s > h1) fl |= F_EDGE;
+        T tol = T(0);
+        if constexpr (F32) {
+            tol = fp32_margin_tol(fmax(fmax(amax3(Pm), amax3(Pp)), fmax(amax3(Pi), amax3(A))));
+            mmin = fmin(fabs(s), fabs(h1 - s)) / tol;
+        }
+#pragma unroll
+        for (int side = -1; side <= 1; side += 2) {
+            // the neighbour's direction about the edge, at angle phi from the 0-face tangent
+            // towards the 0-face normal, must lie in the exterior (0, n pi), 1 <= n <= 2: phi in
+            // (0, pi) when y > 0; otherwise phi in [pi, 2 pi) lies below n pi iff
+            // sin(n pi - phi) > 0 (or phi = pi < n pi = 2 pi) -- no arctangent needed
+            v3<T> r = (side < 0 ? Pm : Pp) - Pi;
+            v3<T> rp = r - e * dot(r, e);
+            const T y = dot(rp, cc), x = dot(rp, b);
+            bool in = y > T(0);
+            const T sn = h3 * x - h4 * y;   // r sin(n pi - phi): distance from the n-face plane
+            if (!in && !(y == T(0) && x >= T(0))) {
+                const T cs = h4 * x + h3 * y;   // r cos(n pi - phi)
+                in = sn > T(0) || (sn == T(0) && cs < T(0));
+            }
+            if (!in) fl |= F_SIDE;
+            if constexpr (F32) mmin = fmin(mmin, fmin(fabs(y), fabs(sn)) / tol);
+        }
+    } else {
+        const T dp = dot(Pm - Pi, nn), dn = dot(Pp - Pi, nn);
+        if (!(dp > T(0)) || !(dn > T(0))) fl |= F_SIDE;
+        if constexpr (F32) {
+            const T tol = fp32_margin_tol(fmax(fmax(amax3(Pm), amax3(Pp)), amax3(Pi)));
+            mmin = fmin(fabs(dp), fabs(dn)) / tol;
+        }
+    }
+    return VertexCheck<T>{fl, mmin};
+}
+
 template <int N = -1, class S>
 DRT_HD uint32_t validity(const Prim<S> *pr, int n, const v3<typename ST<S>::R> *P) {
     typedef typename ST<S>::R T;
@@ -558,53 +617,10 @@ DRT_HD uint32_t validity(const Prim<S> *pr, int n, const v3<typename ST<S>::R> *
     for (int i = 1; i <= MAXI; ++i) {
         if (i > nv) break;
         const Prim<S> &q = pr[i - 1];
-        if (q.type == T_R) {
-            v3<T> c = val(q.p), nn = val(q.a);
-            v3<T> r = P[i] - c;
-            T al = dot(r, q.b), be = dot(r, cross(q.b, nn));
-            if (fabs(al) > q.h1 || fabs(be) > q.h2) fl |= F_FACE;
-            const T dp = dot(P[i - 1] - c, nn), dn = dot(P[i + 1] - c, nn);
-            if (!(dp > T(0)) || !(dn > T(0))) fl |= F_SIDE;
-            if constexpr (F32) {
-                const T tol = fp32_margin_tol(fmax(fmax(amax3(P[i - 1]), amax3(P[i + 1])), fmax(amax3(P[i]), amax3(c))));
-                mmin = fmin(mmin, fmin(fmin(fabs(fabs(al) - q.h1), fabs(fabs(be) - q.h2)), fmin(fabs(dp), fabs(dn))) / tol);
-            }
-        } else if (q.type == T_D) {
-            v3<T> A = val(q.p), e = val(q.a);
-            T s = dot(P[i] - A, e);
-            if (s < T(0) || s > q.h1) fl |= F_EDGE;
-            T tol = T(0);
-            if constexpr (F32) {
-                tol = fp32_margin_tol(fmax(fmax(amax3(P[i - 1]), amax3(P[i + 1])), fmax(amax3(P[i]), amax3(A))));
-                mmin = fmin(mmin, fmin(fabs(s), fabs(q.h1 - s)) / tol);
-            }
-#pragma unroll (N >= 0 ? 8 : 1)
-            for (int side = -1; side <= 1; side += 2) {
-                // the neighbour's direction about the edge, at angle phi from the 0-face tangent
-                // towards the 0-face normal, must lie in the exterior (0, n pi), 1 <= n <= 2: phi in
-                // (0, pi) when y > 0; otherwise phi in [pi, 2 pi) lies below n pi iff
-                // sin(n pi - phi) > 0 (or phi = pi < n pi = 2 pi) -- no arctangent needed
-                v3<T> r = P[i + side] - P[i];
-                v3<T> rp = r - e * dot(r, e);
-                const T y = dot(rp, q.c), x = dot(rp, q.b);
-                bool in = y > T(0);
-                const T sn = q.h3 * x - q.h4 * y;   // r sin(n pi - phi): distance from the n-face plane
-                if (!in && !(y == T(0) && x >= T(0))) {
-                    const T cs = q.h4 * x + q.h3 * y;   // r cos(n pi - phi)
-                    in = sn > T(0) || (sn == T(0) && cs < T(0));
-                }
-                if (!in) fl |= F_SIDE;
-                if constexpr (F32) mmin = fmin(mmin, fmin(fabs(y), fabs(sn)) / tol);
-            }
-        } else {
-            v3<T> nn = val(q.a);
-            const T dp = dot(P[i - 1] - P[i], nn), dn = dot(P[i + 1] - P[i], nn);
-            if (!(dp > T(0)) || !(dn > T(0))) fl |= F_SIDE;
-            if constexpr (F32) {
-                const T tol = fp32_margin_tol(fmax(fmax(amax3(P[i - 1]), amax3(P[i + 1])), amax3(P[i])));
-                mmin = fmin(mmin, fmin(fabs(dp), fabs(dn)) / tol);
-            }
-        }
+        const VertexCheck<T> v =
+            vertex_validity_inl(q.type, val(q.p), val(q.a), q.b, q.c, q.h1, q.h2, q.h3, q.h4, P[i - 1], P[i], P[i + 1]);
+        fl |= v.fl;
+        mmin = fmin(mmin, v.m);
     }
     if constexpr (F32) {
         if (mmin < T(1)) fl |= F_REDO64;
@@ -1019,8 +1035,10 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
             d = T(0);
         }
     }
-    const T k = T(2 * PI) * fc / T(C0);
-    const T ieps = T(1) / (T(2 * PI) * fc * T(EPS0));   // eps_c = eps_r - j sigma ieps
+    // one division per call: the wavenumber, eps_c = eps_r - j sigma ieps and lambda / (4 pi) from 1/fc
+    const T ifc = T(1) / fc;
+    const T k = fc * T(2 * PI / C0);
+    const T ieps = ifc * T(1 / (2 * PI * EPS0));
     c3<T> E = cscale(vertical_pol(kd[1]), C<T>(T(1), T(0)));
     v3<T> klast = kd[1];
 #pragma unroll (N >= 0 ? 8 : 1)
@@ -1045,8 +1063,7 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
             else E = tile_field_inl(E, kin, kout, val(q.a), tl);
         }
     }
-    T lam = T(C0) / fc;
-    return cdot(E, vertical_pol(klast)) * (lam / T(4 * PI) * spread);
+    return cdot(E, vertical_pol(klast)) * (ifc * T(C0 / (4 * PI)) * spread);
 }
 
 // App. A Eq. doppler_freq: f' = f0 prod_i (c - v_i.k_i) / (c - v_{i-1}.k_i), evaluated without
@@ -1202,7 +1219,7 @@ DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const Fre
         }
     }
     fl |= validity<N>(pr, n, P);
-    T tau = d / T(C0);
+    T tau = d * T(1 / C0);
     cx<T> a = (fl & F_DEGEN) ? C<T>(T(0), T(0)) : amplitude<N>(L, pr, n, seg, T(fg.fc));
     if constexpr (OUT) {
         if (out.tau || out.amp || out.doppler || out.angles || out.flags || out.points) {
@@ -1230,7 +1247,7 @@ DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const Fre
         }
     }
     if (rec.rec_a) {
-        double f0 = fg.fc - 0.5 * fg.bandwidth, df = fg.bandwidth / fg.n_bins;
+        const double f0 = fg.f0, df = fg.df;
         write_record(rec, (size_t)ti * L.n_paths + p, tau, a, fl, f0, df);
     }
     if (rec64) {   // (Re a, Im a, tau), a = 0 when the path does not exist
@@ -1589,8 +1606,8 @@ DRT_HD void path_base_fp64(const LinkDev &L, const TimeGridD &tg, const FreqGrid
             r.seg[i - 1][1] = (float)sg.y;
             r.seg[i - 1][2] = (float)sg.z;
         }
-        double f0 = fg.fc - 0.5 * fg.bandwidth, df = fg.bandwidth / fg.n_bins;
-        double x = f0 * d / C0, y = df * d / C0;
+        const double dc = d * (1 / C0);   // path length over c (s)
+        const double x = fg.f0 * dc, y = fg.df * dc;
         double st = y - floor(y);
         double hi = ldexp(rint(ldexp(st, 12)), -12);   // 12 leading bits: k * hi exact in FP32
         r.d = d;
