@@ -659,9 +659,12 @@ DRT_HD void fresnel(const MatV<T> &m, T ieps, T ct, cx<T> &rte, cx<T> &rtm) {
     }
     cx<T> ec = C<T>(m.eps_r, -m.sigma * ieps);
     cx<T> sq = csqrt_(C<T>(ec.re - T(1) + ct * ct, ec.im));
-    rte = cdiv(C<T>(ct - sq.re, -sq.im), C<T>(ct + sq.re, sq.im));
     cx<T> ecct = ec * ct;
-    rtm = cdiv(ecct - sq, ecct + sq);
+    // the two quotients a / b = a conj(b) / |b|^2 share one reciprocal: 1 / (|b1|^2 |b2|^2)
+    const cx<T> a1 = C<T>(ct - sq.re, -sq.im), b1 = C<T>(ct + sq.re, sq.im), a2 = ecct - sq, b2 = ecct + sq;
+    const T n1 = cabs2(b1), n2 = cabs2(b2), r = T(1) / (n1 * n2), i1 = n2 * r, i2 = n1 * r;
+    rte = C<T>(fma(a1.re, b1.re, a1.im * b1.im) * i1, fma(a1.im, b1.re, -a1.re * b1.im) * i1);
+    rtm = C<T>(fma(a2.re, b2.re, a2.im * b2.im) * i2, fma(a2.im, b2.re, -a2.re * b2.im) * i2);
 }
 
 // UTD transition function F(X) = 2j sqrt(X) exp(jX) int_sqrt(X)^inf exp(-j u^2) du for X >= 0,
@@ -800,22 +803,70 @@ template <class T> DRT_HD cx<T> utd_term(T eps, T n, T inv2n, T kL) {
     return transition_F(T(2) * kL * sh * sh) * (c2 / s2);
 }
 
+// the same term for a right-angled wedge (n = 3/2) from su, cu = sin, cos of eps / 6 (eps/2 = 3 eps/6,
+// eps/2n = 2 eps/6)
+template <class T> DRT_HD cx<T> utd_term_ra(T eps, T su, T cu, T kL) {
+    if (fabs(eps) < T(1e-9)) {
+        T m = T(1.5) * sqrt(T(2 * PI) * kL) * (eps >= T(0) ? T(1) : T(-1)) * T(0.70710678118654752440);
+        return C<T>(m, m);
+    }
+    const T sh = su * (T(3) - T(4) * su * su), s2 = T(2) * su * cu, c2 = T(1) - T(2) * su * su;
+    return transition_F(T(2) * kL * sh * sh) * (c2 / s2);
+}
+// sin, cos of x / 6 + pi / 6 - m pi / 2 from sin, cos of x / 6 (sx, cx): a turn by pi / 6, then m
+// quarter turns (exact)
+template <class T> DRT_HD void ra_shift(T sx, T cx, int m, T &s, T &c) {
+    const T c6 = T(0.86602540378443864676), s6 = T(0.5);
+    T a = sx * c6 + cx * s6, b = cx * c6 - sx * s6;   // sin, cos of x/6 + pi/6
+    switch (m & 3) {   // minus m quarter turns
+    case 0: s = a; c = b; break;
+    case 1: s = -b; c = a; break;
+    case 2: s = -a; c = -b; break;
+    default: s = b; c = -a; break;
+    }
+}
+
 // soft / hard wedge diffraction coefficients: Kouyoumjian-Pathak with the spherical-wave distance
 // parameter L, Luebbers' face-coefficient weights for lossy wedges
 // (sphip = |sin phi'|, snphi = |sin(n pi - phi)|: the incidence sines of the 0-face and n-face
 // reflection coefficients, passed in from the direction components)
 template <class T>
-DRT_HD void utd(T n, T phi, T phip, T sphip, T snphi, T sinb0, T L, T k, const MatV<T> &m, T ieps, cx<T> &Ds,
-                cx<T> &Dh) {
+DRT_HD void utd(T n, T phi, T phip, T sphip, T snphi, T sinb0, T L, T k, T isk, const MatV<T> &m, T ieps,
+                cx<T> &Ds, cx<T> &Dh) {
+    // isk = 1 / sqrt(2 pi k), once per call; 1/(2n) without a division for right-angled wedges
     T kL = k * L;
-    T pref = T(1) / (T(2) * n * sqrt(T(2 * PI) * k) * sinb0);
+    const T inv2n = n == T(1.5) ? T(1.0 / 3.0) : T(1) / (T(2) * n), itpn = inv2n * T(1 / PI);   // 1/(2n), 1/(2 pi n)
+    T pref = inv2n * isk / sinb0;
     cx<T> Cc = C<T>(-pref * T(0.70710678118654752440), pref * T(0.70710678118654752440));  // -exp(-j pi/4) pref
     T bm = phi - phip, bp = phi + phip, tpn = T(2 * PI) * n;
-    const T inv2n = T(1) / (T(2) * n), itpn = inv2n * T(1 / PI);   // 1/(2n), 1/(2 pi n)
-    cx<T> t1 = utd_term(T(PI) + bm - tpn * round((bm + T(PI)) * itpn), n, inv2n, kL);
-    cx<T> t2 = utd_term(T(PI) - bm + tpn * round((bm - T(PI)) * itpn), n, inv2n, kL);
-    cx<T> t3 = utd_term(T(PI) - bp + tpn * round((bp - T(PI)) * itpn), n, inv2n, kL);   // 0-face
-    cx<T> t4 = utd_term(T(PI) + bp - tpn * round((bp + T(PI)) * itpn), n, inv2n, kL);   // n-face
+    const T N1 = round((bm + T(PI)) * itpn), N2 = round((bm - T(PI)) * itpn);
+    const T N3 = round((bp - T(PI)) * itpn), N4 = round((bp + T(PI)) * itpn);
+    const T e1 = T(PI) + bm - tpn * N1, e2 = T(PI) - bm + tpn * N2;
+    const T e3 = T(PI) - bp + tpn * N3, e4 = T(PI) + bp - tpn * N4;
+    cx<T> t1, t2, t3, t4;
+    if (n == T(1.5)) {
+        // right-angled wedge: the four sin, cos of eps_i / 6 from those of phi / 6 and phi' / 6 (two
+        // sincos instead of four): eps_i / 6 = pi/6 +- (phi -+ phi') / 6 -+ N_i pi / 2
+        T sa, ca, sb, cb;
+        sincos(phi * T(1.0 / 6.0), &sa, &ca);
+        sincos(phip * T(1.0 / 6.0), &sb, &cb);
+        const T sm = sa * cb - ca * sb, cm = ca * cb + sa * sb;   // (phi - phi') / 6
+        const T sp = sa * cb + ca * sb, cp = ca * cb - sa * sb;   // (phi + phi') / 6
+        T s, c;
+        ra_shift(sm, cm, (int)N1, s, c);
+        t1 = utd_term_ra(e1, s, c, kL);
+        ra_shift(-sm, cm, -(int)N2, s, c);
+        t2 = utd_term_ra(e2, s, c, kL);
+        ra_shift(-sp, cp, -(int)N3, s, c);
+        t3 = utd_term_ra(e3, s, c, kL);   // 0-face
+        ra_shift(sp, cp, (int)N4, s, c);
+        t4 = utd_term_ra(e4, s, c, kL);   // n-face
+    } else {
+        t1 = utd_term(e1, n, inv2n, kL);
+        t2 = utd_term(e2, n, inv2n, kL);
+        t3 = utd_term(e3, n, inv2n, kL);   // 0-face
+        t4 = utd_term(e4, n, inv2n, kL);   // n-face
+    }
     cx<T> r0s, r0h, rns, rnh;
     fresnel(m, ieps, sphip, r0s, r0h);
     fresnel(m, ieps, snphi, rns, rnh);
@@ -899,7 +950,7 @@ DRT_HD c3<T> refl_field_inl(c3<T> E, v3<T> kin, v3<T> kout, v3<T> nf, MatV<T> m,
 // Lf: the distance parameter over sin^2 b0
 template <class T>
 DRT_HD c3<T> diff_field_inl(c3<T> E, v3<T> kin, v3<T> kout, v3<T> e, v3<T> t0, v3<T> n0, T wn, T snp, T cnp, T Lf,
-                            T k, MatV<T> m, T ieps) {
+                            T k, T isk, MatV<T> m, T ieps) {
     v3<T> wi = -kin + e * dot(kin, e);
     v3<T> wo = kout - e * dot(kout, e);
     const T yi = dot(wi, n0), xi = dot(wi, t0), yo = dot(wo, n0), xo = dot(wo, t0);
@@ -911,12 +962,12 @@ DRT_HD c3<T> diff_field_inl(c3<T> E, v3<T> kin, v3<T> kout, v3<T> e, v3<T> t0, v
     const T Lp = Lf * sinb0 * sinb0;
     T sphip = T(0), snphi = T(0);
     if (!m.pec) {   // Luebbers' face coefficients: sin phi' and sin(n pi - phi) from components
-        const T ri = sqrt(xi * xi + yi * yi), ro = sqrt(xo * xo + yo * yo);
-        sphip = ri > T(0) ? fabs(yi) / ri : T(0);
-        snphi = ro > T(0) ? fabs(snp * xo - cnp * yo) / ro : T(0);
+        const T ri2 = xi * xi + yi * yi, ro2 = xo * xo + yo * yo;
+        sphip = ri2 > T(0) ? fabs(yi) * rsqrt(ri2) : T(0);
+        snphi = ro2 > T(0) ? fabs(snp * xo - cnp * yo) * rsqrt(ro2) : T(0);
     }
     cx<T> Ds, Dh;
-    utd(wn, phi, phip, sphip, snphi, sinb0, Lp, k, m, ieps, Ds, Dh);
+    utd(wn, phi, phip, sphip, snphi, sinb0, Lp, k, isk, m, ieps, Ds, Dh);
     v3<T> php = -unit(cross(e, kin)), bpv = cross(php, kin);
     v3<T> ph = unit(cross(e, kout)), bv = cross(ph, kout);
     return cscale(bv, -(Ds * cdot(E, bpv))) + cscale(ph, -(Dh * cdot(E, php)));
@@ -934,14 +985,15 @@ DRT_HD c3<T> tile_field_inl(c3<T> E, v3<T> kin, v3<T> kout, v3<T> nt, TileV<T> t
     T lobe_h = T(1);   // ((1 + cos psi)/2)^(alpha/2): the field of the power lobe
     for (int j = 0; j < alpha / 2; ++j) lobe_h *= hb;
     if (alpha & 1) lobe_h *= sqrt(hb);
-    T amp = tl.s * sqrt(tl.area * cti / Fa) * lobe_h;
+    const T qa = tl.area * cti;   // sqrt(qa / Fa) by one reciprocal square root
+    T amp = tl.s * (qa > T(0) ? qa * rsqrt(qa * Fa) : sqrt(qa / Fa)) * lobe_h;
     cx<T> ph = C<T>(tl.cph, tl.sph);
-    T nE = cnorm(E);
+    const T e2 = cabs2(E.x) + cabs2(E.y) + cabs2(E.z), nE = sqrt(e2);
     cx<T> ek = cdot(E, kout);
     c3<T> Ep = E + cscale(kout, -ek);
-    T nEp = cnorm(Ep);
-    if (nEp < T(1e-12) * nE || nE == T(0)) Ep = cscale(vertical_pol(kout), C<T>(nE, T(0)));
-    else Ep = cscale(Ep, C<T>(nE / nEp, T(0)));
+    const T ep2 = cabs2(Ep.x) + cabs2(Ep.y) + cabs2(Ep.z);
+    if (ep2 < T(1e-24) * e2 || e2 == T(0)) Ep = cscale(vertical_pol(kout), C<T>(nE, T(0)));
+    else Ep = cscale(Ep, C<T>(nE * rsqrt(ep2), T(0)));
     return cscale(Ep, ph * amp);
 }
 
@@ -951,8 +1003,8 @@ template <class T> DRT_NOINL c3<T> refl_field_out(c3<T> E, v3<T> kin, v3<T> kout
 }
 template <class T>
 DRT_NOINL c3<T> diff_field_out(c3<T> E, v3<T> kin, v3<T> kout, v3<T> e, v3<T> t0, v3<T> n0, T wn, T snp, T cnp, T Lf,
-                               T k, MatV<T> m, T ieps) {
-    return diff_field_inl(E, kin, kout, e, t0, n0, wn, snp, cnp, Lf, k, m, ieps);
+                               T k, T isk, MatV<T> m, T ieps) {
+    return diff_field_inl(E, kin, kout, e, t0, n0, wn, snp, cnp, Lf, k, isk, m, ieps);
 }
 template <class T> DRT_NOINL c3<T> tile_field_out(c3<T> E, v3<T> kin, v3<T> kout, v3<T> nt, TileV<T> tl) {
     return tile_field_inl(E, kin, kout, nt, tl);
@@ -988,7 +1040,8 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
         }
     }
     // spreading and, per diffraction, L / sin^2 b0
-    T spread = T(1), Lfac[MAXI + 1];
+    // spread^2 = sp_num / sp_den, one square root per call
+    T sp_num = T(1), sp_den = T(1), Lfac[MAXI + 1];
     {
         T d = T(0), re = T(0);          // distance since the point source or latest diffraction; its rho_e
         bool after_d = false;
@@ -1002,8 +1055,11 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
                 if (after_d) X1 = mirror_dir(X1, val(pr[i - 1].a));
                 continue;
             }
-            if (!after_d) spread /= d;
-            else spread *= sqrt(re / (d * (re + d)));
+            if (!after_d) sp_den *= d * d;
+            else {
+                sp_num *= re;
+                sp_den *= d * (re + d);
+            }
             if (ty == T_S) {
                 after_d = false;
                 d = T(0);
@@ -1037,7 +1093,7 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
     }
     // one division per call: the wavenumber, eps_c = eps_r - j sigma ieps and lambda / (4 pi) from 1/fc
     const T ifc = T(1) / fc;
-    const T k = fc * T(2 * PI / C0);
+    const T k = fc * T(2 * PI / C0), isk = rsqrt(T(2 * PI) * k);
     const T ieps = ifc * T(1 / (2 * PI * EPS0));
     c3<T> E = cscale(vertical_pol(kd[1]), C<T>(T(1), T(0)));
     v3<T> klast = kd[1];
@@ -1055,14 +1111,15 @@ DRT_HD cx<T> amplitude(const LinkDev &L, const Prim<S> *pr, int n, const v3<T> *
         } else if (q.type == T_D) {
             const MatV<T> m = matv<T>(L.mats[q.mat]);
             if constexpr (OUTL)
-                E = diff_field_out(E, kin, kout, val(q.a), q.b, q.c, q.h2, q.h3, q.h4, Lfac[i], k, m, ieps);
-            else E = diff_field_inl(E, kin, kout, val(q.a), q.b, q.c, q.h2, q.h3, q.h4, Lfac[i], k, m, ieps);
+                E = diff_field_out(E, kin, kout, val(q.a), q.b, q.c, q.h2, q.h3, q.h4, Lfac[i], k, isk, m, ieps);
+            else E = diff_field_inl(E, kin, kout, val(q.a), q.b, q.c, q.h2, q.h3, q.h4, Lfac[i], k, isk, m, ieps);
         } else {
             const TileV<T> tl = tilev<T>(L, q.idx);
             if constexpr (OUTL) E = tile_field_out(E, kin, kout, val(q.a), tl);
             else E = tile_field_inl(E, kin, kout, val(q.a), tl);
         }
     }
+    const T spread = sqrt(sp_num / sp_den);
     return cdot(E, vertical_pol(klast)) * (ifc * T(C0 / (4 * PI)) * spread);
 }
 
