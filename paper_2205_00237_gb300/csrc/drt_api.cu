@@ -99,6 +99,7 @@ struct drt_ctx {
     // multi-diffraction paths run beside the FP32 kernel), joined back with events
     cudaStream_t side[2] = {nullptr, nullptr};
     cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+    cudaEvent_t ev_aux[3] = {nullptr, nullptr, nullptr};   // further dependencies between them
     // tracing: (kind, start, stop) per bracketed launch
     bool profiling = false;
     struct Mark { int kind; cudaEvent_t a, b; };
@@ -281,21 +282,6 @@ template <class F> drt_status traced(drt_ctx *c, int kind, cudaStream_t s, F &&l
     return DRT_OK;
 }
 
-// the chains that run the generic code (several diffractions in a segment, 4 vertices) get a launch of
-// their own on side[1], beside the launches of the other chains on s: fork after the work queued on s
-// so far, join before anything after it
-template <class F> cudaError_t split_multi(drt_ctx *c, const LinkDev &L, cudaStream_t s, F &&launch) {
-    const bool split = L.len_start[MAXI] > 0 && L.len_start[MAXI] < L.n_paths;
-    if (!split) return launch(s);
-    cudaStream_t sm = c->side[1];
-    cudaError_t e = cudaEventRecord(c->ev_fork, s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(sm, c->ev_fork, 0);
-    if (e == cudaSuccess) e = launch(sm);
-    if (e == cudaSuccess) e = cudaEventRecord(c->ev_join[1], sm);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join[1], 0);
-    return e;
-}
-
 // pose table + extrapolation (+ records) for one link
 drt_status run_extrapolation(drt_ctx *c, Link &L, const drt_time_grid *tg, const drt_freq_grid *fg,
                              const OutD &out, const RecD &rec, int32_t precision, cudaStream_t s,
@@ -312,33 +298,42 @@ drt_status run_extrapolation(drt_ctx *c, Link &L, const drt_time_grid *tg, const
         void *pb = c->poseb.ptr, *bs = c->base.ptr, *rd = c->redo.ptr;
         double *p64 = reinterpret_cast<double *>(c->pose64.ptr);
         double *warm = reinterpret_cast<double *>(c->warm.ptr);
-        // fork: the multi-diffraction warm starts (a few latency-bound solves) on side[1] beside the
-        // FP64 anchors of the other paths on side[0], the FP32 base poses on the caller's stream;
-        // the multi-diffraction anchors follow their warm starts
+        // Three streams.  side[0]: FP64 chunk-base poses, then the anchors of the chains with at most one
+        // diffraction per segment.  side[1]: the multi-diffraction warm starts (a few latency-bound
+        // solves), their anchors (after the chunk-base poses), then the kernels of the generic range.
+        // s: the FP32 base poses, then, once their anchors are in, the kernels of chain lengths 0..3,
+        // which so do not wait for the warm starts; s joins side[1] at the end.
         cudaStream_t sa = c->side[0], sw = c->side[1];
         const int nb = L.dev.n_bulk;
+        cudaEvent_t ev_p64 = c->ev_aux[0], ev_base0 = c->ev_aux[1], ev_pb = c->ev_aux[2];
+        CUDA_TRY(cudaMemsetAsync(rd, 0, sizeof(int), s));   // the redo counter, before any kernel that queues
         CUDA_TRY(cudaEventRecord(c->ev_fork, s));
         CUDA_TRY(cudaStreamWaitEvent(sa, c->ev_fork, 0));
         CUDA_TRY(cudaStreamWaitEvent(sw, c->ev_fork, 0));
         if (drt_status st = traced(c, 3, sw, [&] { return launch_warm_fp64(L.dev, t, warm, sw); })) return st;
-        CUDA_TRY(cudaEventRecord(c->ev_join[1], sw));
-        if (drt_status st = traced(c, 3, sa, [&] {
-                cudaError_t e = launch_base_pose64(L.dev, t, p64, sa);
-                return e != cudaSuccess ? e : launch_base_paths(L.dev, t, f, p64, bs, warm, 0, nb, sa);
+        if (drt_status st = traced(c, 3, sa, [&] { return launch_base_pose64(L.dev, t, p64, sa); })) return st;
+        CUDA_TRY(cudaEventRecord(ev_p64, sa));
+        if (drt_status st = traced(c, 3, sa, [&] { return launch_base_paths(L.dev, t, f, p64, bs, warm, 0, nb, sa); }))
+            return st;
+        CUDA_TRY(cudaEventRecord(ev_base0, sa));
+        CUDA_TRY(cudaStreamWaitEvent(sw, ev_p64, 0));
+        if (drt_status st = traced(c, 3, sw, [&] {
+                return launch_base_paths(L.dev, t, f, p64, bs, warm, nb, L.dev.n_paths, sw);
             }))
             return st;
-        CUDA_TRY(cudaStreamWaitEvent(sa, c->ev_join[1], 0));
-        if (drt_status st = traced(c, 3, sa, [&] {
-                return launch_base_paths(L.dev, t, f, p64, bs, warm, nb, L.dev.n_paths, sa);
-            }))
-            return st;
-        CUDA_TRY(cudaEventRecord(c->ev_join[0], sa));
         if (drt_status st = traced(c, 0, s, [&] { return launch_pose_bulk(L.dev, t, pb, s); })) return st;
-        CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[0], 0));
+        CUDA_TRY(cudaEventRecord(ev_pb, s));
+        CUDA_TRY(cudaStreamWaitEvent(s, ev_base0, 0));
+        CUDA_TRY(cudaStreamWaitEvent(sw, ev_pb, 0));
+        CUDA_TRY(cudaStreamWaitEvent(sw, ev_base0, 0));   // the 4-vertex chains of the generic range
         if (drt_status st = traced(c, 1, s, [&] {
-                return split_multi(c, L.dev, s, [&](cudaStream_t sm) {
-                    return launch_extrapolate_bulk(L.dev, t, f, pb, bs, warm, out, rec, rd, s, sm);
-                });
+                cudaError_t e = launch_extrapolate_bulk(L.dev, t, f, pb, bs, warm, out, rec, rd, s, nullptr, true,
+                                                        false, false);
+                if (e == cudaSuccess)
+                    e = launch_extrapolate_bulk(L.dev, t, f, pb, bs, warm, out, rec, rd, s, sw, false, true, false);
+                if (e == cudaSuccess) e = cudaEventRecord(c->ev_join[1], sw);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join[1], 0);
+                return e;
             }))
             return st;
         if (!defer_redo)   // else the caller runs the redo beside the synthesis (synth_into)
@@ -644,6 +639,11 @@ drt_status drt_create(drt_ctx **out, int32_t device, uint64_t hbm_budget_bytes) 
             return fail(DRT_ECUDA, "stream/event creation failed");
         }
     }
+    for (int i = 0; i < 3; ++i)
+        if (cudaEventCreateWithFlags(&c->ev_aux[i], cudaEventDisableTiming) != cudaSuccess) {
+            drt_destroy(c);
+            return fail(DRT_ECUDA, "event creation failed");
+        }
     if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
         drt_destroy(c);
         return fail(DRT_ECUDA, "event creation failed");
@@ -669,6 +669,8 @@ void drt_destroy(drt_ctx *c) {
         if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
     }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    for (int i = 0; i < 3; ++i)
+        if (c->ev_aux[i]) cudaEventDestroy(c->ev_aux[i]);
     for (auto &m : c->marks) {
         cudaEventDestroy(m.a);
         cudaEventDestroy(m.b);

@@ -196,10 +196,13 @@ size_t bulk_redo_bytes(const LinkDev &L, const TimeGridD &tg);
 cudaError_t launch_base_pose64(const LinkDev &L, const TimeGridD &tg, double *pose64, cudaStream_t s);
 cudaError_t launch_base_paths(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const double *pose64,
                               void *base, const double *warm, int p0, int p1, cudaStream_t s);
-// the redo scratch holds an int counter (zeroed here, on the stream) followed by the (path, step) list
+// the redo scratch holds an int counter (zeroed here, on s, when zero is set) followed by the
+// (path, step) list; lengths / generic select the launches of chain lengths 0..3 (on s) and of the
+// generic range (on s_multi, else s)
 cudaError_t launch_extrapolate_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const void *poseb,
                                     const void *base, const double *warm, const OutD &out, const RecD &rec,
-                                    void *redo, cudaStream_t s, cudaStream_t s_multi = nullptr);
+                                    void *redo, cudaStream_t s, cudaStream_t s_multi = nullptr, bool lengths = true,
+                                    bool generic = true, bool zero = true);
 cudaError_t launch_redo(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const OutD &out, const RecD &rec,
                         void *redo, const double *warm, cudaStream_t s);
 // the redo for an H synthesis: (Re a, Im a, tau) per queued step into out3 ([cap][3] doubles), then

@@ -66,15 +66,16 @@ k_extrapolate_bulk_out(const LinkDev L, const TimeGridD tg, const FreqGridD fg, 
 
 cudaError_t launch_extrapolate_bulk(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg, const void *poseb,
                                     const void *base, const double *warm, const OutD &out, const RecD &rec, void *redo,
-                                    cudaStream_t s, cudaStream_t s_multi) {
-    cudaError_t e = cudaMemsetAsync(redo, 0, sizeof(int), s);
+                                    cudaStream_t s, cudaStream_t s_multi, bool lengths, bool generic, bool zero) {
+    cudaError_t e = zero ? cudaMemsetAsync(redo, 0, sizeof(int), s) : cudaSuccess;
     if (e != cudaSuccess) return e;
     if (L.n_paths == 0 || tg.n_steps == 0) return cudaSuccess;
     const int tx = (tg.n_steps + EXT_T - 1) / EXT_T;
     const PoseB *pb = reinterpret_cast<const PoseB *>(poseb);
     const BaseRec *bs = reinterpret_cast<const BaseRec *>(base);
     const RedoList rl = redo_list(redo, L, tg);
-    if (!any_output(out)) {
+    if (!lengths) {
+    } else if (!any_output(out)) {
         for (int n = 0; n < MAXI; ++n) {
             const int a = L.len_start[n], b = L.len_start[n + 1];
             if (b <= a) continue;
@@ -93,8 +94,7 @@ cudaError_t launch_extrapolate_bulk(const LinkDev &L, const TimeGridD &tg, const
         else k_extrapolate_bulk_out<false><<<grid, EXT_T, 0, s>>>(L, tg, fg, pb, bs, warm, out, rec, rl, 0, L.len_start[MAXI]);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (L.n_paths > L.len_start[MAXI]) {
-        const dim3 grid(tx, L.n_paths - L.len_start[MAXI]);
+    if (generic && L.n_paths > L.len_start[MAXI]) {
         cudaStream_t sm = s_multi ? s_multi : s;
         return launch_extrapolate_bulk_generic(L, tg, fg, pb, bs, warm, out, rec, rl, sm);
     }
