@@ -108,6 +108,10 @@ struct drt_ctx {
     Server *server = nullptr;
     void *arena = nullptr;
     size_t arena_bytes = 0;
+    // device blocks of unloaded links, kept for the next loads (size -> block): loading and unloading
+    // links in a loop then costs no cudaMalloc / cudaFree; the blocks count against the HBM budget
+    std::multimap<size_t, void *> link_pool;
+    size_t link_pool_bytes = 0;
 };
 
 namespace {
@@ -124,6 +128,42 @@ drt_status dev_alloc(drt_ctx *c, size_t bytes, void **out) {
 
 void dev_free(drt_ctx *c, void *p, size_t bytes) {
     if (p) {
+        cudaFree(p);
+        c->used -= bytes;
+    }
+}
+
+// Link storage: a pooled block of at least `bytes` (at most twice that, so small links do not hold
+// large blocks), else a new allocation, after returning pooled blocks to the device when the budget
+// needs the room.  *got receives the block's size.
+constexpr size_t LINK_POOL_CAP = (size_t)1 << 30;   // pooled bytes kept at most
+drt_status link_block_alloc(drt_ctx *c, size_t bytes, void **out, size_t *got) {
+    bytes = std::max<size_t>(bytes, 256);
+    auto it = c->link_pool.lower_bound(bytes);
+    if (it != c->link_pool.end() && it->first <= 2 * bytes) {
+        *out = it->second;
+        *got = it->first;
+        c->link_pool_bytes -= it->first;
+        c->link_pool.erase(it);
+        return DRT_OK;
+    }
+    while (c->budget && c->used + bytes > c->budget && !c->link_pool.empty()) {
+        auto last = std::prev(c->link_pool.end());
+        cudaFree(last->second);
+        c->used -= last->first;
+        c->link_pool_bytes -= last->first;
+        c->link_pool.erase(last);
+    }
+    *got = bytes;
+    return dev_alloc(c, bytes, out);
+}
+// the caller has made sure that no queued work still reads the block
+void link_block_free(drt_ctx *c, void *p, size_t bytes) {
+    if (!p) return;
+    if (c->link_pool_bytes + bytes <= LINK_POOL_CAP) {
+        c->link_pool.emplace(bytes, p);
+        c->link_pool_bytes += bytes;
+    } else {
         cudaFree(p);
         c->used -= bytes;
     }
@@ -156,9 +196,10 @@ struct LinkImage {
     }
     drt_status upload(drt_ctx *c, Link &L) {
         void *p = nullptr;
-        if (drt_status st = dev_alloc(c, host.size(), &p)) return st;
+        size_t got = 0;
+        if (drt_status st = link_block_alloc(c, host.size(), &p, &got)) return st;
         L.allocs.push_back(p);
-        L.bytes += host.size();
+        L.bytes += got;
         if (!host.empty()) CUDA_TRY(cudaMemcpy(p, host.data(), host.size(), cudaMemcpyHostToDevice));
         for (auto &b : bind) b(reinterpret_cast<char *>(p));
         return DRT_OK;
@@ -659,6 +700,7 @@ void drt_destroy(drt_ctx *c) {
     cudaDeviceSynchronize();
     for (auto &kv : c->links)
         for (void *p : kv.second.allocs) cudaFree(p);
+    for (auto &kv : c->link_pool) cudaFree(kv.second);
     for (Scratch *s : {&c->pose, &c->rec_a, &c->rec_b, &c->h, &c->poseb, &c->base, &c->pose64, &c->redo, &c->warm, &c->redo3, &c->pp_tau,
                        &c->pp_amp, &c->pp_fd, &c->pp_fl, &c->lt_tot, &c->lt_major, &c->win_sel, &c->win_starts,
                        &c->tr_faces, &c->tr_rays, &c->tr_count})
@@ -683,6 +725,8 @@ void drt_destroy(drt_ctx *c) {
 namespace {
 
 // validate, pack and upload one link (the caller holds the context lock and set the device)
+void free_link(drt_ctx *c, Link &L);
+
 drt_status load_link(drt_ctx *c, const drt_scene *s, const drt_path_set *ps, Link &L) {
     PackedLink H;
     if (drt_status st = pack_link(s, ps, H)) return st;
@@ -723,18 +767,15 @@ drt_status load_link(drt_ctx *c, const drt_scene *s, const drt_path_set *ps, Lin
         if (e != cudaSuccess) st = fail(DRT_ECUDA, "t0 edge parameters: %s", cudaGetErrorString(e));
     }
     if (st) {
-        for (void *p : L.allocs) cudaFree(p);
-        c->used -= L.bytes;
-        L.allocs.clear();
-        L.bytes = 0;
+        free_link(c, L);
         return st;
     }
     return DRT_OK;
 }
 
+// a link holds one block (see LinkImage); the caller has made sure no queued work reads it
 void free_link(drt_ctx *c, Link &L) {
-    for (void *p : L.allocs) cudaFree(p);
-    c->used -= L.bytes;
+    for (void *p : L.allocs) link_block_free(c, p, L.bytes);
     L.allocs.clear();
     L.bytes = 0;
 }
@@ -765,8 +806,7 @@ drt_status drt_unload(drt_ctx *c, uint64_t link) {
         return fail(DRT_EBUSY, "link %llu has %d pending requests", (unsigned long long)link, L->inflight->load());
     CUDA_TRY(cudaSetDevice(c->device));
     CUDA_TRY(cudaDeviceSynchronize());
-    for (void *p : L->allocs) cudaFree(p);
-    c->used -= L->bytes;
+    free_link(c, *L);
     c->links.erase(link);
     return DRT_OK;
 }
