@@ -57,11 +57,11 @@ PATHSET = os.path.join(ROOT, "tests", "golden", "pathset_canyon_seed0.npz")
 # until they are measured again.  FP64 peak of the GB300 derived from its unit counts: 152 SMs x 2
 # DFMA/clk x 2 FLOP x 2.07 GHz = 1.26 TFLOP/s (no FP64 tensor path is used); FP32 peak 152 SMs x 128
 # lanes x 2 FLOP x 2.07 GHz = 80.5 TFLOP/s; 8 FP32 FLOP per synthesis term.
-KERNEL_HASH = "1441519e8e8f17d0"
-FP64_FLOP_PER_PATH_STEP = 1533.7
-K1_DRAM_BYTES_PER_CALL = 9.40e6
-K1_FP64_PIPE_ACTIVE = 0.867
-FP32_FLOP_PER_PATH_STEP = 1751.0
+KERNEL_HASH = "ad23931f41c56c9a"
+FP64_FLOP_PER_PATH_STEP = 1441.4
+K1_DRAM_BYTES_PER_CALL = 8.25e6
+K1_FP64_PIPE_ACTIVE = 0.863
+FP32_FLOP_PER_PATH_STEP = 1370.8
 FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9
 SYNTH_FLOP_PER_TERM = 8.0

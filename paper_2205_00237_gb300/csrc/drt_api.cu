@@ -480,6 +480,13 @@ drt_status drt::pack_link(const drt_scene *s, const drt_path_set *ps, PackedLink
     std::vector<BodyD> &bodies = H.bodies;
     bodies.resize(s->n_bodies);
     std::memcpy(bodies.data(), s->bodies, sizeof(BodyD) * s->n_bodies);
+    H.body_fixed.resize(s->n_bodies);
+    for (int i = 0; i < s->n_bodies; ++i) {   // a body at rest poses its primitives at their t0 placement
+        const BodyD &b = bodies[i];
+        bool fixed = b.w0 == 0.0 && b.wdot == 0.0;
+        for (int j = 0; j < 3; ++j) fixed = fixed && b.v[j] == 0.0 && b.a[j] == 0.0;
+        H.body_fixed[i] = fixed ? 1 : 0;
+    }
     auto rel = [&](int body, const double *x, double *o) {
         for (int j = 0; j < 3; ++j) o[j] = x[j] - s->bodies[body].o[j];
     };
@@ -745,6 +752,7 @@ drt_status load_link(drt_ctx *c, const drt_scene *s, const drt_path_set *ps, Lin
     LinkDev &d = L.dev;
     LinkImage img;
     img.add(H.bodies, &d.bodies);
+    img.add(H.body_fixed, &d.body_fixed);
     img.add(H.faces, &d.faces);
     img.add(H.edges, &d.edges);
     img.add(H.tiles, &d.tiles);

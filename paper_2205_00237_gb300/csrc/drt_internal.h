@@ -42,6 +42,7 @@ struct LinkDev {
     int32_t multi_start[MAXI];
     TermD tx, rx;
     const BodyD *bodies;
+    const int32_t *body_fixed;   // per body: 1 when it does not move (no velocity, acceleration or rotation)
     const FaceD *faces;
     const EdgeD *edges;
     const TileD *tiles;
@@ -154,6 +155,7 @@ struct PackedLink {
     LinkDev dev{};
     drt_scene_view view{};
     std::vector<BodyD> bodies;
+    std::vector<int32_t> body_fixed;
     std::vector<FaceD> faces;
     std::vector<EdgeD> edges;
     std::vector<TileD> tiles;

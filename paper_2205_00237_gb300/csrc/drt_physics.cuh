@@ -157,17 +157,61 @@ DRT_HD int prim_body(const LinkDev &L, int type, int idx) {
     return type == T_R ? L.faces[idx].body : type == T_D ? L.edges[idx].body : L.tiles[idx].body;
 }
 
+// A primitive of a body at rest: its t0 placement at every instant, with zero rates.  This is what
+// posing gives for such a body (identity rotation, O = o, no velocity) without the pose record or
+// the rotations: most primitives of the synthetic scenes (facades, their edges and tiles, the ground)
+// are at rest.
+template <class T> DRT_HD Prim<dl<T>> load_prim_fixed(const LinkDev &L, int type, int idx) {
+    Prim<dl<T>> q;
+    q.type = type;
+    q.idx = idx;
+    const double *o = L.bodies[prim_body(L, type, idx)].o;
+    const v3<T> zero = V3<T>(T(0), T(0), T(0));
+    auto at = [&](const double *rel) { return dual(V3<T>(o[0] + rel[0], o[1] + rel[1], o[2] + rel[2]), zero); };
+    auto dir = [&](const double *d) { return dual(V3<T>(d[0], d[1], d[2]), zero); };
+    if (type == T_R) {
+        const FaceD &f = L.faces[idx];
+        q.p = at(f.c);
+        q.a = dir(f.n);
+        q.b = V3<T>(f.u[0], f.u[1], f.u[2]);
+        q.h1 = T(f.hu);
+        q.h2 = T(f.hw);
+        q.mat = f.mat;
+    } else if (type == T_D) {
+        const EdgeD &e = L.edges[idx];
+        q.p = at(e.a);
+        q.a = dir(e.e);
+        q.b = V3<T>(e.t0[0], e.t0[1], e.t0[2]);
+        q.c = V3<T>(e.n0[0], e.n0[1], e.n0[2]);
+        q.h1 = T(e.len);
+        q.h2 = T(e.wn);
+        q.h3 = T(e.snp);
+        q.h4 = T(e.cnp);
+        q.mat = e.mat;
+    } else {
+        const TileD &tl = L.tiles[idx];
+        q.p = at(tl.c);
+        q.a = dir(tl.n);
+        q.mat = tl.mat;
+    }
+    return q;
+}
+
 // FP64 form: primitives posed from the pose table
 template <class T>
 DRT_HD Prim<dl<T>> load_prim(const LinkDev &L, const double *pose, int n_steps, int ti, int type, int idx) {
-    return load_prim_row<T>(L, pose_at(pose, n_steps, prim_body(L, type, idx), ti), type, idx);
+    const int body = prim_body(L, type, idx);
+    if (L.body_fixed[body]) return load_prim_fixed<T>(L, type, idx);
+    return load_prim_row<T>(L, pose_at(pose, n_steps, body, ti), type, idx);
 }
 
 // FP64 primitive posed directly from the body kinematics at time t (FP32-bulk redo path)
 template <class T>
 DRT_HD Prim<dl<T>> load_prim_direct(const LinkDev &L, double t, int type, int idx) {
+    const int body = prim_body(L, type, idx);
+    if (L.body_fixed[body]) return load_prim_fixed<T>(L, type, idx);
     double P[POSE_W];
-    body_pose_row(L.bodies[prim_body(L, type, idx)], t, P);
+    body_pose_row(L.bodies[body], t, P);
     return load_prim_row<T>(L, P, type, idx);
 }
 
@@ -1558,6 +1602,37 @@ DRT_HD Prim<dd> load_prim_dd(const LinkDev &L, const PoseB &row, float tau, int 
     Prim<dd> q;
     q.type = type;
     q.idx = idx;
+    if (L.body_fixed[prim_body_f(L, type, idx)]) {   // at rest: t0 placement, zero deltas and rates
+        const v3<float> O = V3<float>(row.O[0], row.O[1], row.O[2]), z = V3<float>(0.f, 0.f, 0.f);
+        auto at = [&](const float *rel) { return ddv(O + V3<float>(rel[0], rel[1], rel[2]), z, z); };
+        auto dir = [&](const float *d) { return ddv(V3<float>(d[0], d[1], d[2]), z, z); };
+        if (type == T_R) {
+            const FaceF &f = L.facesF[idx];
+            q.p = at(f.c);
+            q.a = dir(f.n);
+            q.b = V3<float>(f.u[0], f.u[1], f.u[2]);
+            q.h1 = f.hu;
+            q.h2 = f.hw;
+            q.mat = f.mat;
+        } else if (type == T_D) {
+            const EdgeF &e = L.edgesF[idx];
+            q.p = at(e.a);
+            q.a = dir(e.e);
+            q.b = V3<float>(e.t0[0], e.t0[1], e.t0[2]);
+            q.c = V3<float>(e.n0[0], e.n0[1], e.n0[2]);
+            q.h1 = e.len;
+            q.h2 = e.wn;
+            q.h3 = e.snp;
+            q.h4 = e.cnp;
+            q.mat = e.mat;
+        } else {
+            const TileF &tl = L.tilesF[idx];
+            q.p = at(tl.c);
+            q.a = dir(tl.n);
+            q.mat = tl.mat;
+        }
+        return q;
+    }
     PoseDD P = pose_dd(row, tau);
     if (type == T_R) {
         const FaceF &f = L.facesF[idx];
@@ -1591,6 +1666,7 @@ DRT_HD Prim<dd> load_prim_dd(const LinkDev &L, const PoseB &row, float tau, int 
 
 // FP64 value-only primitive posed from its body's pose record (chunk-base solve)
 DRT_HD Prim<double> load_prim_value(const LinkDev &L, const double *Pr, int type, int idx) {
+    if (L.body_fixed[prim_body(L, type, idx)]) return val_prim(load_prim_fixed<double>(L, type, idx));
     Pose<double> P = load_pose<double>(Pr);
     Prim<double> q;
     q.type = type;
