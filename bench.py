@@ -57,7 +57,7 @@ PATHSET = os.path.join(ROOT, "tests", "golden", "pathset_canyon_seed0.npz")
 # until they are measured again.  FP64 peak of the GB300 derived from its unit counts: 152 SMs x 2
 # DFMA/clk x 2 FLOP x 2.07 GHz = 1.26 TFLOP/s (no FP64 tensor path is used); FP32 peak 152 SMs x 128
 # lanes x 2 FLOP x 2.07 GHz = 80.5 TFLOP/s; 8 FP32 FLOP per synthesis term.
-KERNEL_HASH = "ad23931f41c56c9a"
+KERNEL_HASH = "beb89e4da9ce2fa0"
 FP64_FLOP_PER_PATH_STEP = 1441.4
 K1_DRAM_BYTES_PER_CALL = 8.25e6
 K1_FP64_PIPE_ACTIVE = 0.863
@@ -72,18 +72,22 @@ RECORD_BYTES = {"fp64": 49, "fp32_bulk": 37}
 
 def kernel_source_hash():
     """Hash of the sources the extrapolation kernels compile from: the kernel translation units
-    (drt_k_*.cu, drt_kernels.cu) and every header; the roofline constants above belong to one version
-    of them (the host-side files drt_api.cu, drt_batch.cu, drt_serve.cu and the tracer do not change them)."""
+    (drt_k_*.cu, drt_kernels.cu) and every header, without their // comments and blank lines; the
+    roofline constants above belong to one version of that code (the host-side files drt_api.cu,
+    drt_batch.cu, drt_serve.cu and the tracer do not change them)."""
     import glob
     import hashlib
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2205_00237_gb300", "csrc")
     for f in sorted(glob.glob(os.path.join(csrc, "drt_k_*.cu")) + [os.path.join(csrc, "drt_kernels.cu")] +
                     glob.glob(os.path.join(csrc, "*.cuh")) + glob.glob(os.path.join(csrc, "*.h")) +
                     [os.path.join(ROOT, "include", "drt.h")]):
-        with open(f, "rb") as fh:
-            h.update(os.path.basename(f).encode())
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        code = [ln.split("//")[0].rstrip() for ln in text.splitlines()]
+        h.update(os.path.basename(f).encode())
+        h.update("\n".join(ln for ln in code if ln).encode())
     return h.hexdigest()[:16]
 
 

@@ -10,7 +10,8 @@
 //   stage 2  multi-diffraction warm start (link, path with >= 2 D in a segment, chunk base 0..n)
 //   stage 3  FP64 chunk anchors           (link, path, chunk)
 //   stage 4  FP32-bulk extrapolation      (link, path, 32 consecutive steps: one warp), one unit
-//            range and launch per chain length 0..3 and one for the chains that need generic code
+//            range and launch per chain length 0..3, per length 2 and 3 of the multi-diffraction
+//            chains, and one for the rest (each path of it running the instance for its length)
 //   stage 5  H synthesis                  (link, 32 consecutive (step, bin tile) pairs: one block)
 // All stages run in waves of links whose per-path-step records (20 B each) fit one record buffer and
 // whose poses, warm starts and anchors fit one scratch region, both reused by the next wave, so a

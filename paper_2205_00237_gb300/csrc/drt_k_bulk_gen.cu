@@ -6,7 +6,8 @@
 
 namespace drt {
 
-// chains with several diffractions in a segment and 4-vertex chains: generic code
+// the generic range (several diffractions in a segment, 4 vertices; every chain when records are
+// asked for): each path runs the instance compiled for its chain length
 template <bool DUAL>
 __global__ void __launch_bounds__(EXT_T, 4)
 k_extrapolate_bulk_gen(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const PoseB *__restrict__ poseb,

@@ -8,7 +8,8 @@
 
 namespace drt {
 
-// any chain (several diffractions in a segment, 4 vertices), generic code
+// the generic range (several diffractions in a segment, 4 vertices): each path runs the instance
+// compiled for its chain length
 template <bool DUAL>
 __global__ void __launch_bounds__(EXT_T)
 k_extrapolate_fp64_gen(const LinkDev L, const TimeGridD tg, const FreqGridD fg, const double *__restrict__ pose,

@@ -584,7 +584,7 @@ DRT_HD float fp32_margin_tol(float scale) { return 2e-6f * (scale + 1.f); }
 
 // Vertex loops run over a fixed bound (MAXI) and stop at the chain length, so their array indices
 // are constants after unrolling and the arrays stay in registers; N >= 0 fixes the length at compile
-// time (shorter code), N < 0 takes the run-time n.
+// time (every caller now passes a fixed N; N < 0 would take the run-time n).
 // The tests at one vertex of type ty (c, nn: its point and normal or edge direction; b, cc, h1..h4 as
 // in Prim) between its neighbours Pm, Pp: its flag bits, and (FP32) its smallest margin over the FP32
 // error bound.  (Called out of line in the FP32 kernels it measured no faster, unlike the field
