@@ -1321,7 +1321,11 @@ DRT_HD void path_step_fp64_core(const LinkDev &L, const TimeGridD &tg, const Fre
     }
     fl |= validity<N>(pr, n, P);
     T tau = d * T(1 / C0);
-    cx<T> a = (fl & F_DEGEN) ? C<T>(T(0), T(0)) : amplitude<N>(L, pr, n, seg, T(fg.fc));
+    // An invalid path-step contributes nothing to H (its records carry a = 0): its field coefficients
+    // are computed only when the caller asked for the amplitude output, which reports them for every
+    // step (a degenerate chain has none)
+    const bool field = !fl || (OUT && out.amp && !(fl & F_DEGEN));
+    cx<T> a = field ? amplitude<N>(L, pr, n, seg, T(fg.fc)) : C<T>(T(0), T(0));
     if constexpr (OUT) {
         if (out.tau || out.amp || out.doppler || out.angles || out.flags || out.points) {
             T fd = 0;
@@ -1954,7 +1958,9 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
         // segment vector: FP64-accurate base + FP32 delta
         seg[i] = V3<float>(B.seg[i - 1][0] + sv.x.d, B.seg[i - 1][1] + sv.y.d, B.seg[i - 1][2] + sv.z.d);
     }
-    cx<T> a = (fl & F_DEGEN) ? C<T>(T(0), T(0)) : amplitude<N>(L, pr, n, seg, fg.fcf);
+    // as in the FP64 form: an invalid step's field coefficients only for the amplitude output
+    const bool field = !fl || (OUT && out.amp && !(fl & F_DEGEN));
+    cx<T> a = field ? amplitude<N>(L, pr, n, seg, fg.fcf) : C<T>(T(0), T(0));
     if constexpr (OUT) {
         if (out.tau || out.amp || out.doppler || out.angles || out.flags || out.points) {
             T fd = 0.f;
@@ -1980,7 +1986,7 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
     };
     phase_record(fg, B, a, rec);
     if (fg2) {
-        const cx<T> a2 = (fl & F_DEGEN) ? C<T>(T(0), T(0)) : amplitude<N>(L, pr, n, seg, fg2->fcf);
+        const cx<T> a2 = field ? amplitude<N>(L, pr, n, seg, fg2->fcf) : C<T>(T(0), T(0));
         phase_record(*fg2, ld_row(R.base2[(size_t)(chunk - R.c0) * R.bstride]), a2, *rec2);
     }
     return true;
