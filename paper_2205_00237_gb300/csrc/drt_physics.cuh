@@ -480,12 +480,16 @@ DRT_HD void newton_diffractions(const Prim<S> *pr, v3<S> *V, const bool *nv, con
         smax_prev = smax;
         // On dual numbers one Newton step from a value within smax of the root leaves the
         // derivative part O(smax) from the implicit-function derivative whatever the start's
-        // derivative was, so FP64 stops at the first step below tol (1e-10 m); FP32, whose tol is
-        // 1e-4 m, takes one more step to refine both parts.
+        // derivative was, so FP64 stops at the first step below tol (1e-10 m); FP32 with rates
+        // (tol 1e-4 m) takes one more step to refine both parts.  FP32 delta numbers without rates
+        // stop at once: by Newton's quadratic convergence the value is then within ~K smax^2 of the
+        // root (K of the order of an inverse leg length, larger near grazing), and from the FP64
+        // warm starts the first step is ~1e-6..1e-5 m (the FP32 rounding of the coordinates), so the
+        // remaining error is far below that rounding.
         if (conv) break;
         if (smax < tol) {
             conv = true;
-            if (sizeof(T) == 8) break;
+            if (sizeof(T) == 8 || std::is_same<S, de>::value) break;
         }
     }
     if (!conv) fl |= F_NOCONV;
