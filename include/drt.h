@@ -402,6 +402,16 @@ drt_status drt_link_info(drt_ctx *ctx, uint64_t link, int32_t *n_paths);
 drt_status drt_profile_enable(drt_ctx *ctx, int32_t on);
 drt_status drt_profile_read(drt_ctx *ctx, int64_t counts[4], double ms[4]);
 
+/* The same record as a timeline: for each bracketed launch group since the last drt_profile_read,
+ * in the order the groups were issued, its kind (as above) and its start and end in ms after the
+ * start of the first group.  A group is one kernel, or one stage whose launches fork onto the
+ * context's side streams and join back before its closing event.  Writes min(cap, count) entries
+ * into the caller's host arrays kind, t0_ms, t1_ms (each of cap elements) and the count to *n; does
+ * not clear the record.  Synchronises the device.  Errors: DRT_EINVAL (NULL arguments, cap < 0),
+ * DRT_ECUDA. */
+drt_status drt_profile_timeline(drt_ctx *ctx, int32_t cap, int32_t *n, int32_t *kind, double *t0_ms,
+                                double *t1_ms);
+
 /* ---------------------------------------------------------------------------------------------
  * Utility: calibrated issue-rate probe of this device's arithmetic pipes, used to quote roofline
  * fractions.  kind 0 = FP64 FMA, 1 = FP32 FMA.  Runs a fixed dependent-chain-free FMA loop over

@@ -680,8 +680,14 @@ drt_status drt_create(drt_ctx **out, int32_t device, uint64_t hbm_budget_bytes) 
         delete c;
         return fail(DRT_ENOMEM, "cudaMalloc failed");
     }
+    // side[1] carries the critical chain of a call (the latency-bound warm starts, then the chains that
+    // wait for them; in the FP32-bulk form also the FP64 redo beside the synthesis): at the greatest
+    // stream priority its blocks are dispatched before those of the other streams' wide launches
+    // (7-8 % off a canyon call in both forms)
+    int prio_lo = 0, prio_hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) prio_lo = prio_hi = 0;
     for (int i = 0; i < 2; ++i) {
-        if (cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+        if (cudaStreamCreateWithPriority(&c->side[i], cudaStreamNonBlocking, i == 1 ? prio_hi : prio_lo) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming) != cudaSuccess) {
             drt_destroy(c);
             return fail(DRT_ECUDA, "stream/event creation failed");
@@ -1124,6 +1130,26 @@ drt_status drt_profile_read(drt_ctx *c, int64_t counts[4], double ms[4]) {
     }
     c->marks.clear();
     return st;
+}
+
+drt_status drt_profile_timeline(drt_ctx *c, int32_t cap, int32_t *n, int32_t *kind, double *t0_ms, double *t1_ms) {
+    if (!c || !n || cap < 0 || (cap > 0 && (!kind || !t0_ms || !t1_ms))) return fail(DRT_EINVAL, "bad timeline arguments");
+    std::lock_guard<std::mutex> lk(c->mu);
+    CUDA_TRY(cudaSetDevice(c->device));
+    CUDA_TRY(cudaDeviceSynchronize());
+    *n = (int32_t)c->marks.size();
+    const int m = std::min<int>(cap, (int)c->marks.size());
+    for (int i = 0; i < m; ++i) {
+        const drt_ctx::Mark &k = c->marks[i];
+        float a = 0.f, b = 0.f;
+        if (cudaEventElapsedTime(&a, c->marks[0].a, k.a) != cudaSuccess ||
+            cudaEventElapsedTime(&b, c->marks[0].a, k.b) != cudaSuccess)
+            return fail(DRT_ECUDA, "cudaEventElapsedTime failed");
+        kind[i] = k.kind;
+        t0_ms[i] = a;
+        t1_ms[i] = b;
+    }
+    return DRT_OK;
 }
 
 drt_status drt_probe_peak(drt_ctx *c, int32_t kind, int32_t blocks, double *flops) {

@@ -28,7 +28,8 @@ EXPORTS = ["drt_create", "drt_destroy", "drt_last_error", "drt_load_paths", "drt
            "drt_profile_read", "drt_synthesize_H_noalloc", "drt_batch_create", "drt_batch_run", "drt_batch_info",
            "drt_batch_destroy", "drt_serve_start", "drt_serve_stop", "drt_submit", "drt_poll", "drt_wait",
            "drt_serve_stats_read", "drt_power_profile", "drt_lifetime_windows", "drt_synthesize_H_windows",
-           "drt_synthesize_H_wideband", "drt_trace_paths", "drt_synthesize_H_retraced", "drt_batch_tuning"]
+           "drt_synthesize_H_wideband", "drt_trace_paths", "drt_synthesize_H_retraced", "drt_batch_tuning",
+           "drt_profile_timeline"]
 PP_DOPPLER, PP_DELAY = 0, 1
 
 
@@ -136,6 +137,9 @@ def load_library(path: str = LIB_PATH):
         L.drt_profile_enable.restype = st
         L.drt_profile_read.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
         L.drt_profile_read.restype = st
+        L.drt_profile_timeline.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                           C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.drt_profile_timeline.restype = st
         L.drt_batch_create.argtypes = [vp, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(_TimeGrid),
                                        C.POINTER(_FreqGrid), C.POINTER(vp), C.c_int32, C.POINTER(vp)]
         L.drt_batch_create.restype = st
@@ -283,6 +287,17 @@ class Context:
         _check(load_library().drt_profile_read(self._h, counts, ms))
         names = ("pose", "extrapolate", "synth", "base")
         return {names[k]: (int(counts[k]), float(ms[k])) for k in range(4)}
+
+    def profile_timeline(self, cap: int = 256):
+        """drt_profile_timeline: [(kind name, start ms, end ms)] of the bracketed launch groups since
+        the last profile_read, in issue order, times after the start of the first; keeps the record."""
+        n = C.c_int32(0)
+        kind = (C.c_int32 * cap)()
+        t0 = (C.c_double * cap)()
+        t1 = (C.c_double * cap)()
+        _check(load_library().drt_profile_timeline(self._h, int(cap), C.byref(n), kind, t0, t1))
+        names = ("pose", "extrapolate", "synth", "base")
+        return [(names[kind[i]], float(t0[i]), float(t1[i])) for i in range(min(cap, n.value))]
 
     def batch(self, links, tgrids, fgrids, Hs, precision: int = FP32_BULK) -> "Batch":
         """drt_batch_create: one batched synthesis plan over loaded links; Hs are complex64 CUDA
