@@ -270,6 +270,11 @@ template <> DRT_HD dd newton_start<dd>(double base, double delta, double rate) {
     return {(float)base, (float)delta, (float)rate};
 }
 
+// the same from an FP32 offset and rate (the FP32-bulk steps' warm starts): no FP64 arithmetic
+template <class S> DRT_HD S newton_start_f(double base, float delta, float rate);
+template <> DRT_HD de newton_start_f<de>(double base, float delta, float) { return {(float)base, delta}; }
+template <> DRT_HD dd newton_start_f<dd>(double base, float delta, float rate) { return {(float)base, delta, rate}; }
+
 // chain length of path p (vertices before the first empty type byte)
 DRT_HD int chain_length(const LinkDev &L, int p) {
     const uint32_t c = L.ptypes[p];
@@ -350,9 +355,9 @@ template <int N, class S> DRT_HD void place_reflections(const Prim<S> *pr, v3<S>
 // -- to the next, through the reflections in between) and eliminates each unknown of the
 // tridiagonal system at the anchor that closes its outgoing leg; the back substitution runs the
 // other way.  Nothing is indexed at run time.
-template <int N, class S>
-DRT_HD void newton_diffractions(const Prim<S> *pr, v3<S> *V, const bool *nv, const double *s0, const double *ds0,
-                                const double *rate0, uint32_t &fl) {
+template <int N, class S, class D = double>
+DRT_HD void newton_diffractions(const Prim<S> *pr, v3<S> *V, const bool *nv, const double *s0, const D *ds0,
+                                const D *rate0, uint32_t &fl) {
     typedef typename ST<S>::R T;
     // convergence threshold on the Newton step (m): near round-off of the working precision
     const T tol = sizeof(T) == 8 ? T(1e-10) : T(1e-4);
@@ -364,7 +369,10 @@ DRT_HD void newton_diffractions(const Prim<S> *pr, v3<S> *V, const bool *nv, con
 #pragma unroll
     for (int i = 1; i <= N; ++i)
         if (nv[i]) {
-            s[i] = newton_start<S>(s0[i - 1], ds0 ? ds0[i - 1] : 0.0, rate0 ? rate0[i - 1] : 0.0);
+            if constexpr (std::is_same<D, float>::value)
+                s[i] = newton_start_f<S>(s0[i - 1], ds0 ? ds0[i - 1] : 0.f, rate0 ? rate0[i - 1] : 0.f);
+            else
+                s[i] = newton_start<S>(s0[i - 1], ds0 ? ds0[i - 1] : 0.0, rate0 ? rate0[i - 1] : 0.0);
             step[i] = zero;
         }
     bool conv = false;
@@ -512,9 +520,9 @@ DRT_HD void solve_geometry_fast(const Prim<S> *pr, v3<S> *V, uint32_t &fl) {
 
 // any chain of N vertices: the diffractions of a segment with two or more of them by Newton (their
 // start values s0 [+ ds0, rate0] indexed by vertex - 1), the others on their Keller cones
-template <int N, class S>
+template <int N, class S, class D = double>
 DRT_HD void solve_geometry_any(const Prim<S> *pr, v3<S> *V, const double *s0, uint32_t &fl,
-                               const double *ds0 = nullptr, const double *rate0 = nullptr) {
+                               const D *ds0 = nullptr, const D *rate0 = nullptr) {
     static_assert(N >= 0 && N <= MAXI, "chain length");
     place_tiles<N>(pr, V);
     // diffractions per segment: running count from the left, then each segment's total from the right
@@ -545,9 +553,9 @@ DRT_HD void solve_geometry_any(const Prim<S> *pr, v3<S> *V, const double *s0, ui
 }
 
 // MULTI: the chain may have several diffractions between point sources
-template <int N, bool MULTI, class S>
+template <int N, bool MULTI, class S, class D = double>
 DRT_HD void solve_geometry(const Prim<S> *pr, v3<S> *V, const double *s0, uint32_t &fl,
-                           const double *ds0 = nullptr, const double *rate0 = nullptr) {
+                           const D *ds0 = nullptr, const D *rate0 = nullptr) {
     static_assert(N >= 0 && N <= MAXI, "chain length");
     if constexpr (MULTI) solve_geometry_any<N>(pr, V, s0, fl, ds0, rate0);
     else solve_geometry_fast<N>(pr, V, fl);
@@ -1267,6 +1275,27 @@ DRT_HD void warm_start_at(const LinkDev &L, const TimeGridD &tg, const double *w
     hermite_start(warm_row(L, warm, c, p), warm_row(L, warm, c + 1, p), (ti - c * tg.chunk) * tg.dt,
                   tg.chunk * tg.dt, ws);
 }
+// The same interpolant for the FP32-bulk steps: the base s stays FP64 (the Newton start's base part),
+// the offset and rate are FP32 (the difference s1 - s0 taken in FP64 first), which keeps the FP64 pipe
+// -- 1/64 of the FP32 rate on this GPU -- out of the FP32 kernels' per-step work but for one
+// subtraction and the conversions per unknown
+struct WarmStart32 { double s[MAXI]; float ds[MAXI], rate[MAXI]; };
+DRT_HD void warm_start_at32(const LinkDev &L, const TimeGridD &tg, const double *warm, int p, int ti,
+                            WarmStart32 &ws) {
+    const int c = ti / tg.chunk;
+    const double *w0 = warm_row(L, warm, c, p), *w1 = warm_row(L, warm, c + 1, p);
+    const float Tc = (float)tg.chunk * tg.dtf, iTc = 1.f / Tc;
+    const float h = (float)(ti - c * tg.chunk) / (float)tg.chunk, h2 = h * h, h3 = h2 * h;
+    const float h10 = h3 - 2.f * h2 + h, h01 = 3.f * h2 - 2.f * h3, h11 = h3 - h2;
+    const float g00 = 6.f * h2 - 6.f * h, g10 = 3.f * h2 - 4.f * h + 1.f, g11 = 3.f * h2 - 2.f * h;
+#pragma unroll
+    for (int j = 0; j < MAXI; ++j) {
+        const float d = (float)(w1[j] - w0[j]), r0 = (float)w0[MAXI + j], r1 = (float)w1[MAXI + j];
+        ws.s[j] = w0[j];
+        ws.ds[j] = h10 * Tc * r0 + h01 * d + h11 * Tc * r1;
+        ws.rate[j] = -g00 * d * iTc + g10 * r0 + g11 * r1;
+    }
+}
 
 // terminal position (and velocity on dual numbers) at time t
 template <class S> DRT_HD v3<S> terminal_as(const TermD &m, double t);
@@ -1896,8 +1925,8 @@ DRT_HD bool bulk_eval(const LinkDev &L, const TimeGridD &tg, const FreqGridD &fg
     V[N + 1] = terminal_as<S>(R.pose[MAXI + 1][chunk - R.c0], tau_t);
     uint32_t fl = 0;
     if (MULTI && warm && p >= L.n_bulk) {
-        WarmStart ws;
-        warm_start_at(L, tg, warm, p, ti, ws);
+        WarmStart32 ws;
+        warm_start_at32(L, tg, warm, p, ti, ws);
         solve_geometry<N, MULTI>(pr, V, ws.s, fl, ws.ds, ws.rate);
     } else {
         solve_geometry<N, MULTI>(pr, V, L.ps0 + (size_t)p * MAXI, fl);
