@@ -60,11 +60,11 @@ PATHSET = os.path.join(ROOT, "tests", "golden", "pathset_canyon_seed0.npz")
 # of H (a complex rotation and a complex accumulation) is 8 slots of the 128 FP32 lanes an SM issues
 # per cycle, so its roofline is 152 x 128 x 2.07 GHz / 8 = 5.0e12 terms/s; its FLOP fraction (8 FLOP
 # per term against the FMA peak) goes beside it.
-KERNEL_HASH = "beb89e4da9ce2fa0"
-FP64_FLOP_PER_PATH_STEP = 1441.4
-K1_DRAM_BYTES_PER_CALL = 8.25e6
-K1_FP64_PIPE_ACTIVE = 0.863
-FP32_FLOP_PER_PATH_STEP = 1370.8
+KERNEL_HASH = "8ff611f473138dd0"
+FP64_FLOP_PER_PATH_STEP = 1210.4
+K1_DRAM_BYTES_PER_CALL = 8.26e6
+K1_FP64_PIPE_ACTIVE = 0.861
+FP32_FLOP_PER_PATH_STEP = 1178.5
 FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9
 SYNTH_FLOP_PER_TERM = 8.0
