@@ -1277,7 +1277,7 @@ DRT_HD void warm_start_at(const LinkDev &L, const TimeGridD &tg, const double *w
 }
 // The same interpolant for the FP32-bulk steps: the base s stays FP64 (the Newton start's base part),
 // the offset and rate are FP32 (the difference s1 - s0 taken in FP64 first), which keeps the FP64 pipe
-// -- 1/64 of the FP32 rate on this GPU -- out of the FP32 kernels' per-step work but for one
+// -- 1/64 of the FP32 rate on GB300 -- out of the FP32 kernels' per-step work but for one
 // subtraction and the conversions per unknown
 struct WarmStart32 { double s[MAXI]; float ds[MAXI], rate[MAXI]; };
 DRT_HD void warm_start_at32(const LinkDev &L, const TimeGridD &tg, const double *warm, int p, int ti,
