@@ -65,6 +65,9 @@ FP64_FLOP_PER_PATH_STEP = 1210.4
 K1_DRAM_BYTES_PER_CALL = 8.26e6
 K1_FP64_PIPE_ACTIVE = 0.861
 FP32_FLOP_PER_PATH_STEP = 1178.5
+# issue activity of k_extrapolate_bulk_n<3> (the largest FP32-bulk launch): share of the SM cycles in
+# which a sub-partition issued an instruction (ncu smsp__issue_active), the kernel's binding measure
+K2_ISSUE_ACTIVE = 0.429
 FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9
 SYNTH_FLOP_PER_TERM = 8.0
@@ -788,6 +791,7 @@ def run_ours(args):
             "k_extrapolate_bulk": {"bound": "alu", "achieved": a1 / 1e12 if a1 else None,
                                    "peak": FP32_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
                                    "frac": a1 / FP32_PEAK_FLOPS if a1 else None,
+                                   "ncu_issue_active": K2_ISSUE_ACTIVE if fresh else None,
                                    "note": None if a1 else "FLOP count not measured on this kernel build"},
             "k_synth": {"bound": "alu", "achieved": slots / 1e12, "peak": FP32_ISSUE_PEAK / 1e12,
                         "unit": "T FP32 issue slots/s (8 per term)", "frac": slots / FP32_ISSUE_PEAK,
