@@ -44,7 +44,8 @@ def test_timeline_matches_profile(ctx, form):
         assert len(mine) == n
         assert abs(sum(mine) - ms) <= 1e-3 * max(ms, 1e-3) + 1e-4
     assert tl[0][1] == 0.0
-    assert all(t1 >= t0 >= 0.0 for _, t0, t1 in tl)
+    # groups on other streams may start a few microseconds before the first one's opening event
+    assert all(t1 >= t0 > -0.05 for _, t0, t1 in tl)
     # on the launch stream the synthesis follows the extrapolation
     ext = [t1 for k, _, t1 in tl if k == "extrapolate"]
     syn = [t0 for k, t0, _ in tl if k == "synth"]
