@@ -42,7 +42,8 @@ def test_timeline_matches_profile(ctx, form):
     for name, (n, ms) in prof.items():
         mine = [t1 - t0 for k, t0, t1 in tl if k == name]
         assert len(mine) == n
-        assert abs(sum(mine) - ms) <= 1e-3 * max(ms, 1e-3) + 1e-4
+        # each difference of two event times may round by the events' resolution (~0.5 us)
+        assert abs(sum(mine) - ms) <= 1e-3 * ms + 2e-3 * n
     assert tl[0][1] == 0.0
     # groups on other streams may start a few microseconds before the first one's opening event
     assert all(t1 >= t0 > -0.05 for _, t0, t1 in tl)
